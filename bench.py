@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PDLP library (prints one JSON line).
+
+Workload (default): the 100k x 250k MIP-relaxation-shaped planted LP with about
+1.5M nonzeros (power-law row lengths, |values| log-uniform in [1e-3, 1e3],
+60% inequality rows, 10% free variables).  One step = the whole hot path on
+inputs already resident in HBM: pdlp_create (validation, K^T, Ruiz +
+Pock-Chambolle preconditioning, transform, graph capture) then pdlp_solve
+(Algorithm 1 with restarts, primal-weight updates and the Eq. (15) checks),
+float64, stopped at an iteration cap.  value = accepted PDHG iterations per
+second over the timed steps (all ranks).  The L2 cache is flushed (256 MiB
+write) between timed steps.
+
+Also reported: time to 1e-8 relative KKT error (Eq. (15)) on the 1M-node
+PageRank LP, float64 against float32 inner solves with float64 refinement;
+the roofline of the step kernels; the end-to-end rate through the C ABI with
+host buffers; and the CPU oracle timed on a bounded sample of the same
+workload.  `--impl reference` times only the CPU oracle.
+
+Multi-GPU (torchrun): every rank solves its own replica (no data-path
+collective); value = the ranks' iterations / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "time-to-1e-8 rel KKT & PDHG iter/s (HBM GB/s vs peak); FP32+refine vs FP64"
+WORKLOADS = ("mip_100k", "pagerank_1m", "planted_200x500")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="mip_100k", choices=WORKLOADS)
+    ap.add_argument("--iter-cap", type=int, default=20000)
+    ap.add_argument("--no-tol", action="store_true", help="skip the time-to-tolerance runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def _make(workload):
+    import lpgen
+    if workload == "mip_100k":
+        return lpgen.mip_relaxation_100k()
+    if workload == "pagerank_1m":
+        return lpgen.pagerank_1m()
+    return lpgen.small_planted()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _alg_bytes(lp, fp):
+    """Algorithmic bytes of one step attempt's two kernels (each array once).
+    primal (over the rows of K^T): values + column indices + row pointers of
+    K^T, y gathered once, c, l, u, x, xs read, x', xs' written.  dual (over the
+    rows of K): values + indices + row pointers of K, x' gathered once, y, q,
+    K x, ys, y-lower-bound read, y', K x', ys' written."""
+    m, n, nnz = lp.m, lp.n, lp.nnz
+    v = 8 if fp == 64 else 4
+    primal = nnz * (v + 4) + 4 * (n + 1) + v * m + 7 * v * n
+    dual = nnz * (v + 4) + 4 * (m + 1) + v * n + 8 * v * m
+    return primal, dual
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the same workload and metric."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    lp = _make(args.workload)
+    oracle.build()
+    cap = {"mip_100k": 300, "pagerank_1m": 40, "planted_200x500": 20000}[args.workload]
+    for _ in range(args.warmup):
+        oracle.solve(lp, iter_limit=max(1, cap // 10))
+    its, secs = 0, 0.0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        _, _, r = oracle.solve(lp, iter_limit=cap)
+        secs += time.perf_counter() - t
+        its += r["iters"]
+    value = its / secs
+    sample = f"{args.workload}: each step = oracle PDLP (setup + {cap} iterations), {args.steps} steps"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "PDHG iter/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": args.workload, "m": lp.m, "n": lp.n, "nnz": lp.nnz,
+                                            "iter_cap": cap},
+           "cpu_baseline": {"value": value, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "PDHG iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2106_04756_gb300 as P
+    from paper_2106_04756_gb300 import build
+    build.build()
+    lp = _make(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def T(a):
+        return torch.as_tensor(np.asarray(a)).to(dev)
+
+    inputs = [T(lp.row_ptr), T(lp.col_idx), T(lp.val), T(lp.c), T(lp.q), T(lp.l), T(lp.u), T(lp.ineq)]
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(cap, precision=P.PDLP_FP64, keep=False):
+        ctx = P.Context(*inputs, lp.m, lp.n, precision=precision, iter_limit=cap, stream=sptr)
+        xo = torch.empty(lp.n, dtype=torch.float64, device=dev)
+        yo = torch.empty(lp.m, dtype=torch.float64, device=dev)
+        _, _, r = ctx.solve(x_out=xo, y_out=yo)
+        if keep:
+            return ctx, r
+        ctx.close()
+        return None, r
+
+    for _ in range(args.warmup):
+        step(args.iter_cap)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = attempts = evals = 0
+    results = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        _, r = step(args.iter_cap)
+        ev[k][1].record(stream)
+        iters += r["iters"]
+        attempts += r["kkt_passes"]
+        evals += r["iters"] // 40 + 1
+        results.append(r)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        it = torch.tensor([iters], dtype=torch.float64, device=dev)
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        total_iters = float(it.item())
+    else:
+        total_iters = float(iters)
+    value = total_iters / elapsed
+    if rank != 0:
+        return
+
+    # ---- roofline of the step kernels (CUDA events, same stream, state of a solve)
+    ctx, _ = step(args.iter_cap, keep=True)
+    kp, kd = ctx.time_step_kernels(200)
+    ctx.close()
+    bp, bd = _alg_bytes(lp, 64)
+    peak, peak_src = _peaks()
+    dom = ("dual", kd, bd) if kd >= kp else ("primal", kp, bp)
+    achieved = dom[2] / (dom[1] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"k_dual<double> (K x' + dual projection + step test)"
+                if dom[0] == "dual" else "k_primal<double> (K^T y + primal projection)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_launch": dom[2], "launch_ms": dom[1]}
+    kernels = {"primal_ms": kp, "dual_ms": kd, "primal_bytes": bp, "dual_bytes": bd,
+               "primal_gbs": bp / (kp * 1e-3) / 1e9, "dual_gbs": bd / (kd * 1e-3) / 1e9}
+    # float32 step kernels on the same workload
+    ctx32, r32 = step(args.iter_cap, precision=P.PDLP_FP32, keep=True)
+    kp32, kd32 = ctx32.time_step_kernels(200)
+    ctx32.close()
+    bp32, bd32 = _alg_bytes(lp, 32)
+    kernels.update({"fp32_primal_ms": kp32, "fp32_dual_ms": kd32,
+                    "fp32_primal_gbs": bp32 / (kp32 * 1e-3) / 1e9, "fp32_dual_gbs": bd32 / (kd32 * 1e-3) / 1e9,
+                    "fp32_iter_per_s": r32["iters"] / r32["seconds"]})
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = 2
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        with P.Context.from_lp(lp, iter_limit=args.iter_cap, stream=sptr) as c2:
+            x_h, y_h, r2 = c2.solve()
+        e2e_iters += r2["iters"]
+    torch.cuda.synchronize(dev)
+    e2e_t = time.perf_counter() - t0
+    h2d = 4 * (lp.m + 1) + 12 * lp.nnz + 8 * (3 * lp.n + lp.m) + lp.m
+    d2h = 8 * (lp.n + lp.m) + 2 * 8 * 16
+    e2e = {"value": e2e_iters / e2e_t, "unit": "PDHG iter/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- time to 1e-8 (Eq. (15)) on the PageRank LP: float64 vs float32 + refinement
+    tol = None
+    if not args.no_tol and args.workload != "pagerank_1m":
+        import lpgen
+        pr = lpgen.pagerank_1m()
+        pin = [T(pr.row_ptr), T(pr.col_idx), T(pr.val), T(pr.c), T(pr.q), T(pr.l), T(pr.u), T(pr.ineq)]
+        tol = {"workload": "pagerank_1m (n=1,000,000, nnz=7,999,982)", "rel_tol": 1e-8}
+        for name, prec in (("fp64", P.PDLP_FP64), ("fp32_refine", P.PDLP_FP32_REFINE)):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            c3 = P.Context(*pin, pr.m, pr.n, precision=prec, stream=sptr, time_limit_s=120.0)
+            _, _, r3 = c3.solve()
+            torch.cuda.synchronize(dev)
+            tol[name] = {"seconds": time.perf_counter() - t0, "status": r3["status_name"], "iters": r3["iters"],
+                         "rel_kkt": r3["rel_kkt"], "refine_rounds": r3["refine_rounds"]}
+            c3.close()
+        del pin
+
+    # ---- CPU oracle on a bounded sample of the same workload
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        cap = {"mip_100k": 600, "pagerank_1m": 60, "planted_200x500": 20000}[args.workload]
+        t0 = time.perf_counter()
+        _, _, ro = oracle.solve(lp, iter_limit=cap)
+        ct = time.perf_counter() - t0
+        cpu = {"value": ro["iters"] / ct, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.workload}, oracle setup + first {cap} iterations ({ct:.1f} s)"}
+
+    launches_per_step = 120 + 2 * attempts / args.steps + 12 * evals / args.steps + 8
+    out = {"metric": METRIC, "value": value, "unit": "PDHG iter/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "m": lp.m, "n": lp.n, "nnz": lp.nnz, "precision": "fp64",
+                      "iter_cap": args.iter_cap, "parallelism": f"replicas x{ws}",
+                      "l2": "flushed between steps (256 MiB write)",
+                      "rel_kkt_at_cap": float(np.median([r["rel_kkt"] for r in results]))},
+           "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(launches_per_step * args.steps), "clocks": clk, "time_to_tol": tol}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

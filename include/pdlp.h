@@ -1,0 +1,211 @@
+/*
+ * pdlp.h -- C ABI of the GB300 (sm_103a) PDLP library.
+ *
+ * PDLP is restarted primal-dual hybrid gradient for linear programming
+ * (Applegate et al., "Practical Large-Scale Linear Programming using
+ * Primal-Dual Hybrid Gradient").  The library solves
+ *
+ *     minimise c^T x  subject to  K_i x >= q_i   (ineq_mask[i] = 1)
+ *                                 K_i x  = q_i   (ineq_mask[i] = 0)
+ *                                 l <= x <= u                        (Section 2, Eq. (1))
+ *
+ * through the saddle problem min_{x in X} max_{y in Y} c^T x - y^T K x + q^T y
+ * (Section 2, Eq. (2)) with Algorithm 1 (restarted, adaptive-step PDHG),
+ * after the diagonal preconditioning of Section 3.5.  Every step of the
+ * iteration runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - Array arguments may be HOST or DEVICE pointers (any memory the CUDA
+ *     runtime can address with unified virtual addressing).  The library
+ *     copies inputs in and results out with cudaMemcpyDefault on the context's
+ *     stream and returns only after the results are in place.
+ *   - Inputs are copied: the caller may free or reuse them when a call returns.
+ *   - Dense vectors are float64, contiguous.  K is CSR: row_ptr int32[m+1]
+ *     (row_ptr[0] = 0, non-decreasing), col_idx int32[nnz] (in [0, n),
+ *     strictly increasing within a row: sorted, no duplicates), val
+ *     float64[nnz] (finite).
+ *   - Bounds may be -INFINITY (l) or +INFINITY (u); l_j <= u_j.  c and q are finite.
+ *   - Return value: PDLP_OK (0) or a negative PDLP_ERR_* code; the message is
+ *     available from pdlp_last_error().  No C++ exception crosses this boundary.
+ *   - One context belongs to one stream; calls on one context must not overlap.
+ */
+#ifndef PDLP_H
+#define PDLP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define PDLP_OK 0
+#define PDLP_ERR_INVALID_ARG (-1) /* malformed CSR, l > u, non-finite data, bad option */
+#define PDLP_ERR_CUDA (-2)        /* a CUDA runtime call failed                           */
+#define PDLP_ERR_OOM (-3)         /* device allocation failed                              */
+#define PDLP_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up                    */
+#define PDLP_ERR_STATE (-5)       /* call out of order (e.g. pdlp_grad before an unroll)  */
+
+/* solver outcome (pdlp_result.status) */
+#define PDLP_RUNNING 0
+#define PDLP_OPTIMAL 1          /* Eq. (15) holds with epsilon = rel_tol            */
+#define PDLP_ITER_LIMIT 2
+#define PDLP_KKT_PASS_LIMIT 3   /* one pass = one product with K and one with K^T   */
+#define PDLP_TIME_LIMIT 4
+#define PDLP_NUMERICAL_ERROR 5  /* a step produced NaN / Inf                        */
+
+/* arithmetic of the iteration */
+#define PDLP_FP64 0         /* K, x, y and all reductions in float64                      */
+#define PDLP_FP32 1         /* K, x, y in float32; reductions, step control in float64    */
+#define PDLP_FP32_REFINE 2  /* float32 inner solves inside a float64 iterative-refinement loop */
+
+/* ---------------------------------------------------------------- types */
+typedef struct pdlp_ctx pdlp_ctx; /* opaque, owned by the library */
+
+typedef struct {
+  int32_t m, n;          /* rows (constraints), columns (variables)          */
+  int64_t nnz;           /* must equal row_ptr[m]; at most 2^31 - 1           */
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const double *val;
+} pdlp_csr;
+
+typedef struct {
+  double rel_tol;           /* epsilon of Eq. (15) (relative = absolute), 1e-8          */
+  int64_t iter_limit;       /* accepted PDHG iterations                                  */
+  int64_t kkt_pass_limit;   /* step attempts (Section 4.1 "KKT passes")                  */
+  double time_limit_s;      /* wall clock of one solve, checked on the device            */
+  int32_t precision;        /* PDLP_FP64 | PDLP_FP32 | PDLP_FP32_REFINE                  */
+  int32_t ruiz_iters;       /* Section 3.5: 10                                           */
+  int32_t pock_chambolle;   /* Section 3.5: 1 = apply Pock-Chambolle alpha = 1 after Ruiz */
+  int32_t eval_every;       /* Section 3: restart / termination check every 40 iterations */
+  int32_t adaptive_restart; /* 1 = restart scheme of Section 3.2, 0 = never restart       */
+  int32_t pw_update;        /* 1 = Algorithm 3 primal weight updates, 0 = keep omega^0    */
+  double pw_smoothing;      /* Algorithm 3 theta: 0.5                                    */
+  double primal_importance; /* multiplies InitializePrimalWeight (Section 3.3): 1.0       */
+  double beta_suff, beta_nec, beta_art; /* Section 3.2: 0.9, 0.1, 0.5                    */
+  double eps_zero;          /* Section 3.3 epsilon_zero: 1e-10                           */
+  double inner_tol;         /* PDLP_FP32_REFINE: Eq. (15) tolerance of each inner solve  */
+  int32_t refine_rounds;    /* PDLP_FP32_REFINE: maximum outer rounds                    */
+  int32_t unroll_T;         /* >0: pdlp_solve runs T unrolled steps for pdlp_grad        */
+  int32_t ckpt_every;       /* unrolled steps between stored checkpoints                 */
+  void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
+} pdlp_options;
+
+typedef struct {
+  int32_t status;                 /* PDLP_OPTIMAL, ... */
+  int32_t returned_average;       /* 1 if the returned point is the step-weighted average */
+  int64_t iters, kkt_passes, restarts;
+  int32_t refine_rounds;          /* outer rounds used by PDLP_FP32_REFINE                 */
+  int32_t pad_;
+  double primal_obj, dual_obj;    /* Eq. (15) at the returned point, original problem     */
+  double gap, pres, dres;         /* absolute left-hand sides of Eq. (15a-c)              */
+  double rel_gap, rel_pres, rel_dres; /* each divided by its right-hand factor            */
+  double seconds;                 /* device wall time of the solve                        */
+} pdlp_result;
+
+/* ---------------------------------------------------------------- calls */
+
+/* Fills *opts with the paper's defaults (Sections 3.1-3.5, Appendix G flags). */
+int pdlp_default_options(pdlp_options *opts);
+
+/* Builds a solver context for one LP in the form of Eq. (1).
+ * Validates the data on the device, copies it, builds K^T (stable CSR
+ * transpose), applies `ruiz_iters` Ruiz steps and one Pock-Chambolle step
+ * (Section 3.5) to K and K^T, transforms c, q, l, u, and captures the CUDA
+ * graphs of the iteration.  Returns PDLP_ERR_INVALID_ARG for malformed input
+ * (nothing is allocated then).  *out receives the context. */
+int pdlp_create(const pdlp_csr *K, const double *c, const double *q, const double *l,
+                const double *u, const uint8_t *ineq_mask, const pdlp_options *opts,
+                pdlp_ctx **out);
+
+/* Runs Algorithm 1 from z^{0,0} = (x0, y0) (NULL = zero vectors, Section 4.1)
+ * until Eq. (15) holds with epsilon = rel_tol or a limit is hit.  x_out (n)
+ * and y_out (m) receive the returned point in the original (unscaled)
+ * space: the iterate that passed the test (current first, then the average),
+ * else the current iterate.  Either output may be NULL.  With
+ * opts.unroll_T > 0 the call instead runs the unrolled map used by pdlp_grad
+ * (see pdlp_unroll) and returns x_T, y_T. */
+int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, double *x_out,
+               double *y_out, pdlp_result *res);
+
+/* Unrolled PDHG for differentiation: T steps of Eq. (3) on the
+ * preconditioned problem with omega = InitializePrimalWeight (fixed) and the
+ * step sizes of Algorithm 2 (accepted steps), which are recorded and then
+ * held constant.  Stores (x, y) every ckpt_every steps for pdlp_grad.
+ * eta_out (T, nullable) receives the step sizes. */
+int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const double *x0,
+                const double *y0, double *x_out, double *y_out, double *eta_out);
+
+/* Vector-Jacobian product of the last unrolled map (x_T, y_T) with respect
+ * to (c, q, values of K): given dL/dx_T (n) and dL/dy_T (m, nullable) writes
+ * dL/dc (n), dL/dq (m) and dL/dK (nnz, in the CSR order of the K passed to
+ * pdlp_create).  The preconditioner and the recorded step sizes are held
+ * constant; gradients accumulate in float64.  PDLP_ERR_STATE if no unrolled
+ * map was run on ctx. */
+int pdlp_grad(pdlp_ctx *ctx, const double *dL_dx, const double *dL_dy, double *dc,
+              double *dq, double *dK_val);
+
+/* Copies out the preconditioned problem built by pdlp_create (Section 3.5),
+ * for inspection.  Any pointer may be NULL.  Sizes: Kval / KTval nnz
+ * (float64, CSR order of K and of K^T), KT_row_ptr n+1, KT_col_idx nnz,
+ * KT_perm nnz (position in K of each K^T entry), D1 m, D2 n, cs/ls/us n, qs m. */
+int pdlp_get_scaled(pdlp_ctx *ctx, double *Kval, int32_t *KT_row_ptr, int32_t *KT_col_idx,
+                    double *KTval, int32_t *KT_perm, double *D1, double *D2, double *cs,
+                    double *qs, double *ls, double *us);
+
+/* Section 3.2 normalized duality gap rho_r(z) on the preconditioned problem of
+ * ctx, for inspection: x (n), y (m) a point of X x Y in the scaled space,
+ * r > 0 the radius, omega the primal weight.  Computes K^T y and K x itself.
+ * *mu receives rho_r(z), *value the maximised gap.  Float64. */
+int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double *y, double omega,
+                        double r, double *mu, double *value);
+
+/* Batched solve of `count` independent LPs in one persistent launch (one CTA
+ * per LP, largest first).  The LPs are packed back to back: LP b has
+ * dims m[b], n[b]; its rows, columns and nonzeros start at row_off[b],
+ * col_off[b], nnz_off[b] (int64, count+1 entries, row_off[count] = total
+ * rows, ...).  row_ptr is the concatenation of the LPs' own row_ptr arrays
+ * without their final entry, i.e. int32[total rows] holding offsets local to
+ * each LP; col_idx (local column numbers) and val are int32 / float64[total
+ * nnz]; c, l, u are float64[total cols]; q float64[total rows]; ineq_mask
+ * uint8[total rows].  x_out / y_out (float64[total cols] / [total rows],
+ * nullable) receive the solutions, res[count] (nullable) the outcomes.
+ * Uses opts.precision (PDLP_FP64 or PDLP_FP32 arithmetic in the SpMVs),
+ * rel_tol, iter_limit and the restart / step settings. */
+int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *n, const int64_t *row_off,
+                     const int64_t *col_off, const int64_t *nnz_off, const int32_t *row_ptr,
+                     const int32_t *col_idx, const double *val, const double *c,
+                     const double *q, const double *l, const double *u,
+                     const uint8_t *ineq_mask, const pdlp_options *opts, double *x_out,
+                     double *y_out, pdlp_result *res);
+
+/* Restart evaluations of the last solve on ctx, oldest first (a ring keeps
+ * the last 256).  Each record is 16 float64: k, t, mu(current), mu(average),
+ * mu_0, candidate (0 current, 1 average), restarted (0/1), primal weight
+ * after the evaluation (Section 3.2 and Algorithm 3), the radii
+ * ||z - z^{n,0}||_omega of the current and the average iterate, and the
+ * relative gap, primal and dual residuals of Eq. (15) of the current, then
+ * the average iterate.  out holds 16 * max_records doubles (host or device);
+ * *count receives the number of evaluations of the solve (may exceed 256). */
+int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *count);
+
+/* Measures the two kernels of one step attempt of Algorithm 2 (the fused
+ * K^T y product with the primal projection, and the fused K x' product with
+ * the dual projection, reductions and step test) by launching each `reps`
+ * times outside the solve graph on the context's stream, bracketed by CUDA
+ * events.  The attempts continue from the state the last solve left (call
+ * pdlp_solve first).  ms[0], ms[1] (host) receive the mean durations in
+ * milliseconds of the primal and the dual kernel. */
+int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms);
+
+/* Message of the last failing call on this thread (ctx may be NULL). */
+const char *pdlp_last_error(const pdlp_ctx *ctx);
+
+/* Frees the context and every device buffer it owns.  NULL is a no-op. */
+void pdlp_destroy(pdlp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDLP_H */

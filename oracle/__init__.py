@@ -82,6 +82,8 @@ def lib():
             L.or_normalized_gap.argtypes = [C.c_int32, C.c_int32] + [P] * 7 + [C.c_double, C.c_double, P]
             L.or_normalized_gap.restype = C.c_double
             L.or_solve.argtypes = [C.POINTER(_Lp), C.POINTER(Opts), P, P, P, P, C.POINTER(Result)]
+            L.or_solve_traced.argtypes = [C.POINTER(_Lp), C.POINTER(Opts), P, P, P, P, C.POINTER(Result), P,
+                                          C.c_int32, C.POINTER(C.c_int32)]
             L.or_pdhg_fixed.argtypes = [C.POINTER(_Lp), C.c_double, C.c_double, C.c_int64, P, P]
             L.or_unroll_schedule.argtypes = [C.POINTER(_Lp), C.c_int32, C.c_int32, C.c_int64, P, P, P, P, P, P]
             L.or_unroll_forward.argtypes = [C.POINTER(_Lp), C.c_int32, C.c_int32, C.c_int64, P,
@@ -193,6 +195,22 @@ def solve(lp, x0=None, y0=None, ylo=None, **opts):
     r = Result()
     lib().or_solve(C.byref(pin.s), C.byref(o), _p(x0), _p(y0), _p(x), _p(y), C.byref(r))
     return x, y, r.asdict()
+
+
+def solve_traced(lp, x0=None, y0=None, ylo=None, trace_cap=256, **opts):
+    """solve() plus the restart evaluations: (x, y, result, trace[records, 8]) with
+    columns k, t, mu_cur, mu_avg, mu0, candidate, restarted, omega."""
+    o = default_opts(**opts)
+    pin = _Pinned(lp, ylo)
+    x0, y0 = _f64(x0), _f64(y0)
+    x = np.zeros(lp.n)
+    y = np.zeros(lp.m)
+    r = Result()
+    tr = np.zeros((trace_cap, 8))
+    cnt = C.c_int32()
+    lib().or_solve_traced(C.byref(pin.s), C.byref(o), _p(x0), _p(y0), _p(x), _p(y), C.byref(r), _p(tr),
+                          trace_cap, C.byref(cnt))
+    return x, y, r.asdict(), tr[:min(cnt.value, trace_cap)]
 
 
 def pdhg_fixed(lp, eta, omega, T, x0=None, y0=None):

@@ -25,6 +25,9 @@
  *  R10 every step attempt costs one KKT pass
  *  R11 Algorithm 2's k is the 1-based number of the step being taken (Algorithm
  *      1's counter plus one), so the first step uses (1 - 2^-0.3)
+ *  R12 the normalized gap is defined for z in Z; the step-weighted average can
+ *      leave its box by an ulp after rounding, so distances to the bounds are
+ *      taken as max(distance, 0)
  */
 #include "pdlp_oracle.h"
 
@@ -33,10 +36,11 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* ORACLE_TRACE=1 in the environment prints one line per restart evaluation. */
+/* ORACLE_TRACE=1 in the environment prints one line per restart evaluation,
+ * ORACLE_TRACE=2 also one line per step attempt. */
 static int trace_on(void) {
   static int on = -1;
-  if (on < 0) { const char *e = getenv("ORACLE_TRACE"); on = e && e[0] == '1'; }
+  if (on < 0) { const char *e = getenv("ORACLE_TRACE"); on = e ? atoi(e) : 0; }
   return on;
 }
 
@@ -259,6 +263,7 @@ double or_normalized_gap(int32_t n, int32_t m, const double *x, const double *y,
     double g = gx[j];
     if (g == 0.0) continue;
     double dist = g > 0.0 ? u[j] - x[j] : x[j] - l[j];
+    if (!(dist > 0.0)) dist = 0.0; /* R12 */
     double ag = fabs(g);
     gap_item e;
     e.a = g * g / omega;
@@ -270,6 +275,7 @@ double or_normalized_gap(int32_t n, int32_t m, const double *x, const double *y,
     double g = gy[i];
     if (g == 0.0) continue;
     double dist = g > 0.0 ? INFINITY : y[i] - ylo[i];
+    if (!(dist > 0.0)) dist = 0.0; /* R12 */
     double ag = fabs(g);
     gap_item e;
     e.a = omega * g * g;
@@ -449,6 +455,13 @@ static void fill_result(or_result *res, const double *kkt) {
 
 void or_solve(const or_lp *lp, const or_opts *o, const double *x0, const double *y0,
               double *x_out, double *y_out, or_result *res) {
+  or_solve_traced(lp, o, x0, y0, x_out, y_out, res, NULL, 0, NULL);
+}
+
+void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const double *y0,
+                     double *x_out, double *y_out, or_result *res, double *trace, int32_t trace_cap,
+                     int32_t *trace_n) {
+  int32_t ntr = 0;
   memset(res, 0, sizeof(*res));
   scaled_lp s;
   scaled_build(lp, o->ruiz_iters, o->pock_chambolle, &s);
@@ -499,6 +512,9 @@ void or_solve(const or_lp *lp, const or_opts *o, const double *x0, const double 
         pdhg_attempt(&s, &z, &zp, eta, omega, k, &eta_bar, &eta_next, &bad);
         kkt_passes += 1; /* R10 */
         if (bad) { status = OR_NUMERICAL_ERROR; break; }
+        if (trace_on() > 1)
+          fprintf(stderr, "  attempt k=%lld eta=%.17g eta_bar=%.17g %s\n", (long long)k, eta, eta_bar,
+                  eta <= eta_bar ? "accept" : "reject");
         if (eta <= eta_bar) break;
         eta = eta_next;
         if (kkt_passes >= o->kkt_pass_limit) { status = OR_KKT_PASS_LIMIT; break; }
@@ -531,6 +547,12 @@ void or_solve(const or_lp *lp, const or_opts *o, const double *x0, const double 
       /* GetRestartCandidate (Section 3.2) */
       double mu_cur = mu_of(&s, &z, x0r, y0r, omega);
       double mu_avg = mu_of(&s, &zbar, x0r, y0r, omega);
+      if (trace_on()) {
+        double kc[8], ka[8];
+        terminated(lp, &s, &z, o->eps, kc, xo, yo);
+        terminated(lp, &s, &zbar, o->eps, ka, xo, yo);
+        fprintf(stderr, "  kkt cur %.6e %.6e %.6e avg %.6e %.6e %.6e\n", kc[5], kc[6], kc[7], ka[5], ka[6], ka[7]);
+      }
       const iterate *cand = mu_cur < mu_avg ? &z : &zbar;
       double muc = mu_cur < mu_avg ? mu_cur : mu_avg;
       /* restart criteria (i), (ii), (iii) */
@@ -541,6 +563,18 @@ void or_solve(const or_lp *lp, const or_opts *o, const double *x0, const double 
         fprintf(stderr, "k=%lld t=%lld mu_cur=%.3e mu_avg=%.3e mu0=%.3e muc_prev=%.3e restart=%d omega=%.4g eta=%.4g\n",
                 (long long)k, (long long)t, mu_cur, mu_avg, mu0, muc_prev, restart, omega, eta_hat);
       muc_prev = muc;
+      if (trace && ntr < trace_cap) {
+        double *rec = trace + (size_t)ntr * 8;
+        rec[0] = (double)k;
+        rec[1] = (double)t;
+        rec[2] = mu_cur;
+        rec[3] = mu_avg;
+        rec[4] = mu0;
+        rec[5] = cand == &z ? 0.0 : 1.0;
+        rec[6] = (double)restart;
+        rec[7] = omega;
+      }
+      ntr += 1;
       if (!restart) continue;
 
       /* restart the outer loop at the candidate; Algorithm 3 */
@@ -552,6 +586,7 @@ void or_solve(const or_lp *lp, const or_opts *o, const double *x0, const double 
       if (trace_on()) fprintf(stderr, "  restart to %s: Dx=%.4e Dy=%.4e\n", cand == &z ? "current" : "average", Dx, Dy);
       if (o->pw_update && Dx > o->eps_zero && Dy > o->eps_zero)
         omega = exp(o->pw_theta * log(Dy / Dx) + (1.0 - o->pw_theta) * log(omega));
+      if (trace && ntr - 1 < trace_cap) trace[(size_t)(ntr - 1) * 8 + 7] = omega;
       /* mu_0 of the new outer loop: mu_n(z^{n,0}, z^{n-1,0}) under the new omega */
       mu0 = mu_of(&s, &z, x0r, y0r, omega);
       memcpy(x0r, z.x, sizeof(double) * (size_t)n);
@@ -572,6 +607,7 @@ void or_solve(const or_lp *lp, const or_opts *o, const double *x0, const double 
   res->omega = omega;
   res->eta = eta_hat;
   res->returned_average = ret_avg;
+  if (trace_n) *trace_n = ntr;
 
   free_iterate(&z); free_iterate(&zp); free_iterate(&zbar);
   free(sx); free(sy); free(x0r); free(y0r); free(xo); free(yo);

@@ -95,6 +95,14 @@ double or_normalized_gap(int32_t n, int32_t m, const double *x, const double *y,
 void or_solve(const or_lp *lp, const or_opts *opts, const double *x0, const double *y0,
               double *x_out, double *y_out, or_result *res);
 
+/* or_solve that also records each restart evaluation (up to trace_cap) as 8
+ * doubles: k, t, mu_current, mu_average, mu_0, candidate (0 current, 1
+ * average), restarted (0/1), primal weight after the evaluation.
+ * *trace_n receives the number of evaluations. */
+void or_solve_traced(const or_lp *lp, const or_opts *opts, const double *x0, const double *y0,
+                     double *x_out, double *y_out, or_result *res, double *trace, int32_t trace_cap,
+                     int32_t *trace_n);
+
 /* Plain PDHG of Eq. (3) with constant eta and omega on the unscaled problem
  * (Appendix A): T steps from (x, y) in place. */
 void or_pdhg_fixed(const or_lp *lp, double eta, double omega, int64_t T,

@@ -1,0 +1,696 @@
+// C ABI of the library (declared in include/pdlp.h): context set-up, the
+// solve graph, float32 iterative refinement, inspection calls.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "prep.cuh"
+#include "refine.cuh"
+#include "solver.cuh"
+#include "unroll.cuh"
+
+using namespace pdlp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// Device buffers of one precision's iteration.
+template <typename T>
+struct Precision {
+  bool ready = false;
+  DevBuf val, tval;  // K~ and K~^T values (only for float: double uses the master copies)
+  DevBuf cs, qs, ls, us, ylos;
+  DevBuf vecs;       // every iterate vector, one allocation
+  DevBuf parts, gkeys, ghist, xo, yo, tickets, normpart, trace;
+  Mat<T> K, KT;
+  Problem<T> P;
+  State<T> S;
+  cudaGraphExec_t graph = nullptr;
+  ~Precision() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+}  // namespace
+
+struct pdlp_ctx {
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  pdlp_options opts;
+  cudaStream_t st = nullptr;           // caller's stream
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams (library-owned)
+  std::string err;
+  // matrix (float64 master copy, preconditioned in place)
+  DevBuf rp, ci, val, trp, tci, tval, perm;
+  DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT;
+  int32_t nblocksK = 0, nblocksKT = 0;
+  std::vector<RowBlock> hblocksK, hblocksKT;
+  // problem data
+  DevBuf c, q, l, u, ylo;            // original space
+  DevBuf cs, qs, ls, us, ylos;       // preconditioned (float64)
+  DevBuf D1, D2;
+  DevBuf xin, yin;                   // start point staging (original space)
+  DevBuf mask;                       // inequality mask as given
+  DevBuf scal;                       // Scalars
+  double eta0 = 1.0;
+  Precision<double> p64;
+  Precision<float> p32;              // plain float32 solve of the LP itself
+  Precision<float> pc32;             // float32 solves of refinement corrections
+  RefineBuffers ref;
+  UnrollBuffers unr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~pdlp_ctx() {
+    if (st) cudaStreamSynchronize(st);
+    for (auto &s : cap)
+      if (s) cudaStreamDestroy(s);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+namespace {
+
+int fail(pdlp_ctx *ctx, int code, const std::string &msg) {
+  g_last_error = msg;
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(pdlp_ctx *ctx, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, PDLP_ERR_OOM, std::string(where) + ": out of device memory");
+  return fail(ctx, PDLP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                 \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+template <typename T>
+T *dalloc(DevBuf &b, size_t count) {
+  return reinterpret_cast<T *>(b.get(sizeof(T) * (count ? count : 1)));
+}
+
+__global__ void k_absmax_bits(const double *v, int64_t n, unsigned long long *out) {
+  unsigned long long mx = 0ull;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v[i]));
+    mx = b > mx ? b : mx;
+  }
+  atomicMax(out, mx);  // non-negative doubles order like their bit patterns
+}
+
+template <typename T>
+int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tval) {
+  K.rows = ctx->m;
+  K.cols = ctx->n;
+  K.rp = reinterpret_cast<const int32_t *>(ctx->rp.ptr());
+  K.ci = reinterpret_cast<const int32_t *>(ctx->ci.ptr());
+  K.val = val;
+  K.blocks = reinterpret_cast<const RowBlock *>(ctx->blocksK.ptr());
+  K.nblocks = ctx->nblocksK;
+  K.longrows = reinterpret_cast<const LongRow *>(ctx->longK.ptr());
+  K.seg_part = reinterpret_cast<double *>(ctx->segK.ptr());
+  K.seg_cnt = reinterpret_cast<unsigned *>(ctx->segcntK.ptr());
+  KT.rows = ctx->n;
+  KT.cols = ctx->m;
+  KT.rp = reinterpret_cast<const int32_t *>(ctx->trp.ptr());
+  KT.ci = reinterpret_cast<const int32_t *>(ctx->tci.ptr());
+  KT.val = tval;
+  KT.blocks = reinterpret_cast<const RowBlock *>(ctx->blocksKT.ptr());
+  KT.nblocks = ctx->nblocksKT;
+  KT.longrows = reinterpret_cast<const LongRow *>(ctx->longKT.ptr());
+  KT.seg_part = reinterpret_cast<double *>(ctx->segKT.ptr());
+  KT.seg_cnt = reinterpret_cast<unsigned *>(ctx->segcntKT.ptr());
+  return PDLP_OK;
+}
+
+// Allocates the iterate state of one precision and captures its solve graph
+// on the problem `P` (already filled in).
+template <typename T>
+int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
+  const int n = ctx->n, m = ctx->m, N = n + m;
+  const size_t nv = 2 * (size_t)n + 2 * (size_t)m + 2 * (size_t)m + 2 * (size_t)n + 2 * (size_t)m +
+                    (size_t)n + (size_t)m + 2 * (size_t)n + (size_t)m;
+  T *v = dalloc<T>(pr.vecs, nv);
+  if (!v) return fail(ctx, PDLP_ERR_OOM, "state allocation failed");
+  CK(cudaMemsetAsync(v, 0, sizeof(T) * nv, ctx->st), "memset state");
+  State<T> &S = pr.S;
+  T *p = v;
+  auto take = [&](size_t k) { T *r = p; p += k; return r; };
+  S.x[0] = take(n); S.x[1] = take(n);
+  S.y[0] = take(m); S.y[1] = take(m);
+  S.Kx[0] = take(m); S.Kx[1] = take(m);
+  S.xs[0] = take(n); S.xs[1] = take(n);
+  S.ys[0] = take(m); S.ys[1] = take(m);
+  S.x0 = take(n); S.y0 = take(m);
+  S.KTy_cur = take(n); S.KTys = take(n);
+  S.Kxbar = take(m);
+  const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
+                    8 * (size_t)ctx->nblocksK + 16;
+  double *parts = dalloc<double>(pr.parts, np);
+  if (!parts) return fail(ctx, PDLP_ERR_OOM, "partials allocation failed");
+  S.part_p = parts;
+  S.part_d = S.part_p + ctx->nblocksKT;
+  S.part_ec = S.part_d + 2 * (size_t)ctx->nblocksK;
+  S.part_er = S.part_ec + 8 * (size_t)ctx->nblocksKT;
+  S.tickets = dalloc<unsigned>(pr.tickets, kNumTickets);
+  S.gkeys = dalloc<unsigned>(pr.gkeys, (size_t)kGapSlots * N);
+  S.ghist = dalloc<double>(pr.ghist, (size_t)kGapSlots * kGapBuckets * 3);
+  S.xo = dalloc<double>(pr.xo, n);
+  S.yo = dalloc<double>(pr.yo, m);
+  S.s = reinterpret_cast<Scalars *>(ctx->scal.ptr());
+  S.trace = dalloc<double>(pr.trace, (size_t)kTraceCap * kTraceLen);
+  if (!S.trace) return fail(ctx, PDLP_ERR_OOM, "trace allocation failed");
+  double *normpart = dalloc<double>(pr.normpart, 4 * 152 + 8);
+  if (!S.tickets || !S.gkeys || !S.ghist || !S.xo || !S.yo || !normpart)
+    return fail(ctx, PDLP_ERR_OOM, "state allocation failed");
+  CK(cudaMemsetAsync(S.tickets, 0, sizeof(unsigned) * kNumTickets, ctx->st), "memset");
+  CK(cudaMemsetAsync(S.ghist, 0, sizeof(double) * kGapSlots * kGapBuckets * 3, ctx->st), "memset");
+  CK(cudaMemsetAsync(normpart, 0, sizeof(double) * (4 * 152 + 8), ctx->st), "memset");
+  CK(set_kernel_attributes<T>(), "kernel attributes");
+  CK(cudaStreamSynchronize(ctx->st), "sync");
+  const pdlp_options &o = ctx->opts;
+  ScalarInit in{};
+  in.eta0 = ctx->eta0;
+  in.rel_tol = tol;
+  in.beta_suff = o.beta_suff;
+  in.beta_nec = o.beta_nec;
+  in.beta_art = o.beta_art;
+  in.pw_theta = o.pw_smoothing;
+  in.eps_zero = o.eps_zero;
+  in.iter_limit = o.iter_limit;
+  in.attempt_limit = o.kkt_pass_limit;
+  in.time_limit_ns = o.time_limit_s > 0 ? (unsigned long long)(o.time_limit_s * 1e9) : 0ull;
+  in.eval_every = o.eval_every;
+  in.adaptive_restart = o.adaptive_restart;
+  in.pw_update = o.pw_update;
+  CK(build_solve_graph<T>(pr.K, pr.KT, pr.P, pr.S, in, o.primal_importance, normpart,
+                          reinterpret_cast<const double *>(ctx->xin.ptr()),
+                          reinterpret_cast<const double *>(ctx->yin.ptr()), 2 * 152, ctx->cap[0],
+                          ctx->cap[1], ctx->cap[2], &pr.graph),
+     "graph capture");
+  pr.ready = true;
+  return PDLP_OK;
+}
+
+// Fills the float64 problem view with the context's own LP.
+void fill_problem64(pdlp_ctx *ctx, Problem<double> &P) {
+  P.m = ctx->m;
+  P.n = ctx->n;
+  P.cs = reinterpret_cast<const double *>(ctx->cs.ptr());
+  P.qs = reinterpret_cast<const double *>(ctx->qs.ptr());
+  P.ls = reinterpret_cast<const double *>(ctx->ls.ptr());
+  P.us = reinterpret_cast<const double *>(ctx->us.ptr());
+  P.ylos = reinterpret_cast<const double *>(ctx->ylos.ptr());
+  P.c = reinterpret_cast<const double *>(ctx->c.ptr());
+  P.q = reinterpret_cast<const double *>(ctx->q.ptr());
+  P.l = reinterpret_cast<const double *>(ctx->l.ptr());
+  P.u = reinterpret_cast<const double *>(ctx->u.ptr());
+  P.ylo = reinterpret_cast<const double *>(ctx->ylo.ptr());
+  P.D1 = reinterpret_cast<const double *>(ctx->D1.ptr());
+  P.D2 = reinterpret_cast<const double *>(ctx->D2.ptr());
+}
+
+int setup_fp64(pdlp_ctx *ctx) {
+  Precision<double> &pr = ctx->p64;
+  if (pr.ready) return PDLP_OK;
+  setup_matrix<double>(ctx, pr.K, pr.KT, reinterpret_cast<const double *>(ctx->val.ptr()),
+                       reinterpret_cast<const double *>(ctx->tval.ptr()));
+  fill_problem64(ctx, pr.P);
+  return setup_state<double>(ctx, pr, ctx->opts.rel_tol);
+}
+
+// float32 copies of K~, K~^T (shared by the plain float32 and the refinement paths)
+int ensure_float_matrix(pdlp_ctx *ctx, Precision<float> &pr, Precision<float> *share) {
+  const float *v = nullptr, *tv = nullptr;
+  if (share && share->val.ptr()) {
+    v = reinterpret_cast<const float *>(share->val.ptr());
+    tv = reinterpret_cast<const float *>(share->tval.ptr());
+  } else {
+    float *a = dalloc<float>(pr.val, ctx->nnz), *b = dalloc<float>(pr.tval, ctx->nnz);
+    if (!a || !b) return fail(ctx, PDLP_ERR_OOM, "float matrix allocation failed");
+    CK(to_float(reinterpret_cast<const double *>(ctx->val.ptr()), ctx->nnz, a, ctx->st), "to_float");
+    CK(to_float(reinterpret_cast<const double *>(ctx->tval.ptr()), ctx->nnz, b, ctx->st), "to_float");
+    v = a;
+    tv = b;
+  }
+  setup_matrix<float>(ctx, pr.K, pr.KT, v, tv);
+  return PDLP_OK;
+}
+
+int setup_fp32(pdlp_ctx *ctx) {
+  Precision<float> &pr = ctx->p32;
+  if (pr.ready) return PDLP_OK;
+  int rc = ensure_float_matrix(ctx, pr, &ctx->pc32);
+  if (rc) return rc;
+  const int n = ctx->n, m = ctx->m;
+  float *cs = dalloc<float>(pr.cs, n), *qs = dalloc<float>(pr.qs, m), *ls = dalloc<float>(pr.ls, n),
+        *us = dalloc<float>(pr.us, n), *ylos = dalloc<float>(pr.ylos, m);
+  if (!cs || !qs || !ls || !us || !ylos) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+  CK(to_float(reinterpret_cast<const double *>(ctx->cs.ptr()), n, cs, ctx->st), "to_float");
+  CK(to_float(reinterpret_cast<const double *>(ctx->qs.ptr()), m, qs, ctx->st), "to_float");
+  CK(to_float(reinterpret_cast<const double *>(ctx->ls.ptr()), n, ls, ctx->st), "to_float");
+  CK(to_float(reinterpret_cast<const double *>(ctx->us.ptr()), n, us, ctx->st), "to_float");
+  CK(to_float(reinterpret_cast<const double *>(ctx->ylos.ptr()), m, ylos, ctx->st), "to_float");
+  Problem<double> P64;
+  fill_problem64(ctx, P64);
+  Problem<float> &P = pr.P;
+  P.m = m;
+  P.n = n;
+  P.cs = cs; P.qs = qs; P.ls = ls; P.us = us; P.ylos = ylos;
+  P.c = P64.c; P.q = P64.q; P.l = P64.l; P.u = P64.u; P.ylo = P64.ylo;
+  P.D1 = P64.D1; P.D2 = P64.D2;
+  return setup_state<float>(ctx, pr, ctx->opts.rel_tol);
+}
+
+int setup_refine(pdlp_ctx *ctx) {
+  Precision<float> &pr = ctx->pc32;
+  if (pr.ready) return PDLP_OK;
+  int rc = ensure_float_matrix(ctx, pr, &ctx->p32);
+  if (rc) return rc;
+  rc = setup_fp64(ctx);  // float64 K~ products for the residuals
+  if (rc) return rc;
+  CK(refine_alloc(ctx->ref, ctx->m, ctx->n, ctx->nblocksK, ctx->nblocksKT), "refinement allocation");
+  Problem<double> P64;
+  fill_problem64(ctx, P64);
+  pr.P = refine_problem(ctx->ref, P64);
+  return setup_state<float>(ctx, pr, ctx->opts.inner_tol);
+}
+
+void read_result(const Scalars &s, double seconds, pdlp_result *res) {
+  memset(res, 0, sizeof(*res));
+  res->status = s.status;
+  res->returned_average = s.ret_which;
+  res->iters = s.k;
+  res->kkt_passes = s.attempts;
+  res->restarts = s.restarts;
+  const double *k = s.kkt[s.ret_which];
+  res->primal_obj = k[0];
+  res->dual_obj = k[1];
+  res->gap = k[2];
+  res->pres = k[3];
+  res->dres = k[4];
+  res->rel_gap = k[5];
+  res->rel_pres = k[6];
+  res->rel_dres = k[7];
+  res->seconds = seconds;
+}
+
+// Launches one precision's solve graph from the staged start point.
+template <typename T>
+int run_graph(pdlp_ctx *ctx, Precision<T> &pr, Scalars *hs) {
+  CK(cudaGraphLaunch(pr.graph, ctx->st), "graph launch");
+  CK(cudaMemcpyAsync(hs, pr.S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st), "scalars");
+  CK(cudaStreamSynchronize(ctx->st), "solve");
+  return PDLP_OK;
+}
+
+int stage_start(pdlp_ctx *ctx, const double *x0, const double *y0) {
+  double *xi = reinterpret_cast<double *>(ctx->xin.ptr()), *yi = reinterpret_cast<double *>(ctx->yin.ptr());
+  if (x0) CK(cudaMemcpyAsync(xi, x0, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "x0");
+  else CK(cudaMemsetAsync(xi, 0, sizeof(double) * ctx->n, ctx->st), "x0");
+  if (y0) CK(cudaMemcpyAsync(yi, y0, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "y0");
+  else CK(cudaMemsetAsync(yi, 0, sizeof(double) * ctx->m, ctx->st), "y0");
+  return PDLP_OK;
+}
+
+int check_options(const pdlp_options *o, std::string &why) {
+  if (!(o->rel_tol >= 0.0)) { why = "rel_tol must be >= 0"; return 0; }
+  if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
+  if (o->eval_every < 1) { why = "eval_every must be >= 1"; return 0; }
+  if (o->ruiz_iters < 0) { why = "ruiz_iters must be >= 0"; return 0; }
+  if (o->iter_limit < 0 || o->kkt_pass_limit < 0) { why = "limits must be >= 0"; return 0; }
+  if (!(o->primal_importance > 0.0)) { why = "primal_importance must be > 0"; return 0; }
+  if (!(o->pw_smoothing >= 0.0 && o->pw_smoothing <= 1.0)) { why = "pw_smoothing must be in [0, 1]"; return 0; }
+  return 1;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" int pdlp_default_options(pdlp_options *o) {
+  if (!o) return fail(nullptr, PDLP_ERR_INVALID_ARG, "opts is NULL");
+  memset(o, 0, sizeof(*o));
+  o->rel_tol = 1e-8;
+  o->iter_limit = 1000000;
+  o->kkt_pass_limit = 4000000;
+  o->time_limit_s = 3600.0;
+  o->precision = PDLP_FP64;
+  o->ruiz_iters = 10;
+  o->pock_chambolle = 1;
+  o->eval_every = 40;
+  o->adaptive_restart = 1;
+  o->pw_update = 1;
+  o->pw_smoothing = 0.5;
+  o->primal_importance = 1.0;
+  o->beta_suff = 0.9;
+  o->beta_nec = 0.1;
+  o->beta_art = 0.5;
+  o->eps_zero = 1e-10;
+  o->inner_tol = 1e-4;
+  o->refine_rounds = 12;
+  o->unroll_T = 0;
+  o->ckpt_every = 50;
+  o->stream = nullptr;
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, const double *l,
+                           const double *u, const uint8_t *ineq_mask, const pdlp_options *opts,
+                           pdlp_ctx **out) {
+  if (out) *out = nullptr;
+  if (!K || !c || !q || !l || !u || !ineq_mask || !out)
+    return fail(nullptr, PDLP_ERR_INVALID_ARG, "NULL argument");
+  if (K->m < 1 || K->n < 1 || K->nnz < 0 || K->nnz > 2147483647ll || !K->row_ptr ||
+      (K->nnz > 0 && (!K->col_idx || !K->val)))
+    return fail(nullptr, PDLP_ERR_INVALID_ARG, "bad CSR dimensions (m, n >= 1, 0 <= nnz < 2^31)");
+  pdlp_options o;
+  if (opts) o = *opts; else pdlp_default_options(&o);
+  std::string why;
+  if (!check_options(&o, why)) return fail(nullptr, PDLP_ERR_INVALID_ARG, why);
+  std::unique_ptr<pdlp_ctx> hold(new pdlp_ctx());
+  pdlp_ctx *ctx = hold.get();
+  ctx->m = K->m;
+  ctx->n = K->n;
+  ctx->nnz = K->nnz;
+  ctx->opts = o;
+  ctx->st = reinterpret_cast<cudaStream_t>(o.stream);
+  for (auto &s : ctx->cap) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+  CK(cudaEventCreate(&ctx->ev0), "event");
+  CK(cudaEventCreate(&ctx->ev1), "event");
+  const int m = K->m, n = K->n;
+  const int64_t nnz = K->nnz;
+  cudaStream_t st = ctx->st;
+  // device copies of the input (host or device pointers)
+  int32_t *rp = dalloc<int32_t>(ctx->rp, (size_t)m + 1), *ci = dalloc<int32_t>(ctx->ci, nnz);
+  double *val = dalloc<double>(ctx->val, nnz);
+  double *dc = dalloc<double>(ctx->c, n), *dq = dalloc<double>(ctx->q, m), *dl = dalloc<double>(ctx->l, n),
+         *du = dalloc<double>(ctx->u, n), *dylo = dalloc<double>(ctx->ylo, m);
+  uint8_t *mask = dalloc<uint8_t>(ctx->mask, m);
+  if (!rp || !ci || !val || !dc || !dq || !dl || !du || !dylo || !mask)
+    return fail(ctx, PDLP_ERR_OOM, "input allocation failed");
+  CK(cudaMemcpyAsync(rp, K->row_ptr, sizeof(int32_t) * ((size_t)m + 1), cudaMemcpyDefault, st), "copy row_ptr");
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(ci, K->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDefault, st), "copy col_idx");
+    CK(cudaMemcpyAsync(val, K->val, sizeof(double) * nnz, cudaMemcpyDefault, st), "copy val");
+  }
+  CK(cudaMemcpyAsync(dc, c, sizeof(double) * n, cudaMemcpyDefault, st), "copy c");
+  CK(cudaMemcpyAsync(dq, q, sizeof(double) * m, cudaMemcpyDefault, st), "copy q");
+  CK(cudaMemcpyAsync(dl, l, sizeof(double) * n, cudaMemcpyDefault, st), "copy l");
+  CK(cudaMemcpyAsync(du, u, sizeof(double) * n, cudaMemcpyDefault, st), "copy u");
+  CK(cudaMemcpyAsync(mask, ineq_mask, sizeof(uint8_t) * m, cudaMemcpyDefault, st), "copy ineq_mask");
+  // validation on the device
+  DevBuf errbuf;
+  unsigned *derr = dalloc<unsigned>(errbuf, 1);
+  unsigned herr = 0;
+  if (!derr) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+  CK(validate(m, n, nnz, rp, ci, val, dc, dq, dl, du, derr, &herr, st), "validate");
+  if (herr) return fail(ctx, PDLP_ERR_INVALID_ARG, validate_message(herr));
+  CK(ylo_from_mask(m, mask, dylo, st), "ylo");
+  // K^T
+  int32_t *trp = dalloc<int32_t>(ctx->trp, (size_t)n + 1), *tci = dalloc<int32_t>(ctx->tci, nnz),
+          *perm = dalloc<int32_t>(ctx->perm, nnz);
+  double *tval = dalloc<double>(ctx->tval, nnz);
+  if (!trp || !tci || !perm || !tval) return fail(ctx, PDLP_ERR_OOM, "transpose allocation failed");
+  {
+    DevBuf tmp;
+    CK(build_transpose(m, n, nnz, rp, ci, trp, tci, perm, tmp, st), "transpose");
+  }
+  // Section 3.5 preconditioning and transform
+  double *D1 = dalloc<double>(ctx->D1, m), *D2 = dalloc<double>(ctx->D2, n);
+  double *cs = dalloc<double>(ctx->cs, n), *qs = dalloc<double>(ctx->qs, m), *ls = dalloc<double>(ctx->ls, n),
+         *us = dalloc<double>(ctx->us, n), *ylos = dalloc<double>(ctx->ylos, m);
+  DevBuf rbuf, cbuf;
+  double *rb = dalloc<double>(rbuf, m), *cb = dalloc<double>(cbuf, n);
+  if (!D1 || !D2 || !cs || !qs || !ls || !us || !ylos || !rb || !cb)
+    return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+  CK(precondition(m, n, nnz, rp, ci, val, trp, tval, perm, o.ruiz_iters, o.pock_chambolle, D1, D2, rb, cb, st),
+     "precondition");
+  CK(transform(m, n, D1, D2, dc, dq, dl, du, dylo, cs, qs, ls, us, ylos, st), "transform");
+  // step size 1 / max |K~_ij| (Algorithm 1 initialisation)
+  {
+    DevBuf mb;
+    unsigned long long *dmax = dalloc<unsigned long long>(mb, 1), hmax = 0ull;
+    if (!dmax) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+    CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st), "memset");
+    if (nnz > 0) k_absmax_bits<<<std::min<int64_t>((nnz + 255) / 256, 1024), 256, 0, st>>>(val, nnz, dmax);
+    CK(cudaGetLastError(), "absmax");
+    CK(cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st), "absmax");
+    CK(cudaStreamSynchronize(st), "sync");
+    double kmax;
+    memcpy(&kmax, &hmax, sizeof(kmax));
+    ctx->eta0 = kmax > 0.0 ? 1.0 / kmax : 1.0;
+  }
+  // row-block schedules of K and K^T
+  {
+    std::vector<int32_t> hrp((size_t)m + 1), htrp((size_t)n + 1);
+    CK(cudaMemcpyAsync(hrp.data(), rp, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost, st), "row_ptr");
+    CK(cudaMemcpyAsync(htrp.data(), trp, sizeof(int32_t) * htrp.size(), cudaMemcpyDeviceToHost, st), "row_ptr");
+    CK(cudaStreamSynchronize(st), "sync");
+    std::vector<LongRow> lK, lKT;
+    int32_t segK = 0, segKT = 0;
+    build_schedule(m, hrp.data(), ctx->hblocksK, lK, segK);
+    build_schedule(n, htrp.data(), ctx->hblocksKT, lKT, segKT);
+    ctx->nblocksK = (int32_t)ctx->hblocksK.size();
+    ctx->nblocksKT = (int32_t)ctx->hblocksKT.size();
+    RowBlock *bK = dalloc<RowBlock>(ctx->blocksK, ctx->hblocksK.size()),
+             *bKT = dalloc<RowBlock>(ctx->blocksKT, ctx->hblocksKT.size());
+    LongRow *LK = dalloc<LongRow>(ctx->longK, lK.size()), *LKT = dalloc<LongRow>(ctx->longKT, lKT.size());
+    double *sK = dalloc<double>(ctx->segK, 2 * (size_t)segK), *sKT = dalloc<double>(ctx->segKT, 2 * (size_t)segKT);
+    unsigned *cK = dalloc<unsigned>(ctx->segcntK, lK.size()), *cKT = dalloc<unsigned>(ctx->segcntKT, lKT.size());
+    if (!bK || !bKT || !LK || !LKT || !sK || !sKT || !cK || !cKT) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+    CK(cudaMemcpy(bK, ctx->hblocksK.data(), sizeof(RowBlock) * ctx->hblocksK.size(), cudaMemcpyHostToDevice), "blocks");
+    CK(cudaMemcpy(bKT, ctx->hblocksKT.data(), sizeof(RowBlock) * ctx->hblocksKT.size(), cudaMemcpyHostToDevice), "blocks");
+    if (!lK.empty()) CK(cudaMemcpy(LK, lK.data(), sizeof(LongRow) * lK.size(), cudaMemcpyHostToDevice), "long rows");
+    if (!lKT.empty()) CK(cudaMemcpy(LKT, lKT.data(), sizeof(LongRow) * lKT.size(), cudaMemcpyHostToDevice), "long rows");
+    CK(cudaMemset(cK, 0, sizeof(unsigned) * std::max<size_t>(lK.size(), 1)), "memset");
+    CK(cudaMemset(cKT, 0, sizeof(unsigned) * std::max<size_t>(lKT.size(), 1)), "memset");
+  }
+  double *xin = dalloc<double>(ctx->xin, n), *yin = dalloc<double>(ctx->yin, m);
+  Scalars *sc = dalloc<Scalars>(ctx->scal, 1);
+  if (!xin || !yin || !sc) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+  CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), st), "memset");
+  int rc = PDLP_OK;
+  if (o.unroll_T > 0) rc = setup_fp64(ctx);
+  else if (o.precision == PDLP_FP64) rc = setup_fp64(ctx);
+  else if (o.precision == PDLP_FP32) rc = setup_fp32(ctx);
+  else rc = setup_refine(ctx);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(st), "create");
+  *out = hold.release();
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, double *x_out, double *y_out,
+                          pdlp_result *res) {
+  if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->opts.unroll_T > 0)
+    return pdlp_unroll(ctx, ctx->opts.unroll_T, ctx->opts.ckpt_every, x0, y0, x_out, y_out, nullptr);
+  int rc = stage_start(ctx, x0, y0);
+  if (rc) return rc;
+  Scalars hs;
+  pdlp_result r;
+  const int prec = ctx->opts.precision;
+  CK(cudaEventRecord(ctx->ev0, ctx->st), "event");
+  const double *xo = nullptr, *yo = nullptr;
+  if (prec == PDLP_FP64) {
+    if ((rc = setup_fp64(ctx))) return rc;
+    if ((rc = run_graph<double>(ctx, ctx->p64, &hs))) return rc;
+    xo = ctx->p64.S.xo;
+    yo = ctx->p64.S.yo;
+    read_result(hs, 0.0, &r);
+  } else if (prec == PDLP_FP32) {
+    if ((rc = setup_fp32(ctx))) return rc;
+    if ((rc = run_graph<float>(ctx, ctx->p32, &hs))) return rc;
+    xo = ctx->p32.S.xo;
+    yo = ctx->p32.S.yo;
+    read_result(hs, 0.0, &r);
+  } else {
+    if ((rc = setup_refine(ctx))) return rc;
+    RefineOutcome ro;
+    cudaError_t e = refine_solve(ctx->ref, ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->pc32.P, ctx->pc32.S,
+                                 ctx->pc32.graph, ctx->opts.rel_tol, ctx->opts.inner_tol, ctx->opts.refine_rounds,
+                                 reinterpret_cast<const double *>(ctx->xin.ptr()),
+                                 reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st, &ro);
+    if (e) return cuda_fail(ctx, e, "refinement");
+    xo = ro.x;
+    yo = ro.y;
+    memset(&r, 0, sizeof(r));
+    r.status = ro.status;
+    r.iters = ro.iters;
+    r.kkt_passes = ro.kkt_passes;
+    r.restarts = ro.restarts;
+    r.refine_rounds = ro.rounds;
+    r.primal_obj = ro.kkt[0];
+    r.dual_obj = ro.kkt[1];
+    r.gap = ro.kkt[2];
+    r.pres = ro.kkt[3];
+    r.dres = ro.kkt[4];
+    r.rel_gap = ro.kkt[5];
+    r.rel_pres = ro.kkt[6];
+    r.rel_dres = ro.kkt[7];
+  }
+  CK(cudaEventRecord(ctx->ev1, ctx->st), "event");
+  if (x_out) CK(cudaMemcpyAsync(x_out, xo, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "x_out");
+  if (y_out) CK(cudaMemcpyAsync(y_out, yo, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "y_out");
+  CK(cudaStreamSynchronize(ctx->st), "solve");
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
+  r.seconds = ms * 1e-3;
+  if (res) *res = r;
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_get_scaled(pdlp_ctx *ctx, double *Kval, int32_t *KT_row_ptr, int32_t *KT_col_idx,
+                               double *KTval, int32_t *KT_perm, double *D1, double *D2, double *cs,
+                               double *qs, double *ls, double *us) {
+  if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  const size_t n = ctx->n, m = ctx->m, nnz = ctx->nnz;
+  cudaStream_t st = ctx->st;
+  auto cp = [&](void *dst, const DevBuf &src, size_t bytes) -> cudaError_t {
+    if (!dst || bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src.ptr(), bytes, cudaMemcpyDefault, st);
+  };
+  CK(cp(Kval, ctx->val, 8 * nnz), "copy");
+  CK(cp(KT_row_ptr, ctx->trp, 4 * (n + 1)), "copy");
+  CK(cp(KT_col_idx, ctx->tci, 4 * nnz), "copy");
+  CK(cp(KTval, ctx->tval, 8 * nnz), "copy");
+  CK(cp(KT_perm, ctx->perm, 4 * nnz), "copy");
+  CK(cp(D1, ctx->D1, 8 * m), "copy");
+  CK(cp(D2, ctx->D2, 8 * n), "copy");
+  CK(cp(cs, ctx->cs, 8 * n), "copy");
+  CK(cp(qs, ctx->qs, 8 * m), "copy");
+  CK(cp(ls, ctx->ls, 8 * n), "copy");
+  CK(cp(us, ctx->us, 8 * n), "copy");
+  CK(cudaStreamSynchronize(st), "copy");
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double *y, double omega, double r,
+                                   double *mu, double *value) {
+  if (!ctx || !x || !y) return fail(ctx, PDLP_ERR_INVALID_ARG, "NULL argument");
+  if (!(r > 0.0) || !(omega > 0.0)) return fail(ctx, PDLP_ERR_INVALID_ARG, "r and omega must be > 0");
+  int rc = setup_fp64(ctx);
+  if (rc) return rc;
+  Precision<double> &pr = ctx->p64;
+  State<double> &S = pr.S;
+  cudaStream_t st = ctx->st;
+  CK(cudaMemcpyAsync(S.x[0], x, sizeof(double) * ctx->n, cudaMemcpyDefault, st), "x");
+  CK(cudaMemcpyAsync(S.y[0], y, sizeof(double) * ctx->m, cudaMemcpyDefault, st), "y");
+  launch_spmv<double>(pr.KT, S.y[0], S.KTy_cur, st);
+  launch_spmv<double>(pr.K, S.x[0], S.Kx[0], st);
+  CK(cudaGetLastError(), "spmv");
+  Scalars hs;
+  CK(cudaMemcpyAsync(&hs, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "scalars");
+  CK(cudaStreamSynchronize(st), "sync");
+  hs.cur = 0;
+  hs.do_gap = 1;
+  hs.restart = 0;
+  for (int a = 0; a < kGapSlots; ++a) {
+    hs.g_active[a] = 0;
+    hs.mu[a] = INFINITY;
+  }
+  hs.g_active[0] = 1;
+  hs.g_r2[0] = r * r;
+  hs.g_omega[0] = omega;
+  hs.g_W[0] = hs.g_V[0] = hs.g_A[0] = 0.0;
+  hs.g_prefix[0] = 0u;
+  CK(cudaMemcpyAsync(S.s, &hs, sizeof(Scalars), cudaMemcpyHostToDevice, st), "scalars");
+  CK(launch_gap_slots<double>(pr.P, S, 0, 1, 0, 2 * 152, st), "gap");
+  CK(cudaMemcpyAsync(&hs, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "scalars");
+  CK(cudaStreamSynchronize(st), "sync");
+  if (mu) *mu = hs.mu[0];
+  if (value) *value = hs.gval[0];
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *count) {
+  if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  const double *tr = nullptr;
+  if (ctx->opts.precision == PDLP_FP64 && ctx->p64.ready) tr = ctx->p64.S.trace;
+  else if (ctx->opts.precision == PDLP_FP32 && ctx->p32.ready) tr = ctx->p32.S.trace;
+  else if (ctx->pc32.ready) tr = ctx->pc32.S.trace;
+  else if (ctx->p64.ready) tr = ctx->p64.S.trace;
+  if (!tr) return fail(ctx, PDLP_ERR_STATE, "no solve has run on this context");
+  Scalars hs;
+  CK(cudaMemcpy(&hs, ctx->scal.ptr(), sizeof(Scalars), cudaMemcpyDeviceToHost), "trace");
+  const int total = hs.trace_n;
+  const int avail = total < kTraceCap ? total : kTraceCap;
+  const int take = max_records < avail ? max_records : avail;
+  if (count) *count = total;
+  // oldest record first
+  for (int r = 0; r < take; ++r) {
+    const int idx = (total - avail + r) % kTraceCap;
+    CK(cudaMemcpy(out + (size_t)r * kTraceLen, tr + (size_t)idx * kTraceLen, sizeof(double) * kTraceLen,
+                  cudaMemcpyDeviceToHost), "trace");
+  }
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms) {
+  if (!ctx || !ms || reps < 1) return fail(ctx, PDLP_ERR_INVALID_ARG, "bad argument");
+  cudaError_t e;
+  const int prec = ctx->opts.precision;
+  if (prec == PDLP_FP64 && ctx->p64.ready)
+    e = time_step_kernels<double>(ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->p64.S, reps, ctx->st, ms, ms + 1);
+  else if (prec == PDLP_FP32 && ctx->p32.ready)
+    e = time_step_kernels<float>(ctx->p32.K, ctx->p32.KT, ctx->p32.P, ctx->p32.S, reps, ctx->st, ms, ms + 1);
+  else if (prec == PDLP_FP32_REFINE && ctx->pc32.ready)
+    e = time_step_kernels<float>(ctx->pc32.K, ctx->pc32.KT, ctx->pc32.P, ctx->pc32.S, reps, ctx->st, ms, ms + 1);
+  else
+    return fail(ctx, PDLP_ERR_STATE, "no solver state for the context's precision");
+  if (e) return cuda_fail(ctx, e, "time_step_kernels");
+  return PDLP_OK;
+}
+
+extern "C" const char *pdlp_last_error(const pdlp_ctx *ctx) {
+  if (ctx && !ctx->err.empty()) return ctx->err.c_str();
+  return g_last_error.c_str();
+}
+
+extern "C" void pdlp_destroy(pdlp_ctx *ctx) { delete ctx; }
+
+// Unrolled map and its adjoint (unroll.cu)
+extern "C" int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const double *x0, const double *y0,
+                           double *x_out, double *y_out, double *eta_out) {
+  if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  if (T < 1 || ckpt_every < 1) return fail(ctx, PDLP_ERR_INVALID_ARG, "T and ckpt_every must be >= 1");
+  int rc = setup_fp64(ctx);
+  if (rc) return rc;
+  rc = stage_start(ctx, x0, y0);
+  if (rc) return rc;
+  Problem<double> P = ctx->p64.P;
+  cudaError_t e = unroll_forward(ctx->unr, ctx->p64.K, ctx->p64.KT, P, ctx->eta0, ctx->opts.eps_zero, T, ckpt_every,
+                                 reinterpret_cast<const double *>(ctx->xin.ptr()),
+                                 reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st);
+  if (e) return cuda_fail(ctx, e, "unroll");
+  if (x_out) CK(cudaMemcpyAsync(x_out, ctx->unr.xo, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "x_out");
+  if (y_out) CK(cudaMemcpyAsync(y_out, ctx->unr.yo, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "y_out");
+  if (eta_out) CK(cudaMemcpyAsync(eta_out, ctx->unr.eta, sizeof(double) * T, cudaMemcpyDefault, ctx->st), "eta");
+  CK(cudaStreamSynchronize(ctx->st), "unroll");
+  return PDLP_OK;
+}
+
+extern "C" int pdlp_grad(pdlp_ctx *ctx, const double *dL_dx, const double *dL_dy, double *dc, double *dq,
+                         double *dK_val) {
+  if (!ctx || !dL_dx) return fail(ctx, PDLP_ERR_INVALID_ARG, "NULL argument");
+  if (!ctx->unr.ready) return fail(ctx, PDLP_ERR_STATE, "pdlp_grad needs a preceding unrolled solve");
+  cudaError_t e = unroll_backward(ctx->unr, ctx->p64.K, ctx->p64.KT, ctx->p64.P,
+                                  reinterpret_cast<const int32_t *>(ctx->perm.ptr()), dL_dx, dL_dy, ctx->st);
+  if (e) return cuda_fail(ctx, e, "grad");
+  if (dc) CK(cudaMemcpyAsync(dc, ctx->unr.dc, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "dc");
+  if (dq) CK(cudaMemcpyAsync(dq, ctx->unr.dq, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "dq");
+  if (dK_val) CK(cudaMemcpyAsync(dK_val, ctx->unr.dK, sizeof(double) * ctx->nnz, cudaMemcpyDefault, ctx->st), "dK");
+  CK(cudaStreamSynchronize(ctx->st), "grad");
+  return PDLP_OK;
+}

@@ -1,0 +1,350 @@
+// Internal definitions shared by the library's translation units.
+//
+// Layout in device memory (one context = one LP):
+//   K   CSR: row_ptr int32[m+1], col_idx int32[nnz], values T[nnz]
+//   K^T CSR: built on the device by a stable radix sort of K's entries by column
+//   vectors: contiguous arrays of T (float64 or float32) per quantity
+//   scalars: one `Scalars` block (float64 / int64) read by every kernel
+// Sparse products use a CSR-stream scheme: rows are grouped into row blocks of
+// at most kNnzPerBlock nonzeros and kMaxRowsPerBlock rows; one CTA stages its
+// block's values and gathered vector entries in shared memory with coalesced
+// loads, then reduces each row with a power-of-two group of lanes.  Rows longer
+// than kNnzPerBlock are split into segments whose partial sums are combined, in
+// segment order, by the last segment CTA to finish.  All reductions are
+// deterministic: fixed thread-to-data assignment and fixed combination order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdlp.h"
+
+namespace pdlp {
+
+constexpr int kThreads = 256;          // CTA size of the sparse-product kernels
+constexpr int kNnzPerBlock = 2048;     // nonzeros staged per CTA
+constexpr int kMaxRowsPerBlock = 256;  // rows per CTA (one lane group per row)
+constexpr int kGapBuckets = 2048;      // radix digit of the normalized-gap selection
+constexpr int kGapThreads = 512;
+constexpr int kGapSlots = 3;           // current, average, restart point
+
+// One CTA's share of a CSR matrix.  row_end < 0 marks a segment of a long row:
+// the long row index is -(row_end + 1).
+struct RowBlock {
+  int32_t row_begin, row_end, nnz_begin, nnz_end;
+};
+
+// A row longer than kNnzPerBlock, processed by `nseg` consecutive CTAs.
+struct LongRow {
+  int32_t row, nseg, part_off, pad;
+};
+
+// CSR matrix plus its row-block schedule.
+template <typename T>
+struct Mat {
+  int32_t rows, cols;
+  const int32_t *rp, *ci;
+  const T *val;
+  const RowBlock *blocks;
+  int32_t nblocks;
+  const LongRow *longrows;
+  double *seg_part;       // one partial per long-row segment (per gathered vector)
+  unsigned int *seg_cnt;  // arrival counter per long row
+};
+
+// Solver outcome codes (same values as the public PDLP_* status codes).
+enum : int { kRunning = 0, kOptimal = 1, kIterLimit = 2, kKktLimit = 3, kTimeLimit = 4, kNumErr = 5 };
+
+// Every scalar of Algorithm 1 / 2 / 3 and of the evaluation, in one block.
+struct Scalars {
+  // --- Algorithm 2 step control
+  double eta;       // step size of the next attempt
+  double omega;     // primal weight omega^n
+  double sum_eta;   // sum of accepted step sizes of this outer loop
+  double dx2, dy2, inter, eta_bar;  // reductions of the last attempt
+  // --- restart state (Section 3.2)
+  double mu0;       // mu_n(z^{n,0}, z^{n-1,0}); +inf in the first outer loop
+  double muc_prev;  // candidate mu of the previous evaluation in this outer loop
+  double inv_avg;   // 1 / sum_eta at the evaluation
+  double mu[kGapSlots];
+  double gval[kGapSlots];
+  // --- evaluation (Eq. (15) on the original problem), [candidate][term]
+  double kkt[2][8];
+  double cand_dx2[2], cand_dy2[2];  // squared distances to z^{n,0} (scaled space)
+  double qnorm, cnorm;              // ||q||_2, ||c||_2 of the original problem
+  double rel_tol;
+  // --- gap radix selection per slot
+  double g_r2[kGapSlots], g_omega[kGapSlots];
+  double g_W[kGapSlots], g_V[kGapSlots], g_A[kGapSlots];
+  unsigned int g_prefix[kGapSlots];
+  int g_active[kGapSlots];
+  // --- options
+  double beta_suff, beta_nec, beta_art, pw_theta, eps_zero;
+  // --- counters and flags
+  long long k, t, attempts, restarts;
+  long long iter_limit, attempt_limit;
+  unsigned long long t0_ns, time_limit_ns, t_end_ns;
+  int cur;        // which of the two buffers holds the current iterate
+  int chunk_acc;  // accepted iterations since the last evaluation
+  int eval_every;
+  int status;
+  int ret_which;  // 0 current, 1 average
+  int phase;      // 0 before the first step, 1 in the loop
+  int do_gap;     // this evaluation runs the restart test
+  int restart;    // a restart was decided at this evaluation
+  int cand;       // restart candidate: 0 current, 1 average
+  int adaptive_restart, pw_update;
+  int avg_valid;
+  int err;        // bounded-wait failures (device-side timeouts)
+  int trace_n;    // restart evaluations recorded so far (ring of kTraceCap)
+};
+
+// One record per restart evaluation: k, t, mu_cur, mu_avg, mu0, candidate,
+// restart (0/1), omega after the update, then the radii r_cur, r_avg, and
+// the relative Eq. (15) terms (gap, primal, dual) of the current and the
+// average iterate.
+constexpr int kTraceCap = 256;
+constexpr int kTraceLen = 16;
+
+// An LP in the form of Eq. (1) on the device: preconditioned data (type T,
+// read in the iteration) and original-space data (float64, read by the
+// termination test).
+template <typename T>
+struct Problem {
+  int32_t m, n;
+  const T *cs, *qs, *ls, *us, *ylos;
+  const double *c, *q, *l, *u, *ylo;  // ylo: 0 / -inf for the paper's Y, general for corrections
+  const double *D1, *D2;
+};
+
+// Iteration state (ping-pong buffers selected by Scalars::cur).
+template <typename T>
+struct State {
+  T *x[2], *y[2], *Kx[2], *xs[2], *ys[2];
+  T *x0, *y0;                  // restart point z^{n,0}
+  T *KTy_cur, *KTys, *Kxbar;   // products at the evaluation
+  double *part_p, *part_d;     // per-CTA partials of the primal / dual kernels
+  double *part_ec, *part_er;   // per-CTA partials of the evaluation kernels
+  unsigned int *tickets;       // arrival counters (one per kernel kind)
+  Scalars *s;
+  unsigned int *gkeys;         // gap keys [kGapSlots][n + m]
+  double *ghist;               // gap histogram [kGapSlots][kGapBuckets][3]
+  double *xo, *yo;             // returned point (original space, float64)
+  double *trace;               // [kTraceCap][kTraceLen]
+};
+
+enum TicketId { kTicketDual = 0, kTicketEvalRows = 1, kTicketGap = 2, kTicketMisc = 3, kNumTickets = 8 };
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Deterministic sum of NV per-thread values over the CTA; the result is
+// valid in thread 0.  `red` must hold NV * (blockDim.x / 32) doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[a * nw + warp] = v[a];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double t = lane < nw ? red[a * nw + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[a] = t;
+    }
+  }
+}
+
+// Fixed-order sum of `count` partials (stride `stride`, offset `off`) by one
+// CTA; result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double *part, int count, int stride,
+                                             double (&out)[NV], double *red) {
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = 0.0;
+  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) out[a] += __ldcg(part + (size_t)b * stride + a);
+  }
+  block_sum<NV>(out, red);
+}
+
+// True in every thread of the CTA that arrives last at `ticket`; that CTA
+// also resets the ticket.  Writes made before the call are visible to it.
+__device__ __forceinline__ bool last_block(unsigned int *ticket) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(ticket, 1u);
+    s_last = (prev == gridDim.x - 1);
+    if (s_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// ------------------------------------------------------- CSR-stream engine
+//
+// spmv_block computes, for the CTA's row block of `A`, the row sums
+// sum_k A_ik * v_a[col_k] for NV gathered vectors v_a, and calls
+// epi(row, sums) once per row: one thread per row with consecutive threads on
+// consecutive rows (coalesced epilogue), or thread 0 for a completed long row.
+//   phase 1: every thread loads kItems column indices and values (coalesced,
+//            all independent), then the kItems * NV gathered entries, and
+//            stages them in shared memory;
+//   phase 2: a power-of-two group of L lanes reduces each row from shared
+//            memory (L from the block's mean row length) into row sums;
+//   phase 3: the epilogue, one thread per row.
+// Shared memory: spmv_smem_bytes<T>(NV) at `sm`.
+constexpr int kItems = kNnzPerBlock / kThreads;
+
+template <typename T>
+__host__ __device__ constexpr size_t spmv_smem_bytes(int nv) {
+  return (size_t)kNnzPerBlock * sizeof(T) * (1 + nv) + (size_t)kMaxRowsPerBlock * sizeof(T) * nv;
+}
+
+template <typename T, int NV, typename Epi>
+__device__ __forceinline__ void spmv_block(const Mat<T> &A, const T *const (&vec)[NV], char *sm,
+                                           Epi &&epi) {
+  const RowBlock rb = A.blocks[blockIdx.x];
+  T *sval = reinterpret_cast<T *>(sm);
+  T *sx = sval + kNnzPerBlock;
+  T *srow = sx + NV * kNnzPerBlock;
+  const int nb = rb.nnz_begin, cnt = rb.nnz_end - rb.nnz_begin;
+  {
+    int cj[kItems];
+    T v[kItems];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const int e = threadIdx.x + it * kThreads;
+      cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
+      v[it] = e < cnt ? __ldg(A.val + nb + e) : T(0);
+    }
+    T xv[NV][kItems];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+#pragma unroll
+      for (int it = 0; it < kItems; ++it) {
+        const int e = threadIdx.x + it * kThreads;
+        xv[a][it] = e < cnt ? vec[a][cj[it]] : T(0);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const int e = threadIdx.x + it * kThreads;
+      if (e < cnt) {
+        sval[e] = v[it];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) sx[a * kNnzPerBlock + e] = xv[a][it];
+      }
+    }
+  }
+  __syncthreads();
+  if (rb.row_end >= 0) {
+    const int nrows = rb.row_end - rb.row_begin;
+    const int avg = nrows > 0 ? cnt / nrows : 1;
+    int L = 1;
+    while (L < 32 && 2 * L <= avg) L *= 2;
+    const int groups = blockDim.x / L;
+    const int g = threadIdx.x / L, lane = threadIdx.x % L;
+    for (int r0 = 0; r0 < nrows; r0 += groups) {
+      const int r = r0 + g;
+      T acc[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] = T(0);
+      if (r < nrows) {
+        const int row = rb.row_begin + r;
+        const int s = __ldg(A.rp + row) - nb, e = __ldg(A.rp + row + 1) - nb;
+        for (int k = s + lane; k < e; k += L) {
+          const T vv = sval[k];
+#pragma unroll
+          for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kNnzPerBlock + k], acc[a]);
+        }
+      }
+      for (int o = L / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o, L);
+      }
+      if (r < nrows && lane == 0) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) srow[a * kMaxRowsPerBlock + r] = acc[a];
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+      T s[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s[a] = srow[a * kMaxRowsPerBlock + r];
+      epi(rb.row_begin + r, s);
+    }
+  } else {
+    // segment of a long row: CTA-wide partial; the last segment CTA to arrive
+    // combines all partials of the row (fixed thread-to-segment assignment)
+    const int lr = -(rb.row_end + 1);
+    const LongRow L = A.longrows[lr];
+    double acc[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const T vv = sval[e];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] = fma((double)vv, (double)sx[a * kNnzPerBlock + e], acc[a]);
+    }
+    __shared__ double red[NV * (kThreads / 32)];
+    block_sum<NV>(acc, red);
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+      const int seg = (nb - __ldg(A.rp + L.row)) / kNnzPerBlock;
+#pragma unroll
+      for (int a = 0; a < NV; ++a) A.seg_part[(size_t)(L.part_off + seg) * NV + a] = acc[a];
+      __threadfence();
+      const unsigned int prev = atomicAdd(A.seg_cnt + lr, 1u);
+      s_last = (prev == (unsigned)(L.nseg - 1));
+      if (s_last) A.seg_cnt[lr] = 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double tot[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) tot[a] = 0.0;
+      for (int sg = threadIdx.x; sg < L.nseg; sg += blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) tot[a] += __ldcg(A.seg_part + (size_t)(L.part_off + sg) * NV + a);
+      }
+      __syncthreads();
+      block_sum<NV>(tot, red);
+      if (threadIdx.x == 0) {
+        T t2[NV];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) t2[a] = (T)tot[a];
+        epi(L.row, t2);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pdlp

@@ -1,0 +1,490 @@
+// Create-time kernels: input validation, the stable CSR transpose that builds
+// K^T, the diagonal preconditioning of Section 3.5 (Ruiz, then Pock-Chambolle
+// with alpha = 1), the transform of (c, q, l, u) and the row-block schedule.
+//
+// Bit-exactness: every floating-point operation here is a single correctly
+// rounded IEEE operation (max, abs, sqrt, division, multiplication, addition
+// in a fixed sequential order), written with the _rn intrinsics so that the
+// compiler cannot contract or reorder them.  The results therefore equal those
+// of any sequential IEEE implementation of the same formulas.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "prep.cuh"
+
+namespace pdlp {
+
+// ------------------------------------------------------------- validation
+
+// Error bits written by k_validate.
+enum : unsigned { kBadRowPtr = 1u, kBadCol = 2u, kUnsorted = 4u, kBadVal = 8u, kBadBounds = 16u,
+                  kBadCost = 32u, kBadRhs = 64u };
+
+__global__ void k_validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                           const double *val, const double *c, const double *q, const double *l,
+                           const double *u, unsigned *err) {
+  unsigned bad = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid == 0 && (rp[0] != 0 || (int64_t)rp[m] != nnz)) bad |= kBadRowPtr;
+  for (int64_t i = tid; i < m; i += stride) {
+    const int32_t s = rp[i], e = rp[i + 1];
+    if (e < s || s < 0 || (int64_t)e > nnz) { bad |= kBadRowPtr; continue; }
+    if (!isfinite(q[i])) bad |= kBadRhs;
+  }
+  for (int64_t k = tid; k < nnz; k += stride) {
+    const int32_t j = ci[k];
+    if (j < 0 || j >= n) bad |= kBadCol;
+    if (!isfinite(val[k])) bad |= kBadVal;
+  }
+  for (int64_t j = tid; j < n; j += stride) {
+    if (!isfinite(c[j])) bad |= kBadCost;
+    if (!(l[j] <= u[j]) || l[j] == INFINITY || u[j] == -INFINITY || isnan(l[j]) || isnan(u[j]))
+      bad |= kBadBounds;
+  }
+  if (bad) atomicOr(err, bad);
+}
+
+// Sortedness needs a valid row_ptr; run after k_validate reported none of kBadRowPtr.
+__global__ void k_validate_sorted(int32_t m, const int32_t *rp, const int32_t *ci, unsigned *err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    for (int32_t k = rp[i] + 1; k < rp[i + 1]; ++k)
+      if (ci[k] <= ci[k - 1]) { atomicOr(err, (unsigned)kUnsorted); break; }
+  }
+}
+
+const char *validate_message(unsigned bits) {
+  if (bits & kBadRowPtr) return "row_ptr must start at 0, be non-decreasing and end at nnz";
+  if (bits & kBadCol) return "col_idx out of range [0, n)";
+  if (bits & kUnsorted) return "col_idx must be strictly increasing within each row";
+  if (bits & kBadVal) return "K has a non-finite value";
+  if (bits & kBadBounds) return "bounds must satisfy l <= u, l != +inf, u != -inf";
+  if (bits & kBadCost) return "c has a non-finite entry";
+  if (bits & kBadRhs) return "q has a non-finite entry";
+  return "invalid input";
+}
+
+// ------------------------------------------------------------------ scans
+
+// Exclusive prefix sum of int32 counts (n entries) into out (n entries) and
+// total in *total; three phases, single-pass-per-phase, deterministic.
+constexpr int kScanThreads = 1024, kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_excl_scan_int(int v, int *sh, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += t;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    sh[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int before = warp > 0 ? sh[warp - 1] : 0;
+  *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void k_scan_tiles(const int *in, int64_t n, int *tile_sum) {
+  __shared__ int sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int s = 0;
+  for (int a = 0; a < kScanItems; ++a) {
+    const int64_t i = base + (int64_t)threadIdx.x * kScanItems + a;
+    if (i < n) s += in[i];
+  }
+  int tot;
+  block_excl_scan_int(s, sh, &tot);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int *tile_sum, int ntiles, int *total) {
+  __shared__ int sh[32];
+  int carry = 0;
+  for (int b0 = 0; b0 < ntiles; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    const int v = b < ntiles ? tile_sum[b] : 0;
+    int tot;
+    const int ex = block_excl_scan_int(v, sh, &tot);
+    if (b < ntiles) tile_sum[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_apply(const int *in, int64_t n, const int *tile_off, int *out) {
+  __shared__ int sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int v[kScanItems], s = 0;
+  for (int a = 0; a < kScanItems; ++a) {
+    const int64_t i = base + (int64_t)threadIdx.x * kScanItems + a;
+    v[a] = i < n ? in[i] : 0;
+    s += v[a];
+  }
+  int tot;
+  int ex = block_excl_scan_int(s, sh, &tot) + tile_off[blockIdx.x];
+  for (int a = 0; a < kScanItems; ++a) {
+    const int64_t i = base + (int64_t)threadIdx.x * kScanItems + a;
+    if (i < n) out[i] = ex;
+    ex += v[a];
+  }
+}
+
+cudaError_t exclusive_scan(const int *in, int64_t n, int *out, int *total, int *tmp, cudaStream_t st) {
+  const int ntiles = (int)((n + kScanTile - 1) / kScanTile);
+  if (ntiles == 0) return cudaMemsetAsync(total, 0, sizeof(int), st);
+  k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(in, n, tmp);
+  k_scan_sums<<<1, kScanThreads, 0, st>>>(tmp, ntiles, total);
+  k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(in, n, tmp, out);
+  return cudaGetLastError();
+}
+
+int64_t scan_tmp_ints(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+// -------------------------------------------------------------- transpose
+//
+// K^T is K's entries stably sorted by column (so rows stay increasing within
+// each column).  LSD radix sort on the column index, 8 bits per pass; each
+// pass is a stable counting sort: per-tile digit histograms, one exclusive
+// scan over the digit-major [digit][tile] table, and a scatter in which an
+// entry's rank inside its tile comes from warp match masks.
+
+constexpr int kSortThreads = 256, kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // entries per tile
+constexpr int kDigits = 256;
+
+__global__ void k_sort_hist(const int32_t *keys, int64_t nnz, int shift, int ntiles, int *hist) {
+  __shared__ int h[kDigits];
+  for (int d = threadIdx.x; d < kDigits; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    if (i < nnz) atomicAdd(&h[(keys[i] >> shift) & 0xff], 1);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kDigits; d += blockDim.x) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+__global__ void k_sort_scatter(const int32_t *keys, const int32_t *vals, int64_t nnz, int shift,
+                               int ntiles, const int *offs, int32_t *keys_out, int32_t *vals_out) {
+  __shared__ int base[kDigits];
+  __shared__ int wcnt[kSortThreads / 32][kDigits];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kDigits; d += blockDim.x) base[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+  const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    for (int e = threadIdx.x; e < (kSortThreads / 32) * kDigits; e += blockDim.x) (&wcnt[0][0])[e] = 0;
+    __syncthreads();
+    const int64_t i = tbase + (int64_t)r * kSortThreads + threadIdx.x;
+    const bool ok = i < nnz;
+    const int32_t key = ok ? keys[i] : 0;
+    const int d = ok ? ((key >> shift) & 0xff) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (ok) {
+      int pos = base[d] + rank;
+      for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+      keys_out[pos] = key;
+      vals_out[pos] = vals[i];
+    }
+    __syncthreads();
+    for (int dd = threadIdx.x; dd < kDigits; dd += blockDim.x) {
+      int s = 0;
+      for (int w = 0; w < kSortThreads / 32; ++w) s += wcnt[w][dd];
+      base[dd] += s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_iota(int32_t *v, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] = (int32_t)i;
+}
+
+__global__ void k_col_count(const int32_t *ci, int64_t nnz, int *cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride)
+    atomicAdd(cnt + ci[k], 1);
+}
+
+// row of each CSR position by binary search in row_ptr; fills K^T col_idx.
+__global__ void k_rows_of(const int32_t *rp, int32_t m, const int32_t *perm, int64_t nnz, int32_t *tci) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += stride) {
+    const int32_t k = perm[t];
+    int32_t lo = 0, hi = m;  // find the last row with rp[row] <= k
+    while (hi - lo > 1) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if (rp[mid] <= k) lo = mid; else hi = mid;
+    }
+    tci[t] = lo;
+  }
+}
+
+template <typename T>
+__global__ void k_gather(const T *src, const int32_t *perm, int64_t nnz, T *dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += stride) dst[t] = src[perm[t]];
+}
+
+static int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  return (int)std::max<int64_t>(g, 1);
+}
+
+cudaError_t build_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                            int32_t *trp, int32_t *tci, int32_t *perm, DevBuf &tmp, cudaStream_t st) {
+  cudaError_t e;
+  // column counts -> K^T row_ptr
+  int *cnt = reinterpret_cast<int *>(tmp.get(sizeof(int) * ((size_t)n + 1) +
+                                             sizeof(int) * (size_t)scan_tmp_ints(n + 1)));
+  if (!cnt) return cudaErrorMemoryAllocation;
+  int *scan_tmp = cnt + n + 1;
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)n + 1), st))) return e;
+  if (nnz > 0) k_col_count<<<grid_for(nnz, 256), 256, 0, st>>>(ci, nnz, cnt);
+  if ((e = exclusive_scan(cnt, n + 1, trp, trp + n, scan_tmp, st))) return e;
+  if (nnz == 0) return cudaGetLastError();
+  // radix sort (key = column, value = CSR position)
+  const int ntiles = (int)((nnz + kSortTile - 1) / kSortTile);
+  const int64_t hist_n = (int64_t)kDigits * ntiles;
+  DevBuf sortbuf;
+  size_t bytes = sizeof(int32_t) * (size_t)nnz * 4 + sizeof(int) * (size_t)hist_n * 2 +
+                 sizeof(int) * (size_t)scan_tmp_ints(hist_n) + 64;
+  char *p = reinterpret_cast<char *>(sortbuf.get(bytes));
+  if (!p) return cudaErrorMemoryAllocation;
+  int32_t *ka = reinterpret_cast<int32_t *>(p), *kb = ka + nnz, *va = kb + nnz, *vb = va + nnz;
+  int *hist = reinterpret_cast<int *>(vb + nnz), *offs = hist + hist_n, *stmp = offs + hist_n;
+  if ((e = cudaMemcpyAsync(ka, ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, st))) return e;
+  k_iota<<<grid_for(nnz, 256), 256, 0, st>>>(va, nnz);
+  int bits = 0;
+  while ((1ll << bits) < (int64_t)n) ++bits;
+  const int passes = std::max(1, (bits + 7) / 8);
+  for (int ps = 0; ps < passes; ++ps) {
+    const int shift = 8 * ps;
+    k_sort_hist<<<ntiles, kSortThreads, 0, st>>>(ka, nnz, shift, ntiles, hist);
+    if ((e = exclusive_scan(hist, hist_n, offs, stmp + scan_tmp_ints(hist_n) - 1, stmp, st))) return e;
+    k_sort_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, nnz, shift, ntiles, offs, kb, vb);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if ((e = cudaMemcpyAsync(perm, va, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToDevice, st))) return e;
+  k_rows_of<<<grid_for(nnz, 256), 256, 0, st>>>(rp, m, perm, nnz, tci);
+  if ((e = cudaGetLastError())) return e;
+  return cudaStreamSynchronize(st);  // sortbuf is freed on return
+}
+
+// ------------------------------------------------------ Section 3.5 scaling
+
+// Ruiz: r_i = max_j |K~_ij| over the row (any order gives the same maximum).
+__global__ void k_row_absmax(int32_t rows, const int32_t *rp, const double *val, double *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < rows; i += nw) {
+    double mx = 0.0;
+    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) mx = fmax(mx, fabs(val[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) out[i] = mx;
+  }
+}
+
+// Pock-Chambolle alpha = 1: r_i = sum_j |K~_ij| accumulated sequentially in CSR
+// order (the order of a plain loop over the row).
+__global__ void k_row_abssum_seq(int32_t rows, const int32_t *rp, const double *val, double *out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
+    double s = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __dadd_rn(s, fabs(val[k]));
+    out[i] = s;
+  }
+}
+
+// norms -> divisors: sqrt(norm), or 1 for an empty (zero) row / column; D /= divisor.
+__global__ void k_norm_to_div(int32_t len, double *nrm, double *D) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+    const double v = nrm[i];
+    const double d = v > 0.0 ? __dsqrt_rn(v) : 1.0;
+    nrm[i] = d;
+    D[i] = __ddiv_rn(D[i], d);
+  }
+}
+
+// K~_ij <- (K~_ij / a_i) / b_j, one warp per row.
+__global__ void k_scale_rows(int32_t rows, const int32_t *rp, const int32_t *ci, double *val,
+                             const double *a, const double *b) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < rows; i += nw) {
+    const double ai = a[i];
+    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) val[k] = __ddiv_rn(__ddiv_rn(val[k], ai), b[ci[k]]);
+  }
+}
+
+__global__ void k_fill(double *v, int64_t n, double x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] = x;
+}
+
+cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                         double *val, const int32_t *trp, double *tval, const int32_t *perm,
+                         int ruiz_iters, int pock_chambolle, double *D1, double *D2, double *rbuf,
+                         double *cbuf, cudaStream_t st) {
+  const int gm = grid_for(m, 256), gn = grid_for(n, 256);
+  const int gmw = grid_for((int64_t)m * 32, 256), gnw = grid_for((int64_t)n * 32, 256);
+  k_fill<<<gm, 256, 0, st>>>(D1, m, 1.0);
+  k_fill<<<gn, 256, 0, st>>>(D2, n, 1.0);
+  auto sync_t = [&]() { if (nnz > 0) k_gather<double><<<grid_for(nnz, 256), 256, 0, st>>>(val, perm, nnz, tval); };
+  sync_t();
+  for (int it = 0; it < ruiz_iters; ++it) {
+    k_row_absmax<<<gmw, 256, 0, st>>>(m, rp, val, rbuf);
+    k_row_absmax<<<gnw, 256, 0, st>>>(n, trp, tval, cbuf);
+    k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
+    k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
+    k_scale_rows<<<gmw, 256, 0, st>>>(m, rp, ci, val, rbuf, cbuf);
+    sync_t();
+  }
+  if (pock_chambolle) {
+    k_row_abssum_seq<<<gm, 256, 0, st>>>(m, rp, val, rbuf);
+    k_row_abssum_seq<<<gn, 256, 0, st>>>(n, trp, tval, cbuf);
+    k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
+    k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
+    k_scale_rows<<<gmw, 256, 0, st>>>(m, rp, ci, val, rbuf, cbuf);
+    sync_t();
+  }
+  return cudaGetLastError();
+}
+
+// c~ = D2 c, l~ = l / D2, u~ = u / D2, q~ = D1 q, ylo~ = ylo / D1
+__global__ void k_transform_cols(int32_t n, const double *D2, const double *c, const double *l,
+                                 const double *u, double *cs, double *ls, double *us) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    cs[j] = __dmul_rn(D2[j], c[j]);
+    ls[j] = __ddiv_rn(l[j], D2[j]);
+    us[j] = __ddiv_rn(u[j], D2[j]);
+  }
+}
+__global__ void k_transform_rows(int32_t m, const double *D1, const double *q, const double *ylo,
+                                 double *qs, double *ylos) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    qs[i] = __dmul_rn(D1[i], q[i]);
+    ylos[i] = __ddiv_rn(ylo[i], D1[i]);
+  }
+}
+
+cudaError_t transform(int32_t m, int32_t n, const double *D1, const double *D2, const double *c,
+                      const double *q, const double *l, const double *u, const double *ylo,
+                      double *cs, double *qs, double *ls, double *us, double *ylos, cudaStream_t st) {
+  k_transform_cols<<<grid_for(n, 256), 256, 0, st>>>(n, D2, c, l, u, cs, ls, us);
+  k_transform_rows<<<grid_for(m, 256), 256, 0, st>>>(m, D1, q, ylo, qs, ylos);
+  return cudaGetLastError();
+}
+
+// y lower bounds of the paper's Y: 0 on inequality rows, -inf on equality rows
+__global__ void k_ylo_from_mask(int32_t m, const uint8_t *ineq, double *ylo) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+    ylo[i] = ineq[i] ? 0.0 : -INFINITY;
+}
+
+cudaError_t ylo_from_mask(int32_t m, const uint8_t *ineq, double *ylo, cudaStream_t st) {
+  k_ylo_from_mask<<<grid_for(m, 256), 256, 0, st>>>(m, ineq, ylo);
+  return cudaGetLastError();
+}
+
+__global__ void k_to_float(const double *src, int64_t n, float *dst) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
+}
+
+cudaError_t to_float(const double *src, int64_t n, float *dst, cudaStream_t st) {
+  if (n > 0) k_to_float<<<grid_for(n, 256), 256, 0, st>>>(src, n, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                     const double *val, const double *c, const double *q, const double *l,
+                     const double *u, unsigned *derr, unsigned *herr, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(derr, 0, sizeof(unsigned), st))) return e;
+  const int64_t big = std::max<int64_t>(std::max<int64_t>(m, n), nnz);
+  k_validate<<<grid_for(big, 256), 256, 0, st>>>(m, n, nnz, rp, ci, val, c, q, l, u, derr);
+  if ((e = cudaMemcpyAsync(herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  if (*herr & kBadRowPtr) return cudaSuccess;
+  k_validate_sorted<<<grid_for(m, 256), 256, 0, st>>>(m, rp, ci, derr);
+  if ((e = cudaMemcpyAsync(herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
+  return cudaStreamSynchronize(st);
+}
+
+// ------------------------------------------------------ row-block schedule
+
+void build_schedule(int32_t rows, const int32_t *rp_host, std::vector<RowBlock> &blocks,
+                    std::vector<LongRow> &longrows, int32_t &nseg_total) {
+  blocks.clear();
+  longrows.clear();
+  nseg_total = 0;
+  int32_t r = 0;
+  while (r < rows) {
+    const int32_t len = rp_host[r + 1] - rp_host[r];
+    if (len > kNnzPerBlock) {
+      LongRow L;
+      L.row = r;
+      L.nseg = (len + kNnzPerBlock - 1) / kNnzPerBlock;
+      L.part_off = nseg_total;
+      L.pad = 0;
+      const int32_t lr = (int32_t)longrows.size();
+      longrows.push_back(L);
+      for (int32_t s = 0; s < L.nseg; ++s) {
+        RowBlock b;
+        b.row_begin = r;
+        b.row_end = -(lr + 1);
+        b.nnz_begin = rp_host[r] + s * kNnzPerBlock;
+        b.nnz_end = std::min(rp_host[r + 1], b.nnz_begin + kNnzPerBlock);
+        blocks.push_back(b);
+      }
+      nseg_total += L.nseg;
+      ++r;
+      continue;
+    }
+    RowBlock b;
+    b.row_begin = r;
+    b.nnz_begin = rp_host[r];
+    int32_t e = r;
+    while (e < rows && e - r < kMaxRowsPerBlock) {
+      const int32_t l2 = rp_host[e + 1] - rp_host[e];
+      if (l2 > kNnzPerBlock) break;
+      if (rp_host[e + 1] - rp_host[r] > kNnzPerBlock) break;
+      ++e;
+    }
+    b.row_end = e;
+    b.nnz_end = rp_host[e];
+    blocks.push_back(b);
+    r = e;
+  }
+}
+
+}  // namespace pdlp

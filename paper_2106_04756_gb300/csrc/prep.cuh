@@ -1,0 +1,59 @@
+// Create-time routines (prep.cu) and a small owning device buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace pdlp {
+
+// Owning device allocation (cudaMalloc / cudaFree); get() reallocates on growth.
+class DevBuf {
+ public:
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { reset(); }
+  void *get(size_t bytes) {
+    if (bytes <= cap_ && p_) return p_;
+    reset();
+    if (cudaMalloc(&p_, bytes ? bytes : 1) != cudaSuccess) { p_ = nullptr; cap_ = 0; return nullptr; }
+    cap_ = bytes;
+    return p_;
+  }
+  void reset() {
+    if (p_) cudaFree(p_);
+    p_ = nullptr;
+    cap_ = 0;
+  }
+  void *ptr() const { return p_; }
+
+ private:
+  void *p_ = nullptr;
+  size_t cap_ = 0;
+};
+
+const char *validate_message(unsigned bits);
+cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                     const double *val, const double *c, const double *q, const double *l,
+                     const double *u, unsigned *derr, unsigned *herr, cudaStream_t st);
+cudaError_t exclusive_scan(const int *in, int64_t n, int *out, int *total, int *tmp, cudaStream_t st);
+int64_t scan_tmp_ints(int64_t n);
+cudaError_t build_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                            int32_t *trp, int32_t *tci, int32_t *perm, DevBuf &tmp, cudaStream_t st);
+cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                         double *val, const int32_t *trp, double *tval, const int32_t *perm,
+                         int ruiz_iters, int pock_chambolle, double *D1, double *D2, double *rbuf,
+                         double *cbuf, cudaStream_t st);
+cudaError_t transform(int32_t m, int32_t n, const double *D1, const double *D2, const double *c,
+                      const double *q, const double *l, const double *u, const double *ylo,
+                      double *cs, double *qs, double *ls, double *us, double *ylos, cudaStream_t st);
+cudaError_t ylo_from_mask(int32_t m, const uint8_t *ineq, double *ylo, cudaStream_t st);
+cudaError_t to_float(const double *src, int64_t n, float *dst, cudaStream_t st);
+void build_schedule(int32_t rows, const int32_t *rp_host, std::vector<RowBlock> &blocks,
+                    std::vector<LongRow> &longrows, int32_t &nseg_total);
+
+}  // namespace pdlp

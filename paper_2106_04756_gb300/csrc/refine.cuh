@@ -1,0 +1,49 @@
+// Float32 inner solves inside a float64 iterative-refinement loop (refine.cu).
+#pragma once
+
+#include "common.cuh"
+#include "prep.cuh"
+
+namespace pdlp {
+
+// Device pointers of the refinement state (passed to kernels by value).
+struct RefView {
+  // current point (original space) and its scaled copy / products
+  double *xh, *yh, *xt, *yt, *Kx, *KTy;
+  double *xb, *yb;  // best point so far (restored if a round makes Eq. (15) worse)
+  // correction LP, original space (float64) and preconditioned (float32)
+  double *c, *q, *l, *u, *ylo;
+  float *cs, *qs, *ls, *us, *ylos;
+  double *partc;
+  unsigned *ticket;
+  double *rsc;  // [0..4] Eq. (15) terms at (xh, yh), [8] primal violation, [9] dual violation
+};
+
+struct RefineBuffers {
+  bool ready = false;
+  int32_t m = 0, n = 0, nbK = 0, nbKT = 0;
+  DevBuf vec;    // float64 vectors
+  DevBuf vec32;  // float32 correction data
+  DevBuf part, rs;
+  RefView v{};
+};
+
+struct RefineOutcome {
+  int status = 0, rounds = 0;
+  long long iters = 0, kkt_passes = 0, restarts = 0;
+  double kkt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const double *x = nullptr, *y = nullptr;  // device, original space
+};
+
+cudaError_t refine_alloc(RefineBuffers &R, int32_t m, int32_t n, int32_t nbK, int32_t nbKT);
+Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64);
+
+// Scales of the correction problem from the violations (see refine.cu).
+void refine_scales(double pv, double dv, double dmax, double *dP, double *dD);
+
+cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
+                         const Problem<float> &Pc, const State<float> &Sc, cudaGraphExec_t inner_graph,
+                         double tol, double inner_tol, int max_rounds, const double *x_stage, const double *y_stage,
+                         cudaStream_t st, RefineOutcome *out);
+
+}  // namespace pdlp

@@ -1,0 +1,930 @@
+// The iteration of Algorithm 1 on the device, templated on the arithmetic of
+// the sparse products and vectors (T = double or float; scalars are double).
+//
+// Per step attempt (Algorithm 2) two kernels run:
+//   k_primal  x' = proj_X(x - (eta/omega)(c - K^T y))   (K^T y over K^T rows)
+//   k_dual    y' = proj_Y(y + eta*omega (q - 2 K x' + K x))  (K x' over K rows)
+//             and, in its last CTA, the step-size test of Eq. (4): accept /
+//             reject, eta' and the loop condition of the CUDA graph.
+// Both also advance the step-weighted sums of Algorithm 1 (into the other
+// ping-pong buffer, so a rejected attempt leaves them untouched).
+// Every `eval_every` accepted iterations the evaluation kernels compute
+// K^T y, K^T y_avg, K x_avg, the termination test of Eq. (15) on the original
+// problem for the current and the average iterate, the normalized duality
+// gaps of Section 3.2 (radix selection of the trust-region breakpoint), the
+// restart decision (criteria (i)-(iii)) and the primal weight of Algorithm 3.
+#include <math.h>
+
+#include "common.cuh"
+#include "solver.cuh"
+
+namespace pdlp {
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ double proj_lambda(double rc, double l, double u) {
+  // Lambda_j from the finiteness of l_j and u_j (Section 2)
+  const bool lf = l > -INFINITY, uf = u < INFINITY;
+  if (!lf && !uf) return 0.0;
+  if (!lf) return rc < 0.0 ? rc : 0.0;
+  if (!uf) return rc > 0.0 ? rc : 0.0;
+  return rc;
+}
+
+__device__ __forceinline__ bool time_up(const Scalars *s) {
+  return s->time_limit_ns != 0ull && global_timer_ns() - s->t0_ns > s->time_limit_ns;
+}
+
+// Algorithm 2's test and step-size update, run by one thread after the
+// reductions of an attempt.  The denominator is the magnitude of the
+// interaction term (so eta_bar >= 1/||K||_2 always); a zero denominator gives
+// eta_bar = +inf.  k counts steps from 1.
+__device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
+                            cudaGraphConditionalHandle h, int has_cond) {
+  const double omega = s->omega, eta = s->eta;
+  s->dx2 = dx2;
+  s->dy2 = dy2;
+  s->inter = inter;
+  const double num = omega * dx2 + dy2 / omega;
+  const double den = 2.0 * fabs(inter);
+  const double eta_bar = den > 0.0 ? num / den : INFINITY;
+  const double kk = (double)(s->k + 1);
+  const double e1 = (1.0 - pow(kk + 1.0, -0.3)) * eta_bar;
+  const double e2 = (1.0 + pow(kk + 1.0, -0.6)) * eta;
+  s->eta_bar = eta_bar;
+  s->attempts += 1;
+  if (!isfinite(num) || isnan(eta_bar) || isnan(inter)) {
+    s->status = kNumErr;
+  } else {
+    if (eta <= eta_bar) {
+      s->cur ^= 1;
+      s->sum_eta += eta;
+      s->k += 1;
+      s->t += 1;
+      s->chunk_acc += 1;
+    }
+    s->eta = e1 < e2 ? e1 : e2;
+  }
+  bool go = s->status == kRunning && s->chunk_acc < s->eval_every && s->k < s->iter_limit &&
+            s->attempts < s->attempt_limit;
+  if (go && time_up(s)) go = false;
+  if (has_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// ------------------------------------------------------------ step kernels
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_primal(Mat<T> KT, Problem<T> P, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[kThreads / 32];
+  const Scalars *sc = S.s;
+  const int cur = sc->cur;
+  const double eta = sc->eta, omega = sc->omega;
+  const T tau = (T)(eta / omega), et = (T)eta;
+  const T *x = S.x[cur];
+  T *xn = S.x[cur ^ 1];
+  const T *xs = S.xs[cur];
+  T *xsn = S.xs[cur ^ 1];
+  double acc[1] = {0.0};
+  const T *const vec[1] = {S.y[cur]};
+  spmv_block<T, 1>(KT, vec, sm, [&](int j, const T(&g)[1]) {
+    const T xj = x[j];
+    const T xp = clampv<T>(xj - tau * (P.cs[j] - g[0]), P.ls[j], P.us[j]);
+    xn[j] = xp;
+    xsn[j] = xs[j] + et * xp;
+    const T d = xp - xj;
+    acc[0] += (double)(d * d);
+  });
+  block_sum<1>(acc, red);
+  if (threadIdx.x == 0) S.part_p[blockIdx.x] = acc[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Problem<T> P, State<T> S,
+                                                   cudaGraphConditionalHandle h, int has_cond) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[2 * (kThreads / 32)];
+  Scalars *sc = S.s;
+  const int cur = sc->cur;
+  const double eta = sc->eta, omega = sc->omega;
+  const T sig = (T)(eta * omega), et = (T)eta;
+  const T *y = S.y[cur], *Kx = S.Kx[cur], *ys = S.ys[cur];
+  T *yn = S.y[cur ^ 1], *Kxn = S.Kx[cur ^ 1], *ysn = S.ys[cur ^ 1];
+  double acc[2] = {0.0, 0.0};
+  const T *const vec[1] = {S.x[cur ^ 1]};
+  spmv_block<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
+    const T kxn = s[0], kx = Kx[i], yi = y[i], lo = P.ylos[i];
+    const T v = yi + sig * (P.qs[i] - T(2) * kxn + kx);
+    const T yp = v > lo ? v : lo;
+    yn[i] = yp;
+    Kxn[i] = kxn;
+    ysn[i] = ys[i] + et * yp;
+    const T dy = yp - yi, dk = kxn - kx;
+    acc[0] += (double)(dy * dy);
+    acc[1] += (double)dy * (double)dk;
+  });
+  block_sum<2>(acc, red);
+  if (threadIdx.x == 0) {
+    S.part_d[2 * blockIdx.x] = acc[0];
+    S.part_d[2 * blockIdx.x + 1] = acc[1];
+  }
+  if (last_block(S.tickets + kTicketDual)) {
+    double p[1], d[2];
+    sum_partials<1>(S.part_p, nblocks_p, 1, p, red);
+    __syncthreads();
+    sum_partials<2>(S.part_d, gridDim.x, 2, d, red);
+    if (threadIdx.x == 0) accept_step(sc, p[0], d[0], d[1], h, has_cond);
+  }
+}
+
+// ------------------------------------------------------ evaluation kernels
+
+// Columns: K^T y (current) and K^T ys (sum for the average) in one pass, and
+// the column terms of Eq. (15) for both candidates.
+// Partial layout per CTA (8): [cand][pobj, dres^2, dobj(lambda), |x - x0|^2].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[8 * (kThreads / 32)];
+  const Scalars *sc = S.s;
+  const int cur = sc->cur;
+  const bool avg = sc->sum_eta > 0.0;
+  const double inv = avg ? 1.0 / sc->sum_eta : 0.0;
+  const T *x = S.x[cur], *xs = S.xs[cur], *x0 = S.x0;
+  double acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a] = 0.0;
+  const T *const vec[2] = {S.y[cur], S.ys[cur]};
+  spmv_block<T, 2>(KT, vec, sm, [&](int j, const T(&g)[2]) {
+    S.KTy_cur[j] = g[0];
+    S.KTys[j] = g[1];
+    const double D2 = P.D2[j], cj = P.c[j], lj = P.l[j], uj = P.u[j], xr = (double)x0[j];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c == 1 && !avg) break;
+      const double xt = c == 0 ? (double)x[j] : (double)xs[j] * inv;
+      const double kt = c == 0 ? (double)g[0] : (double)g[1] * inv;
+      const double xo = D2 * xt, rc = cj - kt / D2;
+      const double lam = proj_lambda(rc, lj, uj);
+      acc[4 * c + 0] += cj * xo;
+      acc[4 * c + 1] += (rc - lam) * (rc - lam);
+      acc[4 * c + 2] += (lam > 0.0 ? lj * lam : 0.0) + (lam < 0.0 ? uj * lam : 0.0);
+      acc[4 * c + 3] += (xt - xr) * (xt - xr);
+    }
+  });
+  block_sum<8>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) S.part_ec[8 * blockIdx.x + a] = acc[a];
+  }
+}
+
+// Finalisation of one evaluation (thread 0 of the last CTA of k_eval_rows).
+__device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er)[8]) {
+  const bool avg = s->sum_eta > 0.0;
+  bool pass[2] = {false, false};
+  for (int c = 0; c < 2; ++c) {
+    if (c == 1 && !avg) break;
+    const double pobj = ec[4 * c + 0] + er[4 * c + 3];
+    const double dobj = ec[4 * c + 2] + er[4 * c + 1];
+    const double pres = sqrt(er[4 * c + 0]), dres = sqrt(ec[4 * c + 1]);
+    const double gap = fabs(dobj - pobj);
+    double *k = s->kkt[c];
+    k[0] = pobj;
+    k[1] = dobj;
+    k[2] = gap;
+    k[3] = pres;
+    k[4] = dres;
+    k[5] = gap / (1.0 + fabs(dobj) + fabs(pobj));
+    k[6] = pres / (1.0 + s->qnorm);
+    k[7] = dres / (1.0 + s->cnorm);
+    s->cand_dx2[c] = ec[4 * c + 3];
+    s->cand_dy2[c] = er[4 * c + 2];
+    pass[c] = k[5] <= s->rel_tol && k[6] <= s->rel_tol && k[7] <= s->rel_tol;
+  }
+  s->inv_avg = avg ? 1.0 / s->sum_eta : 0.0;
+  if (s->status == kRunning || s->status == kNumErr) {
+    if (pass[0]) { s->status = kOptimal; s->ret_which = 0; }
+    else if (pass[1]) { s->status = kOptimal; s->ret_which = 1; }
+  }
+  if (s->status == kRunning) {
+    if (s->k >= s->iter_limit) s->status = kIterLimit;
+    else if (s->attempts >= s->attempt_limit) s->status = kKktLimit;
+    else if (time_up(s)) s->status = kTimeLimit;
+  }
+  s->do_gap = (s->status == kRunning && s->phase == 1 && s->adaptive_restart) ? 1 : 0;
+  s->restart = 0;
+  if (s->do_gap) {
+    for (int c = 0; c < 2; ++c) {
+      const double r2 = (c == 1 && !avg) ? 0.0 : s->omega * s->cand_dx2[c] + s->cand_dy2[c] / s->omega;
+      s->g_r2[c] = r2;
+      s->g_omega[c] = s->omega;
+      s->g_W[c] = s->g_V[c] = s->g_A[c] = 0.0;
+      s->g_prefix[c] = 0u;
+      s->g_active[c] = r2 > 0.0 ? 1 : 0;
+      s->mu[c] = INFINITY;  // r = 0 gives mu = +inf
+      s->gval[c] = 0.0;
+    }
+  }
+  s->phase = 1;
+}
+
+// Rows: K xs (for K x_avg) and the row terms of Eq. (15) for both candidates.
+// Partial layout per CTA (8): [cand][pres^2, dobj(q^T y), |y - y0|^2, pobj extra].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, int nblocks_c, Problem<T> P, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[8 * (kThreads / 32)];
+  Scalars *sc = S.s;
+  const int cur = sc->cur;
+  const bool avg = sc->sum_eta > 0.0;
+  const double inv = avg ? 1.0 / sc->sum_eta : 0.0;
+  const T *y = S.y[cur], *ys = S.ys[cur], *Kx = S.Kx[cur], *y0 = S.y0;
+  double acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a] = 0.0;
+  const T *const vec[1] = {S.xs[cur]};
+  spmv_block<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
+    S.Kxbar[i] = s[0];
+    const double D1 = P.D1[i], qi = P.q[i], lo = P.ylo[i], yr = (double)y0[i];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c == 1 && !avg) break;
+      const double yt = c == 0 ? (double)y[i] : (double)ys[i] * inv;
+      const double kx = c == 0 ? (double)Kx[i] : (double)s[0] * inv;
+      double r = qi - kx / D1;
+      if (lo > -INFINITY) {                      // inequality row
+        if (lo != 0.0) acc[4 * c + 3] += lo * r;  // general dual bound only
+        r = r > 0.0 ? r : 0.0;
+      }
+      acc[4 * c + 0] += r * r;
+      acc[4 * c + 1] += qi * (D1 * yt);
+      acc[4 * c + 2] += (yt - yr) * (yt - yr);
+    }
+  });
+  block_sum<8>(acc, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) S.part_er[8 * blockIdx.x + a] = acc[a];
+  }
+  if (last_block(S.tickets + kTicketEvalRows)) {
+    double ec[8], er[8];
+    sum_partials<8>(S.part_ec, nblocks_c, 8, ec, red);
+    __syncthreads();
+    sum_partials<8>(S.part_er, gridDim.x, 8, er, red);
+    if (threadIdx.x == 0) eval_finish(sc, ec, er);
+  }
+}
+
+// --------------------------------------------- normalized gap (Section 3.2)
+//
+// For slot s with point z, gradient g = (K^T y - c, q - K x), weight omega and
+// radius r, the maximiser of g^T d over ||d||_omega <= r, z + d in Z is
+// d(t) = (clip(t g_x/omega, l - x, u - x), clip(t omega g_y, ylo - y, inf)) at
+// the t with phi(t) = ||d(t)||^2_omega = r^2.  Item i (a coordinate with
+// g_i != 0) stays unclipped until its breakpoint t_i; with
+// a_i (unclipped t^2 and t coefficient), w_i (clipped contribution to phi)
+// and v_i (clipped contribution to g^T d):
+//     phi(t) = sum_{t_i <= t} w_i + t^2 sum_{t_i > t} a_i.
+// The breakpoint is found by a three-pass radix selection on the float32 bits
+// of t_i (11, 11, 10 bits): each pass histograms (w, v, a) over the digit of
+// the items still in the selected bucket, and the last CTA picks the last
+// bucket whose lower edge has phi < r^2.
+
+struct GapItem {
+  unsigned key;  // float bits of t_i, 0xffffffff = no item
+  double a, w, v;
+};
+
+template <typename T>
+__device__ __forceinline__ GapItem gap_item(const Problem<T> &P, const State<T> &S, const Scalars *sc,
+                                            int slot, int i) {
+  const int cur = sc->cur, n = P.n;
+  const double inv = sc->inv_avg, om = sc->g_omega[slot];
+  GapItem it;
+  it.key = 0xffffffffu;
+  it.a = it.w = it.v = 0.0;
+  if (i < n) {
+    double x, kt;
+    if (slot == 0) { x = (double)S.x[cur][i]; kt = (double)S.KTy_cur[i]; }
+    else if (slot == 1) { x = (double)S.xs[cur][i] * inv; kt = (double)S.KTys[i] * inv; }
+    else { x = (double)S.x[cur][i]; kt = sc->cand == 0 ? (double)S.KTy_cur[i] : (double)S.KTys[i] * inv; }
+    const double g = kt - (double)P.cs[i];
+    if (g == 0.0) return it;
+    // distances to the bounds are >= 0 for a point of Z; the average can sit
+    // an ulp outside its box after rounding, which counts as on the bound
+    double dist = g > 0.0 ? (double)P.us[i] - x : x - (double)P.ls[i];
+    if (!(dist > 0.0)) dist = 0.0;
+    const double ag = fabs(g);
+    it.a = g * g / om;
+    if (isinf(dist)) { it.key = 0x7f800000u; return it; }
+    const float tf = (float)(om * dist) / (float)ag;
+    it.key = __float_as_uint(tf > 0.0f ? tf : 0.0f);
+    it.w = om * dist * dist;
+    it.v = ag * dist;
+  } else {
+    const int r = i - n;
+    double y, kx;
+    if (slot == 0) { y = (double)S.y[cur][r]; kx = (double)S.Kx[cur][r]; }
+    else if (slot == 1) { y = (double)S.ys[cur][r] * inv; kx = (double)S.Kxbar[r] * inv; }
+    else { y = (double)S.y[cur][r]; kx = (double)S.Kx[cur][r]; }
+    const double g = (double)P.qs[r] - kx;
+    if (g == 0.0) return it;
+    double dist = g > 0.0 ? INFINITY : y - (double)P.ylos[r];
+    if (!(dist > 0.0)) dist = 0.0;
+    const double ag = fabs(g);
+    it.a = om * g * g;
+    if (isinf(dist)) { it.key = 0x7f800000u; return it; }
+    const float tf = (float)dist / ((float)om * (float)ag);
+    it.key = __float_as_uint(tf > 0.0f ? tf : 0.0f);
+    it.w = dist * dist / om;
+    it.v = ag * dist;
+  }
+  return it;
+}
+
+__device__ __forceinline__ void gap_digits(int pass, int &shift, int &nb, int &pshift) {
+  shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+  nb = pass == 2 ? 1024 : 2048;
+  pshift = pass == 0 ? 32 : (pass == 1 ? 21 : 10);
+}
+
+// Selection over one slot's global histogram (3 x 2048 doubles), whole CTA.
+__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *sh) {
+  int shift, nb, pshift;
+  gap_digits(pass, shift, nb, pshift);
+  // sh: [3][2048] copy of the histogram, then [2049] suffix sums of a
+  for (int b = threadIdx.x; b < kGapBuckets; b += blockDim.x) {
+    for (int a = 0; a < 3; ++a) {
+      sh[a * kGapBuckets + b] = b < nb ? __ldcg(gh + (size_t)b * 3 + a) : 0.0;
+      gh[(size_t)b * 3 + a] = 0.0;  // clear for the next pass
+    }
+  }
+  __syncthreads();
+  // sequential scan by thread 0 keeps the summation order fixed (once per pass)
+  if (threadIdx.x == 0) {
+    const double r2 = s->g_r2[slot];
+    const unsigned base = pass == 0 ? 0u : (s->g_prefix[slot] >> pshift) << pshift;
+    double *suf = sh + 3 * kGapBuckets;  // suf[b] = A_above + sum_{b' >= b} a
+    suf[nb] = s->g_A[slot];
+    for (int b = nb - 1; b >= 0; --b) suf[b] = suf[b + 1] + sh[2 * kGapBuckets + b];
+    // at bucket b's lower edge, buckets < b are clipped and buckets >= b unclipped
+    int best = 0;
+    double Wb = s->g_W[slot], Vb = s->g_V[slot], Wbest = Wb, Vbest = Vb;
+    for (int b = 0; b < nb; ++b) {
+      const double Tb = (double)__uint_as_float(base | ((unsigned)b << shift));
+      const double Ab = suf[b];
+      const double phi = Ab > 0.0 ? Wb + Tb * Tb * Ab : Wb;
+      if (!(phi < r2)) break;
+      best = b;
+      Wbest = Wb;
+      Vbest = Vb;
+      Wb += sh[b];
+      Vb += sh[kGapBuckets + b];
+    }
+    const double Aafter = suf[best + 1];
+    s->g_W[slot] = Wbest;
+    s->g_V[slot] = Vbest;
+    s->g_A[slot] = Aafter;
+    s->g_prefix[slot] = base | ((unsigned)best << shift);
+    if (pass == 2) {
+      // the items of the final bucket share one float key: count them as clipped
+      const double Wf = Wbest + sh[best], Vf = Vbest + sh[kGapBuckets + best];
+      double val;
+      if (Aafter > 0.0) {
+        const double rem = r2 - Wf;
+        const double t = sqrt((rem > 0.0 ? rem : 0.0) / Aafter);
+        val = Vf + t * Aafter;
+      } else {
+        val = Vf;
+      }
+      s->gval[slot] = val;
+      s->mu[slot] = val / sqrt(r2);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGapThreads) k_gap_pass(Problem<T> P, State<T> S, int pass, int s_begin,
+                                                          int s_end, int when_restart) {
+  extern __shared__ __align__(16) double hist[];  // [slots][3][kGapBuckets]
+  Scalars *sc = S.s;
+  if (when_restart ? !sc->restart : !sc->do_gap) return;  // uniform over the grid
+  const int ns = s_end - s_begin;
+  int shift, nb, pshift;
+  gap_digits(pass, shift, nb, pshift);
+  for (int e = threadIdx.x; e < ns * 3 * kGapBuckets; e += blockDim.x) hist[e] = 0.0;
+  __syncthreads();
+  const int N = P.n + P.m;
+  bool act[kGapSlots];
+  unsigned pref[kGapSlots];
+  for (int s = 0; s < kGapSlots; ++s) {
+    act[s] = s >= s_begin && s < s_end && sc->g_active[s];
+    pref[s] = pass == 0 ? 0u : sc->g_prefix[s] >> pshift;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int s = s_begin; s < s_end; ++s) {
+      if (!act[s]) continue;
+      unsigned *keys = S.gkeys + (size_t)s * N;
+      GapItem it;
+      if (pass == 0) {
+        it = gap_item<T>(P, S, sc, s, i);
+        keys[i] = it.key;
+        if (it.key == 0xffffffffu) continue;
+      } else {
+        const unsigned key = keys[i];
+        if (key == 0xffffffffu || (key >> pshift) != pref[s]) continue;
+        it = gap_item<T>(P, S, sc, s, i);
+      }
+      const int b = (int)((it.key >> shift) & (unsigned)(nb - 1));
+      double *h = hist + (size_t)(s - s_begin) * 3 * kGapBuckets;
+      atomicAdd(h + b, it.w);
+      atomicAdd(h + kGapBuckets + b, it.v);
+      atomicAdd(h + 2 * kGapBuckets + b, it.a);
+    }
+  }
+  __syncthreads();
+  for (int s = s_begin; s < s_end; ++s) {
+    if (!act[s]) continue;
+    const double *h = hist + (size_t)(s - s_begin) * 3 * kGapBuckets;
+    double *gh = S.ghist + (size_t)s * kGapBuckets * 3;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      for (int a = 0; a < 3; ++a) {
+        const double v = h[a * kGapBuckets + b];
+        if (v != 0.0) atomicAdd(gh + (size_t)b * 3 + a, v);
+      }
+    }
+  }
+  if (last_block(S.tickets + kTicketGap)) {
+    for (int s = s_begin; s < s_end; ++s) {
+      if (!act[s]) continue;
+      gap_select(sc, s, pass, S.ghist + (size_t)s * kGapBuckets * 3, hist);
+    }
+  }
+}
+
+// --------------------------------------------------- restart (Section 3.2)
+
+// GetRestartCandidate, criteria (i)-(iii) and Algorithm 3.  One thread.
+__global__ void k_decide(Scalars *s, double *trace) {
+  if (!s->do_gap) return;
+  const double mu_c = s->mu[0];
+  const double mu_a = s->sum_eta > 0.0 ? s->mu[1] : INFINITY;
+  const int cand = mu_c < mu_a ? 0 : 1;
+  const double muc = cand == 0 ? mu_c : mu_a;
+  int restart = 0;
+  if (muc <= s->beta_suff * s->mu0) restart = 1;
+  else if (muc <= s->beta_nec * s->mu0 && muc > s->muc_prev) restart = 1;
+  else if ((double)s->t >= s->beta_art * (double)s->k) restart = 1;
+  s->muc_prev = muc;
+  s->cand = cand;
+  s->restart = restart;
+  double *rec = trace + (size_t)(s->trace_n % kTraceCap) * kTraceLen;
+  s->trace_n += 1;
+  rec[0] = (double)s->k;
+  rec[1] = (double)s->t;
+  rec[2] = mu_c;
+  rec[3] = mu_a;
+  rec[4] = s->mu0;
+  rec[5] = (double)cand;
+  rec[6] = (double)restart;
+  rec[7] = s->omega;
+  rec[8] = sqrt(s->g_r2[0]);
+  rec[9] = sqrt(s->g_r2[1]);
+  rec[10] = s->kkt[0][5];
+  rec[11] = s->kkt[0][6];
+  rec[12] = s->kkt[0][7];
+  rec[13] = s->kkt[1][5];
+  rec[14] = s->kkt[1][6];
+  rec[15] = s->kkt[1][7];
+  if (!restart) return;
+  const double dx2 = s->cand_dx2[cand], dy2 = s->cand_dy2[cand];
+  const double Dx = sqrt(dx2), Dy = sqrt(dy2);
+  if (s->pw_update && Dx > s->eps_zero && Dy > s->eps_zero)
+    s->omega = exp(s->pw_theta * log(Dy / Dx) + (1.0 - s->pw_theta) * log(s->omega));
+  rec[7] = s->omega;
+  // slot 2: mu_n(z^{n+1,0}, z^{n,0}) under the new primal weight
+  const double r2 = s->omega * dx2 + dy2 / s->omega;
+  s->g_r2[2] = r2;
+  s->g_omega[2] = s->omega;
+  s->g_W[2] = s->g_V[2] = s->g_A[2] = 0.0;
+  s->g_prefix[2] = 0u;
+  s->g_active[2] = r2 > 0.0 ? 1 : 0;
+  s->mu[2] = INFINITY;
+  s->gval[2] = 0.0;
+}
+
+// z^{n+1,0} = candidate; current iterate = candidate; sums reset.
+template <typename T>
+__global__ void k_apply_restart(Problem<T> P, State<T> S) {
+  const Scalars *sc = S.s;
+  if (!sc->restart) return;
+  const int cur = sc->cur, cand = sc->cand;
+  const double inv = sc->inv_avg;
+  const int n = P.n, N = P.n + P.m;
+  T *x = S.x[cur], *xs = S.xs[cur], *y = S.y[cur], *ys = S.ys[cur], *Kx = S.Kx[cur];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const T v = cand == 0 ? x[i] : (T)((double)xs[i] * inv);
+      x[i] = v;
+      S.x0[i] = v;
+      xs[i] = T(0);
+    } else {
+      const int r = i - n;
+      const T v = cand == 0 ? y[r] : (T)((double)ys[r] * inv);
+      y[r] = v;
+      S.y0[r] = v;
+      ys[r] = T(0);
+      if (cand == 1) Kx[r] = (T)((double)S.Kxbar[r] * inv);
+    }
+  }
+}
+
+// End of an evaluation: book-keeping of the restart and the loop conditions.
+__global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
+                         int has_inner) {
+  if (s->restart) {
+    s->mu0 = s->mu[2];
+    s->sum_eta = 0.0;
+    s->t = 0;
+    s->muc_prev = INFINITY;
+    s->restarts += 1;
+    s->restart = 0;
+  }
+  s->do_gap = 0;
+  s->chunk_acc = 0;
+  if (s->status == kRunning && time_up(s)) s->status = kTimeLimit;
+  const bool run = s->status == kRunning;
+  cudaGraphSetConditional(h_outer, run ? 1u : 0u);
+  if (has_inner) cudaGraphSetConditional(h_inner, run ? 1u : 0u);
+}
+
+// ------------------------------------------------------------- set-up / out
+
+// Norms of the problem data: ||c||, ||q|| (original), ||c~||, ||q~|| (scaled)
+// -> InitializePrimalWeight (Section 3.3) times primal_importance.
+template <typename T>
+__global__ void k_problem_norms(Problem<T> P, Scalars *s, double primal_importance, double *part) {
+  __shared__ double red[4 * (kThreads / 32)];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int N = P.n + P.m;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    if (i < P.n) {
+      acc[0] += P.c[i] * P.c[i];
+      const double cs = (double)P.cs[i];
+      acc[2] += cs * cs;
+    } else {
+      const int r = i - P.n;
+      acc[1] += P.q[r] * P.q[r];
+      const double qs = (double)P.qs[r];
+      acc[3] += qs * qs;
+    }
+  }
+  block_sum<4>(acc, red);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 4; ++a) part[4 * blockIdx.x + a] = acc[a];
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // tickets live after the 4*gridDim partials
+    unsigned *ticket = reinterpret_cast<unsigned *>(part + 4 * gridDim.x);
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (s_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot[4];
+  sum_partials<4>(part, gridDim.x, 4, tot, red);
+  if (threadIdx.x == 0) {
+    s->cnorm = sqrt(tot[0]);
+    s->qnorm = sqrt(tot[1]);
+    const double nc = sqrt(tot[2]), nq = sqrt(tot[3]);
+    const double w = (nc > s->eps_zero && nq > s->eps_zero) ? nc / nq : 1.0;
+    s->omega = w * primal_importance;
+  }
+}
+
+// Start point z^{0,0} (scaled, projected onto X x Y), sums, restart point.
+template <typename T>
+__global__ void k_init_point(Problem<T> P, State<T> S, const double *x0, const double *y0) {
+  const int n = P.n, N = P.n + P.m;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const double v = x0 ? x0[i] / P.D2[i] : 0.0;
+      const T x = clampv<T>((T)v, P.ls[i], P.us[i]);
+      S.x[0][i] = x;
+      S.x0[i] = x;
+      S.xs[0][i] = T(0);
+      S.xs[1][i] = T(0);
+    } else {
+      const int r = i - n;
+      const double v = y0 ? y0[r] / P.D1[r] : 0.0;
+      const T lo = P.ylos[r];
+      const T y = (T)v > lo ? (T)v : lo;
+      S.y[0][r] = y;
+      S.y0[r] = y;
+      S.ys[0][r] = T(0);
+      S.ys[1][r] = T(0);
+    }
+  }
+}
+
+// Plain row sums out[i] = sum_k A_ik v[col_k] over the row-block schedule.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_spmv(Mat<T> A, const T *v, T *out) {
+  extern __shared__ __align__(16) char sm[];
+  const T *const vec[1] = {v};
+  spmv_block<T, 1>(A, vec, sm, [&](int i, const T(&s)[1]) { out[i] = s[0]; });
+}
+
+__global__ void k_init_scalars(Scalars *s, ScalarInit in) {
+  s->eta = in.eta0;
+  s->sum_eta = 0.0;
+  s->mu0 = INFINITY;
+  s->muc_prev = INFINITY;
+  s->inv_avg = 0.0;
+  s->rel_tol = in.rel_tol;
+  s->beta_suff = in.beta_suff;
+  s->beta_nec = in.beta_nec;
+  s->beta_art = in.beta_art;
+  s->pw_theta = in.pw_theta;
+  s->eps_zero = in.eps_zero;
+  s->k = s->t = s->attempts = s->restarts = 0;
+  s->iter_limit = in.iter_limit;
+  s->attempt_limit = in.attempt_limit;
+  s->time_limit_ns = in.time_limit_ns;
+  s->t0_ns = global_timer_ns();
+  s->t_end_ns = 0;
+  s->cur = 0;
+  s->chunk_acc = 0;
+  s->eval_every = in.eval_every;
+  s->status = kRunning;
+  s->ret_which = 0;
+  s->phase = 0;
+  s->do_gap = 0;
+  s->restart = 0;
+  s->cand = 0;
+  s->adaptive_restart = in.adaptive_restart;
+  s->pw_update = in.pw_update;
+  s->err = 0;
+  s->trace_n = 0;
+  for (int a = 0; a < kGapSlots; ++a) { s->g_active[a] = 0; s->mu[a] = INFINITY; }
+}
+
+// Returned point in the original space: x = D2 x~, y = D1 y~.
+template <typename T>
+__global__ void k_output(Problem<T> P, State<T> S) {
+  Scalars *sc = S.s;
+  const int cur = sc->cur, which = sc->ret_which;
+  const double inv = sc->inv_avg;
+  const int n = P.n, N = P.n + P.m;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->t_end_ns = global_timer_ns();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    if (i < n) {
+      const double x = which == 0 ? (double)S.x[cur][i] : (double)S.xs[cur][i] * inv;
+      S.xo[i] = P.D2[i] * x;
+    } else {
+      const int r = i - n;
+      const double y = which == 0 ? (double)S.y[cur][r] : (double)S.ys[cur][r] * inv;
+      S.yo[r] = P.D1[r] * y;
+    }
+  }
+}
+
+// ------------------------------------------------------- graph construction
+
+// histogram of `ns` slots; the selection also needs room for 2049 suffix sums
+static size_t gap_smem(int ns) {
+  const int rows = 3 * ns > 4 ? 3 * ns : 4;
+  return sizeof(double) * ((size_t)rows * kGapBuckets + 8);
+}
+
+template <typename T>
+static size_t spmv_smem(int nv) {
+  return spmv_smem_bytes<T>(nv);
+}
+
+template <typename T>
+cudaError_t set_kernel_attributes() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_primal<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  if ((e = cudaFuncSetAttribute(k_dual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  if ((e = cudaFuncSetAttribute(k_eval_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(2)))) return e;
+  if ((e = cudaFuncSetAttribute(k_eval_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  if ((e = cudaFuncSetAttribute(k_spmv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  const int gsm = (int)gap_smem(2);
+  if ((e = cudaFuncSetAttribute(k_gap_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm))) return e;
+  return cudaSuccess;
+}
+
+template <typename T>
+static void launch_gap(const Problem<T> &P, const State<T> &S, int s_begin, int s_end, int when_restart,
+                       int grid, cudaStream_t st) {
+  const size_t smem = gap_smem(s_end - s_begin);
+  for (int pass = 0; pass < 3; ++pass)
+    k_gap_pass<T><<<grid, kGapThreads, smem, st>>>(P, S, pass, s_begin, s_end, when_restart);
+}
+
+template <typename T>
+cudaError_t launch_gap_slots(const Problem<T> &P, const State<T> &S, int s_begin, int s_end, int when_restart,
+                             int grid, cudaStream_t st) {
+  launch_gap<T>(P, S, s_begin, s_end, when_restart, grid, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+void launch_spmv(const Mat<T> &A, const T *v, T *out, cudaStream_t st) {
+  if (A.nblocks > 0) k_spmv<T><<<A.nblocks, kThreads, spmv_smem<T>(1), st>>>(A, v, out);
+}
+
+template <typename T>
+void launch_problem_norms(const Problem<T> &P, Scalars *s, double primal_importance, double *part,
+                          int grid, cudaStream_t st) {
+  k_problem_norms<T><<<grid, kThreads, 0, st>>>(P, s, primal_importance, part);
+}
+
+template <typename T>
+void launch_init(const Problem<T> &P, const State<T> &S, const Mat<T> &K, const ScalarInit &in,
+                 const double *x0, const double *y0, cudaStream_t st) {
+  k_init_scalars<<<1, 1, 0, st>>>(S.s, in);
+  const int N = P.n + P.m;
+  k_init_point<T><<<(N + 255) / 256, 256, 0, st>>>(P, S, x0, y0);
+  launch_spmv<T>(K, S.x[0], S.Kx[0], st);
+}
+
+template <typename T>
+void launch_eval(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, cudaStream_t st) {
+  if (KT.nblocks > 0) k_eval_cols<T><<<KT.nblocks, kThreads, spmv_smem<T>(2), st>>>(KT, P, S);
+  k_eval_rows<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S);
+}
+
+template <typename T>
+void launch_output(const Problem<T> &P, const State<T> &S, cudaStream_t st) {
+  const int N = P.n + P.m;
+  k_output<T><<<(N + 255) / 256, 256, 0, st>>>(P, S);
+}
+
+// The graph that `st` is capturing into.
+static cudaError_t capture_graph(cudaStream_t st, cudaGraph_t *g) {
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t *deps;
+  size_t ndeps;
+  return cudaStreamGetCaptureInfo(st, &cs, nullptr, g, &deps, nullptr, &ndeps);
+}
+
+// Appends a conditional WHILE node on handle h (created in the capturing
+// graph) after everything captured so far on `st`; returns its body graph.
+static cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+  cudaError_t e;
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t *deps;
+  size_t ndeps;
+  if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &ndeps))) return e;
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p))) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The whole solve as one graph:
+//   norms, init, K x0, evaluation (termination check at the start), finish
+//   WHILE running:
+//     WHILE chunk not done: primal, dual (+ accept)
+//     evaluation, gap (slots 0,1), decide, apply restart, gap (slot 2), finish
+//   output
+// Every loop is bounded: each inner pass makes one step attempt and the
+// accept kernel stops the inner loop at attempt_limit; the evaluation turns
+// the status to a limit once k or the attempts reach their limits, and the
+// outer condition is the status.
+template <typename T>
+cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                              const ScalarInit &in, double primal_importance, double *norm_part,
+                              const double *x0_dev, const double *y0_dev, int gap_grid,
+                              cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec) {
+  cudaError_t e;
+  cudaGraph_t graph = nullptr;
+  *exec = nullptr;
+  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal))) return e;
+  const int N = P.n + P.m;
+  launch_problem_norms<T>(P, S.s, primal_importance, norm_part, 152, st);
+  k_init_scalars<<<1, 1, 0, st>>>(S.s, in);
+  k_init_point<T><<<(N + 255) / 256, 256, 0, st>>>(P, S, x0_dev, y0_dev);
+  launch_spmv<T>(K, S.x[0], S.Kx[0], st);
+  launch_eval<T>(K, KT, P, S, st);
+  cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
+  cudaGraph_t g = nullptr, body_outer = nullptr, body_inner = nullptr;
+  e = capture_graph(st, &g);
+  if (!e) e = cudaGraphConditionalHandleCreate(&h_outer, g, 0u, cudaGraphCondAssignDefault);
+  if (!e) {
+    k_finish<<<1, 1, 0, st>>>(S.s, h_outer, h_outer, 0);  // loop entry decided by the check at the start
+    e = add_while(st, h_outer, &body_outer);
+  }
+  if (!e) e = cudaStreamBeginCaptureToGraph(st2, body_outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (!e) {
+    e = cudaGraphConditionalHandleCreate(&h_inner, body_outer, 1u, cudaGraphCondAssignDefault);
+    if (!e) e = add_while(st2, h_inner, &body_inner);
+    if (!e) e = cudaStreamBeginCaptureToGraph(st3, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
+      k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT.nblocks, P, S, h_inner, 1);
+      cudaGraph_t tmp;
+      e = cudaStreamEndCapture(st3, &tmp);
+    }
+    if (!e) {
+      launch_eval<T>(K, KT, P, S, st2);
+      launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
+      k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
+      k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
+      launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
+      k_finish<<<1, 1, 0, st2>>>(S.s, h_outer, h_inner, 1);
+    }
+    cudaGraph_t tmp2;
+    cudaError_t e2 = cudaStreamEndCapture(st2, &tmp2);
+    if (!e) e = e2;
+  }
+  launch_output<T>(P, S, st);
+  cudaError_t e3 = cudaStreamEndCapture(st, &graph);
+  if (!e) e = e3;
+  if (!e) e = cudaGetLastError();
+  if (!e) e = cudaGraphInstantiate(exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  return e;
+}
+
+// Times the two step kernels of one attempt outside the graph: `reps`
+// launches of k_primal then k_dual (no loop condition), each pair bracketed by
+// CUDA events on `st`.  The attempts advance the iterate like a solve does.
+template <typename T>
+cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                              int reps, cudaStream_t st, float *ms_primal, float *ms_dual) {
+  cudaEvent_t e0, e1, e2;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0))) return e;
+  if ((e = cudaEventCreate(&e1))) return e;
+  if ((e = cudaEventCreate(&e2))) return e;
+  double tp = 0.0, td = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, st);
+    if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+    cudaEventRecord(e1, st);
+    k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
+    cudaEventRecord(e2, st);
+    if ((e = cudaEventSynchronize(e2))) break;
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, e0, e1);
+    cudaEventElapsedTime(&b, e1, e2);
+    tp += a;
+    td += b;
+  }
+  if (!e) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  *ms_primal = (float)(tp / reps);
+  *ms_dual = (float)(td / reps);
+  return e;
+}
+
+template cudaError_t time_step_kernels<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                               const State<double> &, int, cudaStream_t, float *, float *);
+template cudaError_t time_step_kernels<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                              const State<float> &, int, cudaStream_t, float *, float *);
+template cudaError_t launch_gap_slots<double>(const Problem<double> &, const State<double> &, int, int, int, int,
+                                              cudaStream_t);
+template cudaError_t launch_gap_slots<float>(const Problem<float> &, const State<float> &, int, int, int, int,
+                                             cudaStream_t);
+template cudaError_t set_kernel_attributes<double>();
+template cudaError_t set_kernel_attributes<float>();
+template void launch_spmv<double>(const Mat<double> &, const double *, double *, cudaStream_t);
+template void launch_spmv<float>(const Mat<float> &, const float *, float *, cudaStream_t);
+template void launch_problem_norms<double>(const Problem<double> &, Scalars *, double, double *, int, cudaStream_t);
+template void launch_problem_norms<float>(const Problem<float> &, Scalars *, double, double *, int, cudaStream_t);
+template void launch_init<double>(const Problem<double> &, const State<double> &, const Mat<double> &,
+                                  const ScalarInit &, const double *, const double *, cudaStream_t);
+template void launch_init<float>(const Problem<float> &, const State<float> &, const Mat<float> &,
+                                 const ScalarInit &, const double *, const double *, cudaStream_t);
+template void launch_eval<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                  const State<double> &, cudaStream_t);
+template void launch_eval<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                 const State<float> &, cudaStream_t);
+template void launch_output<double>(const Problem<double> &, const State<double> &, cudaStream_t);
+template void launch_output<float>(const Problem<float> &, const State<float> &, cudaStream_t);
+template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                               const State<double> &, const ScalarInit &, double, double *,
+                                               const double *, const double *, int, cudaStream_t,
+                                               cudaStream_t, cudaStream_t, cudaGraphExec_t *);
+template cudaError_t build_solve_graph<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                              const State<float> &, const ScalarInit &, double, double *,
+                                              const double *, const double *, int, cudaStream_t,
+                                              cudaStream_t, cudaStream_t, cudaGraphExec_t *);
+
+}  // namespace pdlp

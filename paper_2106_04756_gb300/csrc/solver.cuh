@@ -1,0 +1,39 @@
+// Launchers of the iteration kernels (solver.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace pdlp {
+
+// Per-solve settings written into Scalars by k_init_scalars.
+struct ScalarInit {
+  double eta0, rel_tol, beta_suff, beta_nec, beta_art, pw_theta, eps_zero;
+  long long iter_limit, attempt_limit;
+  unsigned long long time_limit_ns;
+  int eval_every, adaptive_restart, pw_update, pad;
+};
+
+template <typename T> cudaError_t set_kernel_attributes();
+template <typename T>
+cudaError_t launch_gap_slots(const Problem<T> &P, const State<T> &S, int s_begin, int s_end, int when_restart,
+                             int grid, cudaStream_t st);
+template <typename T>
+cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                              int reps, cudaStream_t st, float *ms_primal, float *ms_dual);
+template <typename T> void launch_spmv(const Mat<T> &A, const T *v, T *out, cudaStream_t st);
+template <typename T>
+void launch_problem_norms(const Problem<T> &P, Scalars *s, double primal_importance, double *part, int grid,
+                          cudaStream_t st);
+template <typename T>
+void launch_init(const Problem<T> &P, const State<T> &S, const Mat<T> &K, const ScalarInit &in,
+                 const double *x0, const double *y0, cudaStream_t st);
+template <typename T>
+void launch_eval(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, cudaStream_t st);
+template <typename T> void launch_output(const Problem<T> &P, const State<T> &S, cudaStream_t st);
+template <typename T>
+cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                              const ScalarInit &in, double primal_importance, double *norm_part,
+                              const double *x0_dev, const double *y0_dev, int gap_grid, cudaStream_t st,
+                              cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec);
+
+}  // namespace pdlp

@@ -1,0 +1,68 @@
+"""The C ABI library loads without a GPU and exports every declared call."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(pdlp_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_04756_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_call():
+    from paper_2106_04756_gb300 import _abi
+    assert set(_declared()) == set(_abi._SIGNATURES)
+
+
+def test_default_options_are_the_papers(lib):
+    import paper_2106_04756_gb300 as P
+    o = P.default_options()
+    assert (o.beta_suff, o.beta_nec, o.beta_art) == (0.9, 0.1, 0.5)
+    assert o.pw_smoothing == 0.5 and o.eval_every == 40 and o.ruiz_iters == 10
+    assert o.pock_chambolle == 1 and o.rel_tol == 1e-8 and o.primal_importance == 1.0
+
+
+def test_create_rejects_bad_arguments_before_any_device_work(lib):
+    import paper_2106_04756_gb300 as P
+    from paper_2106_04756_gb300 import _abi
+    out = C.c_void_p()
+    rc = _abi.load().pdlp_create(None, None, None, None, None, None, None, C.byref(out))
+    assert rc == _abi.PDLP_ERR_INVALID_ARG and not out.value
+    # negative sizes
+    rp = np.zeros(2, np.int32)
+    csr = _abi.pdlp_csr(-1, 3, 0, rp.ctypes.data, None, None)
+    z = np.zeros(3)
+    rc = _abi.load().pdlp_create(C.byref(csr), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
+                                 np.zeros(3, np.uint8).ctypes.data, None, C.byref(out))
+    assert rc == _abi.PDLP_ERR_INVALID_ARG
+    assert b"CSR" in _abi.load().pdlp_last_error(None)
+    # a bad option
+    o = P.default_options(precision=7)
+    csr = _abi.pdlp_csr(1, 1, 0, rp.ctypes.data, None, None)
+    rc = _abi.load().pdlp_create(C.byref(csr), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
+                                 np.zeros(3, np.uint8).ctypes.data, C.byref(o), C.byref(out))
+    assert rc == _abi.PDLP_ERR_INVALID_ARG
