@@ -199,6 +199,32 @@ int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *cou
  * milliseconds of the primal and the dual kernel. */
 int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms);
 
+/* The normalized duality gap of pdlp_normalized_gap, for callers that cannot
+ * allocate device memory (for example when another allocator already owns
+ * the GPU's memory, or when the cost and implicit synchronisation of
+ * cudaMalloc / cudaFree are not acceptable).  The paper has no counterpart of
+ * this call; it allocates nothing.
+ *   n, m             numbers of primal and dual coordinates, n + m <= 1048576
+ *                    (larger sizes return PDLP_ERR_INVALID_ARG);
+ *   x, gx, l, u      DEVICE float64[n]: point, gradient K^T y - c, bounds;
+ *   y, gy, ylo       DEVICE float64[m]: point, gradient q - K x, lower bounds
+ *                    of y (-INFINITY on equality rows);
+ *   omega, r         primal weight and radius, both > 0;
+ *   stream           cudaStream_t for the work (NULL = legacy default stream);
+ *   *mu, *value      HOST outputs: rho_r(z) and the maximised gap (value nullable).
+ * Scratch is one static device array of about 4.05 MiB, held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current) and sets the kernel's shared-memory limit; make that first call
+ * before any stream capture.  Every call clears the parts of the array that
+ * must start at zero; all calls share the array, so calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  Returns after the result is on the host. */
+int pdlp_normalized_gap_noalloc(int32_t n, int32_t m, const double *x, const double *y,
+                                const double *gx, const double *gy, const double *l,
+                                const double *u, const double *ylo, double omega, double r,
+                                void *stream, double *mu, double *value);
+
 /* Message of the last failing call on this thread (ctx may be NULL). */
 const char *pdlp_last_error(const pdlp_ctx *ctx);
 

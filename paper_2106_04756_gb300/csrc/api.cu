@@ -39,6 +39,11 @@ struct Precision {
 
 }  // namespace
 
+namespace pdlp {
+// Records a message returned by pdlp_last_error(NULL) on this thread.
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace pdlp
+
 struct pdlp_ctx {
   int32_t m = 0, n = 0;
   int64_t nnz = 0;
