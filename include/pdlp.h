@@ -89,6 +89,10 @@ typedef struct {
   int32_t refine_rounds;    /* PDLP_FP32_REFINE: maximum outer rounds                    */
   int32_t unroll_T;         /* >0: pdlp_solve runs T unrolled steps for pdlp_grad        */
   int32_t ckpt_every;       /* unrolled steps between stored checkpoints                 */
+  int32_t use_graph;        /* 1: one CUDA graph per solve (conditional WHILE nodes);
+                               0: the same kernels launched from a host loop that reads
+                               the state after every step attempt (for profilers)       */
+  int32_t pad_;
   void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
 } pdlp_options;
 

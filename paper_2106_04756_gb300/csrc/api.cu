@@ -31,6 +31,8 @@ struct Precision {
   Mat<T> K, KT;
   Problem<T> P;
   State<T> S;
+  ScalarInit init{};
+  double *normpart_ptr = nullptr;
   cudaGraphExec_t graph = nullptr;
   ~Precision() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -198,9 +200,15 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   in.eval_every = o.eval_every;
   in.adaptive_restart = o.adaptive_restart;
   in.pw_update = o.pw_update;
+  pr.init = in;
+  pr.normpart_ptr = normpart;
+  if (!o.use_graph) {
+    pr.ready = true;
+    return PDLP_OK;
+  }
   CK(build_solve_graph<T>(pr.K, pr.KT, pr.P, pr.S, in, o.primal_importance, normpart,
                           reinterpret_cast<const double *>(ctx->xin.ptr()),
-                          reinterpret_cast<const double *>(ctx->yin.ptr()), 2 * 152, ctx->cap[0],
+                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, ctx->cap[0],
                           ctx->cap[1], ctx->cap[2], &pr.graph),
      "graph capture");
   pr.ready = true;
@@ -313,6 +321,13 @@ void read_result(const Scalars &s, double seconds, pdlp_result *res) {
 // Launches one precision's solve graph from the staged start point.
 template <typename T>
 int run_graph(pdlp_ctx *ctx, Precision<T> &pr, Scalars *hs) {
+  if (!ctx->opts.use_graph) {
+    CK(run_stepped<T>(pr.K, pr.KT, pr.P, pr.S, pr.init, ctx->opts.primal_importance, pr.normpart_ptr,
+                      reinterpret_cast<const double *>(ctx->xin.ptr()),
+                      reinterpret_cast<const double *>(ctx->yin.ptr()), 152, ctx->st, hs),
+       "stepped solve");
+    return PDLP_OK;
+  }
   CK(cudaGraphLaunch(pr.graph, ctx->st), "graph launch");
   CK(cudaMemcpyAsync(hs, pr.S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st), "scalars");
   CK(cudaStreamSynchronize(ctx->st), "solve");
@@ -366,6 +381,7 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->refine_rounds = 12;
   o->unroll_T = 0;
   o->ckpt_every = 50;
+  o->use_graph = 1;
   o->stream = nullptr;
   return PDLP_OK;
 }
@@ -523,8 +539,11 @@ extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, dou
   } else {
     if ((rc = setup_refine(ctx))) return rc;
     RefineOutcome ro;
-    cudaError_t e = refine_solve(ctx->ref, ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->pc32.P, ctx->pc32.S,
-                                 ctx->pc32.graph, ctx->opts.rel_tol, ctx->opts.inner_tol, ctx->opts.refine_rounds,
+    auto run_inner = [ctx](Scalars *h) -> cudaError_t {
+      return run_graph<float>(ctx, ctx->pc32, h) == PDLP_OK ? cudaSuccess : cudaErrorUnknown;
+    };
+    cudaError_t e = refine_solve(ctx->ref, ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->pc32.S, run_inner,
+                                 ctx->opts.rel_tol, ctx->opts.refine_rounds,
                                  reinterpret_cast<const double *>(ctx->xin.ptr()),
                                  reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st, &ro);
     if (e) return cuda_fail(ctx, e, "refinement");
@@ -611,7 +630,7 @@ extern "C" int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double 
   hs.g_W[0] = hs.g_V[0] = hs.g_A[0] = 0.0;
   hs.g_prefix[0] = 0u;
   CK(cudaMemcpyAsync(S.s, &hs, sizeof(Scalars), cudaMemcpyHostToDevice, st), "scalars");
-  CK(launch_gap_slots<double>(pr.P, S, 0, 1, 0, 2 * 152, st), "gap");
+  CK(launch_gap_slots<double>(pr.P, S, 0, 1, 0, 152, st), "gap");
   CK(cudaMemcpyAsync(&hs, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "scalars");
   CK(cudaStreamSynchronize(st), "sync");
   if (mu) *mu = hs.mu[0];

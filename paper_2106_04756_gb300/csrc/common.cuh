@@ -175,6 +175,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *red) {
   }
 }
 
+// Deterministic CTA sum of NV per-thread values with few float64 instructions
+// (float64 throughput is low on this part): values go to shared memory, one
+// warp adds blockDim/32 of them per lane, then a 5-step shuffle.  The result
+// is valid in thread 0.  `red` must hold NV * blockDim.x doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum_lean(double (&v)[NV], double *red) {
+  const int nt = blockDim.x, lane = threadIdx.x & 31;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) red[a * nt + threadIdx.x] = v[a];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double t = 0.0;
+      for (int k = lane; k < nt; k += 32) t += red[a * nt + k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[a] = t;
+    }
+  }
+}
+
 // Fixed-order sum of `count` partials (stride `stride`, offset `off`) by one
 // CTA; result valid in thread 0.
 template <int NV>

@@ -245,11 +245,9 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64) {
 }
 
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
-                         const Problem<float> &Pc, const State<float> &Sc, cudaGraphExec_t inner_graph,
-                         double tol, double inner_tol, int max_rounds, const double *x_stage,
-                         const double *y_stage, cudaStream_t st, RefineOutcome *out) {
-  (void)inner_tol;
-  (void)Pc;
+                         const State<float> &Sc, const std::function<cudaError_t(Scalars *)> &run_inner,
+                         double tol, int max_rounds, const double *x_stage, const double *y_stage,
+                         cudaStream_t st, RefineOutcome *out) {
   cudaError_t e;
   const int N = P.n + P.m, grid = (N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024;
   RefView V = R.v;
@@ -304,8 +302,7 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
     // inner float32 solve from zero (the staging buffers are the graph's start point)
     if ((e = cudaMemsetAsync(const_cast<double *>(x_stage), 0, sizeof(double) * P.n, st))) return e;
     if ((e = cudaMemsetAsync(const_cast<double *>(y_stage), 0, sizeof(double) * P.m, st))) return e;
-    if ((e = cudaGraphLaunch(inner_graph, st))) return e;
-    if ((e = cudaMemcpyAsync(&hs, Sc.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = run_inner(&hs))) return e;
     k_ref_update<<<grid, 256, 0, st>>>(P, V, Sc.xo, Sc.yo, dP, dD);
     if ((e = cudaGetLastError())) return e;
     if ((e = cudaStreamSynchronize(st))) return e;

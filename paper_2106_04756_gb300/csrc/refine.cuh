@@ -1,6 +1,8 @@
 // Float32 inner solves inside a float64 iterative-refinement loop (refine.cu).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 #include "prep.cuh"
 
@@ -41,9 +43,11 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64);
 // Scales of the correction problem from the violations (see refine.cu).
 void refine_scales(double pv, double dv, double dmax, double *dP, double *dD);
 
+// run_inner runs one float32 solve of the correction problem held in R (start
+// point: the staging buffers) and returns its final scalars in *hs (host).
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
-                         const Problem<float> &Pc, const State<float> &Sc, cudaGraphExec_t inner_graph,
-                         double tol, double inner_tol, int max_rounds, const double *x_stage, const double *y_stage,
+                         const State<float> &Sc, const std::function<cudaError_t(Scalars *)> &run_inner,
+                         double tol, int max_rounds, const double *x_stage, const double *y_stage,
                          cudaStream_t st, RefineOutcome *out);
 
 }  // namespace pdlp

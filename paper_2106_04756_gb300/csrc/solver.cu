@@ -76,7 +76,7 @@ __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_primal(Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kThreads];
   const Scalars *sc = S.s;
   const int cur = sc->cur;
   const double eta = sc->eta, omega = sc->omega;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_primal(Mat<T> KT, Problem<T> P, St
     const T d = xp - xj;
     acc[0] += (double)(d * d);
   });
-  block_sum<1>(acc, red);
+  block_sum_lean<1>(acc, red);
   if (threadIdx.x == 0) S.part_p[blockIdx.x] = acc[0];
 }
 
@@ -103,7 +103,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Problem<T> P, State<T> S,
                                                    cudaGraphConditionalHandle h, int has_cond) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[2 * (kThreads / 32)];
+  __shared__ double red[2 * kThreads];
   Scalars *sc = S.s;
   const int cur = sc->cur;
   const double eta = sc->eta, omega = sc->omega;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Prob
     acc[0] += (double)(dy * dy);
     acc[1] += (double)dy * (double)dk;
   });
-  block_sum<2>(acc, red);
+  block_sum_lean<2>(acc, red);
   if (threadIdx.x == 0) {
     S.part_d[2 * blockIdx.x] = acc[0];
     S.part_d[2 * blockIdx.x + 1] = acc[1];
@@ -282,27 +282,33 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, int nblocks_c,
 // radius r, the maximiser of g^T d over ||d||_omega <= r, z + d in Z is
 // d(t) = (clip(t g_x/omega, l - x, u - x), clip(t omega g_y, ylo - y, inf)) at
 // the t with phi(t) = ||d(t)||^2_omega = r^2.  Item i (a coordinate with
-// g_i != 0) stays unclipped until its breakpoint t_i; with
-// a_i (unclipped t^2 and t coefficient), w_i (clipped contribution to phi)
-// and v_i (clipped contribution to g^T d):
+// g_i != 0) stays unclipped until its breakpoint t_i; with a_i (unclipped t^2
+// and t coefficient), w_i (clipped contribution to phi) and v_i (clipped
+// contribution to g^T d):
 //     phi(t) = sum_{t_i <= t} w_i + t^2 sum_{t_i > t} a_i.
-// The breakpoint is found by a three-pass radix selection on the float32 bits
-// of t_i (11, 11, 10 bits): each pass histograms (w, v, a) over the digit of
-// the items still in the selected bucket, and the last CTA picks the last
-// bucket whose lower edge has phi < r^2.
+// Items with t_i = 0 are clipped for every t > 0 and contribute nothing, so
+// they are dropped; items with t_i = +inf (no bound in the direction of g)
+// only ever contribute a_i.  The breakpoint is found by a three-pass radix
+// selection on the float32 bits of t_i (11, 11, 10 bits): each pass
+// histograms (w, v, a) over the digit of the items still in the selected
+// bucket, and the last CTA picks the last bucket whose lower edge has
+// phi < r^2 (parallel scans in fixed order).
+
+constexpr unsigned kKeyNone = 0xffffffffu;  // no item (g = 0 or t = 0)
+constexpr unsigned kKeyInf = 0x7f800000u;   // t = +inf
 
 struct GapItem {
-  unsigned key;  // float bits of t_i, 0xffffffff = no item
+  unsigned key;
   double a, w, v;
 };
 
 template <typename T>
-__device__ __forceinline__ GapItem gap_item(const Problem<T> &P, const State<T> &S, const Scalars *sc,
-                                            int slot, int i) {
+__device__ __forceinline__ GapItem gap_item(const Problem<T> &P, const State<T> &S, const Scalars *sc, int slot,
+                                            int i, double om, double inv_om) {
   const int cur = sc->cur, n = P.n;
-  const double inv = sc->inv_avg, om = sc->g_omega[slot];
+  const double inv = sc->inv_avg;
   GapItem it;
-  it.key = 0xffffffffu;
+  it.key = kKeyNone;
   it.a = it.w = it.v = 0.0;
   if (i < n) {
     double x, kt;
@@ -313,13 +319,14 @@ __device__ __forceinline__ GapItem gap_item(const Problem<T> &P, const State<T> 
     if (g == 0.0) return it;
     // distances to the bounds are >= 0 for a point of Z; the average can sit
     // an ulp outside its box after rounding, which counts as on the bound
-    double dist = g > 0.0 ? (double)P.us[i] - x : x - (double)P.ls[i];
-    if (!(dist > 0.0)) dist = 0.0;
+    const double dist = g > 0.0 ? (double)P.us[i] - x : x - (double)P.ls[i];
+    if (!(dist > 0.0)) return it;
     const double ag = fabs(g);
-    it.a = g * g / om;
-    if (isinf(dist)) { it.key = 0x7f800000u; return it; }
+    it.a = g * g * inv_om;
+    if (isinf(dist)) { it.key = kKeyInf; return it; }
     const float tf = (float)(om * dist) / (float)ag;
-    it.key = __float_as_uint(tf > 0.0f ? tf : 0.0f);
+    if (!(tf > 0.0f)) { it.key = kKeyNone; return it; }
+    it.key = __float_as_uint(tf);
     it.w = om * dist * dist;
     it.v = ag * dist;
   } else {
@@ -330,14 +337,15 @@ __device__ __forceinline__ GapItem gap_item(const Problem<T> &P, const State<T> 
     else { y = (double)S.y[cur][r]; kx = (double)S.Kx[cur][r]; }
     const double g = (double)P.qs[r] - kx;
     if (g == 0.0) return it;
-    double dist = g > 0.0 ? INFINITY : y - (double)P.ylos[r];
-    if (!(dist > 0.0)) dist = 0.0;
+    const double dist = g > 0.0 ? INFINITY : y - (double)P.ylos[r];
+    if (!(dist > 0.0)) return it;
     const double ag = fabs(g);
     it.a = om * g * g;
-    if (isinf(dist)) { it.key = 0x7f800000u; return it; }
+    if (isinf(dist)) { it.key = kKeyInf; return it; }
     const float tf = (float)dist / ((float)om * (float)ag);
-    it.key = __float_as_uint(tf > 0.0f ? tf : 0.0f);
-    it.w = dist * dist / om;
+    if (!(tf > 0.0f)) { it.key = kKeyNone; return it; }
+    it.key = __float_as_uint(tf);
+    it.w = dist * dist * inv_om;
     it.v = ag * dist;
   }
   return it;
@@ -349,60 +357,143 @@ __device__ __forceinline__ void gap_digits(int pass, int &shift, int &nb, int &p
   pshift = pass == 0 ? 32 : (pass == 1 ? 21 : 10);
 }
 
-// Selection over one slot's global histogram (3 x 2048 doubles), whole CTA.
-__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *sh) {
-  int shift, nb, pshift;
-  gap_digits(pass, shift, nb, pshift);
-  // sh: [3][2048] copy of the histogram, then [2049] suffix sums of a
-  for (int b = threadIdx.x; b < kGapBuckets; b += blockDim.x) {
-    for (int a = 0; a < 3; ++a) {
-      sh[a * kGapBuckets + b] = b < nb ? __ldcg(gh + (size_t)b * 3 + a) : 0.0;
-      gh[(size_t)b * 3 + a] = 0.0;  // clear for the next pass
+// Exclusive prefix (reverse = false: over lower threads; true: over higher
+// threads) of one double per thread, CTA-wide, fixed order.  `sh` holds 32
+// doubles.  Every thread of the CTA must call it.
+__device__ __forceinline__ double block_scan_excl(double v, bool reverse, double *sh) {
+  (void)v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    if (!reverse) {
+      const double t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    } else {
+      const double t = __shfl_down_sync(0xffffffffu, x, o);
+      if (lane + o < 32) x += t;
     }
   }
   __syncthreads();
-  // sequential scan by thread 0 keeps the summation order fixed (once per pass)
-  if (threadIdx.x == 0) {
-    const double r2 = s->g_r2[slot];
-    const unsigned base = pass == 0 ? 0u : (s->g_prefix[slot] >> pshift) << pshift;
-    double *suf = sh + 3 * kGapBuckets;  // suf[b] = A_above + sum_{b' >= b} a
-    suf[nb] = s->g_A[slot];
-    for (int b = nb - 1; b >= 0; --b) suf[b] = suf[b + 1] + sh[2 * kGapBuckets + b];
-    // at bucket b's lower edge, buckets < b are clipped and buckets >= b unclipped
-    int best = 0;
-    double Wb = s->g_W[slot], Vb = s->g_V[slot], Wbest = Wb, Vbest = Vb;
-    for (int b = 0; b < nb; ++b) {
-      const double Tb = (double)__uint_as_float(base | ((unsigned)b << shift));
-      const double Ab = suf[b];
-      const double phi = Ab > 0.0 ? Wb + Tb * Tb * Ab : Wb;
-      if (!(phi < r2)) break;
-      best = b;
-      Wbest = Wb;
-      Vbest = Vb;
-      Wb += sh[b];
-      Vb += sh[kGapBuckets + b];
+  if ((!reverse && lane == 31) || (reverse && lane == 0)) sh[warp] = x;  // warp totals
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      if (!reverse) {
+        const double t = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += t;
+      } else {
+        const double t = __shfl_down_sync(0xffffffffu, w, o);
+        if (lane + o < 32) w += t;
+      }
     }
-    const double Aafter = suf[best + 1];
-    s->g_W[slot] = Wbest;
-    s->g_V[slot] = Vbest;
-    s->g_A[slot] = Aafter;
-    s->g_prefix[slot] = base | ((unsigned)best << shift);
+    sh[lane] = w;  // inclusive scan of the warp totals (in the scan direction)
+  }
+  __syncthreads();
+  double before;
+  if (!reverse) before = warp > 0 ? sh[warp - 1] : 0.0;
+  else before = warp + 1 < nw ? sh[warp + 1] : 0.0;
+  // exclusive value: the neighbour's inclusive value (no subtraction, so no
+  // cancellation when this thread's own term dominates)
+  double ex;
+  if (!reverse) {
+    ex = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) ex = 0.0;
+  } else {
+    ex = __shfl_down_sync(0xffffffffu, x, 1);
+    if (lane == 31) ex = 0.0;
+  }
+  const double r = before + ex;
+  __syncthreads();
+  return r;
+}
+
+// Selection over one slot's global histogram, whole CTA (kGapThreads threads,
+// 4 consecutive buckets per thread).
+__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *sh) {
+  int shift, nb, pshift;
+  gap_digits(pass, shift, nb, pshift);
+  constexpr int kPer = kGapBuckets / kGapThreads;  // 4
+  __shared__ double scan_sh[32];
+  __shared__ int s_best;
+  double w[kPer], v[kPer], a[kPer];
+  const int b0 = threadIdx.x * kPer;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int b = b0 + k;
+    w[k] = b < nb ? __ldcg(gh + (size_t)b * 3 + 0) : 0.0;
+    v[k] = b < nb ? __ldcg(gh + (size_t)b * 3 + 1) : 0.0;
+    a[k] = b < nb ? __ldcg(gh + (size_t)b * 3 + 2) : 0.0;
+    gh[(size_t)b * 3 + 0] = 0.0;  // clear for the next pass
+    gh[(size_t)b * 3 + 1] = 0.0;
+    gh[(size_t)b * 3 + 2] = 0.0;
+  }
+  double tw = 0.0, tv = 0.0, ta = 0.0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) { tw += w[k]; tv += v[k]; ta += a[k]; }
+  const double W0 = s->g_W[slot], V0 = s->g_V[slot], A0 = s->g_A[slot], r2 = s->g_r2[slot];
+  const double wex = W0 + block_scan_excl(tw, false, scan_sh);
+  const double vex = V0 + block_scan_excl(tv, false, scan_sh);
+  const double asuf = A0 + block_scan_excl(ta, true, scan_sh);  // buckets after this thread's
+  const unsigned base = pass == 0 ? 0u : (s->g_prefix[slot] >> pshift) << pshift;
+  // per bucket: W below, V below, A at and after, A after
+  double Wb[kPer], Vb[kPer], Ain[kPer], Aout[kPer];
+  {
+    double cw = wex, cv = vex;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) { Wb[k] = cw; Vb[k] = cv; cw += w[k]; cv += v[k]; }
+    double ca = asuf;
+#pragma unroll
+    for (int k = kPer - 1; k >= 0; --k) { Aout[k] = ca; ca += a[k]; Ain[k] = ca; }
+  }
+  // phi is nondecreasing over the buckets with a real lower edge; the chosen
+  // bucket is the one before the first whose edge fails phi < r^2 (edges past
+  // +inf are NaN bit patterns and fail)
+  int first_fail = nb;
+#pragma unroll
+  for (int k = kPer - 1; k >= 0; --k) {
+    const int b = b0 + k;
+    if (b >= nb) continue;
+    const float Tf = __uint_as_float(base | ((unsigned)b << shift));
+    const double Tb = (double)Tf;
+    const double phi = Ain[k] > 0.0 ? Wb[k] + Tb * Tb * Ain[k] : Wb[k];
+    if (isnan(Tf) || !(phi < r2)) first_fail = b;
+  }
+  int bm = first_fail;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bm = min(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  __shared__ int wbest[32];
+  if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = bm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = nb;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = min(m, wbest[q]);
+    s_best = m > 0 ? m - 1 : 0;  // bucket 0's lower edge has phi < r^2 by construction
+  }
+  __syncthreads();
+  const int bsel = s_best;
+  if (bsel >= b0 && bsel < b0 + kPer) {
+    const int k = bsel - b0;
+    s->g_W[slot] = Wb[k];
+    s->g_V[slot] = Vb[k];
+    s->g_A[slot] = Aout[k];
+    s->g_prefix[slot] = base | ((unsigned)bsel << shift);
     if (pass == 2) {
       // the items of the final bucket share one float key: count them as clipped
-      const double Wf = Wbest + sh[best], Vf = Vbest + sh[kGapBuckets + best];
-      double val;
-      if (Aafter > 0.0) {
+      const double Wf = Wb[k] + w[k], Vf = Vb[k] + v[k], Aa = Aout[k];
+      double val = Vf;
+      if (Aa > 0.0) {
         const double rem = r2 - Wf;
-        const double t = sqrt((rem > 0.0 ? rem : 0.0) / Aafter);
-        val = Vf + t * Aafter;
-      } else {
-        val = Vf;
+        val = Vf + sqrt((rem > 0.0 ? rem : 0.0) / Aa) * Aa;
       }
       s->gval[slot] = val;
       s->mu[slot] = val / sqrt(r2);
     }
   }
   __syncthreads();
+  (void)sh;
 }
 
 template <typename T>
@@ -419,9 +510,13 @@ __global__ void __launch_bounds__(kGapThreads) k_gap_pass(Problem<T> P, State<T>
   const int N = P.n + P.m;
   bool act[kGapSlots];
   unsigned pref[kGapSlots];
+  double om[kGapSlots], inv_om[kGapSlots], ainf[kGapSlots];
   for (int s = 0; s < kGapSlots; ++s) {
     act[s] = s >= s_begin && s < s_end && sc->g_active[s];
     pref[s] = pass == 0 ? 0u : sc->g_prefix[s] >> pshift;
+    om[s] = sc->g_omega[s];
+    inv_om[s] = act[s] ? 1.0 / om[s] : 0.0;
+    ainf[s] = 0.0;
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     for (int s = s_begin; s < s_end; ++s) {
@@ -429,19 +524,30 @@ __global__ void __launch_bounds__(kGapThreads) k_gap_pass(Problem<T> P, State<T>
       unsigned *keys = S.gkeys + (size_t)s * N;
       GapItem it;
       if (pass == 0) {
-        it = gap_item<T>(P, S, sc, s, i);
+        it = gap_item<T>(P, S, sc, s, i, om[s], inv_om[s]);
         keys[i] = it.key;
-        if (it.key == 0xffffffffu) continue;
+        if (it.key == kKeyNone) continue;
+        if (it.key == kKeyInf) { ainf[s] += it.a; continue; }
       } else {
         const unsigned key = keys[i];
-        if (key == 0xffffffffu || (key >> pshift) != pref[s]) continue;
-        it = gap_item<T>(P, S, sc, s, i);
+        if (key >= kKeyInf || (key >> pshift) != pref[s]) continue;  // none, inf, other bucket
+        it = gap_item<T>(P, S, sc, s, i, om[s], inv_om[s]);
       }
       const int b = (int)((it.key >> shift) & (unsigned)(nb - 1));
       double *h = hist + (size_t)(s - s_begin) * 3 * kGapBuckets;
       atomicAdd(h + b, it.w);
       atomicAdd(h + kGapBuckets + b, it.v);
       atomicAdd(h + 2 * kGapBuckets + b, it.a);
+    }
+  }
+  if (pass == 0) {  // unbounded directions: their a goes to the +inf bucket, one atomic per warp
+    for (int s = s_begin; s < s_end; ++s) {
+      if (!act[s]) continue;
+      double t = ainf[s];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if ((threadIdx.x & 31) == 0 && t != 0.0)
+        atomicAdd(hist + (size_t)(s - s_begin) * 3 * kGapBuckets + 2 * kGapBuckets + (kKeyInf >> 21), t);
     }
   }
   __syncthreads();
@@ -543,7 +649,7 @@ __global__ void k_apply_restart(Problem<T> P, State<T> S) {
 
 // End of an evaluation: book-keeping of the restart and the loop conditions.
 __global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
-                         int has_inner) {
+                         int has_inner, int has_cond = 1) {
   if (s->restart) {
     s->mu0 = s->mu[2];
     s->sum_eta = 0.0;
@@ -556,8 +662,8 @@ __global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGra
   s->chunk_acc = 0;
   if (s->status == kRunning && time_up(s)) s->status = kTimeLimit;
   const bool run = s->status == kRunning;
-  cudaGraphSetConditional(h_outer, run ? 1u : 0u);
-  if (has_inner) cudaGraphSetConditional(h_inner, run ? 1u : 0u);
+  if (has_cond) cudaGraphSetConditional(h_outer, run ? 1u : 0u);
+  if (has_cond && has_inner) cudaGraphSetConditional(h_inner, run ? 1u : 0u);
 }
 
 // ------------------------------------------------------------- set-up / out
@@ -918,6 +1024,56 @@ template void launch_eval<float>(const Mat<float> &, const Mat<float> &, const P
                                  const State<float> &, cudaStream_t);
 template void launch_output<double>(const Problem<double> &, const State<double> &, cudaStream_t);
 template void launch_output<float>(const Problem<float> &, const State<float> &, cudaStream_t);
+// The same solve with every kernel launched from a host loop (no graph):
+// the state is read back after each step attempt and each evaluation.  Used
+// where graph kernels cannot be observed individually (profilers) and as a
+// fallback; the kernels and their order are those of the graph.
+template <typename T>
+cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                        const ScalarInit &in, double primal_importance, double *norm_part, const double *x0_dev,
+                        const double *y0_dev, int gap_grid, cudaStream_t st, Scalars *host) {
+  cudaError_t e;
+  const int N = P.n + P.m;
+  auto read = [&]() -> cudaError_t {
+    cudaError_t e2 = cudaMemcpyAsync(host, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    if (e2) return e2;
+    return cudaStreamSynchronize(st);
+  };
+  launch_problem_norms<T>(P, S.s, primal_importance, norm_part, 152, st);
+  k_init_scalars<<<1, 1, 0, st>>>(S.s, in);
+  k_init_point<T><<<(N + 255) / 256, 256, 0, st>>>(P, S, x0_dev, y0_dev);
+  launch_spmv<T>(K, S.x[0], S.Kx[0], st);
+  launch_eval<T>(K, KT, P, S, st);
+  k_finish<<<1, 1, 0, st>>>(S.s, 0, 0, 0, 0);
+  if ((e = cudaGetLastError()) || (e = read())) return e;
+  while (host->status == kRunning) {
+    for (;;) {
+      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+      k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
+      if ((e = cudaGetLastError()) || (e = read())) return e;
+      const bool go = host->status == kRunning && host->chunk_acc < host->eval_every &&
+                      host->k < host->iter_limit && host->attempts < host->attempt_limit;
+      if (!go) break;
+    }
+    launch_eval<T>(K, KT, P, S, st);
+    launch_gap<T>(P, S, 0, 2, 0, gap_grid, st);
+    k_decide<<<1, 1, 0, st>>>(S.s, S.trace);
+    k_apply_restart<T><<<(N + 255) / 256, 256, 0, st>>>(P, S);
+    launch_gap<T>(P, S, 2, 3, 1, gap_grid, st);
+    k_finish<<<1, 1, 0, st>>>(S.s, 0, 0, 0, 0);
+    if ((e = cudaGetLastError()) || (e = read())) return e;
+  }
+  launch_output<T>(P, S, st);
+  if ((e = cudaGetLastError())) return e;
+  return read();
+}
+
+template cudaError_t run_stepped<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                         const State<double> &, const ScalarInit &, double, double *,
+                                         const double *, const double *, int, cudaStream_t, Scalars *);
+template cudaError_t run_stepped<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                        const State<float> &, const ScalarInit &, double, double *,
+                                        const double *, const double *, int, cudaStream_t, Scalars *);
 template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
                                                const State<double> &, const ScalarInit &, double, double *,
                                                const double *, const double *, int, cudaStream_t,

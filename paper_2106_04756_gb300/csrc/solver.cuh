@@ -36,4 +36,9 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
                               const double *x0_dev, const double *y0_dev, int gap_grid, cudaStream_t st,
                               cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec);
 
+template <typename T>
+cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                        const ScalarInit &in, double primal_importance, double *norm_part, const double *x0_dev,
+                        const double *y0_dev, int gap_grid, cudaStream_t st, Scalars *host);
+
 }  // namespace pdlp

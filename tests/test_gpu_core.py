@@ -64,14 +64,14 @@ def test_normalized_gap_matches_oracle(gpu_lib, oracle_lib, name):
         g = ctx.get_scaled()
         Ks = sp.csr_matrix((g["Kval"], lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
         ylo = np.where(lp.ineq == 1, 0.0, -np.inf)
-        for trial in range(3):
+        for trial in range(6):
             lo = np.where(np.isfinite(g["ls"]), g["ls"], -5.0)
             hi = np.where(np.isfinite(g["us"]), g["us"], 5.0)
             x = np.clip(lo + (hi - lo) * rng.random(lp.n), g["ls"], g["us"])
             y = rng.standard_normal(lp.m)
             y = np.maximum(y, ylo)
             omega = float(np.exp(rng.uniform(-2, 2)))
-            r = float(rng.uniform(0.1, 10.0))
+            r = float(10.0 ** rng.uniform(-1, 3))  # small to larger than the box
             mu, val = ctx.normalized_gap(x, y, omega, r)
             gx = Ks.T @ y - g["cs"]
             gy = g["qs"] - Ks @ x
@@ -83,6 +83,33 @@ def test_normalized_gap_matches_oracle(gpu_lib, oracle_lib, name):
 # the PDHG trajectory; on the MIP-shaped instance they grow about 1000x per 40
 # iterations (measured: 1e-14 at k = 40, 7e-11 at k = 79, 7e-7 at k = 120).
 TRAJ_TOL = {20: 1e-9, 39: 1e-9, 120: 1e-5}
+
+
+@pytest.mark.parametrize("name", ["planted_200x500", "mip_2000x5000", "dense_row"])
+def test_normalized_gap_at_bound_points_matches_oracle(gpu_lib, oracle_lib, name):
+    """Points like PDHG iterates: 30% of x on a bound, 40% of inequality y at 0."""
+    lp = CASES[name]()
+    rng = np.random.default_rng(6)
+    with P.Context.from_lp(lp) as ctx:
+        g = ctx.get_scaled()
+        Ks = sp.csr_matrix((g["Kval"], lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+        ylo = np.where(lp.ineq == 1, 0.0, -np.inf)
+        for trial in range(6):
+            lo = np.where(np.isfinite(g["ls"]), g["ls"], -5.0)
+            hi = np.where(np.isfinite(g["us"]), g["us"], 5.0)
+            x = np.clip(lo + (hi - lo) * rng.random(lp.n), g["ls"], g["us"])
+            at = rng.random(lp.n) < 0.3
+            x[at] = np.where(rng.random(at.sum()) < 0.5, g["ls"][at], g["us"][at])
+            x = np.where(np.isfinite(x), x, 0.0)
+            y = np.maximum(rng.standard_normal(lp.m), ylo)
+            y[(lp.ineq == 1) & (rng.random(lp.m) < 0.4)] = 0.0
+            omega = float(np.exp(rng.uniform(-2, 2)))
+            r = float(10.0 ** rng.uniform(-1, 3))  # small to larger than the box
+            mu, val = ctx.normalized_gap(x, y, omega, r)
+            gx = Ks.T @ y - g["cs"]
+            gy = g["qs"] - Ks @ x
+            mu_ref, _ = oracle.normalized_gap(x, y, gx, gy, g["ls"], g["us"], ylo, omega, r)
+            assert abs(mu - mu_ref) <= 1e-6 * abs(mu_ref), (trial, mu, mu_ref)
 
 
 @pytest.mark.parametrize("name", ["planted_200x500", "mip_2000x5000", "dense_row"])
@@ -213,3 +240,15 @@ def test_restart_trace_matches_oracle(gpu_lib, oracle_lib, name):
         if abs(mu_c - mu_a) <= 2 * tol * max(abs(mu_c), abs(mu_a)):
             break
         assert a[5] == b[5] and a[6] == b[6], (a, b)
+
+
+@pytest.mark.parametrize("prec", [P.PDLP_FP64, P.PDLP_FP32_REFINE])
+def test_host_stepped_mode_equals_graph(gpu_lib, prec):
+    """use_graph = 0 launches the graph's kernels from a host loop: the same
+    kernels in the same order give the same bits."""
+    lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
+    kw = dict(precision=prec, iter_limit=600, refine_rounds=2)
+    xa, ya, ra = P.solve(lp, use_graph=1, **kw)
+    xb, yb, rb = P.solve(lp, use_graph=0, **kw)
+    assert ra["iters"] == rb["iters"] and ra["kkt_passes"] == rb["kkt_passes"]
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
