@@ -57,7 +57,7 @@ struct pdlp_ctx {
   DevBuf rp, ci, val, trp, tci, tval, perm;
   DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT;
   int32_t nblocksK = 0, nblocksKT = 0;
-  std::vector<RowBlock> hblocksK, hblocksKT;
+  std::vector<Chunk> hblocksK, hblocksKT;  // warp-chunk schedules
   // problem data
   DevBuf c, q, l, u, ylo;            // original space
   DevBuf cs, qs, ls, us, ylos;       // preconditioned (float64)
@@ -122,7 +122,8 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   K.rp = reinterpret_cast<const int32_t *>(ctx->rp.ptr());
   K.ci = reinterpret_cast<const int32_t *>(ctx->ci.ptr());
   K.val = val;
-  K.blocks = reinterpret_cast<const RowBlock *>(ctx->blocksK.ptr());
+  K.chunks = reinterpret_cast<const Chunk *>(ctx->blocksK.ptr());
+  K.nchunks = (int32_t)ctx->hblocksK.size();
   K.nblocks = ctx->nblocksK;
   K.longrows = reinterpret_cast<const LongRow *>(ctx->longK.ptr());
   K.seg_part = reinterpret_cast<double *>(ctx->segK.ptr());
@@ -132,7 +133,8 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   KT.rp = reinterpret_cast<const int32_t *>(ctx->trp.ptr());
   KT.ci = reinterpret_cast<const int32_t *>(ctx->tci.ptr());
   KT.val = tval;
-  KT.blocks = reinterpret_cast<const RowBlock *>(ctx->blocksKT.ptr());
+  KT.chunks = reinterpret_cast<const Chunk *>(ctx->blocksKT.ptr());
+  KT.nchunks = (int32_t)ctx->hblocksKT.size();
   KT.nblocks = ctx->nblocksKT;
   KT.longrows = reinterpret_cast<const LongRow *>(ctx->longKT.ptr());
   KT.seg_part = reinterpret_cast<double *>(ctx->segKT.ptr());
@@ -482,16 +484,15 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     int32_t segK = 0, segKT = 0;
     build_schedule(m, hrp.data(), ctx->hblocksK, lK, segK);
     build_schedule(n, htrp.data(), ctx->hblocksKT, lKT, segKT);
-    ctx->nblocksK = (int32_t)ctx->hblocksK.size();
-    ctx->nblocksKT = (int32_t)ctx->hblocksKT.size();
-    RowBlock *bK = dalloc<RowBlock>(ctx->blocksK, ctx->hblocksK.size()),
-             *bKT = dalloc<RowBlock>(ctx->blocksKT, ctx->hblocksKT.size());
+    ctx->nblocksK = (int32_t)((ctx->hblocksK.size() + kWarps - 1) / kWarps);
+    ctx->nblocksKT = (int32_t)((ctx->hblocksKT.size() + kWarps - 1) / kWarps);
+    Chunk *bK = dalloc<Chunk>(ctx->blocksK, ctx->hblocksK.size()), *bKT = dalloc<Chunk>(ctx->blocksKT, ctx->hblocksKT.size());
     LongRow *LK = dalloc<LongRow>(ctx->longK, lK.size()), *LKT = dalloc<LongRow>(ctx->longKT, lKT.size());
     double *sK = dalloc<double>(ctx->segK, 2 * (size_t)segK), *sKT = dalloc<double>(ctx->segKT, 2 * (size_t)segKT);
     unsigned *cK = dalloc<unsigned>(ctx->segcntK, lK.size()), *cKT = dalloc<unsigned>(ctx->segcntKT, lKT.size());
     if (!bK || !bKT || !LK || !LKT || !sK || !sKT || !cK || !cKT) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
-    CK(cudaMemcpy(bK, ctx->hblocksK.data(), sizeof(RowBlock) * ctx->hblocksK.size(), cudaMemcpyHostToDevice), "blocks");
-    CK(cudaMemcpy(bKT, ctx->hblocksKT.data(), sizeof(RowBlock) * ctx->hblocksKT.size(), cudaMemcpyHostToDevice), "blocks");
+    CK(cudaMemcpy(bK, ctx->hblocksK.data(), sizeof(Chunk) * ctx->hblocksK.size(), cudaMemcpyHostToDevice), "chunks");
+    CK(cudaMemcpy(bKT, ctx->hblocksKT.data(), sizeof(Chunk) * ctx->hblocksKT.size(), cudaMemcpyHostToDevice), "chunks");
     if (!lK.empty()) CK(cudaMemcpy(LK, lK.data(), sizeof(LongRow) * lK.size(), cudaMemcpyHostToDevice), "long rows");
     if (!lKT.empty()) CK(cudaMemcpy(LKT, lKT.data(), sizeof(LongRow) * lKT.size(), cudaMemcpyHostToDevice), "long rows");
     CK(cudaMemset(cK, 0, sizeof(unsigned) * std::max<size_t>(lK.size(), 1)), "memset");

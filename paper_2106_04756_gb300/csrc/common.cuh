@@ -5,13 +5,15 @@
 //   K^T CSR: built on the device by a stable radix sort of K's entries by column
 //   vectors: contiguous arrays of T (float64 or float32) per quantity
 //   scalars: one `Scalars` block (float64 / int64) read by every kernel
-// Sparse products use a CSR-stream scheme: rows are grouped into row blocks of
-// at most kNnzPerBlock nonzeros and kMaxRowsPerBlock rows; one CTA stages its
-// block's values and gathered vector entries in shared memory with coalesced
-// loads, then reduces each row with a power-of-two group of lanes.  Rows longer
-// than kNnzPerBlock are split into segments whose partial sums are combined, in
-// segment order, by the last segment CTA to finish.  All reductions are
-// deterministic: fixed thread-to-data assignment and fixed combination order.
+// Sparse products use a CSR-stream scheme at warp granularity: rows are
+// grouped into warp chunks of at most kChunkNnz nonzeros and kChunkRows rows;
+// each warp stages its chunk's values and gathered vector entries in its own
+// shared-memory slice with coalesced loads, reduces each row with a
+// power-of-two group of lanes and runs the fused epilogue one lane per row.
+// Longer rows are looped over by one warp; rows longer than kSegNnz are split
+// into segments whose partial sums are combined, in segment order, by the
+// last segment warp to finish.  All reductions are deterministic: fixed
+// thread-to-data assignment and fixed combination order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,31 +24,36 @@
 namespace pdlp {
 
 constexpr int kThreads = 256;          // CTA size of the sparse-product kernels
-constexpr int kNnzPerBlock = 2048;     // nonzeros staged per CTA
-constexpr int kMaxRowsPerBlock = 256;  // rows per CTA (one lane group per row)
+constexpr int kWarps = kThreads / 32;  // warps per CTA, one chunk per warp
+constexpr int kChunkNnz = 256;         // nonzeros staged per warp chunk
+constexpr int kChunkRows = 32;         // rows per warp chunk (one epilogue lane per row)
+constexpr int kSegNnz = 1024;          // rows longer than this are split across warps (<= 4 warp rounds each)
 constexpr int kGapBuckets = 2048;      // radix digit of the normalized-gap selection
 constexpr int kGapThreads = 512;
 constexpr int kGapSlots = 3;           // current, average, restart point
 
-// One CTA's share of a CSR matrix.  row_end < 0 marks a segment of a long row:
-// the long row index is -(row_end + 1).
-struct RowBlock {
+// One warp's share of a CSR matrix.  Three kinds:
+//   rows [row_begin, row_end) with at most kChunkNnz nonzeros and kChunkRows rows;
+//   one row (row_end = row_begin + 1) longer than kChunkNnz, looped over by the warp;
+//   row_end < 0: a segment [nnz_begin, nnz_end) of long row -(row_end + 1).
+struct Chunk {
   int32_t row_begin, row_end, nnz_begin, nnz_end;
 };
 
-// A row longer than kNnzPerBlock, processed by `nseg` consecutive CTAs.
+// A row longer than kSegNnz, processed by `nseg` warps (consecutive chunks).
 struct LongRow {
   int32_t row, nseg, part_off, pad;
 };
 
-// CSR matrix plus its row-block schedule.
+// CSR matrix plus its warp-chunk schedule.
 template <typename T>
 struct Mat {
   int32_t rows, cols;
   const int32_t *rp, *ci;
   const T *val;
-  const RowBlock *blocks;
-  int32_t nblocks;
+  const Chunk *chunks;
+  int32_t nchunks;
+  int32_t nblocks;        // CTAs = ceil(nchunks / kWarps)
   const LongRow *longrows;
   double *seg_part;       // one partial per long-row segment (per gathered vector)
   unsigned int *seg_cnt;  // arrival counter per long row
@@ -60,6 +67,9 @@ struct Scalars {
   // --- Algorithm 2 step control
   double eta;       // step size of the next attempt
   double omega;     // primal weight omega^n
+  double tau, sigma;  // eta / omega and eta * omega of the next attempt (Section 2)
+  double inv_omega;   // 1 / omega
+  double fac_red, fac_grow;  // Algorithm 2 factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 of this step
   double sum_eta;   // sum of accepted step sizes of this outer loop
   double dx2, dy2, inter, eta_bar;  // reductions of the last attempt
   // --- restart state (Section 3.2)
@@ -230,143 +240,169 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
 
 // ------------------------------------------------------- CSR-stream engine
 //
-// spmv_block computes, for the CTA's row block of `A`, the row sums
-// sum_k A_ik * v_a[col_k] for NV gathered vectors v_a, and calls
-// epi(row, sums) once per row: one thread per row with consecutive threads on
-// consecutive rows (coalesced epilogue), or thread 0 for a completed long row.
-//   phase 1: every thread loads kItems column indices and values (coalesced,
-//            all independent), then the kItems * NV gathered entries, and
-//            stages them in shared memory;
-//   phase 2: a power-of-two group of L lanes reduces each row from shared
-//            memory (L from the block's mean row length) into row sums;
-//   phase 3: the epilogue, one thread per row.
-// Shared memory: spmv_smem_bytes<T>(NV) at `sm`.
-constexpr int kItems = kNnzPerBlock / kThreads;
+// spmv_warp computes, for the calling warp's chunk of `A`, the row sums
+// sum_k A_ik * v_a[col_k] for NV gathered vectors v_a and calls
+// epi(row, sums) once per row: lane r for row r of a chunk (coalesced), or
+// lane 0 for a long row.  Warps work independently (no CTA barrier):
+//   staging: each lane loads up to kChunkNnz/32 column indices and values
+//            (coalesced, independent), then the gathered entries, into the
+//            warp's shared-memory slice;
+//   rows:    a power-of-two group of L lanes per row (L * rows <= 32) sums the
+//            row from shared memory, then shuffles;
+//   long rows: the warp loops over the row, kChunkNnz nonzeros per round;
+//   segments of rows longer than kSegNnz: warp partials combined, in segment
+//            order, by the last segment warp to arrive.
+// All sums have a fixed order (deterministic).  `wsm` is the warp's slice of
+// spmv_warp_smem<T>(NV) bytes; `active` is false for the idle warps of the
+// last CTA (they return at once).
+constexpr int kLaneItems = kChunkNnz / 32;
+
+template <typename T>
+__host__ __device__ constexpr size_t spmv_warp_smem(int nv) {
+  return (size_t)kChunkNnz * sizeof(T) * (1 + nv) + (size_t)kChunkRows * sizeof(T) * nv;
+}
 
 template <typename T>
 __host__ __device__ constexpr size_t spmv_smem_bytes(int nv) {
-  return (size_t)kNnzPerBlock * sizeof(T) * (1 + nv) + (size_t)kMaxRowsPerBlock * sizeof(T) * nv;
+  return spmv_warp_smem<T>(nv) * kWarps;
 }
 
 template <typename T, int NV, typename Epi>
-__device__ __forceinline__ void spmv_block(const Mat<T> &A, const T *const (&vec)[NV], char *sm,
-                                           Epi &&epi) {
-  const RowBlock rb = A.blocks[blockIdx.x];
-  T *sval = reinterpret_cast<T *>(sm);
-  T *sx = sval + kNnzPerBlock;
-  T *srow = sx + NV * kNnzPerBlock;
-  const int nb = rb.nnz_begin, cnt = rb.nnz_end - rb.nnz_begin;
-  {
-    int cj[kItems];
-    T v[kItems];
+__device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)[NV], char *sm_cta, Epi &&epi) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunk = blockIdx.x * kWarps + wid;
+  if (chunk >= A.nchunks) return;
+  T *sval = reinterpret_cast<T *>(sm_cta + spmv_warp_smem<T>(NV) * wid);
+  T *sx = sval + kChunkNnz;
+  T *srow = sx + NV * kChunkNnz;
+  const Chunk c = A.chunks[chunk];
+  const int nb = c.nnz_begin, cnt = c.nnz_end - c.nnz_begin;
+  if (c.row_end >= 0 && cnt <= kChunkNnz) {
+    {
+      int cj[kLaneItems];
+      T v[kLaneItems];
 #pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-      const int e = threadIdx.x + it * kThreads;
+      for (int it = 0; it < kLaneItems; ++it) {
+        const int e = lane + 32 * it;
+        cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
+        v[it] = e < cnt ? __ldg(A.val + nb + e) : T(0);
+      }
+      T xv[NV][kLaneItems];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+#pragma unroll
+        for (int it = 0; it < kLaneItems; ++it) {
+          const int e = lane + 32 * it;
+          xv[a][it] = e < cnt ? vec[a][cj[it]] : T(0);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < kLaneItems; ++it) {
+        const int e = lane + 32 * it;
+        if (e < cnt) {
+          sval[e] = v[it];
+#pragma unroll
+          for (int a = 0; a < NV; ++a) sx[a * kChunkNnz + e] = xv[a][it];
+        }
+      }
+    }
+    __syncwarp();
+    const int nrows = c.row_end - c.row_begin;
+    int L = 32;
+    while (L > 1 && L * nrows > 32) L >>= 1;
+    const int g = lane / L, gl = lane % L;
+    T acc[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] = T(0);
+    if (g < nrows) {
+      const int row = c.row_begin + g;
+      const int s = __ldg(A.rp + row) - nb, e = __ldg(A.rp + row + 1) - nb;
+      for (int k = s + gl; k < e; k += L) {
+        const T vv = sval[k];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kChunkNnz + k], acc[a]);
+      }
+    }
+    for (int o = L / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o, L);
+    }
+    if (g < nrows && gl == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) srow[a * kChunkRows + g] = acc[a];
+    }
+    __syncwarp();
+    if (lane < nrows) {
+      T s2[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s2[a] = srow[a * kChunkRows + lane];
+      epi(c.row_begin + lane, s2);
+    }
+    return;
+  }
+  // a long row or a segment of one: the warp loops, kChunkNnz nonzeros per round
+  T acc[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) acc[a] = T(0);
+  for (int base = 0; base < cnt; base += kChunkNnz) {
+    int cj[kLaneItems];
+    T v[kLaneItems];
+#pragma unroll
+    for (int it = 0; it < kLaneItems; ++it) {
+      const int e = base + lane + 32 * it;
       cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
       v[it] = e < cnt ? __ldg(A.val + nb + e) : T(0);
     }
-    T xv[NV][kItems];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-#pragma unroll
-      for (int it = 0; it < kItems; ++it) {
-        const int e = threadIdx.x + it * kThreads;
-        xv[a][it] = e < cnt ? vec[a][cj[it]] : T(0);
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < kItems; ++it) {
-      const int e = threadIdx.x + it * kThreads;
+    for (int it = 0; it < kLaneItems; ++it) {
+      const int e = base + lane + 32 * it;
       if (e < cnt) {
-        sval[e] = v[it];
 #pragma unroll
-        for (int a = 0; a < NV; ++a) sx[a * kNnzPerBlock + e] = xv[a][it];
+        for (int a = 0; a < NV; ++a) acc[a] = fma(v[it], vec[a][cj[it]], acc[a]);
       }
     }
   }
-  __syncthreads();
-  if (rb.row_end >= 0) {
-    const int nrows = rb.row_end - rb.row_begin;
-    const int avg = nrows > 0 ? cnt / nrows : 1;
-    int L = 1;
-    while (L < 32 && 2 * L <= avg) L *= 2;
-    const int groups = blockDim.x / L;
-    const int g = threadIdx.x / L, lane = threadIdx.x % L;
-    for (int r0 = 0; r0 < nrows; r0 += groups) {
-      const int r = r0 + g;
-      T acc[NV];
 #pragma unroll
-      for (int a = 0; a < NV; ++a) acc[a] = T(0);
-      if (r < nrows) {
-        const int row = rb.row_begin + r;
-        const int s = __ldg(A.rp + row) - nb, e = __ldg(A.rp + row + 1) - nb;
-        for (int k = s + lane; k < e; k += L) {
-          const T vv = sval[k];
+  for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-          for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kNnzPerBlock + k], acc[a]);
-        }
-      }
-      for (int o = L / 2; o > 0; o >>= 1) {
+    for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o);
+  }
+  if (c.row_end >= 0) {
+    if (lane == 0) epi(c.row_begin, acc);
+    return;
+  }
+  const int lr = -(c.row_end + 1);
+  const LongRow L = A.longrows[lr];
+  const int seg = (nb - __ldg(A.rp + L.row)) / kSegNnz;
+  int last = 0;
+  if (lane == 0) {
 #pragma unroll
-        for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o, L);
-      }
-      if (r < nrows && lane == 0) {
+    for (int a = 0; a < NV; ++a) A.seg_part[(size_t)(L.part_off + seg) * NV + a] = (double)acc[a];
+    __threadfence();
+    const unsigned prev = atomicAdd(A.seg_cnt + lr, 1u);
+    last = prev == (unsigned)(L.nseg - 1);
+    if (last) A.seg_cnt[lr] = 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  double tot[NV];
 #pragma unroll
-        for (int a = 0; a < NV; ++a) srow[a * kMaxRowsPerBlock + r] = acc[a];
-      }
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
-      T s[NV];
+  for (int a = 0; a < NV; ++a) tot[a] = 0.0;
+  for (int sg = lane; sg < L.nseg; sg += 32) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) s[a] = srow[a * kMaxRowsPerBlock + r];
-      epi(rb.row_begin + r, s);
-    }
-  } else {
-    // segment of a long row: CTA-wide partial; the last segment CTA to arrive
-    // combines all partials of the row (fixed thread-to-segment assignment)
-    const int lr = -(rb.row_end + 1);
-    const LongRow L = A.longrows[lr];
-    double acc[NV];
+    for (int a = 0; a < NV; ++a) tot[a] += __ldcg(A.seg_part + (size_t)(L.part_off + sg) * NV + a);
+  }
 #pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const T vv = sval[e];
+  for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) acc[a] = fma((double)vv, (double)sx[a * kNnzPerBlock + e], acc[a]);
-    }
-    __shared__ double red[NV * (kThreads / 32)];
-    block_sum<NV>(acc, red);
-    __shared__ int s_last;
-    if (threadIdx.x == 0) {
-      const int seg = (nb - __ldg(A.rp + L.row)) / kNnzPerBlock;
+    for (int a = 0; a < NV; ++a) tot[a] += __shfl_down_sync(0xffffffffu, tot[a], o);
+  }
+  if (lane == 0) {
+    T t2[NV];
 #pragma unroll
-      for (int a = 0; a < NV; ++a) A.seg_part[(size_t)(L.part_off + seg) * NV + a] = acc[a];
-      __threadfence();
-      const unsigned int prev = atomicAdd(A.seg_cnt + lr, 1u);
-      s_last = (prev == (unsigned)(L.nseg - 1));
-      if (s_last) A.seg_cnt[lr] = 0u;
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double tot[NV];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) tot[a] = 0.0;
-      for (int sg = threadIdx.x; sg < L.nseg; sg += blockDim.x) {
-#pragma unroll
-        for (int a = 0; a < NV; ++a) tot[a] += __ldcg(A.seg_part + (size_t)(L.part_off + sg) * NV + a);
-      }
-      __syncthreads();
-      block_sum<NV>(tot, red);
-      if (threadIdx.x == 0) {
-        T t2[NV];
-#pragma unroll
-        for (int a = 0; a < NV; ++a) t2[a] = (T)tot[a];
-        epi(L.row, t2);
-      }
-    }
-    __syncthreads();
+    for (int a = 0; a < NV; ++a) t2[a] = (T)tot[a];
+    epi(L.row, t2);
   }
 }
 

@@ -45,12 +45,11 @@ __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
   s->dx2 = dx2;
   s->dy2 = dy2;
   s->inter = inter;
-  const double num = omega * dx2 + dy2 / omega;
+  const double num = omega * dx2 + dy2 * s->inv_omega;
   const double den = 2.0 * fabs(inter);
   const double eta_bar = den > 0.0 ? num / den : INFINITY;
-  const double kk = (double)(s->k + 1);
-  const double e1 = (1.0 - pow(kk + 1.0, -0.3)) * eta_bar;
-  const double e2 = (1.0 + pow(kk + 1.0, -0.6)) * eta;
+  const double e1 = s->fac_red * eta_bar;  // factors of this step, computed by k_primal
+  const double e2 = s->fac_grow * eta;
   s->eta_bar = eta_bar;
   s->attempts += 1;
   if (!isfinite(num) || isnan(eta_bar) || isnan(inter)) {
@@ -64,6 +63,8 @@ __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
       s->chunk_acc += 1;
     }
     s->eta = e1 < e2 ? e1 : e2;
+    s->tau = s->eta * s->inv_omega;
+    s->sigma = s->eta * omega;
   }
   bool go = s->status == kRunning && s->chunk_acc < s->eval_every && s->k < s->iter_limit &&
             s->attempts < s->attempt_limit;
@@ -77,17 +78,28 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_primal(Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
   __shared__ double red[kThreads];
+  if (blockIdx.x == (unsigned)KT.nblocks) {
+    // one extra CTA: the Algorithm 2 factors of this step (k counted from 1),
+    // computed while the others run the sparse product; the step test of
+    // k_dual reads them
+    if (threadIdx.x == 0) {
+      Scalars *sw = S.s;
+      const double kk = (double)(sw->k + 1);
+      sw->fac_red = 1.0 - pow(kk + 1.0, -0.3);
+      sw->fac_grow = 1.0 + pow(kk + 1.0, -0.6);
+    }
+    return;
+  }
   const Scalars *sc = S.s;
   const int cur = sc->cur;
-  const double eta = sc->eta, omega = sc->omega;
-  const T tau = (T)(eta / omega), et = (T)eta;
+  const T tau = (T)sc->tau, et = (T)sc->eta;
   const T *x = S.x[cur];
   T *xn = S.x[cur ^ 1];
   const T *xs = S.xs[cur];
   T *xsn = S.xs[cur ^ 1];
   double acc[1] = {0.0};
   const T *const vec[1] = {S.y[cur]};
-  spmv_block<T, 1>(KT, vec, sm, [&](int j, const T(&g)[1]) {
+  spmv_warp<T, 1>(KT, vec, sm, [&](int j, const T(&g)[1]) {
     const T xj = x[j];
     const T xp = clampv<T>(xj - tau * (P.cs[j] - g[0]), P.ls[j], P.us[j]);
     xn[j] = xp;
@@ -106,13 +118,12 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Prob
   __shared__ double red[2 * kThreads];
   Scalars *sc = S.s;
   const int cur = sc->cur;
-  const double eta = sc->eta, omega = sc->omega;
-  const T sig = (T)(eta * omega), et = (T)eta;
+  const T sig = (T)sc->sigma, et = (T)sc->eta;
   const T *y = S.y[cur], *Kx = S.Kx[cur], *ys = S.ys[cur];
   T *yn = S.y[cur ^ 1], *Kxn = S.Kx[cur ^ 1], *ysn = S.ys[cur ^ 1];
   double acc[2] = {0.0, 0.0};
   const T *const vec[1] = {S.x[cur ^ 1]};
-  spmv_block<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
+  spmv_warp<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
     const T kxn = s[0], kx = Kx[i], yi = y[i], lo = P.ylos[i];
     const T v = yi + sig * (P.qs[i] - T(2) * kxn + kx);
     const T yp = v > lo ? v : lo;
@@ -155,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P,
 #pragma unroll
   for (int a = 0; a < 8; ++a) acc[a] = 0.0;
   const T *const vec[2] = {S.y[cur], S.ys[cur]};
-  spmv_block<T, 2>(KT, vec, sm, [&](int j, const T(&g)[2]) {
+  spmv_warp<T, 2>(KT, vec, sm, [&](int j, const T(&g)[2]) {
     S.KTy_cur[j] = g[0];
     S.KTys[j] = g[1];
     const double D2 = P.D2[j], cj = P.c[j], lj = P.l[j], uj = P.u[j], xr = (double)x0[j];
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, int nblocks_c,
 #pragma unroll
   for (int a = 0; a < 8; ++a) acc[a] = 0.0;
   const T *const vec[1] = {S.xs[cur]};
-  spmv_block<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
+  spmv_warp<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
     S.Kxbar[i] = s[0];
     const double D1 = P.D1[i], qi = P.q[i], lo = P.ylo[i], yr = (double)y0[i];
 #pragma unroll
@@ -609,6 +620,9 @@ __global__ void k_decide(Scalars *s, double *trace) {
   const double Dx = sqrt(dx2), Dy = sqrt(dy2);
   if (s->pw_update && Dx > s->eps_zero && Dy > s->eps_zero)
     s->omega = exp(s->pw_theta * log(Dy / Dx) + (1.0 - s->pw_theta) * log(s->omega));
+  s->inv_omega = 1.0 / s->omega;
+  s->tau = s->eta * s->inv_omega;
+  s->sigma = s->eta * s->omega;
   rec[7] = s->omega;
   // slot 2: mu_n(z^{n+1,0}, z^{n,0}) under the new primal weight
   const double r2 = s->omega * dx2 + dy2 / s->omega;
@@ -743,11 +757,14 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_spmv(Mat<T> A, const T *v, T *out) {
   extern __shared__ __align__(16) char sm[];
   const T *const vec[1] = {v};
-  spmv_block<T, 1>(A, vec, sm, [&](int i, const T(&s)[1]) { out[i] = s[0]; });
+  spmv_warp<T, 1>(A, vec, sm, [&](int i, const T(&s)[1]) { out[i] = s[0]; });
 }
 
 __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->eta = in.eta0;
+  s->inv_omega = 1.0 / s->omega;  // omega^0 was set by k_problem_norms
+  s->tau = in.eta0 * s->inv_omega;
+  s->sigma = in.eta0 * s->omega;
   s->sum_eta = 0.0;
   s->mu0 = INFINITY;
   s->muc_prev = INFINITY;
@@ -940,7 +957,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     if (!e) e = add_while(st2, h_inner, &body_inner);
     if (!e) e = cudaStreamBeginCaptureToGraph(st3, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (!e) {
-      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
+      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks + 1, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
       k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT.nblocks, P, S, h_inner, 1);
       cudaGraph_t tmp;
       e = cudaStreamEndCapture(st3, &tmp);
@@ -980,7 +997,7 @@ cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   double tp = 0.0, td = 0.0;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, st);
-    if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+    if (KT.nblocks > 0) k_primal<T><<<KT.nblocks + 1, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
     cudaEventRecord(e1, st);
     k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
     cudaEventRecord(e2, st);
@@ -1048,7 +1065,7 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
   if ((e = cudaGetLastError()) || (e = read())) return e;
   while (host->status == kRunning) {
     for (;;) {
-      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks + 1, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
       k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
       if ((e = cudaGetLastError()) || (e = read())) return e;
       const bool go = host->status == kRunning && host->chunk_acc < host->eval_every &&
