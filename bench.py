@@ -245,7 +245,7 @@ def main():
 
     # ---- roofline of the step kernels (CUDA events, same stream, state of a solve)
     ctx, _ = step(args.iter_cap, keep=True)
-    kp, kd = ctx.time_step_kernels(200)
+    kp, kd, _kc = ctx.time_step_kernels(200)
     ctx.close()
     bp, bd = _alg_bytes(lp, 64)
     peak, peak_src = _peaks()
@@ -260,7 +260,7 @@ def main():
                "primal_gbs": bp / (kp * 1e-3) / 1e9, "dual_gbs": bd / (kd * 1e-3) / 1e9}
     # float32 step kernels on the same workload
     ctx32, r32 = step(args.iter_cap, precision=P.PDLP_FP32, keep=True)
-    kp32, kd32 = ctx32.time_step_kernels(200)
+    kp32, kd32, _kc32 = ctx32.time_step_kernels(200)
     ctx32.close()
     bp32, bd32 = _alg_bytes(lp, 32)
     kernels.update({"fp32_primal_ms": kp32, "fp32_dual_ms": kd32,

@@ -92,7 +92,9 @@ typedef struct {
   int32_t use_graph;        /* 1: one CUDA graph per solve (conditional WHILE nodes);
                                0: the same kernels launched from a host loop that reads
                                the state after every step attempt (for profilers)       */
-  int32_t pad_;
+  int32_t persistent;       /* 1: all step attempts between two evaluations run in one
+                               cooperative kernel with grid-wide barriers; 0 (default):
+                               one launch per half-step (primal, dual)                  */
   void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
 } pdlp_options;
 
@@ -200,7 +202,11 @@ int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *cou
  * times outside the solve graph on the context's stream, bracketed by CUDA
  * events.  The attempts continue from the state the last solve left (call
  * pdlp_solve first).  ms[0], ms[1] (host) receive the mean durations in
- * milliseconds of the primal and the dual kernel. */
+ * milliseconds of the primal and the dual kernel; ms[2] receives the mean
+ * duration of one step attempt inside the persistent step kernel, timed over
+ * `reps` launches of it that each run up to eval_every accepted steps (0 when
+ * the context's `persistent` option is 0).  This call leaves the state
+ * advanced: solve again before reading results. */
 int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms);
 
 /* The normalized duality gap of pdlp_normalized_gap, for callers that cannot

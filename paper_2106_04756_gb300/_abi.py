@@ -42,7 +42,7 @@ class pdlp_options(C.Structure):
                 ("beta_suff", C.c_double), ("beta_nec", C.c_double), ("beta_art", C.c_double),
                 ("eps_zero", C.c_double), ("inner_tol", C.c_double), ("refine_rounds", C.c_int32),
                 ("unroll_T", C.c_int32), ("ckpt_every", C.c_int32), ("use_graph", C.c_int32),
-                ("pad_", C.c_int32), ("stream", C.c_void_p)]
+                ("persistent", C.c_int32), ("stream", C.c_void_p)]
 
 
 class pdlp_result(C.Structure):

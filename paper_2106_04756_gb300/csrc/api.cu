@@ -33,6 +33,7 @@ struct Precision {
   State<T> S;
   ScalarInit init{};
   double *normpart_ptr = nullptr;
+  int chunk_grid = 0;  // CTAs of the persistent step kernel (0: one launch per half-step)
   cudaGraphExec_t graph = nullptr;
   ~Precision() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -163,14 +164,18 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   S.x0 = take(n); S.y0 = take(m);
   S.KTy_cur = take(n); S.KTys = take(n);
   S.Kxbar = take(m);
+  pr.chunk_grid = 0;
+  if (ctx->opts.persistent) CK(chunk_grid<T>(&pr.chunk_grid), "persistent kernel occupancy");
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
-                    8 * (size_t)ctx->nblocksK + 16;
+                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.chunk_grid + 16;
   double *parts = dalloc<double>(pr.parts, np);
   if (!parts) return fail(ctx, PDLP_ERR_OOM, "partials allocation failed");
   S.part_p = parts;
   S.part_d = S.part_p + ctx->nblocksKT;
   S.part_ec = S.part_d + 2 * (size_t)ctx->nblocksK;
   S.part_er = S.part_ec + 8 * (size_t)ctx->nblocksKT;
+  S.part_cp = S.part_er + 8 * (size_t)ctx->nblocksK;
+  S.part_cd = S.part_cp + pr.chunk_grid;
   S.tickets = dalloc<unsigned>(pr.tickets, kNumTickets);
   S.gkeys = dalloc<unsigned>(pr.gkeys, (size_t)kGapSlots * N);
   S.ghist = dalloc<double>(pr.ghist, (size_t)kGapSlots * kGapBuckets * 3);
@@ -210,7 +215,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   }
   CK(build_solve_graph<T>(pr.K, pr.KT, pr.P, pr.S, in, o.primal_importance, normpart,
                           reinterpret_cast<const double *>(ctx->xin.ptr()),
-                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, ctx->cap[0],
+                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.chunk_grid, ctx->cap[0],
                           ctx->cap[1], ctx->cap[2], &pr.graph),
      "graph capture");
   pr.ready = true;
@@ -326,13 +331,15 @@ int run_graph(pdlp_ctx *ctx, Precision<T> &pr, Scalars *hs) {
   if (!ctx->opts.use_graph) {
     CK(run_stepped<T>(pr.K, pr.KT, pr.P, pr.S, pr.init, ctx->opts.primal_importance, pr.normpart_ptr,
                       reinterpret_cast<const double *>(ctx->xin.ptr()),
-                      reinterpret_cast<const double *>(ctx->yin.ptr()), 152, ctx->st, hs),
+                      reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.chunk_grid, ctx->st, hs),
        "stepped solve");
-    return PDLP_OK;
+  } else {
+    CK(cudaGraphLaunch(pr.graph, ctx->st), "graph launch");
+    CK(cudaMemcpyAsync(hs, pr.S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st), "scalars");
+    CK(cudaStreamSynchronize(ctx->st), "solve");
   }
-  CK(cudaGraphLaunch(pr.graph, ctx->st), "graph launch");
-  CK(cudaMemcpyAsync(hs, pr.S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, ctx->st), "scalars");
-  CK(cudaStreamSynchronize(ctx->st), "solve");
+  if (hs->status == kWaitTimeout || hs->err)
+    return fail(ctx, PDLP_ERR_TIMEOUT, "a grid-wide barrier of the persistent step kernel timed out");
   return PDLP_OK;
 }
 
@@ -348,7 +355,7 @@ int stage_start(pdlp_ctx *ctx, const double *x0, const double *y0) {
 int check_options(const pdlp_options *o, std::string &why) {
   if (!(o->rel_tol >= 0.0)) { why = "rel_tol must be >= 0"; return 0; }
   if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
-  if (o->eval_every < 1) { why = "eval_every must be >= 1"; return 0; }
+  if (o->eval_every < 1 || o->eval_every > kMaxEval) { why = "eval_every must be in [1, 256]"; return 0; }
   if (o->ruiz_iters < 0) { why = "ruiz_iters must be >= 0"; return 0; }
   if (o->iter_limit < 0 || o->kkt_pass_limit < 0) { why = "limits must be >= 0"; return 0; }
   if (!(o->primal_importance > 0.0)) { why = "primal_importance must be > 0"; return 0; }
@@ -384,6 +391,7 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->unroll_T = 0;
   o->ckpt_every = 50;
   o->use_graph = 1;
+  o->persistent = 0;
   o->stream = nullptr;
   return PDLP_OK;
 }
@@ -675,6 +683,17 @@ extern "C" int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms) {
   else
     return fail(ctx, PDLP_ERR_STATE, "no solver state for the context's precision");
   if (e) return cuda_fail(ctx, e, "time_step_kernels");
+  ms[2] = 0.f;
+  if (prec == PDLP_FP64 && ctx->p64.chunk_grid > 0)
+    e = time_chunk_kernel<double>(ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->p64.S, ctx->p64.chunk_grid, reps,
+                                  ctx->st, ms + 2);
+  else if (prec == PDLP_FP32 && ctx->p32.chunk_grid > 0)
+    e = time_chunk_kernel<float>(ctx->p32.K, ctx->p32.KT, ctx->p32.P, ctx->p32.S, ctx->p32.chunk_grid, reps,
+                                 ctx->st, ms + 2);
+  else if (prec == PDLP_FP32_REFINE && ctx->pc32.chunk_grid > 0)
+    e = time_chunk_kernel<float>(ctx->pc32.K, ctx->pc32.KT, ctx->pc32.P, ctx->pc32.S, ctx->pc32.chunk_grid,
+                                 reps, ctx->st, ms + 2);
+  if (e) return cuda_fail(ctx, e, "time_chunk_kernel");
   return PDLP_OK;
 }
 

@@ -31,6 +31,7 @@ constexpr int kSegNnz = 1024;          // rows longer than this are split across
 constexpr int kGapBuckets = 2048;      // radix digit of the normalized-gap selection
 constexpr int kGapThreads = 512;
 constexpr int kGapSlots = 3;           // current, average, restart point
+constexpr int kMaxEval = 256;          // largest eval_every (step-factor table size)
 
 // One warp's share of a CSR matrix.  Three kinds:
 //   rows [row_begin, row_end) with at most kChunkNnz nonzeros and kChunkRows rows;
@@ -60,7 +61,8 @@ struct Mat {
 };
 
 // Solver outcome codes (same values as the public PDLP_* status codes).
-enum : int { kRunning = 0, kOptimal = 1, kIterLimit = 2, kKktLimit = 3, kTimeLimit = 4, kNumErr = 5 };
+enum : int { kRunning = 0, kOptimal = 1, kIterLimit = 2, kKktLimit = 3, kTimeLimit = 4, kNumErr = 5,
+             kWaitTimeout = 6 };
 
 // Every scalar of Algorithm 1 / 2 / 3 and of the evaluation, in one block.
 struct Scalars {
@@ -69,7 +71,11 @@ struct Scalars {
   double omega;     // primal weight omega^n
   double tau, sigma;  // eta / omega and eta * omega of the next attempt (Section 2)
   double inv_omega;   // 1 / omega
-  double fac_red, fac_grow;  // Algorithm 2 factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 of this step
+  double fac_red, fac_grow;  // (unused)
+  // Algorithm 2 factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 for the steps
+  // k = fac_k0 + i of the current chunk (k counted from 1), filled by k_finish
+  double fac_tab[2][kMaxEval];
+  long long fac_k0;
   double sum_eta;   // sum of accepted step sizes of this outer loop
   double dx2, dy2, inter, eta_bar;  // reductions of the last attempt
   // --- restart state (Section 3.2)
@@ -134,6 +140,7 @@ struct State {
   T *x0, *y0;                  // restart point z^{n,0}
   T *KTy_cur, *KTys, *Kxbar;   // products at the evaluation
   double *part_p, *part_d;     // per-CTA partials of the primal / dual kernels
+  double *part_cp, *part_cd;   // per-CTA partials of the persistent chunk kernel
   double *part_ec, *part_er;   // per-CTA partials of the evaluation kernels
   unsigned int *tickets;       // arrival counters (one per kernel kind)
   Scalars *s;
@@ -143,7 +150,8 @@ struct State {
   double *trace;               // [kTraceCap][kTraceLen]
 };
 
-enum TicketId { kTicketDual = 0, kTicketEvalRows = 1, kTicketGap = 2, kTicketMisc = 3, kNumTickets = 8 };
+enum TicketId { kTicketDual = 0, kTicketEvalRows = 1, kTicketGap = 2, kTicketMisc = 3, kTicketBarCount = 4,
+                kTicketBarGen = 5, kTicketChunk = 6, kNumTickets = 8 };
 
 // ------------------------------------------------------------------ helpers
 
@@ -267,12 +275,19 @@ __host__ __device__ constexpr size_t spmv_smem_bytes(int nv) {
   return spmv_warp_smem<T>(nv) * kWarps;
 }
 
-template <typename T, int NV, typename Epi>
-__device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)[NV], char *sm_cta, Epi &&epi) {
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int chunk = blockIdx.x * kWarps + wid;
-  if (chunk >= A.nchunks) return;
-  T *sval = reinterpret_cast<T *>(sm_cta + spmv_warp_smem<T>(NV) * wid);
+// Loads of data other CTAs of the same launch may have written: through L2
+// only when CG (L1 is not coherent across SMs), plain otherwise.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <typename T, int NV, bool CG = false, typename Epi>
+__device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *const (&vec)[NV], char *wsm,
+                                           Epi &&epi) {
+  const int lane = threadIdx.x & 31;
+  T *sval = reinterpret_cast<T *>(wsm);
   T *sx = sval + kChunkNnz;
   T *srow = sx + NV * kChunkNnz;
   const Chunk c = A.chunks[chunk];
@@ -293,7 +308,7 @@ __device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)
 #pragma unroll
         for (int it = 0; it < kLaneItems; ++it) {
           const int e = lane + 32 * it;
-          xv[a][it] = e < cnt ? vec[a][cj[it]] : T(0);
+          xv[a][it] = e < cnt ? ldv<CG>(vec[a] + cj[it]) : T(0);
         }
       }
 #pragma unroll
@@ -358,7 +373,7 @@ __device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)
       const int e = base + lane + 32 * it;
       if (e < cnt) {
 #pragma unroll
-        for (int a = 0; a < NV; ++a) acc[a] = fma(v[it], vec[a][cj[it]], acc[a]);
+        for (int a = 0; a < NV; ++a) acc[a] = fma(v[it], ldv<CG>(vec[a] + cj[it]), acc[a]);
       }
     }
   }
@@ -404,6 +419,52 @@ __device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)
     for (int a = 0; a < NV; ++a) t2[a] = (T)tot[a];
     epi(L.row, t2);
   }
+}
+
+// One chunk per warp, chunk index from the CTA and warp position.
+template <typename T, int NV, typename Epi>
+__device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)[NV], char *sm_cta, Epi &&epi) {
+  const int wid = threadIdx.x >> 5;
+  const int chunk = blockIdx.x * kWarps + wid;
+  if (chunk >= A.nchunks) return;
+  spmv_chunk<T, NV, false>(A, chunk, vec, sm_cta + spmv_warp_smem<T>(NV) * wid, epi);
+}
+
+// Grid-wide barrier of a cooperative launch.  The wait is bounded by
+// kBarrierTimeoutNs of %globaltimer: on expiry (or if another CTA already
+// failed) it records the failure in *err and returns false without waiting.
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned *gen, int *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = gen;
+    volatile int *verr = err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      *count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = global_timer_ns();
+      while (*vgen == g) {
+        if (*verr || global_timer_ns() - t0 > kBarrierTimeoutNs) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok && !*verr;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 }  // namespace pdlp

@@ -14,6 +14,7 @@
 // gaps of Section 3.2 (radix selection of the trust-region breakpoint), the
 // restart decision (criteria (i)-(iii)) and the primal weight of Algorithm 3.
 #include <math.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "solver.cuh"
@@ -48,8 +49,18 @@ __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
   const double num = omega * dx2 + dy2 * s->inv_omega;
   const double den = 2.0 * fabs(inter);
   const double eta_bar = den > 0.0 ? num / den : INFINITY;
-  const double e1 = s->fac_red * eta_bar;  // factors of this step, computed by k_primal
-  const double e2 = s->fac_grow * eta;
+  const long long idx = s->k - s->fac_k0;
+  double fr, fg;
+  if (idx >= 0 && idx < s->eval_every && idx < kMaxEval) {
+    fr = s->fac_tab[0][idx];  // precomputed by k_finish for this chunk
+    fg = s->fac_tab[1][idx];
+  } else {
+    const double kk = (double)(s->k + 1);
+    fr = 1.0 - pow(kk + 1.0, -0.3);
+    fg = 1.0 + pow(kk + 1.0, -0.6);
+  }
+  const double e1 = fr * eta_bar;
+  const double e2 = fg * eta;
   s->eta_bar = eta_bar;
   s->attempts += 1;
   if (!isfinite(num) || isnan(eta_bar) || isnan(inter)) {
@@ -78,18 +89,6 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_primal(Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
   __shared__ double red[kThreads];
-  if (blockIdx.x == (unsigned)KT.nblocks) {
-    // one extra CTA: the Algorithm 2 factors of this step (k counted from 1),
-    // computed while the others run the sparse product; the step test of
-    // k_dual reads them
-    if (threadIdx.x == 0) {
-      Scalars *sw = S.s;
-      const double kk = (double)(sw->k + 1);
-      sw->fac_red = 1.0 - pow(kk + 1.0, -0.3);
-      sw->fac_grow = 1.0 + pow(kk + 1.0, -0.6);
-    }
-    return;
-  }
   const Scalars *sc = S.s;
   const int cur = sc->cur;
   const T tau = (T)sc->tau, et = (T)sc->eta;
@@ -145,6 +144,88 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Prob
     __syncthreads();
     sum_partials<2>(S.part_d, gridDim.x, 2, d, red);
     if (threadIdx.x == 0) accept_step(sc, p[0], d[0], d[1], h, has_cond);
+  }
+}
+
+// ------------------------------------------------- persistent chunk kernel
+//
+// One cooperative launch runs step attempts until eval_every steps have been
+// accepted (or a limit, an error or the attempt cap of the launch): per
+// attempt the primal phase (K^T y over the rows of K^T), a grid barrier, the
+// dual phase (K x' over the rows of K), the step test in the CTA that arrives
+// last, and a second barrier after which every CTA reads the decision.  Warps
+// take chunks round-robin.  Data written by other CTAs of the launch
+// (iterates, scalars) are read through L2 only.  Same arithmetic as
+// k_primal / k_dual.
+constexpr int kMaxAttemptsPerLaunch = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_chunk(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[2 * kThreads];
+  Scalars *sc = S.s;
+  const int wid = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kWarps + wid, nw = gridDim.x * kWarps;
+  char *wsm = sm + spmv_warp_smem<T>(1) * wid;
+  unsigned *bar_count = S.tickets + kTicketBarCount, *bar_gen = S.tickets + kTicketBarGen;
+  const int eval_every = sc->eval_every;
+  const long long iter_limit = sc->iter_limit, attempt_limit = sc->attempt_limit;
+  for (int att = 0; att < kMaxAttemptsPerLaunch; ++att) {
+    // the previous step test's results (written before the last barrier)
+    const int status = __ldcg(&sc->status), chunk_acc = __ldcg(&sc->chunk_acc), err = __ldcg(&sc->err);
+    const long long k = __ldcg(&sc->k), attempts = __ldcg(&sc->attempts);
+    if (status != kRunning || err || chunk_acc >= eval_every || k >= iter_limit || attempts >= attempt_limit) break;
+    const int cur = __ldcg(&sc->cur);
+    const T tau = (T)__ldcg(&sc->tau), sig = (T)__ldcg(&sc->sigma), et = (T)__ldcg(&sc->eta);
+    {
+      const T *x = S.x[cur], *xs = S.xs[cur];
+      T *xn = S.x[cur ^ 1], *xsn = S.xs[cur ^ 1];
+      double acc[1] = {0.0};
+      const T *const vec[1] = {S.y[cur]};
+      for (int ch = gw; ch < KT.nchunks; ch += nw)
+        spmv_chunk<T, 1, true>(KT, ch, vec, wsm, [&](int j, const T(&g)[1]) {
+          const T xj = __ldcg(x + j);
+          const T xp = clampv<T>(xj - tau * (P.cs[j] - g[0]), P.ls[j], P.us[j]);
+          xn[j] = xp;
+          xsn[j] = __ldcg(xs + j) + et * xp;
+          const T d = xp - xj;
+          acc[0] += (double)(d * d);
+        });
+      block_sum_lean<1>(acc, red);
+      if (threadIdx.x == 0) S.part_cp[blockIdx.x] = acc[0];
+    }
+    if (!grid_sync(bar_count, bar_gen, &sc->err)) break;
+    {
+      const T *y = S.y[cur], *Kx = S.Kx[cur], *ys = S.ys[cur];
+      T *yn = S.y[cur ^ 1], *Kxn = S.Kx[cur ^ 1], *ysn = S.ys[cur ^ 1];
+      double acc[2] = {0.0, 0.0};
+      const T *const vec[1] = {S.x[cur ^ 1]};
+      for (int ch = gw; ch < K.nchunks; ch += nw)
+        spmv_chunk<T, 1, true>(K, ch, vec, wsm, [&](int i, const T(&s)[1]) {
+          const T kxn = s[0], kx = __ldcg(Kx + i), yi = __ldcg(y + i), lo = P.ylos[i];
+          const T v = yi + sig * (P.qs[i] - T(2) * kxn + kx);
+          const T yp = v > lo ? v : lo;
+          yn[i] = yp;
+          Kxn[i] = kxn;
+          ysn[i] = __ldcg(ys + i) + et * yp;
+          const T dy = yp - yi, dk = kxn - kx;
+          acc[0] += (double)(dy * dy);
+          acc[1] += (double)dy * (double)dk;
+        });
+      block_sum_lean<2>(acc, red);
+      if (threadIdx.x == 0) {
+        S.part_cd[2 * blockIdx.x] = acc[0];
+        S.part_cd[2 * blockIdx.x + 1] = acc[1];
+      }
+    }
+    if (last_block(S.tickets + kTicketChunk)) {
+      double pp[1], dd[2];
+      sum_partials<1>(S.part_cp, gridDim.x, 1, pp, red);
+      __syncthreads();
+      sum_partials<2>(S.part_cd, gridDim.x, 2, dd, red);
+      if (threadIdx.x == 0) accept_step(sc, pp[0], dd[0], dd[1], 0, 0);
+    }
+    if (!grid_sync(bar_count, bar_gen, &sc->err)) break;
   }
 }
 
@@ -661,9 +742,30 @@ __global__ void k_apply_restart(Problem<T> P, State<T> S) {
   }
 }
 
-// End of an evaluation: book-keeping of the restart and the loop conditions.
+__device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
+                             int has_inner, int has_cond);
+
+// End of an evaluation: book-keeping of the restart and the loop conditions,
+// and the Algorithm 2 factors of the next chunk.
 __global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
                          int has_inner, int has_cond = 1) {
+  if (threadIdx.x == 0) {
+    finish_state(s, h_outer, h_inner, has_inner, has_cond);
+    s->fac_k0 = s->k;
+  }
+  __syncthreads();
+  // Algorithm 2 factors of the next chunk's steps (k counted from 1)
+  const long long k0 = s->fac_k0;
+  const int ne = s->eval_every < kMaxEval ? s->eval_every : kMaxEval;
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    const double kk = (double)(k0 + i + 1);
+    s->fac_tab[0][i] = 1.0 - pow(kk + 1.0, -0.3);
+    s->fac_tab[1][i] = 1.0 + pow(kk + 1.0, -0.6);
+  }
+}
+
+__device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
+                             int has_inner, int has_cond) {
   if (s->restart) {
     s->mu0 = s->mu[2];
     s->sum_eta = 0.0;
@@ -674,6 +776,7 @@ __global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGra
   }
   s->do_gap = 0;
   s->chunk_acc = 0;
+  if (s->err) s->status = kWaitTimeout;
   if (s->status == kRunning && time_up(s)) s->status = kTimeLimit;
   const bool run = s->status == kRunning;
   if (has_cond) cudaGraphSetConditional(h_outer, run ? 1u : 0u);
@@ -731,6 +834,7 @@ __global__ void k_problem_norms(Problem<T> P, Scalars *s, double primal_importan
 template <typename T>
 __global__ void k_init_point(Problem<T> P, State<T> S, const double *x0, const double *y0) {
   const int n = P.n, N = P.n + P.m;
+  if (blockIdx.x == 0 && threadIdx.x == 0) S.tickets[kTicketBarCount] = 0u;  // barrier arrivals of k_chunk
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     if (i < n) {
       const double v = x0 ? x0[i] / P.D2[i] : 0.0;
@@ -852,6 +956,43 @@ static void launch_gap(const Problem<T> &P, const State<T> &S, int s_begin, int 
 }
 
 template <typename T>
+cudaError_t launch_chunk(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, int grid,
+                         cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = spmv_smem<T>(1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_chunk<T>, K, KT, P, S);
+}
+
+// CTAs of the persistent kernel: every SM's resident maximum (cooperative
+// launches need all CTAs resident at once).
+template <typename T>
+cudaError_t chunk_grid(int *grid) {
+  cudaError_t e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev))) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  if ((e = cudaFuncSetAttribute(k_chunk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1))))
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chunk<T>, kThreads, spmv_smem<T>(1)))) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  // Two CTAs per SM measured best on 100k x 250k (fewer barrier arrivals than
+  // the occupancy maximum); PDLP_PERSISTENT_CTAS_PER_SM overrides it.
+  int want = 2;
+  if (const char *env = getenv("PDLP_PERSISTENT_CTAS_PER_SM")) want = atoi(env);
+  if (want >= 1 && want < per) per = want;
+  *grid = sms * per;
+  return cudaSuccess;
+}
+
+template <typename T>
 cudaError_t launch_gap_slots(const Problem<T> &P, const State<T> &S, int s_begin, int s_end, int when_restart,
                              int grid, cudaStream_t st) {
   launch_gap<T>(P, S, s_begin, s_end, when_restart, grid, st);
@@ -931,7 +1072,7 @@ static cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cuda
 template <typename T>
 cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               const ScalarInit &in, double primal_importance, double *norm_part,
-                              const double *x0_dev, const double *y0_dev, int gap_grid,
+                              const double *x0_dev, const double *y0_dev, int gap_grid, int chunk_grid_size,
                               cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec) {
   cudaError_t e;
   cudaGraph_t graph = nullptr;
@@ -948,16 +1089,30 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   e = capture_graph(st, &g);
   if (!e) e = cudaGraphConditionalHandleCreate(&h_outer, g, 0u, cudaGraphCondAssignDefault);
   if (!e) {
-    k_finish<<<1, 1, 0, st>>>(S.s, h_outer, h_outer, 0);  // loop entry decided by the check at the start
+    k_finish<<<1, 64, 0, st>>>(S.s, h_outer, h_outer, 0);  // loop entry decided by the check at the start
     e = add_while(st, h_outer, &body_outer);
   }
   if (!e) e = cudaStreamBeginCaptureToGraph(st2, body_outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (!e) {
+  if (!e && chunk_grid_size > 0) {
+    // one persistent cooperative kernel per chunk of step attempts
+    e = launch_chunk<T>(K, KT, P, S, chunk_grid_size, st2);
+    if (!e) {
+      launch_eval<T>(K, KT, P, S, st2);
+      launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
+      k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
+      k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
+      launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
+      k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_outer, 0);
+    }
+    cudaGraph_t tmp2;
+    cudaError_t e2 = cudaStreamEndCapture(st2, &tmp2);
+    if (!e) e = e2;
+  } else if (!e) {
     e = cudaGraphConditionalHandleCreate(&h_inner, body_outer, 1u, cudaGraphCondAssignDefault);
     if (!e) e = add_while(st2, h_inner, &body_inner);
     if (!e) e = cudaStreamBeginCaptureToGraph(st3, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (!e) {
-      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks + 1, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
+      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
       k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT.nblocks, P, S, h_inner, 1);
       cudaGraph_t tmp;
       e = cudaStreamEndCapture(st3, &tmp);
@@ -968,7 +1123,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
       k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
       k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
       launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
-      k_finish<<<1, 1, 0, st2>>>(S.s, h_outer, h_inner, 1);
+      k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_inner, 1);
     }
     cudaGraph_t tmp2;
     cudaError_t e2 = cudaStreamEndCapture(st2, &tmp2);
@@ -982,6 +1137,56 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   if (graph) cudaGraphDestroy(graph);
   return e;
 }
+
+// Reopens a finished state for timing: clears the chunk counter, the limits,
+// the status and the barrier counters.
+__global__ void k_reset_chunk(Scalars *s, unsigned *tickets) {
+  s->chunk_acc = 0;
+  s->status = kRunning;
+  s->err = 0;
+  s->iter_limit = 1ll << 62;
+  s->attempt_limit = 1ll << 62;
+  tickets[kTicketBarCount] = 0u;
+  tickets[kTicketChunk] = 0u;
+}
+
+// Mean duration of one step attempt inside the persistent kernel: `reps`
+// launches (each runs until eval_every steps are accepted), event-timed on
+// `st`, divided by the attempts they made.
+template <typename T>
+cudaError_t time_chunk_kernel(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                              int grid, int reps, cudaStream_t st, float *ms_attempt) {
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0))) return e;
+  if ((e = cudaEventCreate(&e1))) return e;
+  Scalars h0, h1;
+  double total = 0.0;
+  long long att = 0;
+  for (int r = 0; r < reps && !e; ++r) {
+    k_reset_chunk<<<1, 1, 0, st>>>(S.s, S.tickets);
+    cudaMemcpyAsync(&h0, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(e0, st);
+    e = launch_chunk<T>(K, KT, P, S, grid, st);
+    cudaEventRecord(e1, st);
+    cudaMemcpyAsync(&h1, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    float a = 0.f;
+    cudaEventElapsedTime(&a, e0, e1);
+    total += a;
+    att += h1.attempts - h0.attempts;
+    if (h1.status != kRunning || h1.err) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_attempt = att > 0 ? (float)(total / att) : 0.f;
+  return e;
+}
+
+template cudaError_t time_chunk_kernel<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                               const State<double> &, int, int, cudaStream_t, float *);
+template cudaError_t time_chunk_kernel<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                              const State<float> &, int, int, cudaStream_t, float *);
 
 // Times the two step kernels of one attempt outside the graph: `reps`
 // launches of k_primal then k_dual (no loop condition), each pair bracketed by
@@ -997,7 +1202,7 @@ cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   double tp = 0.0, td = 0.0;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, st);
-    if (KT.nblocks > 0) k_primal<T><<<KT.nblocks + 1, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+    if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
     cudaEventRecord(e1, st);
     k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
     cudaEventRecord(e2, st);
@@ -1021,6 +1226,12 @@ template cudaError_t time_step_kernels<double>(const Mat<double> &, const Mat<do
                                                const State<double> &, int, cudaStream_t, float *, float *);
 template cudaError_t time_step_kernels<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                               const State<float> &, int, cudaStream_t, float *, float *);
+template cudaError_t launch_chunk<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                          const State<double> &, int, cudaStream_t);
+template cudaError_t launch_chunk<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                         const State<float> &, int, cudaStream_t);
+template cudaError_t chunk_grid<double>(int *);
+template cudaError_t chunk_grid<float>(int *);
 template cudaError_t launch_gap_slots<double>(const Problem<double> &, const State<double> &, int, int, int, int,
                                               cudaStream_t);
 template cudaError_t launch_gap_slots<float>(const Problem<float> &, const State<float> &, int, int, int, int,
@@ -1048,7 +1259,7 @@ template void launch_output<float>(const Problem<float> &, const State<float> &,
 template <typename T>
 cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                         const ScalarInit &in, double primal_importance, double *norm_part, const double *x0_dev,
-                        const double *y0_dev, int gap_grid, cudaStream_t st, Scalars *host) {
+                        const double *y0_dev, int gap_grid, int chunk_grid_size, cudaStream_t st, Scalars *host) {
   cudaError_t e;
   const int N = P.n + P.m;
   auto read = [&]() -> cudaError_t {
@@ -1061,14 +1272,18 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
   k_init_point<T><<<(N + 255) / 256, 256, 0, st>>>(P, S, x0_dev, y0_dev);
   launch_spmv<T>(K, S.x[0], S.Kx[0], st);
   launch_eval<T>(K, KT, P, S, st);
-  k_finish<<<1, 1, 0, st>>>(S.s, 0, 0, 0, 0);
+  k_finish<<<1, 64, 0, st>>>(S.s, 0, 0, 0, 0);
   if ((e = cudaGetLastError()) || (e = read())) return e;
   while (host->status == kRunning) {
     for (;;) {
-      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks + 1, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
-      k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
+      if (chunk_grid_size > 0) {
+        if ((e = launch_chunk<T>(K, KT, P, S, chunk_grid_size, st))) return e;
+      } else {
+        if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+        k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
+      }
       if ((e = cudaGetLastError()) || (e = read())) return e;
-      const bool go = host->status == kRunning && host->chunk_acc < host->eval_every &&
+      const bool go = host->status == kRunning && !host->err && host->chunk_acc < host->eval_every &&
                       host->k < host->iter_limit && host->attempts < host->attempt_limit;
       if (!go) break;
     }
@@ -1077,7 +1292,7 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
     k_decide<<<1, 1, 0, st>>>(S.s, S.trace);
     k_apply_restart<T><<<(N + 255) / 256, 256, 0, st>>>(P, S);
     launch_gap<T>(P, S, 2, 3, 1, gap_grid, st);
-    k_finish<<<1, 1, 0, st>>>(S.s, 0, 0, 0, 0);
+    k_finish<<<1, 64, 0, st>>>(S.s, 0, 0, 0, 0);
     if ((e = cudaGetLastError()) || (e = read())) return e;
   }
   launch_output<T>(P, S, st);
@@ -1087,17 +1302,17 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
 
 template cudaError_t run_stepped<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
                                          const State<double> &, const ScalarInit &, double, double *,
-                                         const double *, const double *, int, cudaStream_t, Scalars *);
+                                         const double *, const double *, int, int, cudaStream_t, Scalars *);
 template cudaError_t run_stepped<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                         const State<float> &, const ScalarInit &, double, double *,
-                                        const double *, const double *, int, cudaStream_t, Scalars *);
+                                        const double *, const double *, int, int, cudaStream_t, Scalars *);
 template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
                                                const State<double> &, const ScalarInit &, double, double *,
-                                               const double *, const double *, int, cudaStream_t,
+                                               const double *, const double *, int, int, cudaStream_t,
                                                cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 template cudaError_t build_solve_graph<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                               const State<float> &, const ScalarInit &, double, double *,
-                                              const double *, const double *, int, cudaStream_t,
+                                              const double *, const double *, int, int, cudaStream_t,
                                               cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 
 }  // namespace pdlp

@@ -112,13 +112,15 @@ def test_normalized_gap_at_bound_points_matches_oracle(gpu_lib, oracle_lib, name
             assert abs(mu - mu_ref) <= 1e-6 * abs(mu_ref), (trial, mu, mu_ref)
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("name", ["planted_200x500", "mip_2000x5000", "dense_row"])
 @pytest.mark.parametrize("iters", [20, 39, 120])
-def test_first_iterates_match_oracle(gpu_lib, oracle_lib, name, iters):
+def test_first_iterates_match_oracle(gpu_lib, oracle_lib, name, iters, persistent):
     """Same algorithm, float64: iterates agree up to the rounding growth above
-    for the first steps; step and restart decisions match exactly."""
+    for the first steps; step and restart decisions match exactly.  Both step
+    engines: the persistent cooperative kernel and one launch per half-step."""
     lp = CASES[name]()
-    x_g, y_g, r_g = P.solve(lp, iter_limit=iters)
+    x_g, y_g, r_g = P.solve(lp, iter_limit=iters, persistent=persistent)
     x_o, y_o, r_o = oracle.solve(lp, iter_limit=iters)
     assert r_g["iters"] == r_o["iters"] == iters
     assert r_g["restarts"] == r_o["restarts"]
@@ -242,13 +244,46 @@ def test_restart_trace_matches_oracle(gpu_lib, oracle_lib, name):
         assert a[5] == b[5] and a[6] == b[6], (a, b)
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("prec", [P.PDLP_FP64, P.PDLP_FP32_REFINE])
-def test_host_stepped_mode_equals_graph(gpu_lib, prec):
+def test_host_stepped_mode_equals_graph(gpu_lib, prec, persistent):
     """use_graph = 0 launches the graph's kernels from a host loop: the same
     kernels in the same order give the same bits."""
     lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
-    kw = dict(precision=prec, iter_limit=600, refine_rounds=2)
+    kw = dict(precision=prec, iter_limit=600, refine_rounds=2, persistent=persistent)
     xa, ya, ra = P.solve(lp, use_graph=1, **kw)
     xb, yb, rb = P.solve(lp, use_graph=0, **kw)
     assert ra["iters"] == rb["iters"] and ra["kkt_passes"] == rb["kkt_passes"]
     assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+
+
+@pytest.mark.parametrize("prec", [P.PDLP_FP64, P.PDLP_FP32])
+def test_persistent_kernel_agrees_with_per_launch_steps(gpu_lib, prec):
+    """The persistent kernel runs the same half-steps; only the grouping of
+    the step-size reductions differs, so both engines take the same step and
+    restart decisions and reach the same point up to rounding."""
+    lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
+    xa, ya, ra = P.solve(lp, precision=prec, persistent=1, iter_limit=200)
+    xb, yb, rb = P.solve(lp, precision=prec, persistent=0, iter_limit=200)
+    assert ra["iters"] == rb["iters"] == 200
+    assert ra["kkt_passes"] == rb["kkt_passes"] and ra["restarts"] == rb["restarts"]
+    tol = 1e-9 if prec == P.PDLP_FP64 else 1e-3
+    assert np.abs(xa - xb).max() <= tol * max(1.0, np.abs(xb).max())
+    assert np.abs(ya - yb).max() <= tol * max(1.0, np.abs(yb).max())
+    # and a solve to tolerance ends in the same state
+    lp = lpgen.small_planted()
+    tol = 1e-8 if prec == P.PDLP_FP64 else 1e-4
+    _, _, ra = P.solve(lp, precision=prec, persistent=1, rel_tol=tol)
+    _, _, rb = P.solve(lp, precision=prec, persistent=0, rel_tol=tol)
+    assert ra["status_name"] == rb["status_name"] == "OPTIMAL"
+
+
+def test_step_kernel_timing_reports_the_persistent_attempt(gpu_lib):
+    lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
+    with P.Context.from_lp(lp, iter_limit=100, persistent=1) as ctx:
+        ctx.solve()
+        kp, kd, kc = ctx.time_step_kernels(5)
+        assert kp > 0 and kd > 0 and kc > 0
+    with P.Context.from_lp(lp, iter_limit=100, persistent=0) as ctx:
+        ctx.solve()
+        assert ctx.time_step_kernels(5)[2] == 0.0
