@@ -92,9 +92,11 @@ typedef struct {
   int32_t use_graph;        /* 1: one CUDA graph per solve (conditional WHILE nodes);
                                0: the same kernels launched from a host loop that reads
                                the state after every step attempt (for profilers)       */
-  int32_t persistent;       /* 1: all step attempts between two evaluations run in one
-                               cooperative kernel with grid-wide barriers; 0 (default):
-                               one launch per half-step (primal, dual)                  */
+  int32_t persistent;       /* 1 (default): all step attempts between two evaluations
+                               run in one cooperative kernel with grid-wide barriers
+                               (one CTA per SM); 0: one launch per half-step (primal,
+                               dual).  Where the kernel's layout does not fit, 1 runs
+                               as 0.                                                     */
   void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
 } pdlp_options;
 

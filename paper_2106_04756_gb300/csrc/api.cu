@@ -33,7 +33,7 @@ struct Precision {
   State<T> S;
   ScalarInit init{};
   double *normpart_ptr = nullptr;
-  int chunk_grid = 0;  // CTAs of the persistent step kernel (0: one launch per half-step)
+  PersistGeo pg{};  // persistent step kernel layout (grid 0: one launch per half-step)
   cudaGraphExec_t graph = nullptr;
   ~Precision() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -56,7 +56,8 @@ struct pdlp_ctx {
   std::string err;
   // matrix (float64 master copy, preconditioned in place)
   DevBuf rp, ci, val, trp, tci, tval, perm;
-  DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT;
+  DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT, lraccK, lraccKT;
+  int32_t nlongK = 0, nlongKT = 0;
   int32_t nblocksK = 0, nblocksKT = 0;
   std::vector<Chunk> hblocksK, hblocksKT;  // warp-chunk schedules
   // problem data
@@ -129,6 +130,8 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   K.longrows = reinterpret_cast<const LongRow *>(ctx->longK.ptr());
   K.seg_part = reinterpret_cast<double *>(ctx->segK.ptr());
   K.seg_cnt = reinterpret_cast<unsigned *>(ctx->segcntK.ptr());
+  K.lr_acc = reinterpret_cast<double *>(ctx->lraccK.ptr());
+  K.nlong = ctx->nlongK;
   KT.rows = ctx->n;
   KT.cols = ctx->m;
   KT.rp = reinterpret_cast<const int32_t *>(ctx->trp.ptr());
@@ -140,6 +143,8 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   KT.longrows = reinterpret_cast<const LongRow *>(ctx->longKT.ptr());
   KT.seg_part = reinterpret_cast<double *>(ctx->segKT.ptr());
   KT.seg_cnt = reinterpret_cast<unsigned *>(ctx->segcntKT.ptr());
+  KT.lr_acc = reinterpret_cast<double *>(ctx->lraccKT.ptr());
+  KT.nlong = ctx->nlongKT;
   return PDLP_OK;
 }
 
@@ -164,10 +169,9 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   S.x0 = take(n); S.y0 = take(m);
   S.KTy_cur = take(n); S.KTys = take(n);
   S.Kxbar = take(m);
-  pr.chunk_grid = 0;
-  if (ctx->opts.persistent) CK(chunk_grid<T>(&pr.chunk_grid), "persistent kernel occupancy");
+  CK(persist_plan<T>(ctx->hblocksKT, ctx->hblocksK, ctx->opts.persistent, &pr.pg), "persistent kernel layout");
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
-                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.chunk_grid + 16;
+                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + 16;
   double *parts = dalloc<double>(pr.parts, np);
   if (!parts) return fail(ctx, PDLP_ERR_OOM, "partials allocation failed");
   S.part_p = parts;
@@ -175,7 +179,6 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   S.part_ec = S.part_d + 2 * (size_t)ctx->nblocksK;
   S.part_er = S.part_ec + 8 * (size_t)ctx->nblocksKT;
   S.part_cp = S.part_er + 8 * (size_t)ctx->nblocksK;
-  S.part_cd = S.part_cp + pr.chunk_grid;
   S.tickets = dalloc<unsigned>(pr.tickets, kNumTickets);
   S.gkeys = dalloc<unsigned>(pr.gkeys, (size_t)kGapSlots * N);
   S.ghist = dalloc<double>(pr.ghist, (size_t)kGapSlots * kGapBuckets * 3);
@@ -215,7 +218,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   }
   CK(build_solve_graph<T>(pr.K, pr.KT, pr.P, pr.S, in, o.primal_importance, normpart,
                           reinterpret_cast<const double *>(ctx->xin.ptr()),
-                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.chunk_grid, ctx->cap[0],
+                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.pg, ctx->cap[0],
                           ctx->cap[1], ctx->cap[2], &pr.graph),
      "graph capture");
   pr.ready = true;
@@ -331,7 +334,7 @@ int run_graph(pdlp_ctx *ctx, Precision<T> &pr, Scalars *hs) {
   if (!ctx->opts.use_graph) {
     CK(run_stepped<T>(pr.K, pr.KT, pr.P, pr.S, pr.init, ctx->opts.primal_importance, pr.normpart_ptr,
                       reinterpret_cast<const double *>(ctx->xin.ptr()),
-                      reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.chunk_grid, ctx->st, hs),
+                      reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.pg, ctx->st, hs),
        "stepped solve");
   } else {
     CK(cudaGraphLaunch(pr.graph, ctx->st), "graph launch");
@@ -356,6 +359,7 @@ int check_options(const pdlp_options *o, std::string &why) {
   if (!(o->rel_tol >= 0.0)) { why = "rel_tol must be >= 0"; return 0; }
   if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
   if (o->eval_every < 1 || o->eval_every > kMaxEval) { why = "eval_every must be in [1, 256]"; return 0; }
+  if (o->persistent < 0 || o->persistent > 1) { why = "persistent must be 0 or 1"; return 0; }
   if (o->ruiz_iters < 0) { why = "ruiz_iters must be >= 0"; return 0; }
   if (o->iter_limit < 0 || o->kkt_pass_limit < 0) { why = "limits must be >= 0"; return 0; }
   if (!(o->primal_importance > 0.0)) { why = "primal_importance must be > 0"; return 0; }
@@ -391,7 +395,7 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->unroll_T = 0;
   o->ckpt_every = 50;
   o->use_graph = 1;
-  o->persistent = 0;
+  o->persistent = 1;
   o->stream = nullptr;
   return PDLP_OK;
 }
@@ -498,7 +502,11 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     LongRow *LK = dalloc<LongRow>(ctx->longK, lK.size()), *LKT = dalloc<LongRow>(ctx->longKT, lKT.size());
     double *sK = dalloc<double>(ctx->segK, 2 * (size_t)segK), *sKT = dalloc<double>(ctx->segKT, 2 * (size_t)segKT);
     unsigned *cK = dalloc<unsigned>(ctx->segcntK, lK.size()), *cKT = dalloc<unsigned>(ctx->segcntKT, lKT.size());
-    if (!bK || !bKT || !LK || !LKT || !sK || !sKT || !cK || !cKT) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+    double *aK = dalloc<double>(ctx->lraccK, kLrAcc * lK.size()), *aKT = dalloc<double>(ctx->lraccKT, kLrAcc * lKT.size());
+    ctx->nlongK = (int32_t)lK.size();
+    ctx->nlongKT = (int32_t)lKT.size();
+    if (!bK || !bKT || !LK || !LKT || !sK || !sKT || !cK || !cKT || !aK || !aKT)
+      return fail(ctx, PDLP_ERR_OOM, "allocation failed");
     CK(cudaMemcpy(bK, ctx->hblocksK.data(), sizeof(Chunk) * ctx->hblocksK.size(), cudaMemcpyHostToDevice), "chunks");
     CK(cudaMemcpy(bKT, ctx->hblocksKT.data(), sizeof(Chunk) * ctx->hblocksKT.size(), cudaMemcpyHostToDevice), "chunks");
     if (!lK.empty()) CK(cudaMemcpy(LK, lK.data(), sizeof(LongRow) * lK.size(), cudaMemcpyHostToDevice), "long rows");
@@ -684,16 +692,14 @@ extern "C" int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms) {
     return fail(ctx, PDLP_ERR_STATE, "no solver state for the context's precision");
   if (e) return cuda_fail(ctx, e, "time_step_kernels");
   ms[2] = 0.f;
-  if (prec == PDLP_FP64 && ctx->p64.chunk_grid > 0)
-    e = time_chunk_kernel<double>(ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->p64.S, ctx->p64.chunk_grid, reps,
-                                  ctx->st, ms + 2);
-  else if (prec == PDLP_FP32 && ctx->p32.chunk_grid > 0)
-    e = time_chunk_kernel<float>(ctx->p32.K, ctx->p32.KT, ctx->p32.P, ctx->p32.S, ctx->p32.chunk_grid, reps,
-                                 ctx->st, ms + 2);
-  else if (prec == PDLP_FP32_REFINE && ctx->pc32.chunk_grid > 0)
-    e = time_chunk_kernel<float>(ctx->pc32.K, ctx->pc32.KT, ctx->pc32.P, ctx->pc32.S, ctx->pc32.chunk_grid,
-                                 reps, ctx->st, ms + 2);
-  if (e) return cuda_fail(ctx, e, "time_chunk_kernel");
+  if (prec == PDLP_FP64 && ctx->p64.pg.grid > 0)
+    e = time_persist<double>(ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->p64.S, ctx->p64.pg, reps, ctx->st, ms + 2);
+  else if (prec == PDLP_FP32 && ctx->p32.pg.grid > 0)
+    e = time_persist<float>(ctx->p32.K, ctx->p32.KT, ctx->p32.P, ctx->p32.S, ctx->p32.pg, reps, ctx->st, ms + 2);
+  else if (prec == PDLP_FP32_REFINE && ctx->pc32.pg.grid > 0)
+    e = time_persist<float>(ctx->pc32.K, ctx->pc32.KT, ctx->pc32.P, ctx->pc32.S, ctx->pc32.pg, reps, ctx->st,
+                            ms + 2);
+  if (e) return cuda_fail(ctx, e, "time_persist");
   return PDLP_OK;
 }
 

@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "pdlp.h"
@@ -27,11 +28,12 @@ constexpr int kThreads = 256;          // CTA size of the sparse-product kernels
 constexpr int kWarps = kThreads / 32;  // warps per CTA, one chunk per warp
 constexpr int kChunkNnz = 256;         // nonzeros staged per warp chunk
 constexpr int kChunkRows = 32;         // rows per warp chunk (one epilogue lane per row)
-constexpr int kSegNnz = 1024;          // rows longer than this are split across warps (<= 4 warp rounds each)
+constexpr int kSegNnz = kChunkNnz;     // rows longer than this are split across warps, one chunk each
 constexpr int kGapBuckets = 2048;      // radix digit of the normalized-gap selection
 constexpr int kGapThreads = 512;
 constexpr int kGapSlots = 3;           // current, average, restart point
 constexpr int kMaxEval = 256;          // largest eval_every (step-factor table size)
+constexpr int kLrAcc = 8;              // epilogue sums kept per long row
 
 // One warp's share of a CSR matrix.  Three kinds:
 //   rows [row_begin, row_end) with at most kChunkNnz nonzeros and kChunkRows rows;
@@ -58,6 +60,8 @@ struct Mat {
   const LongRow *longrows;
   double *seg_part;       // one partial per long-row segment (per gathered vector)
   unsigned int *seg_cnt;  // arrival counter per long row
+  double *lr_acc;         // epilogue sums of each long row [nlong][kLrAcc]
+  int32_t nlong;
 };
 
 // Solver outcome codes (same values as the public PDLP_* status codes).
@@ -140,7 +144,7 @@ struct State {
   T *x0, *y0;                  // restart point z^{n,0}
   T *KTy_cur, *KTys, *Kxbar;   // products at the evaluation
   double *part_p, *part_d;     // per-CTA partials of the primal / dual kernels
-  double *part_cp, *part_cd;   // per-CTA partials of the persistent chunk kernel
+  double *part_cp;             // per-CTA partials of the persistent kernel [CTA][3]
   double *part_ec, *part_er;   // per-CTA partials of the evaluation kernels
   unsigned int *tickets;       // arrival counters (one per kernel kind)
   Scalars *s;
@@ -150,8 +154,10 @@ struct State {
   double *trace;               // [kTraceCap][kTraceLen]
 };
 
-enum TicketId { kTicketDual = 0, kTicketEvalRows = 1, kTicketGap = 2, kTicketMisc = 3, kTicketBarCount = 4,
-                kTicketBarGen = 5, kTicketChunk = 6, kNumTickets = 8 };
+// Arrival counters; [kTicketBar, kTicketBar + 1] hold the 64-bit barrier
+// counter of the persistent kernel (8-byte aligned).
+enum TicketId { kTicketDual = 0, kTicketEvalRows = 1, kTicketGap = 2, kTicketMisc = 3, kTicketBar = 4,
+                kNumTickets = 8 };
 
 // ------------------------------------------------------------------ helpers
 
@@ -230,6 +236,19 @@ __device__ __forceinline__ void sum_partials(const double *part, int count, int 
   block_sum<NV>(out, red);
 }
 
+// Fixed-order sum of the NA epilogue sums of A's long rows (after their
+// producers finished); result valid in thread 0.
+template <int NA, typename M>
+__device__ __forceinline__ void sum_long_rows(const M &A, double (&out)[NA], double *red) {
+#pragma unroll
+  for (int a = 0; a < NA; ++a) out[a] = 0.0;
+  for (int r = threadIdx.x; r < A.nlong; r += blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) out[a] += __ldcg(A.lr_acc + (size_t)r * kLrAcc + a);
+  }
+  block_sum<NA>(out, red);
+}
+
 // True in every thread of the CTA that arrives last at `ticket`; that CTA
 // also resets the ticket.  Writes made before the call are visible to it.
 __device__ __forceinline__ bool last_block(unsigned int *ticket) {
@@ -250,19 +269,21 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
 //
 // spmv_warp computes, for the calling warp's chunk of `A`, the row sums
 // sum_k A_ik * v_a[col_k] for NV gathered vectors v_a and calls
-// epi(row, sums) once per row: lane r for row r of a chunk (coalesced), or
-// lane 0 for a long row.  Warps work independently (no CTA barrier):
+// epi(row, sums, acc) once per row: lane r for row r of a chunk (coalesced),
+// or lane 0 for a long row.  `acc` is where the epilogue adds its NA
+// reduction terms: the caller's per-thread array, except for rows split into
+// segments, whose terms go to the row's own slot A.lr_acc[row][0..NA) (the
+// warp that runs that epilogue depends on timing; consumers add the slots in
+// row order after the per-CTA partials).  Warps work independently:
 //   staging: each lane loads up to kChunkNnz/32 column indices and values
 //            (coalesced, independent), then the gathered entries, into the
 //            warp's shared-memory slice;
 //   rows:    a power-of-two group of L lanes per row (L * rows <= 32) sums the
 //            row from shared memory, then shuffles;
-//   long rows: the warp loops over the row, kChunkNnz nonzeros per round;
 //   segments of rows longer than kSegNnz: warp partials combined, in segment
 //            order, by the last segment warp to arrive.
 // All sums have a fixed order (deterministic).  `wsm` is the warp's slice of
-// spmv_warp_smem<T>(NV) bytes; `active` is false for the idle warps of the
-// last CTA (they return at once).
+// spmv_warp_smem<T>(NV) bytes.
 constexpr int kLaneItems = kChunkNnz / 32;
 
 template <typename T>
@@ -283,9 +304,9 @@ __device__ __forceinline__ T ldv(const T *p) {
   else return *p;
 }
 
-template <typename T, int NV, bool CG = false, typename Epi>
+template <typename T, int NV, int NA, bool CG = false, typename Epi>
 __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *const (&vec)[NV], char *wsm,
-                                           Epi &&epi) {
+                                           double (&acc_out)[NA], Epi &&epi) {
   const int lane = threadIdx.x & 31;
   T *sval = reinterpret_cast<T *>(wsm);
   T *sx = sval + kChunkNnz;
@@ -351,7 +372,7 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
       T s2[NV];
 #pragma unroll
       for (int a = 0; a < NV; ++a) s2[a] = srow[a * kChunkRows + lane];
-      epi(c.row_begin + lane, s2);
+      epi(c.row_begin + lane, s2, acc_out);
     }
     return;
   }
@@ -383,7 +404,7 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
     for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o);
   }
   if (c.row_end >= 0) {
-    if (lane == 0) epi(c.row_begin, acc);
+    if (lane == 0) epi(c.row_begin, acc, acc_out);
     return;
   }
   const int lr = -(c.row_end + 1);
@@ -417,54 +438,159 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
     T t2[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) t2[a] = (T)tot[a];
-    epi(L.row, t2);
+    // the row's epilogue sums go to its own slot, summed in row order by the
+    // consumer, so the result does not depend on which warp finished last
+    double la[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) la[a] = 0.0;
+    epi(L.row, t2, la);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) A.lr_acc[(size_t)lr * kLrAcc + a] = la[a];
   }
 }
 
 // One chunk per warp, chunk index from the CTA and warp position.
-template <typename T, int NV, typename Epi>
-__device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)[NV], char *sm_cta, Epi &&epi) {
+template <typename T, int NV, int NA, typename Epi>
+__device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)[NV], char *sm_cta,
+                                          double (&acc)[NA], Epi &&epi) {
   const int wid = threadIdx.x >> 5;
   const int chunk = blockIdx.x * kWarps + wid;
   if (chunk >= A.nchunks) return;
-  spmv_chunk<T, NV, false>(A, chunk, vec, sm_cta + spmv_warp_smem<T>(NV) * wid, epi);
+  spmv_chunk<T, NV, NA, false>(A, chunk, vec, sm_cta + spmv_warp_smem<T>(NV) * wid, acc, epi);
 }
 
-// Grid-wide barrier of a cooperative launch.  The wait is bounded by
-// kBarrierTimeoutNs of %globaltimer: on expiry (or if another CTA already
-// failed) it records the failure in *err and returns false without waiting.
+// Grid-wide barrier of a cooperative launch on a monotonic 64-bit arrival
+// counter: the n-th barrier of a launch whose counter started at `base`
+// completes when the counter reaches base + n * gridDim.x.  The wait is
+// bounded by kBarrierTimeoutNs of %globaltimer: on expiry (or when another
+// CTA has already failed) it records the failure in *err and returns false.
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
-__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned *gen, int *err) {
+__device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned long long target, int *err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = gen;
+    volatile unsigned long long *vc = count;
     volatile int *verr = err;
-    const unsigned g = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    atomicAdd(count, 1ull);
     int ok = 1;
-    if (arrived == gridDim.x) {
-      *count = 0u;
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
+    if (*vc < target) {
       const unsigned long long t0 = global_timer_ns();
-      while (*vgen == g) {
-        if (*verr || global_timer_ns() - t0 > kBarrierTimeoutNs) {
+      unsigned spins = 0;
+      while (*vc < target) {
+        if ((++spins & 63u) == 0u && (*verr || global_timer_ns() - t0 > kBarrierTimeoutNs)) {
           atomicExch(err, 1);
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(8);
       }
     }
     __threadfence();
-    s_ok = ok && !*verr;
+    s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Step control of Algorithm 2 (the scalars one attempt reads and updates).
+struct StepCtl {
+  double eta, omega, inv_omega, tau, sigma, sum_eta;
+  double dx2, dy2, inter, eta_bar;
+  long long k, t, attempts;
+  int cur, chunk_acc, status, pad;
+};
+
+// Algorithm 2's test on the reductions of one attempt: eta_bar from the
+// omega-weighted movement and the magnitude of the interaction term (a zero
+// denominator gives eta_bar = +inf), acceptance iff eta <= eta_bar, then the
+// next step size min(fr * eta_bar, fg * eta) with the factors
+// fr = 1 - (k+1)^-0.3 and fg = 1 + (k+1)^-0.6 of the step count k before the
+// attempt (k counted from 1).
+__device__ __forceinline__ void step_update(StepCtl &c, double dx2, double dy2, double inter, double fr, double fg) {
+  c.dx2 = dx2;
+  c.dy2 = dy2;
+  c.inter = inter;
+  const double num = c.omega * dx2 + dy2 * c.inv_omega;
+  const double den = 2.0 * fabs(inter);
+  const double eta_bar = den > 0.0 ? num / den : INFINITY;
+  const double e1 = fr * eta_bar;
+  const double e2 = fg * c.eta;
+  c.eta_bar = eta_bar;
+  c.attempts += 1;
+  if (!isfinite(num) || isnan(eta_bar) || isnan(inter)) {
+    c.status = kNumErr;
+    return;
+  }
+  if (c.eta <= eta_bar) {
+    c.cur ^= 1;
+    c.sum_eta += c.eta;
+    c.k += 1;
+    c.t += 1;
+    c.chunk_acc += 1;
+  }
+  c.eta = e1 < e2 ? e1 : e2;
+  c.tau = c.eta * c.inv_omega;
+  c.sigma = c.eta * c.omega;
+}
+
+__device__ __forceinline__ void load_step(const Scalars *s, StepCtl &c) {
+  c.eta = s->eta;
+  c.omega = s->omega;
+  c.inv_omega = s->inv_omega;
+  c.tau = s->tau;
+  c.sigma = s->sigma;
+  c.sum_eta = s->sum_eta;
+  c.dx2 = s->dx2;
+  c.dy2 = s->dy2;
+  c.inter = s->inter;
+  c.eta_bar = s->eta_bar;
+  c.k = s->k;
+  c.t = s->t;
+  c.attempts = s->attempts;
+  c.cur = s->cur;
+  c.chunk_acc = s->chunk_acc;
+  c.status = s->status;
+}
+
+__device__ __forceinline__ void store_step(Scalars *s, const StepCtl &c) {
+  s->eta = c.eta;
+  s->tau = c.tau;
+  s->sigma = c.sigma;
+  s->sum_eta = c.sum_eta;
+  s->dx2 = c.dx2;
+  s->dy2 = c.dy2;
+  s->inter = c.inter;
+  s->eta_bar = c.eta_bar;
+  s->k = c.k;
+  s->t = c.t;
+  s->attempts = c.attempts;
+  s->cur = c.cur;
+  s->chunk_acc = c.chunk_acc;
+  s->status = c.status;
+}
+
+// Shared-memory layout of the persistent step kernel: each warp has a slice
+// of warp_bytes (its staging buffers, then the descriptors of its chunks of
+// K^T and of K at byte offsets o_desc_p, o_desc_d).  grid == 0: not used.
+struct PersistGeo {
+  int32_t grid;   // CTAs (all co-resident)
+  int32_t smem;   // dynamic shared memory per CTA
+  int32_t warp_bytes;
+  int32_t o_desc_p, o_desc_d;
+};
+
+// Algorithm 2's factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 for the next
+// eval_every steps k = fac_k0 + i + 1 (k counted from 1), by one CTA.
+__device__ __forceinline__ void fill_step_factors(Scalars *s) {
+  const long long k0 = s->fac_k0;
+  const int ne = s->eval_every < kMaxEval ? s->eval_every : kMaxEval;
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    const double kk = (double)(k0 + i + 1);
+    s->fac_tab[0][i] = 1.0 - pow(kk + 1.0, -0.3);
+    s->fac_tab[1][i] = 1.0 + pow(kk + 1.0, -0.6);
+  }
 }
 
 }  // namespace pdlp

@@ -1,0 +1,498 @@
+// Persistent cooperative step kernel: the inner loop of Algorithm 1 (step
+// attempts of Algorithm 2 between two evaluations, Section 3.1 / 3.4) in one
+// launch of one 512-thread CTA per SM.
+//
+// Per attempt:
+//   primal phase  x' = proj_X(x - tau (c - K^T y)) over the rows of K^T (eq. (3))
+//   grid barrier
+//   dual phase    y' = proj_Y(y + sigma (q - 2 K x' + K x)) over the rows of K
+//   grid barrier  (after each CTA published its partial sums)
+//   step test     every CTA sums all partials in the same fixed order and runs
+//                 Algorithm 2's test on its own copy of the step control, so all
+//                 CTAs take the same decision without a third barrier.
+//
+// Work placement: warp w of the grid owns the warp chunks w, w + W, w + 2W, ...
+// of K^T and of K (W warps in the grid) for the whole launch; their
+// descriptors are copied into the warp's shared-memory slice once per launch.
+// A warp keeps two chunks in flight: while one is reduced, the loads of the
+// next (column indices, then values, row starts and epilogue operands by
+// cp.async, and the gathered entries through L2) are outstanding.  The
+// phases are bound by the rate of scattered gathers.  Per-row arithmetic is
+// that of k_primal / k_dual; only the grouping of the three step-test sums
+// differs.
+#include <math.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.cuh"
+
+namespace pdlp {
+
+namespace {
+
+constexpr int kPThreads = 512;
+constexpr int kPWarps = kPThreads / 32;
+constexpr int kMaxAttemptsPerLaunch = 4096;
+__host__ __device__ inline int round16(int b) { return (b + 15) & ~15; }
+
+// Asynchronous global -> shared copies (cp.async, cached in L1).  Used only
+// for data no other CTA writes during the launch (matrix values, row starts
+// and the warp's own rows' operands); entries written by other CTAs (the
+// gathered vector) are loaded through L2 (ld.global.cg).
+template <typename T>
+__device__ __forceinline__ void cp_async(T *dst, const T *src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Per-warp staging buffer of one chunk in flight (kBufElems elements of T,
+// then kChunkRows + 1 ints of row starts in streaming mode).
+constexpr int kPre = 5;  // epilogue operands per row
+constexpr int kBufElems = 2 * kChunkNnz + kChunkRows + kPre * kChunkRows;
+template <typename T>
+__host__ __device__ constexpr int buf_bytes() {
+  return (int)((kBufElems * sizeof(T) + (kChunkRows + 1) * 4 + 15) / 16 * 16);
+}
+
+// Primal epilogue of eq. (3) for column j of K (row j of K^T).  Operands
+// x_j, xs_j, c_j, l_j, u_j are staged (pre[k * 32 + lane]) with the chunk.
+template <typename T>
+struct PrimalPhase {
+  const T *x, *xs, *cs, *ls, *us;
+  T *xn, *xsn;
+  T tau, et;
+  static constexpr int NA = 1;
+  double acc[NA];
+  __device__ __forceinline__ void stage(int j, T *pre) const {
+    cp_async(pre, x + j);
+    cp_async(pre + 32, xs + j);
+    cp_async(pre + 64, cs + j);
+    cp_async(pre + 96, ls + j);
+    cp_async(pre + 128, us + j);
+  }
+  __device__ __forceinline__ void load(int j, T *pre) const {
+    pre[0] = __ldcg(x + j);
+    pre[32] = __ldcg(xs + j);
+    pre[64] = cs[j];
+    pre[96] = ls[j];
+    pre[128] = us[j];
+  }
+  __device__ __forceinline__ void epi(int j, T g, const T *pre, double *a) {
+    const T xj = pre[0];
+    const T xp = clampv<T>(xj - tau * (pre[64] - g), pre[96], pre[128]);
+    xn[j] = xp;
+    xsn[j] = pre[32] + et * xp;
+    const T d = xp - xj;
+    a[0] += (double)(d * d);
+  }
+};
+
+// Dual epilogue of eq. (3) for row i of K, with the sums of Algorithm 2's
+// test.  Staged operands: (Kx)_i, y_i, ys_i, q_i, ylo_i.
+template <typename T>
+struct DualPhase {
+  const T *y, *Kx, *ys, *qs, *ylos;
+  T *yn, *Kxn, *ysn;
+  T sig, et;
+  static constexpr int NA = 2;
+  double acc[NA];
+  __device__ __forceinline__ void stage(int i, T *pre) const {
+    cp_async(pre, Kx + i);
+    cp_async(pre + 32, y + i);
+    cp_async(pre + 64, ys + i);
+    cp_async(pre + 96, qs + i);
+    cp_async(pre + 128, ylos + i);
+  }
+  __device__ __forceinline__ void load(int i, T *pre) const {
+    pre[0] = __ldcg(Kx + i);
+    pre[32] = __ldcg(y + i);
+    pre[64] = __ldcg(ys + i);
+    pre[96] = qs[i];
+    pre[128] = ylos[i];
+  }
+  __device__ __forceinline__ void epi(int i, T kxn, const T *pre, double *a) {
+    const T kx = pre[0], yi = pre[32], lo = pre[128];
+    const T v = yi + sig * (pre[96] - T(2) * kxn + kx);
+    const T yp = v > lo ? v : lo;
+    yn[i] = yp;
+    Kxn[i] = kxn;
+    ysn[i] = pre[64] + et * yp;
+    const T dy = yp - yi, dk = kxn - kx;
+    a[0] += (double)(dy * dy);
+    a[1] += (double)dy * (double)dk;
+  }
+};
+
+// Copies the descriptors of the warp's chunks (w, w + W, ...) into shared
+// memory; returns their count.
+template <typename T>
+__device__ int load_desc(const Mat<T> &A, int gw, int nw, Chunk *desc) {
+  const int count = gw < A.nchunks ? (A.nchunks - 1 - gw) / nw + 1 : 0;
+  for (int i = threadIdx.x & 31; i < count; i += 32) desc[i] = A.chunks[gw + i * nw];
+  __syncwarp();
+  return count;
+}
+
+// Reduces a staged chunk and runs its epilogue: rows of a normal chunk by
+// groups of L lanes (the arithmetic of spmv_chunk), segments of long rows by
+// a warp sum whose partials the last segment warp combines in segment order
+// (that row's reduction terms go to its slot A.lr_acc).
+template <typename T, typename Ph>
+__device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *buf, Ph &ph,
+                                       const T (&xg)[kLaneItems]) {
+  const int lane = threadIdx.x & 31;
+  T *sval = reinterpret_cast<T *>(buf);
+  T *sx = sval + kChunkNnz;
+  T *srow = sx + kChunkNnz;
+  T *pre = srow + kChunkRows;
+  const int *srp = reinterpret_cast<const int *>(sval + kBufElems);
+  const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
+  if (c.row_end >= 0) {
+    const int nrows = c.row_end - c.row_begin;
+#pragma unroll
+    for (int it = 0; it < kLaneItems; ++it) {
+      const int e = lane + 32 * it;
+      if (e < cnt) sx[e] = xg[it];
+    }
+    __syncwarp();
+    int L = 32;
+    while (L > 1 && L * nrows > 32) L >>= 1;
+    const int g = lane / L, gl = lane % L;
+    T acc = T(0);
+    if (g < nrows) {
+      const int s = srp[g] - nb;
+      const int e = g + 1 < nrows ? srp[g + 1] - nb : cnt;
+      for (int k = s + gl; k < e; k += L) acc = fma(sval[k], sx[k], acc);
+    }
+    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, L);
+    if (g < nrows && gl == 0) srow[g] = acc;
+    __syncwarp();
+    if (lane < nrows) ph.epi(c.row_begin + lane, srow[lane], pre + lane, ph.acc);
+    return;
+  }
+  T acc = T(0);
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    if (e < cnt) acc = fma(sval[e], xg[it], acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  const int lr = -(c.row_end + 1);
+  const LongRow LR = A.longrows[lr];
+  const int seg = (nb - __ldg(A.rp + LR.row)) / kSegNnz;
+  int last = 0;
+  if (lane == 0) {
+    A.seg_part[LR.part_off + seg] = (double)acc;
+    __threadfence();
+    const unsigned prev = atomicAdd(A.seg_cnt + lr, 1u);
+    last = prev == (unsigned)(LR.nseg - 1);
+    if (last) A.seg_cnt[lr] = 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  double tot = 0.0;
+  for (int sg = lane; sg < LR.nseg; sg += 32) tot += __ldcg(A.seg_part + LR.part_off + sg);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+  if (lane == 0) {
+    double la[Ph::NA];
+#pragma unroll
+    for (int a = 0; a < Ph::NA; ++a) la[a] = 0.0;
+    ph.load(LR.row, pre);
+    ph.epi(LR.row, (T)tot, pre, la);
+#pragma unroll
+    for (int a = 0; a < Ph::NA; ++a) A.lr_acc[(size_t)lr * kLrAcc + a] = la[a];
+  }
+}
+
+// Starts the loads of one chunk: column indices (global, to registers), then
+// values, row starts and epilogue operands by cp.async into the staging
+// buffer `buf`, and the gathered vector entries (through L2) into xg.
+template <typename T, typename Ph>
+__device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *vec, const Ph &ph, char *buf,
+                                      T (&xg)[kLaneItems]) {
+  const int lane = threadIdx.x & 31;
+  T *sval = reinterpret_cast<T *>(buf);
+  T *pre = sval + 2 * kChunkNnz + kChunkRows;
+  int *srp = reinterpret_cast<int *>(sval + kBufElems);
+  const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
+  const int nrows = c.row_end >= 0 ? c.row_end - c.row_begin : 0;
+  int cj[kLaneItems];
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
+    if (e < cnt) cp_async(sval + e, A.val + nb + e);
+  }
+  if (lane < nrows) {
+    cp_async(srp + lane, A.rp + c.row_begin + lane);
+    ph.stage(c.row_begin + lane, pre + lane);
+  }
+  cp_async_commit();
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    xg[it] = e < cnt ? __ldcg(vec + cj[it]) : T(0);
+  }
+}
+
+// One phase over the warp's chunks with two chunks in flight (two staging
+// buffers, gathered entries in registers a / b): the loads of chunk i + 2
+// start once chunk i is done.
+template <typename T, typename Ph>
+__device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, int count, const T *vec, char *wsm,
+                                          Ph &ph) {
+  char *b0 = wsm, *b1 = wsm + buf_bytes<T>();
+  T ga[kLaneItems], gb[kLaneItems];
+  if (count > 0) issue<T>(A, desc[0], vec, ph, b0, ga);
+  if (count > 1) issue<T>(A, desc[1], vec, ph, b1, gb);
+  for (int i = 0; i < count; i += 2) {
+    if (i + 1 < count)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
+    __syncwarp();
+    finish<T>(A, desc[i], b0, ph, ga);
+    __syncwarp();
+    if (i + 2 < count) issue<T>(A, desc[i + 2], vec, ph, b0, ga);
+    if (i + 1 < count) {
+      if (i + 2 < count)
+        cp_async_wait<1>();
+      else
+        cp_async_wait<0>();
+      __syncwarp();
+      finish<T>(A, desc[i + 1], b1, ph, gb);
+      __syncwarp();
+      if (i + 3 < count) issue<T>(A, desc[i + 3], vec, ph, b1, gb);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_persist(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S, PersistGeo geo) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[3 * kPWarps];
+  __shared__ double fac[2][kMaxEval];
+  __shared__ StepCtl ctl;
+  __shared__ long long s_fac_k0, s_iter_limit, s_attempt_limit;
+  __shared__ int s_eval_every;
+  __shared__ unsigned long long s_base;
+  Scalars *sc = S.s;
+  const int wid = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kPWarps + wid, nw = gridDim.x * kPWarps;
+  const unsigned long long G = gridDim.x;
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(S.tickets + kTicketBar);
+  char *wsm = sm + (size_t)geo.warp_bytes * wid;
+  Chunk *dp = reinterpret_cast<Chunk *>(wsm + geo.o_desc_p);
+  Chunk *dd = reinterpret_cast<Chunk *>(wsm + geo.o_desc_d);
+  if (threadIdx.x == 0) {
+    load_step(sc, ctl);
+    s_fac_k0 = sc->fac_k0;
+    s_iter_limit = sc->iter_limit;
+    s_attempt_limit = sc->attempt_limit;
+    s_eval_every = sc->eval_every;
+    // the counter is a multiple of G between launches; CTAs that already
+    // arrived at the first barrier add less than G
+    const unsigned long long c0 = *reinterpret_cast<volatile unsigned long long *>(bar);
+    s_base = c0 / G * G;
+  }
+  const int ne = sc->eval_every < kMaxEval ? sc->eval_every : kMaxEval;
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+    fac[0][i] = sc->fac_tab[0][i];
+    fac[1][i] = sc->fac_tab[1][i];
+  }
+  const int cnt_p = load_desc(KT, gw, nw, dp);
+  const int cnt_d = load_desc(K, gw, nw, dd);
+  __syncthreads();
+  unsigned long long target = s_base;
+  for (int att = 0; att < kMaxAttemptsPerLaunch; ++att) {
+    if (ctl.status != kRunning || ctl.chunk_acc >= s_eval_every || ctl.k >= s_iter_limit ||
+        ctl.attempts >= s_attempt_limit)
+      break;
+    const int cur = ctl.cur;
+    PrimalPhase<T> pp{S.x[cur], S.xs[cur], P.cs, P.ls, P.us, S.x[cur ^ 1], S.xs[cur ^ 1],
+                      (T)ctl.tau, (T)ctl.eta, {0.0}};
+    run_phase<T>(KT, dp, cnt_p, S.y[cur], wsm, pp);
+    target += G;
+    if (!grid_barrier(bar, target, &sc->err)) break;
+    DualPhase<T> dph{S.y[cur], S.Kx[cur], S.ys[cur], P.qs, P.ylos, S.y[cur ^ 1], S.Kx[cur ^ 1], S.ys[cur ^ 1],
+                     (T)ctl.sigma, (T)ctl.eta, {0.0, 0.0}};
+    run_phase<T>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
+    {
+      double v[3] = {pp.acc[0], dph.acc[0], dph.acc[1]};
+      block_sum<3>(v, red);
+      if (threadIdx.x == 0) {
+        S.part_cp[3 * blockIdx.x + 0] = v[0];
+        S.part_cp[3 * blockIdx.x + 1] = v[1];
+        S.part_cp[3 * blockIdx.x + 2] = v[2];
+      }
+    }
+    target += G;
+    if (!grid_barrier(bar, target, &sc->err)) break;
+    {
+      // the same fixed-order sum in every CTA, all loads in one round: each
+      // thread adds its per-CTA partials, then its rows split into segments
+      double t[3] = {0.0, 0.0, 0.0};
+      for (int b = threadIdx.x; b < (int)G; b += blockDim.x) {
+        t[0] += __ldcg(S.part_cp + 3 * b + 0);
+        t[1] += __ldcg(S.part_cp + 3 * b + 1);
+        t[2] += __ldcg(S.part_cp + 3 * b + 2);
+      }
+      for (int r = threadIdx.x; r < KT.nlong; r += blockDim.x) t[0] += __ldcg(KT.lr_acc + (size_t)r * kLrAcc);
+      for (int r = threadIdx.x; r < K.nlong; r += blockDim.x) {
+        t[1] += __ldcg(K.lr_acc + (size_t)r * kLrAcc);
+        t[2] += __ldcg(K.lr_acc + (size_t)r * kLrAcc + 1);
+      }
+      block_sum<3>(t, red);
+      if (threadIdx.x == 0) {
+        const long long idx = ctl.k - s_fac_k0;
+        double fr, fg;
+        if (idx >= 0 && idx < ne) {
+          fr = fac[0][idx];
+          fg = fac[1][idx];
+        } else {
+          const double kk = (double)(ctl.k + 1);
+          fr = 1.0 - pow(kk + 1.0, -0.3);
+          fg = 1.0 + pow(kk + 1.0, -0.6);
+        }
+        step_update(ctl, t[0], t[1], t[2], fr, fg);
+      }
+      __syncthreads();
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) store_step(sc, ctl);
+}
+
+// Reopens a finished state for timing: running status, no limits, a zero
+// barrier counter and the step factors of the next steps.
+__global__ void k_persist_reopen(Scalars *s, unsigned *tickets) {
+  if (threadIdx.x == 0) {
+    s->chunk_acc = 0;
+    s->status = kRunning;
+    s->err = 0;
+    s->iter_limit = 1ll << 62;
+    s->attempt_limit = 1ll << 62;
+    s->fac_k0 = s->k;
+    tickets[kTicketBar] = 0u;
+    tickets[kTicketBar + 1] = 0u;
+  }
+  __syncthreads();
+  fill_step_factors(s);
+}
+
+template <typename T>
+void layout(PersistGeo &g, int cmax_p, int cmax_d) {
+  g.o_desc_p = 2 * buf_bytes<T>();
+  g.o_desc_d = g.o_desc_p + 16 * cmax_p;
+  g.warp_bytes = round16(g.o_desc_d + 16 * cmax_d);
+  g.smem = g.warp_bytes * kPWarps;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t persist_plan(const std::vector<Chunk> &chunks_kt, const std::vector<Chunk> &chunks_k, int mode,
+                         PersistGeo *pg) {
+  *pg = PersistGeo{};
+  if (mode == 0) return cudaSuccess;
+  cudaError_t e;
+  int dev = 0, sms = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev))) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, k_persist<T>))) return e;
+  const int budget = optin - (int)fa.sharedSizeBytes;
+  const int grid = sms;
+  const int nw = grid * kPWarps;
+  PersistGeo g{};
+  g.grid = grid;
+  layout<T>(g, (int)((chunks_kt.size() + nw - 1) / nw), (int)((chunks_k.size() + nw - 1) / nw));
+  if (g.smem > budget) return cudaSuccess;  // too many chunks per warp: one launch per half-step
+  // the attribute is per kernel, shared by every context: set it to the budget
+  if ((e = cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
+  int per = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist<T>, kPThreads, g.smem))) return e;
+  if (per < 1) return cudaSuccess;
+  *pg = g;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                           const PersistGeo &pg, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)pg.grid);
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = (size_t)pg.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persist<T>, K, KT, P, S, pg);
+}
+
+// Mean duration of one step attempt inside the persistent kernel: `reps`
+// launches (each runs until eval_every steps are accepted), event-timed on
+// `st`, divided by the attempts they made.
+template <typename T>
+cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                         const PersistGeo &pg, int reps, cudaStream_t st, float *ms_attempt) {
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0))) return e;
+  if ((e = cudaEventCreate(&e1))) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  Scalars h0, h1;
+  double total = 0.0;
+  long long att = 0;
+  for (int r = 0; r < reps && !e; ++r) {
+    k_persist_reopen<<<1, 64, 0, st>>>(S.s, S.tickets);
+    if ((e = cudaMemcpyAsync(&h0, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st))) break;
+    cudaEventRecord(e0, st);
+    e = launch_persist<T>(K, KT, P, S, pg, st);
+    cudaEventRecord(e1, st);
+    if (!e) e = cudaMemcpyAsync(&h1, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) break;
+    float a = 0.f;
+    cudaEventElapsedTime(&a, e0, e1);
+    total += a;
+    att += h1.attempts - h0.attempts;
+    if (h1.status != kRunning || h1.err) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_attempt = att > 0 ? (float)(total / att) : 0.f;
+  return e;
+}
+
+#define PDLP_INST(T)                                                                                        \
+  template cudaError_t persist_plan<T>(const std::vector<Chunk> &, const std::vector<Chunk> &, int,          \
+                                       PersistGeo *);                                                       \
+  template cudaError_t launch_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &, \
+                                         const PersistGeo &, cudaStream_t);                                 \
+  template cudaError_t time_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &,   \
+                                       const PersistGeo &, int, cudaStream_t, float *);
+PDLP_INST(double)
+PDLP_INST(float)
+#undef PDLP_INST
+
+}  // namespace pdlp

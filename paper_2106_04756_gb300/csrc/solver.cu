@@ -36,49 +36,27 @@ __device__ __forceinline__ bool time_up(const Scalars *s) {
   return s->time_limit_ns != 0ull && global_timer_ns() - s->t0_ns > s->time_limit_ns;
 }
 
-// Algorithm 2's test and step-size update, run by one thread after the
-// reductions of an attempt.  The denominator is the magnitude of the
-// interaction term (so eta_bar >= 1/||K||_2 always); a zero denominator gives
-// eta_bar = +inf.  k counts steps from 1.
+// Algorithm 2's test and step-size update (step_update), run by one thread
+// after the reductions of an attempt, on the scalars in global memory; the
+// factors come from the table k_finish fills for the current chunk.
 __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
                             cudaGraphConditionalHandle h, int has_cond) {
-  const double omega = s->omega, eta = s->eta;
-  s->dx2 = dx2;
-  s->dy2 = dy2;
-  s->inter = inter;
-  const double num = omega * dx2 + dy2 * s->inv_omega;
-  const double den = 2.0 * fabs(inter);
-  const double eta_bar = den > 0.0 ? num / den : INFINITY;
-  const long long idx = s->k - s->fac_k0;
+  StepCtl c;
+  load_step(s, c);
+  const long long idx = c.k - s->fac_k0;
   double fr, fg;
   if (idx >= 0 && idx < s->eval_every && idx < kMaxEval) {
-    fr = s->fac_tab[0][idx];  // precomputed by k_finish for this chunk
+    fr = s->fac_tab[0][idx];
     fg = s->fac_tab[1][idx];
   } else {
-    const double kk = (double)(s->k + 1);
+    const double kk = (double)(c.k + 1);
     fr = 1.0 - pow(kk + 1.0, -0.3);
     fg = 1.0 + pow(kk + 1.0, -0.6);
   }
-  const double e1 = fr * eta_bar;
-  const double e2 = fg * eta;
-  s->eta_bar = eta_bar;
-  s->attempts += 1;
-  if (!isfinite(num) || isnan(eta_bar) || isnan(inter)) {
-    s->status = kNumErr;
-  } else {
-    if (eta <= eta_bar) {
-      s->cur ^= 1;
-      s->sum_eta += eta;
-      s->k += 1;
-      s->t += 1;
-      s->chunk_acc += 1;
-    }
-    s->eta = e1 < e2 ? e1 : e2;
-    s->tau = s->eta * s->inv_omega;
-    s->sigma = s->eta * omega;
-  }
-  bool go = s->status == kRunning && s->chunk_acc < s->eval_every && s->k < s->iter_limit &&
-            s->attempts < s->attempt_limit;
+  step_update(c, dx2, dy2, inter, fr, fg);
+  store_step(s, c);
+  bool go = c.status == kRunning && c.chunk_acc < s->eval_every && c.k < s->iter_limit &&
+            c.attempts < s->attempt_limit;
   if (go && time_up(s)) go = false;
   if (has_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
 }
@@ -98,20 +76,20 @@ __global__ void __launch_bounds__(kThreads) k_primal(Mat<T> KT, Problem<T> P, St
   T *xsn = S.xs[cur ^ 1];
   double acc[1] = {0.0};
   const T *const vec[1] = {S.y[cur]};
-  spmv_warp<T, 1>(KT, vec, sm, [&](int j, const T(&g)[1]) {
+  spmv_warp<T, 1>(KT, vec, sm, acc, [&](int j, const T(&g)[1], double(&a)[1]) {
     const T xj = x[j];
     const T xp = clampv<T>(xj - tau * (P.cs[j] - g[0]), P.ls[j], P.us[j]);
     xn[j] = xp;
     xsn[j] = xs[j] + et * xp;
     const T d = xp - xj;
-    acc[0] += (double)(d * d);
+    a[0] += (double)(d * d);
   });
   block_sum_lean<1>(acc, red);
   if (threadIdx.x == 0) S.part_p[blockIdx.x] = acc[0];
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Problem<T> P, State<T> S,
+__global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S,
                                                    cudaGraphConditionalHandle h, int has_cond) {
   extern __shared__ __align__(16) char sm[];
   __shared__ double red[2 * kThreads];
@@ -122,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Prob
   T *yn = S.y[cur ^ 1], *Kxn = S.Kx[cur ^ 1], *ysn = S.ys[cur ^ 1];
   double acc[2] = {0.0, 0.0};
   const T *const vec[1] = {S.x[cur ^ 1]};
-  spmv_warp<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
+  spmv_warp<T, 1>(K, vec, sm, acc, [&](int i, const T(&s)[1], double(&a)[2]) {
     const T kxn = s[0], kx = Kx[i], yi = y[i], lo = P.ylos[i];
     const T v = yi + sig * (P.qs[i] - T(2) * kxn + kx);
     const T yp = v > lo ? v : lo;
@@ -130,8 +108,8 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Prob
     Kxn[i] = kxn;
     ysn[i] = ys[i] + et * yp;
     const T dy = yp - yi, dk = kxn - kx;
-    acc[0] += (double)(dy * dy);
-    acc[1] += (double)dy * (double)dk;
+    a[0] += (double)(dy * dy);
+    a[1] += (double)dy * (double)dk;
   });
   block_sum_lean<2>(acc, red);
   if (threadIdx.x == 0) {
@@ -139,93 +117,15 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, int nblocks_p, Prob
     S.part_d[2 * blockIdx.x + 1] = acc[1];
   }
   if (last_block(S.tickets + kTicketDual)) {
-    double p[1], d[2];
-    sum_partials<1>(S.part_p, nblocks_p, 1, p, red);
+    double p[1], d[2], lp[1], ld[2];
+    sum_partials<1>(S.part_p, KT.nblocks, 1, p, red);
     __syncthreads();
     sum_partials<2>(S.part_d, gridDim.x, 2, d, red);
-    if (threadIdx.x == 0) accept_step(sc, p[0], d[0], d[1], h, has_cond);
-  }
-}
-
-// ------------------------------------------------- persistent chunk kernel
-//
-// One cooperative launch runs step attempts until eval_every steps have been
-// accepted (or a limit, an error or the attempt cap of the launch): per
-// attempt the primal phase (K^T y over the rows of K^T), a grid barrier, the
-// dual phase (K x' over the rows of K), the step test in the CTA that arrives
-// last, and a second barrier after which every CTA reads the decision.  Warps
-// take chunks round-robin.  Data written by other CTAs of the launch
-// (iterates, scalars) are read through L2 only.  Same arithmetic as
-// k_primal / k_dual.
-constexpr int kMaxAttemptsPerLaunch = 4096;
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_chunk(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S) {
-  extern __shared__ __align__(16) char sm[];
-  __shared__ double red[2 * kThreads];
-  Scalars *sc = S.s;
-  const int wid = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kWarps + wid, nw = gridDim.x * kWarps;
-  char *wsm = sm + spmv_warp_smem<T>(1) * wid;
-  unsigned *bar_count = S.tickets + kTicketBarCount, *bar_gen = S.tickets + kTicketBarGen;
-  const int eval_every = sc->eval_every;
-  const long long iter_limit = sc->iter_limit, attempt_limit = sc->attempt_limit;
-  for (int att = 0; att < kMaxAttemptsPerLaunch; ++att) {
-    // the previous step test's results (written before the last barrier)
-    const int status = __ldcg(&sc->status), chunk_acc = __ldcg(&sc->chunk_acc), err = __ldcg(&sc->err);
-    const long long k = __ldcg(&sc->k), attempts = __ldcg(&sc->attempts);
-    if (status != kRunning || err || chunk_acc >= eval_every || k >= iter_limit || attempts >= attempt_limit) break;
-    const int cur = __ldcg(&sc->cur);
-    const T tau = (T)__ldcg(&sc->tau), sig = (T)__ldcg(&sc->sigma), et = (T)__ldcg(&sc->eta);
-    {
-      const T *x = S.x[cur], *xs = S.xs[cur];
-      T *xn = S.x[cur ^ 1], *xsn = S.xs[cur ^ 1];
-      double acc[1] = {0.0};
-      const T *const vec[1] = {S.y[cur]};
-      for (int ch = gw; ch < KT.nchunks; ch += nw)
-        spmv_chunk<T, 1, true>(KT, ch, vec, wsm, [&](int j, const T(&g)[1]) {
-          const T xj = __ldcg(x + j);
-          const T xp = clampv<T>(xj - tau * (P.cs[j] - g[0]), P.ls[j], P.us[j]);
-          xn[j] = xp;
-          xsn[j] = __ldcg(xs + j) + et * xp;
-          const T d = xp - xj;
-          acc[0] += (double)(d * d);
-        });
-      block_sum_lean<1>(acc, red);
-      if (threadIdx.x == 0) S.part_cp[blockIdx.x] = acc[0];
-    }
-    if (!grid_sync(bar_count, bar_gen, &sc->err)) break;
-    {
-      const T *y = S.y[cur], *Kx = S.Kx[cur], *ys = S.ys[cur];
-      T *yn = S.y[cur ^ 1], *Kxn = S.Kx[cur ^ 1], *ysn = S.ys[cur ^ 1];
-      double acc[2] = {0.0, 0.0};
-      const T *const vec[1] = {S.x[cur ^ 1]};
-      for (int ch = gw; ch < K.nchunks; ch += nw)
-        spmv_chunk<T, 1, true>(K, ch, vec, wsm, [&](int i, const T(&s)[1]) {
-          const T kxn = s[0], kx = __ldcg(Kx + i), yi = __ldcg(y + i), lo = P.ylos[i];
-          const T v = yi + sig * (P.qs[i] - T(2) * kxn + kx);
-          const T yp = v > lo ? v : lo;
-          yn[i] = yp;
-          Kxn[i] = kxn;
-          ysn[i] = __ldcg(ys + i) + et * yp;
-          const T dy = yp - yi, dk = kxn - kx;
-          acc[0] += (double)(dy * dy);
-          acc[1] += (double)dy * (double)dk;
-        });
-      block_sum_lean<2>(acc, red);
-      if (threadIdx.x == 0) {
-        S.part_cd[2 * blockIdx.x] = acc[0];
-        S.part_cd[2 * blockIdx.x + 1] = acc[1];
-      }
-    }
-    if (last_block(S.tickets + kTicketChunk)) {
-      double pp[1], dd[2];
-      sum_partials<1>(S.part_cp, gridDim.x, 1, pp, red);
-      __syncthreads();
-      sum_partials<2>(S.part_cd, gridDim.x, 2, dd, red);
-      if (threadIdx.x == 0) accept_step(sc, pp[0], dd[0], dd[1], 0, 0);
-    }
-    if (!grid_sync(bar_count, bar_gen, &sc->err)) break;
+    __syncthreads();
+    sum_long_rows<1>(KT, lp, red);
+    __syncthreads();
+    sum_long_rows<2>(K, ld, red);
+    if (threadIdx.x == 0) accept_step(sc, p[0] + lp[0], d[0] + ld[0], d[1] + ld[1], h, has_cond);
   }
 }
 
@@ -247,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P,
 #pragma unroll
   for (int a = 0; a < 8; ++a) acc[a] = 0.0;
   const T *const vec[2] = {S.y[cur], S.ys[cur]};
-  spmv_warp<T, 2>(KT, vec, sm, [&](int j, const T(&g)[2]) {
+  spmv_warp<T, 2>(KT, vec, sm, acc, [&](int j, const T(&g)[2], double(&acc)[8]) {
     S.KTy_cur[j] = g[0];
     S.KTys[j] = g[1];
     const double D2 = P.D2[j], cj = P.c[j], lj = P.l[j], uj = P.u[j], xr = (double)x0[j];
@@ -324,7 +224,7 @@ __device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er
 // Rows: K xs (for K x_avg) and the row terms of Eq. (15) for both candidates.
 // Partial layout per CTA (8): [cand][pres^2, dobj(q^T y), |y - y0|^2, pobj extra].
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, int nblocks_c, Problem<T> P, State<T> S) {
+__global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
   __shared__ double red[8 * (kThreads / 32)];
   Scalars *sc = S.s;
@@ -336,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, int nblocks_c,
 #pragma unroll
   for (int a = 0; a < 8; ++a) acc[a] = 0.0;
   const T *const vec[1] = {S.xs[cur]};
-  spmv_warp<T, 1>(K, vec, sm, [&](int i, const T(&s)[1]) {
+  spmv_warp<T, 1>(K, vec, sm, acc, [&](int i, const T(&s)[1], double(&acc)[8]) {
     S.Kxbar[i] = s[0];
     const double D1 = P.D1[i], qi = P.q[i], lo = P.ylo[i], yr = (double)y0[i];
 #pragma unroll
@@ -360,11 +260,22 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, int nblocks_c,
     for (int a = 0; a < 8; ++a) S.part_er[8 * blockIdx.x + a] = acc[a];
   }
   if (last_block(S.tickets + kTicketEvalRows)) {
-    double ec[8], er[8];
-    sum_partials<8>(S.part_ec, nblocks_c, 8, ec, red);
+    double ec[8], er[8], lc[8], lr[8];
+    sum_partials<8>(S.part_ec, KT.nblocks, 8, ec, red);
     __syncthreads();
     sum_partials<8>(S.part_er, gridDim.x, 8, er, red);
-    if (threadIdx.x == 0) eval_finish(sc, ec, er);
+    __syncthreads();
+    sum_long_rows<8>(KT, lc, red);
+    __syncthreads();
+    sum_long_rows<8>(K, lr, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        ec[a] += lc[a];
+        er[a] += lr[a];
+      }
+      eval_finish(sc, ec, er);
+    }
   }
 }
 
@@ -754,14 +665,7 @@ __global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGra
     s->fac_k0 = s->k;
   }
   __syncthreads();
-  // Algorithm 2 factors of the next chunk's steps (k counted from 1)
-  const long long k0 = s->fac_k0;
-  const int ne = s->eval_every < kMaxEval ? s->eval_every : kMaxEval;
-  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
-    const double kk = (double)(k0 + i + 1);
-    s->fac_tab[0][i] = 1.0 - pow(kk + 1.0, -0.3);
-    s->fac_tab[1][i] = 1.0 + pow(kk + 1.0, -0.6);
-  }
+  fill_step_factors(s);  // for the next chunk's steps
 }
 
 __device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
@@ -834,7 +738,10 @@ __global__ void k_problem_norms(Problem<T> P, Scalars *s, double primal_importan
 template <typename T>
 __global__ void k_init_point(Problem<T> P, State<T> S, const double *x0, const double *y0) {
   const int n = P.n, N = P.n + P.m;
-  if (blockIdx.x == 0 && threadIdx.x == 0) S.tickets[kTicketBarCount] = 0u;  // barrier arrivals of k_chunk
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // barrier counter of the persistent kernel
+    S.tickets[kTicketBar] = 0u;
+    S.tickets[kTicketBar + 1] = 0u;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     if (i < n) {
       const double v = x0 ? x0[i] / P.D2[i] : 0.0;
@@ -861,7 +768,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_spmv(Mat<T> A, const T *v, T *out) {
   extern __shared__ __align__(16) char sm[];
   const T *const vec[1] = {v};
-  spmv_warp<T, 1>(A, vec, sm, [&](int i, const T(&s)[1]) { out[i] = s[0]; });
+  double none[1] = {0.0};
+  spmv_warp<T, 1>(A, vec, sm, none, [&](int i, const T(&s)[1], double(&)[1]) { out[i] = s[0]; });
 }
 
 __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
@@ -956,43 +864,6 @@ static void launch_gap(const Problem<T> &P, const State<T> &S, int s_begin, int 
 }
 
 template <typename T>
-cudaError_t launch_chunk(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, int grid,
-                         cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = spmv_smem<T>(1);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_chunk<T>, K, KT, P, S);
-}
-
-// CTAs of the persistent kernel: every SM's resident maximum (cooperative
-// launches need all CTAs resident at once).
-template <typename T>
-cudaError_t chunk_grid(int *grid) {
-  cudaError_t e;
-  int dev = 0, sms = 0, per = 0;
-  if ((e = cudaGetDevice(&dev))) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-  if ((e = cudaFuncSetAttribute(k_chunk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1))))
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chunk<T>, kThreads, spmv_smem<T>(1)))) return e;
-  if (per < 1) return cudaErrorInvalidConfiguration;
-  // Two CTAs per SM measured best on 100k x 250k (fewer barrier arrivals than
-  // the occupancy maximum); PDLP_PERSISTENT_CTAS_PER_SM overrides it.
-  int want = 2;
-  if (const char *env = getenv("PDLP_PERSISTENT_CTAS_PER_SM")) want = atoi(env);
-  if (want >= 1 && want < per) per = want;
-  *grid = sms * per;
-  return cudaSuccess;
-}
-
-template <typename T>
 cudaError_t launch_gap_slots(const Problem<T> &P, const State<T> &S, int s_begin, int s_end, int when_restart,
                              int grid, cudaStream_t st) {
   launch_gap<T>(P, S, s_begin, s_end, when_restart, grid, st);
@@ -1022,7 +893,7 @@ void launch_init(const Problem<T> &P, const State<T> &S, const Mat<T> &K, const 
 template <typename T>
 void launch_eval(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, cudaStream_t st) {
   if (KT.nblocks > 0) k_eval_cols<T><<<KT.nblocks, kThreads, spmv_smem<T>(2), st>>>(KT, P, S);
-  k_eval_rows<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S);
+  k_eval_rows<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S);
 }
 
 template <typename T>
@@ -1072,7 +943,7 @@ static cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cuda
 template <typename T>
 cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               const ScalarInit &in, double primal_importance, double *norm_part,
-                              const double *x0_dev, const double *y0_dev, int gap_grid, int chunk_grid_size,
+                              const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
                               cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec) {
   cudaError_t e;
   cudaGraph_t graph = nullptr;
@@ -1093,9 +964,9 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     e = add_while(st, h_outer, &body_outer);
   }
   if (!e) e = cudaStreamBeginCaptureToGraph(st2, body_outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (!e && chunk_grid_size > 0) {
+  if (!e && pg.grid > 0) {
     // one persistent cooperative kernel per chunk of step attempts
-    e = launch_chunk<T>(K, KT, P, S, chunk_grid_size, st2);
+    e = launch_persist<T>(K, KT, P, S, pg, st2);
     if (!e) {
       launch_eval<T>(K, KT, P, S, st2);
       launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
@@ -1113,7 +984,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     if (!e) e = cudaStreamBeginCaptureToGraph(st3, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (!e) {
       if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
-      k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT.nblocks, P, S, h_inner, 1);
+      k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT, P, S, h_inner, 1);
       cudaGraph_t tmp;
       e = cudaStreamEndCapture(st3, &tmp);
     }
@@ -1138,56 +1009,6 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   return e;
 }
 
-// Reopens a finished state for timing: clears the chunk counter, the limits,
-// the status and the barrier counters.
-__global__ void k_reset_chunk(Scalars *s, unsigned *tickets) {
-  s->chunk_acc = 0;
-  s->status = kRunning;
-  s->err = 0;
-  s->iter_limit = 1ll << 62;
-  s->attempt_limit = 1ll << 62;
-  tickets[kTicketBarCount] = 0u;
-  tickets[kTicketChunk] = 0u;
-}
-
-// Mean duration of one step attempt inside the persistent kernel: `reps`
-// launches (each runs until eval_every steps are accepted), event-timed on
-// `st`, divided by the attempts they made.
-template <typename T>
-cudaError_t time_chunk_kernel(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
-                              int grid, int reps, cudaStream_t st, float *ms_attempt) {
-  cudaEvent_t e0, e1;
-  cudaError_t e;
-  if ((e = cudaEventCreate(&e0))) return e;
-  if ((e = cudaEventCreate(&e1))) return e;
-  Scalars h0, h1;
-  double total = 0.0;
-  long long att = 0;
-  for (int r = 0; r < reps && !e; ++r) {
-    k_reset_chunk<<<1, 1, 0, st>>>(S.s, S.tickets);
-    cudaMemcpyAsync(&h0, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(e0, st);
-    e = launch_chunk<T>(K, KT, P, S, grid, st);
-    cudaEventRecord(e1, st);
-    cudaMemcpyAsync(&h1, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
-    if (!e) e = cudaStreamSynchronize(st);
-    float a = 0.f;
-    cudaEventElapsedTime(&a, e0, e1);
-    total += a;
-    att += h1.attempts - h0.attempts;
-    if (h1.status != kRunning || h1.err) break;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  *ms_attempt = att > 0 ? (float)(total / att) : 0.f;
-  return e;
-}
-
-template cudaError_t time_chunk_kernel<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
-                                               const State<double> &, int, int, cudaStream_t, float *);
-template cudaError_t time_chunk_kernel<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
-                                              const State<float> &, int, int, cudaStream_t, float *);
-
 // Times the two step kernels of one attempt outside the graph: `reps`
 // launches of k_primal then k_dual (no loop condition), each pair bracketed by
 // CUDA events on `st`.  The attempts advance the iterate like a solve does.
@@ -1204,7 +1025,7 @@ cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     cudaEventRecord(e0, st);
     if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
     cudaEventRecord(e1, st);
-    k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
+    k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
     cudaEventRecord(e2, st);
     if ((e = cudaEventSynchronize(e2))) break;
     float a = 0.f, b = 0.f;
@@ -1226,12 +1047,6 @@ template cudaError_t time_step_kernels<double>(const Mat<double> &, const Mat<do
                                                const State<double> &, int, cudaStream_t, float *, float *);
 template cudaError_t time_step_kernels<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                               const State<float> &, int, cudaStream_t, float *, float *);
-template cudaError_t launch_chunk<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
-                                          const State<double> &, int, cudaStream_t);
-template cudaError_t launch_chunk<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
-                                         const State<float> &, int, cudaStream_t);
-template cudaError_t chunk_grid<double>(int *);
-template cudaError_t chunk_grid<float>(int *);
 template cudaError_t launch_gap_slots<double>(const Problem<double> &, const State<double> &, int, int, int, int,
                                               cudaStream_t);
 template cudaError_t launch_gap_slots<float>(const Problem<float> &, const State<float> &, int, int, int, int,
@@ -1259,7 +1074,7 @@ template void launch_output<float>(const Problem<float> &, const State<float> &,
 template <typename T>
 cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                         const ScalarInit &in, double primal_importance, double *norm_part, const double *x0_dev,
-                        const double *y0_dev, int gap_grid, int chunk_grid_size, cudaStream_t st, Scalars *host) {
+                        const double *y0_dev, int gap_grid, const PersistGeo &pg, cudaStream_t st, Scalars *host) {
   cudaError_t e;
   const int N = P.n + P.m;
   auto read = [&]() -> cudaError_t {
@@ -1276,11 +1091,11 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
   if ((e = cudaGetLastError()) || (e = read())) return e;
   while (host->status == kRunning) {
     for (;;) {
-      if (chunk_grid_size > 0) {
-        if ((e = launch_chunk<T>(K, KT, P, S, chunk_grid_size, st))) return e;
+      if (pg.grid > 0) {
+        if ((e = launch_persist<T>(K, KT, P, S, pg, st))) return e;
       } else {
         if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
-        k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT.nblocks, P, S, 0, 0);
+        k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
       }
       if ((e = cudaGetLastError()) || (e = read())) return e;
       const bool go = host->status == kRunning && !host->err && host->chunk_acc < host->eval_every &&
@@ -1302,17 +1117,17 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
 
 template cudaError_t run_stepped<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
                                          const State<double> &, const ScalarInit &, double, double *,
-                                         const double *, const double *, int, int, cudaStream_t, Scalars *);
+                                         const double *, const double *, int, const PersistGeo &, cudaStream_t, Scalars *);
 template cudaError_t run_stepped<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                         const State<float> &, const ScalarInit &, double, double *,
-                                        const double *, const double *, int, int, cudaStream_t, Scalars *);
+                                        const double *, const double *, int, const PersistGeo &, cudaStream_t, Scalars *);
 template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
                                                const State<double> &, const ScalarInit &, double, double *,
-                                               const double *, const double *, int, int, cudaStream_t,
+                                               const double *, const double *, int, const PersistGeo &, cudaStream_t,
                                                cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 template cudaError_t build_solve_graph<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                               const State<float> &, const ScalarInit &, double, double *,
-                                              const double *, const double *, int, int, cudaStream_t,
+                                              const double *, const double *, int, const PersistGeo &, cudaStream_t,
                                               cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 
 }  // namespace pdlp

@@ -1,6 +1,8 @@
 // Launchers of the iteration kernels (solver.cu).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace pdlp {
@@ -33,19 +35,23 @@ template <typename T> void launch_output(const Problem<T> &P, const State<T> &S,
 template <typename T>
 cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               const ScalarInit &in, double primal_importance, double *norm_part,
-                              const double *x0_dev, const double *y0_dev, int gap_grid, int chunk_grid_size,
+                              const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
                               cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec);
+// Persistent step kernel (persistent.cu).  mode 0: off.  Leaves pg->grid = 0
+// when the kernel's layout does not fit.
 template <typename T>
-cudaError_t launch_chunk(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, int grid,
-                         cudaStream_t st);
-template <typename T> cudaError_t chunk_grid(int *grid);
+cudaError_t persist_plan(const std::vector<Chunk> &chunks_kt, const std::vector<Chunk> &chunks_k, int mode,
+                         PersistGeo *pg);
 template <typename T>
-cudaError_t time_chunk_kernel(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
-                              int grid, int reps, cudaStream_t st, float *ms_attempt);
+cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                           const PersistGeo &pg, cudaStream_t st);
+template <typename T>
+cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                         const PersistGeo &pg, int reps, cudaStream_t st, float *ms_attempt);
 
 template <typename T>
 cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                         const ScalarInit &in, double primal_importance, double *norm_part, const double *x0_dev,
-                        const double *y0_dev, int gap_grid, int chunk_grid_size, cudaStream_t st, Scalars *host);
+                        const double *y0_dev, int gap_grid, const PersistGeo &pg, cudaStream_t st, Scalars *host);
 
 }  // namespace pdlp
