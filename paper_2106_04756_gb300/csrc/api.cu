@@ -169,6 +169,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   S.x0 = take(n); S.y0 = take(m);
   S.KTy_cur = take(n); S.KTys = take(n);
   S.Kxbar = take(m);
+  S.eta_log = nullptr;
   CK(persist_plan<T>(ctx->hblocksKT, ctx->hblocksK, ctx->opts.persistent, &pr.pg), "persistent kernel layout");
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
                     8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + 16;
@@ -714,19 +715,27 @@ extern "C" void pdlp_destroy(pdlp_ctx *ctx) { delete ctx; }
 extern "C" int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const double *x0, const double *y0,
                            double *x_out, double *y_out, double *eta_out) {
   if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
-  if (T < 1 || ckpt_every < 1) return fail(ctx, PDLP_ERR_INVALID_ARG, "T and ckpt_every must be >= 1");
+  if (T < 1 || ckpt_every < 1 || ckpt_every > kMaxEval)
+    return fail(ctx, PDLP_ERR_INVALID_ARG, "need T >= 1 and 1 <= ckpt_every <= 256");
   int rc = setup_fp64(ctx);
   if (rc) return rc;
   rc = stage_start(ctx, x0, y0);
   if (rc) return rc;
-  Problem<double> P = ctx->p64.P;
-  cudaError_t e = unroll_forward(ctx->unr, ctx->p64.K, ctx->p64.KT, P, ctx->eta0, ctx->opts.eps_zero, T, ckpt_every,
-                                 reinterpret_cast<const double *>(ctx->xin.ptr()),
+  Precision<double> &pr = ctx->p64;
+  UnrollBuffers &U = ctx->unr;
+  U.nnz = ctx->nnz;
+  cudaError_t e = unroll_forward(U, pr.K, pr.KT, pr.P, pr.S, pr.pg, pr.init, ctx->opts.primal_importance,
+                                 pr.normpart_ptr, T, ckpt_every, reinterpret_cast<const double *>(ctx->xin.ptr()),
                                  reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st);
   if (e) return cuda_fail(ctx, e, "unroll");
-  if (x_out) CK(cudaMemcpyAsync(x_out, ctx->unr.xo, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "x_out");
-  if (y_out) CK(cudaMemcpyAsync(y_out, ctx->unr.yo, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "y_out");
-  if (eta_out) CK(cudaMemcpyAsync(eta_out, ctx->unr.eta, sizeof(double) * T, cudaMemcpyDefault, ctx->st), "eta");
+  if (U.status == kWaitTimeout)
+    return fail(ctx, PDLP_ERR_TIMEOUT, "a grid-wide barrier of the persistent step kernel timed out");
+  if (!U.ready)
+    return fail(ctx, PDLP_ERR_STATE, U.status == kNumErr ? "unrolled map stopped: numerical error"
+                                                         : "unrolled map stopped: attempt limit");
+  if (x_out) CK(cudaMemcpyAsync(x_out, U.xo, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "x_out");
+  if (y_out) CK(cudaMemcpyAsync(y_out, U.yo, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "y_out");
+  if (eta_out) CK(cudaMemcpyAsync(eta_out, U.eta, sizeof(double) * T, cudaMemcpyDefault, ctx->st), "eta");
   CK(cudaStreamSynchronize(ctx->st), "unroll");
   return PDLP_OK;
 }
@@ -735,8 +744,7 @@ extern "C" int pdlp_grad(pdlp_ctx *ctx, const double *dL_dx, const double *dL_dy
                          double *dK_val) {
   if (!ctx || !dL_dx) return fail(ctx, PDLP_ERR_INVALID_ARG, "NULL argument");
   if (!ctx->unr.ready) return fail(ctx, PDLP_ERR_STATE, "pdlp_grad needs a preceding unrolled solve");
-  cudaError_t e = unroll_backward(ctx->unr, ctx->p64.K, ctx->p64.KT, ctx->p64.P,
-                                  reinterpret_cast<const int32_t *>(ctx->perm.ptr()), dL_dx, dL_dy, ctx->st);
+  cudaError_t e = unroll_backward(ctx->unr, ctx->p64.K, ctx->p64.KT, ctx->p64.P, dL_dx, dL_dy, ctx->st);
   if (e) return cuda_fail(ctx, e, "grad");
   if (dc) CK(cudaMemcpyAsync(dc, ctx->unr.dc, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "dc");
   if (dq) CK(cudaMemcpyAsync(dq, ctx->unr.dq, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "dq");

@@ -152,6 +152,7 @@ struct State {
   double *ghist;               // gap histogram [kGapSlots][kGapBuckets][3]
   double *xo, *yo;             // returned point (original space, float64)
   double *trace;               // [kTraceCap][kTraceLen]
+  double *eta_log;             // nullable: step size of each accepted step, by step index
 };
 
 // Arrival counters; [kTicketBar, kTicketBar + 1] hold the 64-bit barrier

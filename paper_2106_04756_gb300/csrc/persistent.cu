@@ -368,7 +368,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
           fr = 1.0 - pow(kk + 1.0, -0.3);
           fg = 1.0 + pow(kk + 1.0, -0.6);
         }
+        const long long k_before = ctl.k;
+        const double eta_try = ctl.eta;
         step_update(ctl, t[0], t[1], t[2], fr, fg);
+        if (S.eta_log && blockIdx.x == 0 && ctl.k > k_before) S.eta_log[k_before] = eta_try;
       }
       __syncthreads();
     }

@@ -40,7 +40,7 @@ __device__ __forceinline__ bool time_up(const Scalars *s) {
 // after the reductions of an attempt, on the scalars in global memory; the
 // factors come from the table k_finish fills for the current chunk.
 __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
-                            cudaGraphConditionalHandle h, int has_cond) {
+                            cudaGraphConditionalHandle h, int has_cond, double *eta_log) {
   StepCtl c;
   load_step(s, c);
   const long long idx = c.k - s->fac_k0;
@@ -53,8 +53,11 @@ __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
     fr = 1.0 - pow(kk + 1.0, -0.3);
     fg = 1.0 + pow(kk + 1.0, -0.6);
   }
+  const long long k_before = c.k;
+  const double eta_try = c.eta;
   step_update(c, dx2, dy2, inter, fr, fg);
   store_step(s, c);
+  if (eta_log && c.k > k_before) eta_log[k_before] = eta_try;
   bool go = c.status == kRunning && c.chunk_acc < s->eval_every && c.k < s->iter_limit &&
             c.attempts < s->attempt_limit;
   if (go && time_up(s)) go = false;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, Mat<T> KT, Problem<
     sum_long_rows<1>(KT, lp, red);
     __syncthreads();
     sum_long_rows<2>(K, ld, red);
-    if (threadIdx.x == 0) accept_step(sc, p[0] + lp[0], d[0] + ld[0], d[1] + ld[1], h, has_cond);
+    if (threadIdx.x == 0) accept_step(sc, p[0] + lp[0], d[0] + ld[0], d[1] + ld[1], h, has_cond, S.eta_log);
   }
 }
 
@@ -869,6 +872,18 @@ cudaError_t launch_gap_slots(const Problem<T> &P, const State<T> &S, int s_begin
   launch_gap<T>(P, S, s_begin, s_end, when_restart, grid, st);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_step_pair(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                             cudaStream_t st) {
+  if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+  k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
+  return cudaGetLastError();
+}
+template cudaError_t launch_step_pair<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
+                                              const State<double> &, cudaStream_t);
+template cudaError_t launch_step_pair<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
+                                             const State<float> &, cudaStream_t);
 
 template <typename T>
 void launch_spmv(const Mat<T> &A, const T *v, T *out, cudaStream_t st) {

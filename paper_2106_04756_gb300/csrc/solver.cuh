@@ -23,6 +23,10 @@ template <typename T>
 cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               int reps, cudaStream_t st, float *ms_primal, float *ms_dual);
 template <typename T> void launch_spmv(const Mat<T> &A, const T *v, T *out, cudaStream_t st);
+// One step attempt (k_primal, k_dual with the step test) outside any graph.
+template <typename T>
+cudaError_t launch_step_pair(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                             cudaStream_t st);
 template <typename T>
 void launch_problem_norms(const Problem<T> &P, Scalars *s, double primal_importance, double *part, int grid,
                           cudaStream_t st);
