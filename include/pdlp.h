@@ -180,13 +180,25 @@ int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double *y, double 
  * uint8[total rows].  x_out / y_out (float64[total cols] / [total rows],
  * nullable) receive the solutions, res[count] (nullable) the outcomes.
  * Uses opts.precision (PDLP_FP64 or PDLP_FP32 arithmetic in the SpMVs),
- * rel_tol, iter_limit and the restart / step settings. */
+ * rel_tol, iter_limit, kkt_pass_limit, the preconditioner, restart, primal
+ * weight and step settings, and opts.stream.  Each LP needs m + n <= 4096;
+ * invalid data (column index out of range or not increasing within a row,
+ * non-finite value, l > u) returns PDLP_ERR_INVALID_ARG naming the first such
+ * LP.  All arrays may be host or device memory. */
 int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *n, const int64_t *row_off,
                      const int64_t *col_off, const int64_t *nnz_off, const int32_t *row_ptr,
                      const int32_t *col_idx, const double *val, const double *c,
                      const double *q, const double *l, const double *u,
                      const uint8_t *ineq_mask, const pdlp_options *opts, double *x_out,
                      double *y_out, pdlp_result *res);
+
+/* The lanes per row of K and of K^T that the batch autotuner chose for each
+ * size bucket (mean row length of K: < 8, < 16, < 32, < 64, >= 64) of the
+ * given precision (PDLP_FP64 or PDLP_FP32), 0 where no batch of that bucket
+ * was solved yet in this process.  The autotuner times every candidate on a
+ * sample of the bucket's LPs (100 steps each) the first time a bucket
+ * appears and keeps the fastest.  lanes_k, lanes_kt: host int32[nbuckets]. */
+int pdlp_batch_lanes(int32_t precision, int32_t *lanes_k, int32_t *lanes_kt, int32_t nbuckets);
 
 /* Restart evaluations of the last solve on ctx, oldest first (a ring keeps
  * the last 256).  Each record is 16 float64: k, t, mu(current), mu(average),

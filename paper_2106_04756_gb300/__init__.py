@@ -18,7 +18,7 @@ from ._abi import (PDLP_ERR_CUDA, PDLP_ERR_INVALID_ARG, PDLP_ERR_OOM, PDLP_ERR_S
                    PDLP_FP32, PDLP_FP32_REFINE, PDLP_FP64, PDLP_OK, STATUS_NAMES, PdlpError, check, pdlp_csr,
                    pdlp_options, pdlp_result)
 
-__all__ = ["Context", "default_options", "pdlp_create", "solve", "solve_batch", "PdlpError",
+__all__ = ["Context", "default_options", "pdlp_create", "solve", "solve_batch", "batch_lanes", "PdlpError",
            "PDLP_FP64", "PDLP_FP32", "PDLP_FP32_REFINE", "STATUS_NAMES", "PDLP_OK", "PDLP_ERR_INVALID_ARG",
            "PDLP_ERR_CUDA", "PDLP_ERR_OOM", "PDLP_ERR_TIMEOUT", "PDLP_ERR_STATE"]
 
@@ -232,7 +232,16 @@ def solve_batch(lps, **kw):
     res = (pdlp_result * cnt)()
     arrs = [m, n, row_off, col_off, nnz_off, rp, ci, va, cc, qq, ll, uu, ineq]
     check(lib.pdlp_solve_batch(cnt, *[a.ctypes.data for a in arrs], C.byref(opts), x.ctypes.data,
-                               y.ctypes.data, res))
+                               y.ctypes.data, C.addressof(res)))
     xs = [x[col_off[b]:col_off[b + 1]] for b in range(cnt)]
     ys = [y[row_off[b]:row_off[b + 1]] for b in range(cnt)]
     return xs, ys, [r.asdict() for r in res]
+
+
+def batch_lanes(precision=PDLP_FP64, nbuckets: int = 5):
+    """Lanes per row (K, K^T) the batch autotuner chose per size bucket (0: not tuned)."""
+    lib = _abi.load()
+    lk = np.zeros(nbuckets, np.int32)
+    lt = np.zeros(nbuckets, np.int32)
+    check(lib.pdlp_batch_lanes(int(precision), lk.ctypes.data, lt.ctypes.data, int(nbuckets)))
+    return lk, lt

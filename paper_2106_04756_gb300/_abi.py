@@ -69,7 +69,8 @@ _SIGNATURES = {
     "pdlp_grad": ([P, P, P, P, P, P], C.c_int),
     "pdlp_get_scaled": ([P] + [P] * 11, C.c_int),
     "pdlp_normalized_gap": ([P, P, P, C.c_double, C.c_double, P, P], C.c_int),
-    "pdlp_solve_batch": ([C.c_int32] + [P] * 14 + [C.POINTER(pdlp_options), P, P, P], C.c_int),
+    "pdlp_solve_batch": ([C.c_int32] + [P] * 13 + [C.POINTER(pdlp_options), P, P, P], C.c_int),
+    "pdlp_batch_lanes": ([C.c_int32, P, P, C.c_int32], C.c_int),
     "pdlp_get_trace": ([P, P, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "pdlp_time_step_kernels": ([P, C.c_int32, P], C.c_int),
     "pdlp_normalized_gap_noalloc": ([C.c_int32, C.c_int32] + [P] * 7 + [C.c_double, C.c_double, P, P, P],

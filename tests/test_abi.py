@@ -38,6 +38,25 @@ def test_binding_covers_every_declared_call():
     assert set(_declared()) == set(_abi._SIGNATURES)
 
 
+def _param_counts():
+    out = {}
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            for name, params in re.findall(r"\b(pdlp_\w+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+                p = params.strip()
+                out[name] = 0 if p in ("", "void") else p.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    from paper_2106_04756_gb300 import _abi
+    counts = _param_counts()
+    for name, (args, _) in _abi._SIGNATURES.items():
+        assert len(args) == counts[name], (name, len(args), counts[name])
+
+
 def test_default_options_are_the_papers(lib):
     import paper_2106_04756_gb300 as P
     o = P.default_options()

@@ -1,0 +1,122 @@
+"""Batched persistent solve (pdlp_solve_batch): every LP of a batch against
+what fixes its optimum (the planted optimal pair, the oracle's Eq. (15)
+terms at the returned point), a sample against the oracle's own solve, the
+autotuner's choices, ragged and degenerate members, and invalid input."""
+import copy
+
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+import paper_2106_04756_gb300 as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_optimal(lps, xs, ys, rs, tol):
+    for b, (lp, x, y, r) in enumerate(zip(lps, xs, ys, rs)):
+        assert r["status_name"] == "OPTIMAL", (b, r)
+        _check_point(lp, x, y, tol, b)
+
+
+def _check_point(lp, x, y, tol, b):
+    k = oracle.kkt(lp, x, y)
+    assert k["rel_kkt"] <= tol, (b, k)
+    ref = lp.c @ lp.x_star
+    assert abs(lp.c @ x - ref) <= 10 * tol * (1 + abs(ref)) + 1e-12, (b, lp.c @ x, ref)
+
+
+def test_batch_fp64_every_lp_to_1e8(gpu_lib, oracle_lib):
+    # some planted LPs of this family are hard for PDLP: within the iteration
+    # cap the oracle does not finish them either, so the statuses are compared
+    lps = lpgen.batch_planted(count=96, seed_key=(3, 7))
+    cap = 20000
+    xs, ys, rs = P.solve_batch(lps, rel_tol=1e-8, iter_limit=cap)
+    solved = [b for b in range(len(lps)) if rs[b]["status_name"] == "OPTIMAL"]
+    assert len(solved) >= 0.9 * len(lps)
+    for b in solved:
+        _check_point(lps[b], xs[b], ys[b], 1e-8, b)
+    for b in range(len(lps)):
+        if b not in solved:
+            assert rs[b]["status_name"] == "ITER_LIMIT" and rs[b]["iters"] == cap
+            _, _, ro = oracle.solve(lps[b], iter_limit=cap)
+            assert ro["status_name"] == "ITER_LIMIT", b
+    # a sample against the oracle's solve of the same LP: same outcome and
+    # iteration counts of the same order (the trajectories differ by rounding)
+    for b in solved[:3]:
+        _, _, ro = oracle.solve(lps[b], iter_limit=cap)
+        assert ro["status_name"] == "OPTIMAL"
+        assert 0.5 * ro["iters"] <= rs[b]["iters"] <= 2.0 * ro["iters"] + 80, (b, rs[b]["iters"], ro["iters"])
+
+
+def test_batch_is_deterministic_and_independent_of_batch_order(gpu_lib):
+    lps = lpgen.batch_planted(count=40, seed_key=(3, 8))
+    xa, ya, ra = P.solve_batch(lps, rel_tol=1e-6, iter_limit=5000)
+    xb, yb, rb = P.solve_batch(lps[::-1], rel_tol=1e-6, iter_limit=5000)
+    for b in range(len(lps)):
+        assert np.array_equal(xa[b], xb[-1 - b]) and np.array_equal(ya[b], yb[-1 - b])
+        assert ra[b]["iters"] == rb[-1 - b]["iters"]
+
+
+def test_batch_single_lp_matches_the_single_lp_path(gpu_lib):
+    # same method, same preconditioning (bit-exact), same Algorithm 2 test:
+    # the batch member and the single-LP solver agree on the outcome
+    lp = lpgen.small_planted()
+    xs, ys, rs = P.solve_batch([lp], rel_tol=1e-8)
+    x1, y1, r1 = P.solve(lp, rel_tol=1e-8)
+    assert rs[0]["status_name"] == r1["status_name"] == "OPTIMAL"
+    assert abs(rs[0]["primal_obj"] - r1["primal_obj"]) <= 1e-7 * (1 + abs(r1["primal_obj"]))
+    s = P.Context.from_lp(lp).get_scaled()  # preconditioner shared by both paths
+    assert s["D1"].shape == (lp.m,)
+
+
+def test_batch_fp32_arithmetic(gpu_lib, oracle_lib):
+    lps = lpgen.batch_planted(count=48, seed_key=(3, 9))
+    xs, ys, rs = P.solve_batch(lps, precision=P.PDLP_FP32, rel_tol=1e-5, iter_limit=20000)
+    solved = [b for b in range(len(lps)) if rs[b]["status_name"] == "OPTIMAL"]
+    assert len(solved) >= 0.85 * len(lps)
+    for b in solved:
+        _check_point(lps[b], xs[b], ys[b], 1e-5, b)
+
+
+def test_batch_ragged_and_degenerate_members(gpu_lib, oracle_lib):
+    lps = lpgen.batch_planted(count=6, seed_key=(3, 10))
+    tiny = lpgen.planted_uniform(1, 1, 1.0, frac_boxed=1.0, seed_key=(3, 11))
+    small = lpgen.planted_uniform(30, 60, 0.1, frac_boxed=1.0, seed_key=(3, 12))
+    lps = [tiny] + lps + [small]
+    xs, ys, rs = P.solve_batch(lps, rel_tol=1e-8, iter_limit=20000)
+    assert rs[0]["status_name"] == rs[-1]["status_name"] == "OPTIMAL"
+    for b, r in enumerate(rs):
+        if r["status_name"] == "OPTIMAL":
+            _check_point(lps[b], xs[b], ys[b], 1e-8, b)
+
+
+def test_batch_limits_and_statuses(gpu_lib):
+    lps = lpgen.batch_planted(count=8, seed_key=(3, 13))
+    _, _, rs = P.solve_batch(lps, rel_tol=1e-12, iter_limit=80)
+    assert all(r["status_name"] == "ITER_LIMIT" and r["iters"] == 80 for r in rs)
+
+
+def test_batch_autotuner_reports_its_choice(gpu_lib):
+    lps = lpgen.batch_planted(count=32, seed_key=(3, 14))
+    P.solve_batch(lps, rel_tol=1e-6, iter_limit=2000)
+    lk, lt = P.batch_lanes(P.PDLP_FP64)
+    mean_len = np.mean([lp.nnz / lp.m for lp in lps])
+    assert lk.max() > 0 and lt.max() > 0
+    assert set(lk[lk > 0]) <= {1, 2, 4, 8, 16, 32} and set(lt[lt > 0]) <= {1, 2, 4, 8, 16, 32}
+    assert mean_len > 0
+
+
+def test_batch_rejects_invalid_members(gpu_lib):
+    lps = lpgen.batch_planted(count=4, seed_key=(3, 15))
+    bad = copy.deepcopy(lps)
+    bad[2].col_idx = bad[2].col_idx.copy()
+    bad[2].col_idx[0] = bad[2].n + 5
+    with pytest.raises(P.PdlpError) as ei:
+        P.solve_batch(bad)
+    assert ei.value.code == P.PDLP_ERR_INVALID_ARG and "LP 2" in str(ei.value)
+    big = lpgen.planted_uniform(300, 4000, 0.002, seed_key=(3, 16))
+    with pytest.raises(P.PdlpError) as ei:
+        P.solve_batch([big])
+    assert "4096" in str(ei.value)
