@@ -11,11 +11,18 @@ float64, stopped at an iteration cap.  value = accepted PDHG iterations per
 second over the timed steps (all ranks).  The L2 cache is flushed (256 MiB
 write) between timed steps.
 
-Also reported: time to 1e-8 relative KKT error (Eq. (15)) on the 1M-node
-PageRank LP, float64 against float32 inner solves with float64 refinement;
-the roofline of the step kernels; the end-to-end rate through the C ABI with
-host buffers; and the CPU oracle timed on a bounded sample of the same
-workload.  `--impl reference` times only the CPU oracle.
+Also reported: the roofline of the dominant kernel (the persistent step
+kernel: algorithmic bytes of its step attempts over their CUDA-event time);
+time to 1e-8 relative KKT error (Eq. (15)) on the 1M-node PageRank LP,
+float64 against float32 inner solves with float64 refinement; the batched
+solve of 4096 small planted LPs (LPs/s and aggregate iterations/s to 1e-6
+and 1e-8, with the autotuner's lanes per row); the unrolled map with its
+adjoint on the 20k x 50k LP (T = 500, checkpoint every 50); the end-to-end
+rate through the C ABI with host buffers; and the CPU oracle timed on a
+bounded sample of the same workload.  `--impl reference` times only the CPU
+oracle.  `--stepped` launches the same kernels from a host loop instead of
+one CUDA graph per solve (for profilers that cannot see inside conditional
+graph nodes).
 
 Multi-GPU (torchrun): every rank solves its own replica (no data-path
 collective); value = the ranks' iterations / the slowest rank's time.
@@ -36,6 +43,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "time-to-1e-8 rel KKT & PDHG iter/s (HBM GB/s vs peak); FP32+refine vs FP64"
+# dram__bytes_read.sum + dram__bytes_write.sum per step attempt of k_persist<double>
+# from one ncu capture (one launch = 40 attempts; see profiles/); reset to
+# None whenever the kernel changes
+CAPTURED_TRAFFIC = {"mip_100k": 1.334e6, "pagerank_1m": 3.26e8}
 WORKLOADS = ("mip_100k", "pagerank_1m", "planted_200x500")
 
 
@@ -49,6 +60,8 @@ def _args():
     ap.add_argument("--iter-cap", type=int, default=20000)
     ap.add_argument("--no-tol", action="store_true", help="skip the time-to-tolerance runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch and unroll lines")
+    ap.add_argument("--stepped", action="store_true", help="host-stepped kernels instead of one graph per solve")
     return ap.parse_args()
 
 
@@ -141,6 +154,52 @@ def _alg_bytes(lp, fp):
     return primal, dual
 
 
+def _batch_line(P):
+    """4096 planted LPs (m in [20, 400], n in [50, 1000], 5% density) in one
+    persistent launch per call: LPs/s and iterations/s to 1e-6 and 1e-8."""
+    import lpgen
+    import torch
+    lps = lpgen.batch_4096()
+    out = {"workload": "batch_4096", "count": len(lps), "nnz_total": int(sum(lp.nnz for lp in lps))}
+    P.solve_batch(lps[:256], rel_tol=1e-6, iter_limit=2000)  # autotuner + warm-up on a slice
+    for name, prec, tol in (("fp64_1e-6", P.PDLP_FP64, 1e-6), ("fp64_1e-8", P.PDLP_FP64, 1e-8),
+                            ("fp32_1e-6", P.PDLP_FP32, 1e-6)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, rs = P.solve_batch(lps, precision=prec, rel_tol=tol, iter_limit=20000)
+        dt = time.perf_counter() - t0
+        its = sum(r["iters"] for r in rs)
+        opt = sum(1 for r in rs if r["status_name"] == "OPTIMAL")
+        out[name] = {"seconds": dt, "lps_per_s": len(lps) / dt, "iter_per_s": its / dt, "optimal": opt,
+                     "iter_cap": 20000}
+    lk, lt = P.batch_lanes(P.PDLP_FP64)
+    lk32, lt32 = P.batch_lanes(P.PDLP_FP32)
+    out["autotuned_lanes_per_row"] = {
+        "buckets_mean_row_len": ["<8", "<16", "<32", "<64", ">=64"],
+        "fp64_K": lk.tolist(), "fp64_KT": lt.tolist(), "fp32_K": lk32.tolist(), "fp32_KT": lt32.tolist()}
+    return out
+
+
+def _unroll_line(P, dev, sptr):
+    """Unrolled map (T = 500, checkpoint every 50) and its adjoint on the
+    20k x 50k planted LP with loss 1/2 ||x_T - x_target||^2."""
+    import lpgen
+    import torch
+    lp = lpgen.unroll_20k()
+    target = np.random.default_rng(4).standard_normal(lp.n)
+    with P.Context.from_lp(lp, stream=sptr) as ctx:
+        ctx.unroll(500, 50)
+        ctx.grad(np.zeros(lp.n))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, _, _ = ctx.unroll(500, 50)
+        t1 = time.perf_counter()
+        ctx.grad(x - target)
+        t2 = time.perf_counter()
+    return {"workload": "mip_20k_50k (m=20,000, n=50,000, nnz=%d)" % lp.nnz, "T": 500, "ckpt_every": 50,
+            "forward_s": t1 - t0, "backward_s": t2 - t1, "backward_over_forward": (t2 - t1) / (t1 - t0)}
+
+
 def run_reference(args):
     """The CPU oracle, as it stands, on the same workload and metric."""
     ws, rank, _ = _dist()
@@ -196,8 +255,10 @@ def main():
     torch.cuda.synchronize(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    use_graph = 0 if args.stepped else 1
+
     def step(cap, precision=P.PDLP_FP64, keep=False):
-        ctx = P.Context(*inputs, lp.m, lp.n, precision=precision, iter_limit=cap, stream=sptr)
+        ctx = P.Context(*inputs, lp.m, lp.n, precision=precision, iter_limit=cap, stream=sptr, use_graph=use_graph)
         xo = torch.empty(lp.n, dtype=torch.float64, device=dev)
         yo = torch.empty(lp.m, dtype=torch.float64, device=dev)
         _, _, r = ctx.solve(x_out=xo, y_out=yo)
@@ -243,28 +304,41 @@ def main():
     if rank != 0:
         return
 
-    # ---- roofline of the step kernels (CUDA events, same stream, state of a solve)
+    # ---- roofline of the dominant kernel: the persistent step kernel.  Each
+    # launch runs the step attempts between two evaluations; its mean time
+    # per attempt comes from CUDA events around `reps` launches on this
+    # stream, continuing from the state of a solve of the same workload.
     ctx, _ = step(args.iter_cap, keep=True)
-    kp, kd, _kc = ctx.time_step_kernels(200)
+    kp, kd, kc = ctx.time_step_kernels(50)
     ctx.close()
     bp, bd = _alg_bytes(lp, 64)
     peak, peak_src = _peaks()
-    dom = ("dual", kd, bd) if kd >= kp else ("primal", kp, bp)
-    achieved = dom[2] / (dom[1] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"k_dual<double> (K x' + dual projection + step test)"
-                if dom[0] == "dual" else "k_primal<double> (K^T y + primal projection)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": None,
-                "algorithmic_bytes_per_launch": dom[2], "launch_ms": dom[1]}
-    kernels = {"primal_ms": kp, "dual_ms": kd, "primal_bytes": bp, "dual_bytes": bd,
+    if kc > 0:
+        achieved = (bp + bd) / (kc * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_persist<double> (persistent step attempts: K^T y + primal "
+                    "projection, grid barrier, K x' + dual projection, step test)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": peak_src + " burst copy (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                    "algorithmic_bytes_per_attempt": bp + bd, "attempt_ms": kc,
+                    "note": "working set ~60 MB fits in L2: algorithmic GB/s, not DRAM GB/s; traffic = "
+                            "DRAM bytes per attempt from one ncu capture of this kernel on this workload"}
+        if args.workload in CAPTURED_TRAFFIC:
+            roofline["traffic"] = CAPTURED_TRAFFIC[args.workload]
+    else:
+        dom = ("dual", kd, bd) if kd >= kp else ("primal", kp, bp)
+        achieved = dom[2] / (dom[1] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"k_{dom[0]}<double>", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                    "algorithmic_bytes_per_launch": dom[2], "launch_ms": dom[1]}
+    kernels = {"persistent_attempt_ms": kc, "primal_ms": kp, "dual_ms": kd, "primal_bytes": bp, "dual_bytes": bd,
                "primal_gbs": bp / (kp * 1e-3) / 1e9, "dual_gbs": bd / (kd * 1e-3) / 1e9}
-    # float32 step kernels on the same workload
+    # float32 arithmetic on the same workload
     ctx32, r32 = step(args.iter_cap, precision=P.PDLP_FP32, keep=True)
-    kp32, kd32, _kc32 = ctx32.time_step_kernels(200)
+    kp32, kd32, kc32 = ctx32.time_step_kernels(50)
     ctx32.close()
     bp32, bd32 = _alg_bytes(lp, 32)
-    kernels.update({"fp32_primal_ms": kp32, "fp32_dual_ms": kd32,
-                    "fp32_primal_gbs": bp32 / (kp32 * 1e-3) / 1e9, "fp32_dual_gbs": bd32 / (kd32 * 1e-3) / 1e9,
+    kernels.update({"fp32_persistent_attempt_ms": kc32, "fp32_primal_ms": kp32, "fp32_dual_ms": kd32,
+                    "fp32_attempt_gbs": (bp32 + bd32) / (kc32 * 1e-3) / 1e9 if kc32 > 0 else None,
                     "fp32_iter_per_s": r32["iters"] / r32["seconds"]})
 
     # ---- end to end through the C ABI with host buffers
@@ -313,7 +387,14 @@ def main():
         cpu = {"value": ro["iters"] / ct, "unit": "PDHG iter/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.workload}, oracle setup + first {cap} iterations ({ct:.1f} s)"}
 
-    launches_per_step = 120 + 2 * attempts / args.steps + 12 * evals / args.steps + 8
+    extra = {}
+    if not args.no_extra:
+        extra["batch"] = _batch_line(P)
+        extra["unroll"] = _unroll_line(P, dev, sptr)
+
+    # per solve: ~120 create/setup launches, 13 per evaluation (persistent
+    # step kernel, 2 evaluation, 6 gap passes, decide, restart, finish) + 8
+    launches_per_step = 120 + 13 * evals / args.steps + 8
     out = {"metric": METRIC, "value": value, "unit": "PDHG iter/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -322,7 +403,7 @@ def main():
                       "l2": "flushed between steps (256 MiB write)",
                       "rel_kkt_at_cap": float(np.median([r["rel_kkt"] for r in results]))},
            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": int(launches_per_step * args.steps), "clocks": clk, "time_to_tol": tol}
+           "gpu_launches": int(launches_per_step * args.steps), "clocks": clk, "time_to_tol": tol, **extra}
     print(json.dumps(out), flush=True)
 
 
