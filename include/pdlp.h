@@ -149,8 +149,10 @@ int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const double *x0,
  * to (c, q, values of K): given dL/dx_T (n) and dL/dy_T (m, nullable) writes
  * dL/dc (n), dL/dq (m) and dL/dK (nnz, in the CSR order of the K passed to
  * pdlp_create).  The preconditioner and the recorded step sizes are held
- * constant; gradients accumulate in float64.  PDLP_ERR_STATE if no unrolled
- * map was run on ctx. */
+ * constant; gradients accumulate in float64.  With opts.precision ==
+ * PDLP_FP32 the forward map (and its recompute from the checkpoints) runs in
+ * float32 and the adjoint in float64.  PDLP_ERR_STATE if no unrolled map was
+ * run on ctx. */
 int pdlp_grad(pdlp_ctx *ctx, const double *dL_dx, const double *dL_dy, double *dc,
               double *dq, double *dK_val);
 

@@ -717,16 +717,26 @@ extern "C" int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const d
   if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
   if (T < 1 || ckpt_every < 1 || ckpt_every > kMaxEval)
     return fail(ctx, PDLP_ERR_INVALID_ARG, "need T >= 1 and 1 <= ckpt_every <= 256");
-  int rc = setup_fp64(ctx);
+  const bool f32 = ctx->opts.precision == PDLP_FP32;
+  int rc = setup_fp64(ctx);  // float64 K~ for the adjoint
+  if (!rc && f32) rc = setup_fp32(ctx);
   if (rc) return rc;
   rc = stage_start(ctx, x0, y0);
   if (rc) return rc;
-  Precision<double> &pr = ctx->p64;
   UnrollBuffers &U = ctx->unr;
   U.nnz = ctx->nnz;
-  cudaError_t e = unroll_forward(U, pr.K, pr.KT, pr.P, pr.S, pr.pg, pr.init, ctx->opts.primal_importance,
-                                 pr.normpart_ptr, T, ckpt_every, reinterpret_cast<const double *>(ctx->xin.ptr()),
-                                 reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st);
+  const double *xin = reinterpret_cast<const double *>(ctx->xin.ptr());
+  const double *yin = reinterpret_cast<const double *>(ctx->yin.ptr());
+  cudaError_t e;
+  if (f32) {
+    Precision<float> &pr = ctx->p32;
+    e = unroll_forward<float>(U, pr.K, pr.KT, pr.P, pr.S, pr.pg, pr.init, ctx->opts.primal_importance,
+                              pr.normpart_ptr, T, ckpt_every, xin, yin, ctx->st);
+  } else {
+    Precision<double> &pr = ctx->p64;
+    e = unroll_forward<double>(U, pr.K, pr.KT, pr.P, pr.S, pr.pg, pr.init, ctx->opts.primal_importance,
+                               pr.normpart_ptr, T, ckpt_every, xin, yin, ctx->st);
+  }
   if (e) return cuda_fail(ctx, e, "unroll");
   if (U.status == kWaitTimeout)
     return fail(ctx, PDLP_ERR_TIMEOUT, "a grid-wide barrier of the persistent step kernel timed out");
@@ -744,7 +754,11 @@ extern "C" int pdlp_grad(pdlp_ctx *ctx, const double *dL_dx, const double *dL_dy
                          double *dK_val) {
   if (!ctx || !dL_dx) return fail(ctx, PDLP_ERR_INVALID_ARG, "NULL argument");
   if (!ctx->unr.ready) return fail(ctx, PDLP_ERR_STATE, "pdlp_grad needs a preceding unrolled solve");
-  cudaError_t e = unroll_backward(ctx->unr, ctx->p64.K, ctx->p64.KT, ctx->p64.P, dL_dx, dL_dy, ctx->st);
+  cudaError_t e =
+      ctx->unr.fp32 ? unroll_backward<float>(ctx->unr, ctx->p32.K, ctx->p32.KT, ctx->p32.P, ctx->p64.K, ctx->p64.KT,
+                                             ctx->p64.P, dL_dx, dL_dy, ctx->st)
+                    : unroll_backward<double>(ctx->unr, ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->p64.K,
+                                              ctx->p64.KT, ctx->p64.P, dL_dx, dL_dy, ctx->st);
   if (e) return cuda_fail(ctx, e, "grad");
   if (dc) CK(cudaMemcpyAsync(dc, ctx->unr.dc, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "dc");
   if (dq) CK(cudaMemcpyAsync(dq, ctx->unr.dq, sizeof(double) * ctx->m, cudaMemcpyDefault, ctx->st), "dq");

@@ -15,7 +15,9 @@
 // preconditioner held fixed.  The reverse sweep runs segment by segment from
 // the last checkpoint: it recomputes the segment's iterates (storing
 // 2 x_{t+1} - x_t, y_t and the two projection masks per step), then walks
-// back through it with one K^T and one K product per step.  All float64.
+// back through it with one K^T and one K product per step.  The forward map
+// runs in float64 or in float32 (then the recompute repeats its float32
+// arithmetic); the adjoint and the gradients are float64.
 #include <math.h>
 #include <string.h>
 
@@ -41,48 +43,49 @@ __global__ void k_unr_segment(Scalars *s) {
   fill_step_factors(s);
 }
 
-__global__ void k_unr_out(int n, int m, const double *x, const double *y, const double *D2, const double *D1,
-                          double *xo, double *yo) {
+template <typename T>
+__global__ void k_unr_out(int n, int m, const T *x, const T *y, const double *D2, const double *D1, double *xo,
+                          double *yo) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
     if (i < n)
-      xo[i] = D2[i] * x[i];
+      xo[i] = D2[i] * (double)x[i];
     else
-      yo[i - n] = D1[i - n] * y[i - n];
+      yo[i - n] = D1[i - n] * (double)y[i - n];
   }
 }
 
-// Forward primal half-step (the arithmetic of k_primal) that also stores
-// xe = 2 x' - x and the mask [l < v < u].
-__global__ void __launch_bounds__(kThreads) k_unr_primal(Mat<double> KT, Problem<double> P, const double *x,
-                                                         const double *y, double *xn, double *xe, uint8_t *mx,
-                                                         double tau) {
+// Forward primal half-step (the arithmetic of k_primal in type T) that also
+// stores xe = 2 x' - x (float64) and the mask [l < v < u].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_unr_primal(Mat<T> KT, Problem<T> P, const T *x, const T *y, T *xn,
+                                                         double *xe, uint8_t *mx, T tau) {
   extern __shared__ __align__(16) char sm[];
   double none[1] = {0.0};
-  const double *const vec[1] = {y};
-  spmv_warp<double, 1>(KT, vec, sm, none, [&](int j, const double(&g)[1], double(&)[1]) {
-    const double xj = x[j];
-    const double v = xj - tau * (P.cs[j] - g[0]);
-    const double xp = clampv<double>(v, P.ls[j], P.us[j]);
+  const T *const vec[1] = {y};
+  spmv_warp<T, 1>(KT, vec, sm, none, [&](int j, const T(&g)[1], double(&)[1]) {
+    const T xj = x[j];
+    const T v = xj - tau * (P.cs[j] - g[0]);
+    const T xp = clampv<T>(v, P.ls[j], P.us[j]);
     xn[j] = xp;
-    xe[j] = 2.0 * xp - xj;
+    xe[j] = 2.0 * (double)xp - (double)xj;
     mx[j] = (v > P.ls[j] && v < P.us[j]) ? 1 : 0;
   });
 }
 
-// Forward dual half-step (the arithmetic of k_dual) that also stores y_t and
-// the mask [w > ylo].
-__global__ void __launch_bounds__(kThreads) k_unr_dual(Mat<double> K, Problem<double> P, const double *xn,
-                                                       const double *Kx, const double *y, double *yn, double *Kxn,
-                                                       double *ys, uint8_t *my, double sigma) {
+// Forward dual half-step (the arithmetic of k_dual in type T) that also
+// stores y_t (float64) and the mask [w > ylo].
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_unr_dual(Mat<T> K, Problem<T> P, const T *xn, const T *Kx, const T *y,
+                                                       T *yn, T *Kxn, double *ys, uint8_t *my, T sigma) {
   extern __shared__ __align__(16) char sm[];
   double none[1] = {0.0};
-  const double *const vec[1] = {xn};
-  spmv_warp<double, 1>(K, vec, sm, none, [&](int i, const double(&s)[1], double(&)[1]) {
-    const double kxn = s[0], kx = Kx[i], yi = y[i], lo = P.ylos[i];
-    const double w = yi + sigma * (P.qs[i] - 2.0 * kxn + kx);
+  const T *const vec[1] = {xn};
+  spmv_warp<T, 1>(K, vec, sm, none, [&](int i, const T(&s)[1], double(&)[1]) {
+    const T kxn = s[0], kx = Kx[i], yi = y[i], lo = P.ylos[i];
+    const T w = yi + sigma * (P.qs[i] - T(2) * kxn + kx);
     yn[i] = w > lo ? w : lo;
     Kxn[i] = kxn;
-    ys[i] = yi;
+    ys[i] = (double)yi;
     my[i] = w > lo ? 1 : 0;
   });
 }
@@ -157,27 +160,32 @@ __global__ void k_row_index(int m, const int32_t *rp, int32_t *row) {
     for (int k = rp[i]; k < rp[i + 1]; ++k) row[k] = i;
 }
 
-size_t spmv_bytes() { return spmv_smem_bytes<double>(1); }
+template <typename T>
+size_t spmv_bytes() {
+  return spmv_smem_bytes<T>(1);
+}
 
 }  // namespace
 
-cudaError_t unroll_forward(UnrollBuffers &U, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
-                           const State<double> &S, const PersistGeo &pg, const ScalarInit &in,
-                           double primal_importance, double *norm_part, int32_t T, int32_t ckpt, const double *x0,
-                           const double *y0, cudaStream_t st) {
+template <typename F>
+cudaError_t unroll_forward(UnrollBuffers &U, const Mat<F> &K, const Mat<F> &KT, const Problem<F> &P,
+                           const State<F> &S, const PersistGeo &pg, const ScalarInit &in, double primal_importance,
+                           double *norm_part, int32_t T, int32_t ckpt, const double *x0, const double *y0,
+                           cudaStream_t st) {
   cudaError_t e;
   const int n = P.n, m = P.m;
   U.ready = false;
+  U.fp32 = sizeof(F) == 4;
   U.T = T;
   U.ckpt = ckpt;
   U.nseg = (T + ckpt - 1) / ckpt;
-  double *ck = reinterpret_cast<double *>(U.ckpts.get(sizeof(double) * (size_t)U.nseg * (n + m)));
+  F *ck = reinterpret_cast<F *>(U.ckpts.get(sizeof(F) * (size_t)U.nseg * (n + m)));
   U.eta = reinterpret_cast<double *>(U.etab.get(sizeof(double) * (size_t)T));
   double *outs = reinterpret_cast<double *>(U.outs.get(sizeof(double) * (size_t)(n + m)));
   if (!ck || !U.eta || !outs) return cudaErrorMemoryAllocation;
   U.xo = outs;
   U.yo = outs + n;
-  State<double> S2 = S;
+  State<F> S2 = S;
   S2.eta_log = U.eta;
   ScalarInit in2 = in;
   in2.iter_limit = T;
@@ -185,20 +193,20 @@ cudaError_t unroll_forward(UnrollBuffers &U, const Mat<double> &K, const Mat<dou
   in2.time_limit_ns = 0ull;
   in2.eval_every = ckpt;
   in2.adaptive_restart = 0;
-  launch_problem_norms<double>(P, S.s, primal_importance, norm_part, 152, st);
-  launch_init<double>(P, S2, K, in2, x0, y0, st);
+  launch_problem_norms<F>(P, S.s, primal_importance, norm_part, 152, st);
+  launch_init<F>(P, S2, K, in2, x0, y0, st);
   if ((e = cudaGetLastError())) return e;
   Scalars h;
   int cur = 0;
   U.status = kRunning;
   for (int sg = 0; sg < U.nseg; ++sg) {
-    double *slot = ck + (size_t)sg * (n + m);
-    if ((e = cudaMemcpyAsync(slot, S.x[cur], sizeof(double) * n, cudaMemcpyDeviceToDevice, st))) return e;
-    if ((e = cudaMemcpyAsync(slot + n, S.y[cur], sizeof(double) * m, cudaMemcpyDeviceToDevice, st))) return e;
+    F *slot = ck + (size_t)sg * (n + m);
+    if ((e = cudaMemcpyAsync(slot, S.x[cur], sizeof(F) * n, cudaMemcpyDeviceToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(slot + n, S.y[cur], sizeof(F) * m, cudaMemcpyDeviceToDevice, st))) return e;
     k_unr_segment<<<1, 64, 0, st>>>(S.s);
     const long long k_end = std::min<long long>(T, (long long)(sg + 1) * ckpt);
     for (;;) {
-      e = pg.grid > 0 ? launch_persist<double>(K, KT, P, S2, pg, st) : launch_step_pair<double>(K, KT, P, S2, st);
+      e = pg.grid > 0 ? launch_persist<F>(K, KT, P, S2, pg, st) : launch_step_pair<F>(K, KT, P, S2, st);
       if (e) return e;
       if ((e = cudaMemcpyAsync(&h, S.s, sizeof(Scalars), cudaMemcpyDeviceToHost, st))) return e;
       if ((e = cudaStreamSynchronize(st))) return e;
@@ -220,7 +228,7 @@ cudaError_t unroll_forward(UnrollBuffers &U, const Mat<double> &K, const Mat<dou
   }
   U.omega = h.omega;
   U.inv_omega = h.inv_omega;
-  k_unr_out<<<ew_grid(n + m), kEw, 0, st>>>(n, m, S.x[cur], S.y[cur], P.D2, P.D1, U.xo, U.yo);
+  k_unr_out<F><<<ew_grid(n + m), kEw, 0, st>>>(n, m, S.x[cur], S.y[cur], P.D2, P.D1, U.xo, U.yo);
   U.eta_host.resize((size_t)T);
   if ((e = cudaMemcpyAsync(U.eta_host.data(), U.eta, sizeof(double) * T, cudaMemcpyDeviceToHost, st))) return e;
   if ((e = cudaStreamSynchronize(st))) return e;
@@ -229,7 +237,9 @@ cudaError_t unroll_forward(UnrollBuffers &U, const Mat<double> &K, const Mat<dou
   return cudaGetLastError();
 }
 
-cudaError_t unroll_backward(UnrollBuffers &U, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
+template <typename F>
+cudaError_t unroll_backward(UnrollBuffers &U, const Mat<F> &Kf, const Mat<F> &KTf, const Problem<F> &Pf,
+                            const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
                             const double *dL_dx, const double *dL_dy, cudaStream_t st) {
   cudaError_t e;
   const int n = P.n, m = P.m, L = U.ckpt;
@@ -237,17 +247,18 @@ cudaError_t unroll_backward(UnrollBuffers &U, const Mat<double> &K, const Mat<do
   // segment store: xe, y_t (float64) and the two masks per step
   char *seg = reinterpret_cast<char *>(U.seg.get((sizeof(double) + 1) * (size_t)L * (n + m)));
   double *work = reinterpret_cast<double *>(U.work.get(sizeof(double) * (size_t)(6 * n + 8 * m)));
+  F *fwork = reinterpret_cast<F *>(U.fwork.get(sizeof(F) * (size_t)(2 * n + 4 * m)));
   double *grads = reinterpret_cast<double *>(U.grads.get(sizeof(double) * (size_t)(2 * (n + m) + 2 * nnz)));
   int32_t *row = reinterpret_cast<int32_t *>(U.rowidx.get(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)));
-  if (!seg || !work || !grads || !row) return cudaErrorMemoryAllocation;
+  if (!seg || !work || !fwork || !grads || !row) return cudaErrorMemoryAllocation;
   double *XE = reinterpret_cast<double *>(seg);
   double *YS = XE + (size_t)L * n;
   uint8_t *MX = reinterpret_cast<uint8_t *>(YS + (size_t)L * m);
   uint8_t *MY = MX + (size_t)L * n;
   double *w = work;
-  double *xa = w, *xb2 = w + n, *xbar = w + 2 * n, *g = w + 3 * n, *gx = w + 4 * n;
-  double *ya = w + 6 * n, *yb2 = ya + m, *Kxa = ya + 2 * m, *Kxb = ya + 3 * m, *ybar = ya + 4 * m, *h = ya + 5 * m,
-         *gy = ya + 6 * m;
+  double *xbar = w + 2 * n, *g = w + 3 * n, *gx = w + 4 * n;
+  double *ybar = w + 6 * n + 4 * m, *h = ybar + m, *gy = ybar + 2 * m;
+  F *xa = fwork, *xb2 = fwork + n, *ya = fwork + 2 * n, *yb2 = ya + m, *Kxa = ya + 2 * m, *Kxb = ya + 3 * m;
   double *dcs = grads, *dqs = grads + n, *dKs = grads + n + m;
   U.dc = dKs + nnz;
   U.dq = U.dc + n;
@@ -257,31 +268,33 @@ cudaError_t unroll_backward(UnrollBuffers &U, const Mat<double> &K, const Mat<do
   if (dL_dy && (e = cudaMemcpyAsync(gy, dL_dy, sizeof(double) * m, cudaMemcpyDefault, st))) return e;
   k_adj_init<<<ew_grid(n + m), kEw, 0, st>>>(n, m, gx, dL_dy ? gy : nullptr, P.D2, P.D1, xbar, ybar);
   if ((e = cudaMemsetAsync(grads, 0, sizeof(double) * (size_t)(n + m + nnz), st))) return e;
-  const size_t sm1 = spmv_bytes();
-  const double *ck = reinterpret_cast<const double *>(U.ckpts.ptr());
+  const size_t sm1 = spmv_bytes<double>(), smf = spmv_bytes<F>();
+  const F *ck = reinterpret_cast<const F *>(U.ckpts.ptr());
   for (int sg = U.nseg - 1; sg >= 0; --sg) {
     const int t0 = sg * L, len = std::min(L, U.T - t0);
-    if ((e = cudaMemcpyAsync(xa, ck + (size_t)sg * (n + m), sizeof(double) * n, cudaMemcpyDeviceToDevice, st)))
+    if ((e = cudaMemcpyAsync(xa, ck + (size_t)sg * (n + m), sizeof(F) * n, cudaMemcpyDeviceToDevice, st)))
       return e;
-    if ((e = cudaMemcpyAsync(ya, ck + (size_t)sg * (n + m) + n, sizeof(double) * m, cudaMemcpyDeviceToDevice, st)))
+    if ((e = cudaMemcpyAsync(ya, ck + (size_t)sg * (n + m) + n, sizeof(F) * m, cudaMemcpyDeviceToDevice, st)))
       return e;
-    launch_spmv<double>(K, xa, Kxa, st);
-    double *xc = xa, *xn = xb2, *yc = ya, *yn = yb2, *kc = Kxa, *kn = Kxb;
+    launch_spmv<F>(Kf, xa, Kxa, st);
+    F *xc = xa, *xn = xb2, *yc = ya, *yn = yb2, *kc = Kxa, *kn = Kxb;
     for (int t = 0; t < len; ++t) {
+      // the forward arithmetic: tau, sigma as the step kernels form them
       const double eta = U.eta_host[(size_t)(t0 + t)];
-      const double tau = eta * U.inv_omega, sigma = eta * U.omega;
-      if (KT.nblocks > 0)
-        k_unr_primal<<<KT.nblocks, kThreads, sm1, st>>>(KT, P, xc, yc, xn, XE + (size_t)t * n, MX + (size_t)t * n,
-                                                         tau);
-      k_unr_dual<<<K.nblocks, kThreads, sm1, st>>>(K, P, xn, kc, yc, yn, kn, YS + (size_t)t * m, MY + (size_t)t * m,
-                                                   sigma);
+      const F tau = (F)(eta * U.inv_omega), sigma = (F)(eta * U.omega);
+      if (KTf.nblocks > 0)
+        k_unr_primal<F><<<KTf.nblocks, kThreads, smf, st>>>(KTf, Pf, xc, yc, xn, XE + (size_t)t * n,
+                                                            MX + (size_t)t * n, tau);
+      k_unr_dual<F><<<Kf.nblocks, kThreads, smf, st>>>(Kf, Pf, xn, kc, yc, yn, kn, YS + (size_t)t * m,
+                                                       MY + (size_t)t * m, sigma);
       std::swap(xc, xn);
       std::swap(yc, yn);
       std::swap(kc, kn);
     }
     for (int t = len - 1; t >= 0; --t) {
+      // the adjoint in float64 with the float64 K~ (the step sizes of the map)
       const double eta = U.eta_host[(size_t)(t0 + t)];
-      const double tau = eta * U.inv_omega, sigma = eta * U.omega;
+      const double tau = (double)(F)(eta * U.inv_omega), sigma = (double)(F)(eta * U.omega);
       k_adj_h<<<ew_grid(m), kEw, 0, st>>>(m, ybar, MY + (size_t)t * m, h);
       if (KT.nblocks > 0)
         k_adj_cols<<<KT.nblocks, kThreads, sm1, st>>>(KT, h, MX + (size_t)t * n, xbar, g, dcs, tau, sigma);
@@ -295,5 +308,17 @@ cudaError_t unroll_backward(UnrollBuffers &U, const Mat<double> &K, const Mat<do
   k_adj_final_K<<<ew_grid(nnz), kEw, 0, st>>>(nnz, row, K.ci, P.D1, P.D2, dKs, U.dK);
   return cudaGetLastError();
 }
+
+#define PDLP_INST(F)                                                                                          \
+  template cudaError_t unroll_forward<F>(UnrollBuffers &, const Mat<F> &, const Mat<F> &, const Problem<F> &,  \
+                                         const State<F> &, const PersistGeo &, const ScalarInit &, double,       \
+                                         double *, int32_t, int32_t, const double *, const double *,              \
+                                         cudaStream_t);                                                            \
+  template cudaError_t unroll_backward<F>(UnrollBuffers &, const Mat<F> &, const Mat<F> &, const Problem<F> &, \
+                                          const Mat<double> &, const Mat<double> &, const Problem<double> &,      \
+                                          const double *, const double *, cudaStream_t);
+PDLP_INST(double)
+PDLP_INST(float)
+#undef PDLP_INST
 
 }  // namespace pdlp

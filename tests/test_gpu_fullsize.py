@@ -1,0 +1,117 @@
+"""Parity at the benchmark sizes, in the launch configuration the benchmark
+times (persistent step kernel inside one CUDA graph per solve): the
+100k x 250k MIP-shaped LP, the 1M-node PageRank LP, the 4096-LP batch and the
+20k x 50k unrolled map with T = 500, checkpoint 50.  Checks are ones the
+oracle can afford at these sizes: bit-exact preprocessing, the first
+iterates, Eq. (15) at returned points, sampled batch members and the full
+adjoint."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+import paper_2106_04756_gb300 as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mip():
+    return lpgen.mip_relaxation_100k()
+
+
+def test_mip100k_preprocessing_is_bit_exact(gpu_lib, oracle_lib, mip):
+    lp = mip
+    with P.Context.from_lp(lp) as ctx:
+        g = ctx.get_scaled()
+    trp, tci, _, perm = oracle.transpose(lp)
+    assert np.array_equal(g["KT_row_ptr"], trp) and np.array_equal(g["KT_col_idx"], tci)
+    assert np.array_equal(g["KT_perm"], perm)
+    v, D1, D2 = oracle.precondition(lp)
+    assert np.array_equal(g["Kval"], v) and np.array_equal(g["KTval"], v[perm])
+    assert np.array_equal(g["D1"], D1) and np.array_equal(g["D2"], D2)
+    cs, qs, ls, us = oracle.transform(lp, D1, D2)
+    for k, ref in (("cs", cs), ("qs", qs), ("ls", ls), ("us", us)):
+        assert np.array_equal(g[k], ref), k
+
+
+@pytest.mark.parametrize("iters", [20, 40])
+def test_mip100k_first_iterates_match_oracle(gpu_lib, oracle_lib, mip, iters):
+    lp = mip
+    x_g, y_g, r_g = P.solve(lp, iter_limit=iters)
+    x_o, y_o, r_o = oracle.solve(lp, iter_limit=iters)
+    assert r_g["iters"] == r_o["iters"] == iters
+    assert r_g["kkt_passes"] == r_o["kkt_passes"] and r_g["restarts"] == r_o["restarts"]
+    tol = {20: 1e-9, 40: 1e-8}[iters]
+    assert np.abs(x_g - x_o).max() <= tol * max(1.0, np.abs(x_o).max())
+    assert np.abs(y_g - y_o).max() <= tol * max(1.0, np.abs(y_o).max())
+
+
+@pytest.mark.parametrize("prec", [P.PDLP_FP64, P.PDLP_FP32])
+def test_mip100k_reported_terms_are_those_of_the_returned_point(gpu_lib, oracle_lib, mip, prec):
+    lp = mip
+    # float64: the device's Eq. (15) terms are the oracle's at the returned
+    # point up to summation order; float32: the device evaluates them from
+    # its float32 products K x, K^T y, so they agree to float32 accuracy
+    x, y, r = P.solve(lp, precision=prec, iter_limit=2000)
+    k = oracle.kkt(lp, x, y)
+    ta, tr = (1e-9, 1e-6) if prec == P.PDLP_FP64 else (1e-5, 1e-3)
+    for key in ("primal_obj", "dual_obj"):
+        assert abs(r[key] - k[key]) <= ta * (1 + abs(k[key])), (key, r[key], k[key])
+    for key in ("rel_gap", "rel_pres", "rel_dres"):
+        assert abs(r[key] - k[key]) <= tr * k[key] + 1e-12, (key, r[key], k[key])
+
+
+def test_pagerank_1m_float32_refinement_to_1e8(gpu_lib, oracle_lib):
+    lp = lpgen.pagerank_1m()
+    x, y, r = P.solve(lp, precision=P.PDLP_FP32_REFINE)
+    assert r["status_name"] == "OPTIMAL", r
+    k = oracle.kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8, k
+    nodes = lp.n
+    G = lp.scipy()[:nodes]
+    S = ((sp.identity(nodes) - G) / 0.85).tocsr()
+    p = np.full(nodes, 1.0 / nodes)
+    for _ in range(200):
+        p = 0.85 * (S @ p) + 0.15 / nodes
+    assert abs(x.sum() - 1.0) <= 1e-7
+    assert np.abs(x - p).max() <= 1e-3 * p.max()
+
+
+def test_batch_4096_sampled_members_match_oracle(gpu_lib, oracle_lib):
+    lps = lpgen.batch_4096()
+    cap = 20000
+    xs, ys, rs = P.solve_batch(lps, rel_tol=1e-6, iter_limit=cap)
+    rng = np.random.default_rng(20210609)
+    solved = [b for b in range(len(lps)) if rs[b]["status_name"] == "OPTIMAL"]
+    unsolved = [b for b in range(len(lps)) if rs[b]["status_name"] != "OPTIMAL"]
+    assert len(solved) >= 0.9 * len(lps)
+    for b in rng.choice(solved, 64, replace=False):
+        lp = lps[b]
+        k = oracle.kkt(lp, xs[b], ys[b])
+        assert k["rel_kkt"] <= 1e-6, (b, k)
+        ref = lp.c @ lp.x_star
+        assert abs(lp.c @ xs[b] - ref) <= 1e-5 * (1 + abs(ref)), (b, lp.c @ xs[b], ref)
+    # members stopped by the cap are slow for the method itself: the oracle
+    # also needs most of the cap (or more) on them
+    for b in rng.choice(unsolved, min(8, len(unsolved)), replace=False):
+        assert rs[b]["status_name"] == "ITER_LIMIT" and rs[b]["iters"] == cap
+        _, _, ro = oracle.solve(lps[b], eps=1e-6, iter_limit=cap)
+        assert ro["status_name"] == "ITER_LIMIT" or ro["iters"] >= cap // 4, (b, ro["iters"])
+
+
+def test_unroll_20k_T500_adjoint_matches_oracle(gpu_lib, oracle_lib):
+    lp = lpgen.unroll_20k()
+    lp.c = lp.c + 0.05 * np.random.default_rng(4).standard_normal(lp.n)
+    T = 500
+    target = np.random.default_rng(5).standard_normal(lp.n)
+    with P.Context.from_lp(lp) as ctx:
+        x, _, eta = ctx.unroll(T, 50)
+        dc, dq, dK = ctx.grad(x - target, None)
+    omega = oracle.unroll_schedule(lp, 1)[1]
+    x2, _ = oracle.unroll_forward(lp, eta, omega)
+    assert np.linalg.norm(x - x2) <= 1e-9 * np.linalg.norm(x2)
+    rc, rq, rk = oracle.unroll_vjp(lp, eta, omega, x - target, None)
+    for a, b in ((dc, rc), (dq, rq), (dK, rk)):
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)

@@ -166,6 +166,25 @@ def test_autograd_function_backward_is_pdlp_grad(gpu_lib):
     assert np.array_equal(kv.grad.cpu().numpy(), dK)
 
 
+def test_float32_forward_float64_adjoint(gpu_lib, oracle_lib):
+    # the float32 map is the float64 map up to float32 rounding: x_T, y_T
+    # agree to 1e-4; the adjoints agree to 1e-2, the difference coming from
+    # dual-projection masks of rows that sit at their bound (y_i = 0), which
+    # float32 rounding puts on the other side of the kink for a few steps
+    lp = CASES["mip_2000x5000"]()
+    T = 120
+    rng = np.random.default_rng(21)
+    gx = rng.standard_normal(lp.n)
+    with P.Context.from_lp(lp, precision=P.PDLP_FP32) as ctx:
+        x, y, eta = ctx.unroll(T, 50)
+        dc, dq, dK = ctx.grad(gx, None)
+    omega = _omega(lp)
+    x2, y2 = oracle.unroll_forward(lp, eta, omega)
+    assert _rel(x, x2) <= 1e-4 and _rel(y, y2) <= 1e-4
+    rc, rq, rk = oracle.unroll_vjp(lp, eta, omega, gx, None)
+    assert _rel(dc, rc) <= 1e-2 and _rel(dq, rq) <= 1e-2 and _rel(dK, rk) <= 1e-2
+
+
 def test_grad_without_unroll_and_bad_checkpoints_are_rejected(gpu_lib):
     lp = CASES["planted_25x40"]()
     with P.Context.from_lp(lp) as ctx:
