@@ -41,6 +41,9 @@ constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kSortMax = 4096;  // n + m of one LP (breakpoint sort in shared memory)
 constexpr int kNumBuckets = 5;  // by mean row length of K: <8, <16, <32, <64, >=64
+// dynamic shared memory: the breakpoint sort, or the product tile of a product
+constexpr size_t kBatchSmem = 96 * 1024;
+static_assert(kBatchSmem >= (size_t)kSortMax * (sizeof(double) + sizeof(int)), "sort buffer");
 
 struct BatchIn {
   int32_t count;
@@ -73,6 +76,7 @@ struct Work {
   int32_t *trp, *tci, *perm, *fill, *rpk;
   T *k, *kt;  // K~ and K~^T values in the arithmetic type
   T *x[2], *y[2], *Kx[2], *xs[2], *ys[2], *x0, *y0, *KTy, *KTys, *Kxs, *xa, *ya;
+  T *csT, *lsT, *usT, *qsT, *yloT;  // scaled data in the arithmetic type
   double *gt, *ga, *gw, *gv;  // gap items
 };
 
@@ -80,7 +84,7 @@ template <typename T>
 size_t work_bytes(int mm, int nn, long long zz) {
   const size_t d = sizeof(double) * (size_t)(4 * zz + 8 * (size_t)nn + 6 * (size_t)mm + 4 * (size_t)(nn + mm));
   const size_t i = sizeof(int32_t) * (size_t)(2 * zz + 2 * (size_t)nn + (size_t)mm + 3);
-  const size_t t = sizeof(T) * (size_t)(2 * zz + 9 * (size_t)nn + 9 * (size_t)mm) + 64;
+  const size_t t = sizeof(T) * (size_t)(2 * zz + 12 * (size_t)nn + 11 * (size_t)mm) + 64;
   return (d + i + t + 255) / 256 * 256;
 }
 
@@ -107,12 +111,15 @@ __device__ Work<T> carve(char *base, int mm, int nn, long long zz) {
   w.KTys = tt(nn); w.xa = tt(nn); tt(nn);
   w.y[0] = tt(mm); w.y[1] = tt(mm); w.Kx[0] = tt(mm); w.Kx[1] = tt(mm); w.ys[0] = tt(mm); w.ys[1] = tt(mm);
   w.y0 = tt(mm); w.Kxs = tt(mm); w.ya = tt(mm);
+  w.csT = tt(nn); w.lsT = tt(nn); w.usT = tt(nn); w.qsT = tt(mm); w.yloT = tt(mm);
   return w;
 }
 
 // ------------------------------------------------------------ CTA helpers
 
-// Fixed-order CTA sum of NV values; the result is returned in every thread.
+// Fixed-order CTA sum of NV values; the result is returned in every thread
+// (thread 0 adds the warp partials; float64 is slow on this part, so the
+// final adds are not repeated in every thread).
 template <int NV>
 __device__ __forceinline__ void cta_sum(double (&v)[NV], double *red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -127,12 +134,17 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double *red) {
     for (int a = 0; a < NV; ++a) red[a * kBWarps + warp] = v[a];
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int a = 0; a < NV; ++a) {
-    double t = 0.0;
-    for (int w = 0; w < kBWarps; ++w) t += red[a * kBWarps + w];
-    v[a] = t;
+    for (int a = 0; a < NV; ++a) {
+      double t = 0.0;
+      for (int w = 0; w < kBWarps; ++w) t += red[a * kBWarps + w];
+      red[NV * kBWarps + a] = t;
+    }
   }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = red[NV * kBWarps + a];
   __syncthreads();
 }
 
@@ -151,20 +163,68 @@ __device__ __forceinline__ double cta_max(double v, double *red) {
 
 // Row sums of a CSR block (rows, rp with rows + 1 entries, values a, columns
 // ci) with L lanes per row; epi(row, sum) runs in the row's first lane.
+// Two passes per tile of whole rows with at most `cap` nonzeros: every
+// product a_k v[ci_k] of the tile is formed with all its loads independent
+// (coalesced a and ci, gathered v) into shared memory `prod`, then each row
+// is summed from shared memory (fixed order: lane gl takes k = s + gl,
+// s + gl + L, ..., then a shuffle tree).  A row longer than `cap` is summed
+// directly from global memory.
 template <typename T, typename Epi>
 __device__ __forceinline__ void cta_spmv(int rows, const int32_t *rp, const int32_t *ci, const T *a, const T *v,
-                                         int L, Epi &&epi) {
+                                         int L, T *prod, int cap, Epi &&epi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = 32 / L, g = lane / L, gl = lane % L;
-  for (int base = warp * per; base < rows; base += kBWarps * per) {
-    const int r = base + g;
-    T acc = T(0);
-    if (r < rows) {
-      const int e = rp[r + 1];
-      for (int k = rp[r] + gl; k < e; k += L) acc = fma(a[k], v[ci[k]], acc);
+  int r0 = 0;
+  while (r0 < rows) {
+    // last row end r1 with rp[r1] - rp[r0] <= cap (same in every thread)
+    const int base = rp[r0];
+    int lo = r0, hi = rows;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rp[mid] - base <= cap) lo = mid;
+      else hi = mid - 1;
     }
-    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, L);
-    if (r < rows && gl == 0) epi(r, acc);
+    int r1 = lo;
+    if (r1 == r0) {  // one row longer than the tile: direct sum by warp 0
+      if (warp == 0) {
+        T acc = T(0);
+        for (int k = base + lane; k < rp[r0 + 1]; k += 32) acc = fma(a[k], v[ci[k]], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) epi(r0, acc);
+      }
+      __syncthreads();
+      r0 += 1;
+      continue;
+    }
+    const int cnt = rp[r1] - base;
+    for (int e0 = threadIdx.x; e0 < cnt; e0 += 4 * kBThreads) {
+      T av[4], vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * kBThreads;
+        av[u] = e < cnt ? a[base + e] : T(0);
+        vv[u] = e < cnt ? v[ci[base + e]] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * kBThreads;
+        if (e < cnt) prod[e] = av[u] * vv[u];
+      }
+    }
+    __syncthreads();
+    for (int rb = r0 + warp * per; rb < r1; rb += kBWarps * per) {
+      const int r = rb + g;
+      T acc = T(0);
+      if (r < r1) {
+        const int e = rp[r + 1] - base;
+        for (int k = rp[r] - base + gl; k < e; k += L) acc += prod[k];
+      }
+      for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, L);
+      if (r < r1 && gl == 0) epi(r, acc);
+    }
+    __syncthreads();
+    r0 = r1;
   }
 }
 
@@ -347,9 +407,13 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
                                                      size_t slab_bytes, int mm, int nn, long long zz) {
   extern __shared__ __align__(16) char bsm[];
   __shared__ double red[3 * kBThreads + 8];
+  __shared__ double fac[2][kMaxEval];  // Algorithm 2 factors of the next eval_every steps
+  __shared__ double s_step[4];
   __shared__ int s_lp;
   double *skey = reinterpret_cast<double *>(bsm);
   int *sidx = reinterpret_cast<int *>(skey + kSortMax);
+  T *prod = reinterpret_cast<T *>(bsm);  // products of the current tile (not live with the sort)
+  const int cap = (int)(kBatchSmem / sizeof(T));
   Work<T> w = carve<T>(slab + slab_bytes * blockIdx.x, mm, nn, zz);
   for (;;) {
     if (threadIdx.x == 0) {
@@ -474,12 +538,17 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
       w.cs[j] = w.D2[j] * c[j];
       w.ls[j] = l[j] / w.D2[j];
       w.us[j] = u[j] / w.D2[j];
+      w.csT[j] = (T)w.cs[j];
+      w.lsT[j] = (T)w.ls[j];
+      w.usT[j] = (T)w.us[j];
       nc2[0] += w.cs[j] * w.cs[j];
       nc2[2] += c[j] * c[j];
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       w.qs[i] = w.D1[i] * q[i];
       w.ylos[i] = (ineq[i] ? 0.0 : -INFINITY) / w.D1[i];
+      w.qsT[i] = (T)w.qs[i];
+      w.yloT[i] = (T)w.ylos[i];
       nc2[1] += w.qs[i] * w.qs[i];
       nc2[3] += q[i] * q[i];
     }
@@ -514,7 +583,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     int32_t *rpk = w.rpk;
     for (int i = threadIdx.x; i <= m; i += blockDim.x) rpk[i] = i < m ? rp_in[i] : nnz;
     __syncthreads();
-    cta_spmv<T>(m, rpk, ci, w.k, w.x[0], Lk, [&](int i, T s) { w.Kx[0][i] = s; });
+    cta_spmv<T>(m, rpk, ci, w.k, w.x[0], Lk, prod, cap, [&](int i, T s) { w.Kx[0][i] = s; });
     __syncthreads();
     // ---- Algorithm 1 with evaluations
     int cur = 0;
@@ -523,6 +592,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     int status = kRunning, ret_avg = 0;
     double kkt[2][8];
     bool first_eval = true;
+    long long fac_k0 = 0;
     for (;;) {
       // ---------- evaluation (at the start and every eval_every steps)
       const bool eval_now = first_eval || (k % o.eval_every == 0) || k >= o.iter_limit ||
@@ -532,13 +602,13 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
         const double inv = avg ? 1.0 / sum_eta : 0.0;
         const T *x = w.x[cur], *y = w.y[cur], *Kx = w.Kx[cur];
         // K^T y (current), K^T ys, K xs
-        cta_spmv<T>(n, w.trp, w.tci, w.kt, y, Lt, [&](int j, T s) { w.KTy[j] = s; });
+        cta_spmv<T>(n, w.trp, w.tci, w.kt, y, Lt, prod, cap, [&](int j, T s) { w.KTy[j] = s; });
         if (avg) {
           for (int j = threadIdx.x; j < n; j += blockDim.x) w.xa[j] = (T)((double)w.xs[cur][j] * inv);
           for (int i = threadIdx.x; i < m; i += blockDim.x) w.ya[i] = (T)((double)w.ys[cur][i] * inv);
           __syncthreads();
-          cta_spmv<T>(n, w.trp, w.tci, w.kt, w.ya, Lt, [&](int j, T s) { w.KTys[j] = s; });
-          cta_spmv<T>(m, rpk, ci, w.k, w.xa, Lk, [&](int i, T s) { w.Kxs[i] = s; });
+          cta_spmv<T>(n, w.trp, w.tci, w.kt, w.ya, Lt, prod, cap, [&](int j, T s) { w.KTys[j] = s; });
+          cta_spmv<T>(m, rpk, ci, w.k, w.xa, Lk, prod, cap, [&](int i, T s) { w.Kxs[i] = s; });
         }
         __syncthreads();
         // Eq. (15) terms for both candidates on the original problem
@@ -663,27 +733,41 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           }
         }
         first_eval = false;
+        // Algorithm 2's factors 1 - (k+1)^-0.3, 1 + (k+1)^-0.6 (k counted from 1)
+        // for the steps up to the next evaluation
+        fac_k0 = k;
+        for (int i = threadIdx.x; i < min(o.eval_every, kMaxEval); i += blockDim.x) {
+          const double kk = (double)(k + i + 1);
+          fac[0][i] = 1.0 - pow(kk + 1.0, -0.3);
+          fac[1][i] = 1.0 + pow(kk + 1.0, -0.6);
+        }
+        __syncthreads();
       }
       // ---------- one accepted step of Algorithm 2
       double eta = eta_hat;
       bool accepted = false;
       while (!accepted) {
-        const T tau = (T)(eta / omega), sig = (T)(eta * omega), et = (T)eta;
+        if (threadIdx.x == 0) {
+          s_step[0] = eta / omega;
+          s_step[1] = eta * omega;
+        }
+        __syncthreads();
+        const T tau = (T)s_step[0], sig = (T)s_step[1], et = (T)eta;
         const T *x = w.x[cur], *y = w.y[cur], *Kx = w.Kx[cur], *xs = w.xs[cur], *ys = w.ys[cur];
         T *xn = w.x[cur ^ 1], *yn = w.y[cur ^ 1], *Kxn = w.Kx[cur ^ 1], *xsn = w.xs[cur ^ 1], *ysn = w.ys[cur ^ 1];
         double s3[3] = {0.0, 0.0, 0.0};
-        cta_spmv<T>(n, w.trp, w.tci, w.kt, y, Lt, [&](int j, T g) {
+        cta_spmv<T>(n, w.trp, w.tci, w.kt, y, Lt, prod, cap, [&](int j, T g) {
           const T xj = x[j];
-          const T xp = clampv<T>(xj - tau * ((T)w.cs[j] - g), (T)w.ls[j], (T)w.us[j]);
+          const T xp = clampv<T>(xj - tau * (w.csT[j] - g), w.lsT[j], w.usT[j]);
           xn[j] = xp;
           xsn[j] = xs[j] + et * xp;
           const T d = xp - xj;
           s3[0] += (double)(d * d);
         });
         __syncthreads();
-        cta_spmv<T>(m, rpk, ci, w.k, xn, Lk, [&](int i, T kxn) {
-          const T kx = Kx[i], yi = y[i], lo = (T)w.ylos[i];
-          const T v = yi + sig * ((T)w.qs[i] - T(2) * kxn + kx);
+        cta_spmv<T>(m, rpk, ci, w.k, xn, Lk, prod, cap, [&](int i, T kxn) {
+          const T kx = Kx[i], yi = y[i], lo = w.yloT[i];
+          const T v = yi + sig * (w.qsT[i] - T(2) * kxn + kx);
           const T yp = v > lo ? v : lo;
           yn[i] = yp;
           Kxn[i] = kxn;
@@ -694,18 +778,33 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
         });
         cta_sum<3>(s3, red);
         passes_used += 1;
-        const double num = omega * s3[0] + s3[1] / omega;
-        const double den = 2.0 * fabs(s3[2]);
-        const double eta_bar = den > 0.0 ? num / den : INFINITY;
-        const double kk = (double)(k + 1);
-        const double e1 = (1.0 - pow(kk + 1.0, -0.3)) * eta_bar;
-        const double e2 = (1.0 + pow(kk + 1.0, -0.6)) * eta;
-        const double eta_next = e1 < e2 ? e1 : e2;
-        if (!isfinite(num) || isnan(eta_bar) || isnan(s3[2])) {
+        // Algorithm 2's test, in one thread
+        if (threadIdx.x == 0) {
+          const double num = omega * s3[0] + s3[1] / omega;
+          const double den = 2.0 * fabs(s3[2]);
+          const double eta_bar = den > 0.0 ? num / den : INFINITY;
+          const long long idx = k - fac_k0;
+          double fr, fg;
+          if (idx >= 0 && idx < min(o.eval_every, kMaxEval)) {
+            fr = fac[0][idx];
+            fg = fac[1][idx];
+          } else {
+            const double kk = (double)(k + 1);
+            fr = 1.0 - pow(kk + 1.0, -0.3);
+            fg = 1.0 + pow(kk + 1.0, -0.6);
+          }
+          const double e1 = fr * eta_bar, e2 = fg * eta;
+          s_step[2] = e1 < e2 ? e1 : e2;
+          s_step[3] = (!isfinite(num) || isnan(eta_bar) || isnan(s3[2])) ? -1.0 : (eta <= eta_bar ? 1.0 : 0.0);
+        }
+        __syncthreads();
+        const double eta_next = s_step[2], verdict = s_step[3];
+        __syncthreads();
+        if (verdict < 0.0) {
           status = kNumErr;
           break;
         }
-        if (eta <= eta_bar) {
+        if (verdict > 0.0) {
           accepted = true;
           cur ^= 1;
           sum_eta += eta;
@@ -757,8 +856,6 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
 
 namespace pdlp {
 namespace {
-
-constexpr size_t kBatchSmem = (size_t)kSortMax * (sizeof(double) + sizeof(int));
 
 struct Tuned {
   bool done[2][kNumBuckets] = {};
