@@ -154,6 +154,22 @@ def _alg_bytes(lp, fp):
     return primal, dual
 
 
+def aggregate_over_ranks(elapsed, iters, device=None):
+    """Whole-job figures of N replicas: the slowest rank's timed seconds and
+    the iterations of all ranks (torch.distributed, any backend; one process
+    per GPU).  Without an initialised process group: the rank's own."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(elapsed), float(iters)
+    t = torch.tensor([float(elapsed), float(iters)], dtype=torch.float64, device=device)
+    mx = t[:1].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t[1:].clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx.item()), float(sm.item())
+
+
 def _batch_line(P):
     """4096 planted LPs (m in [20, 400], n in [50, 1000], 5% density) in one
     persistent launch per call: LPs/s and iterations/s to 1e-6 and 1e-8."""
@@ -290,16 +306,7 @@ def main():
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     elapsed = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-        it = torch.tensor([iters], dtype=torch.float64, device=dev)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_iters = float(it.item())
-    else:
-        total_iters = float(iters)
+    elapsed, total_iters = aggregate_over_ranks(elapsed, iters, dev if ws > 1 else None)
     value = total_iters / elapsed
     if rank != 0:
         return
