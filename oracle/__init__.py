@@ -51,7 +51,8 @@ class Opts(C.Structure):
                 ("ruiz_iters", C.c_int32), ("pock_chambolle", C.c_int32),
                 ("pw_theta", C.c_double), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
                 ("beta_art", C.c_double), ("eval_every", C.c_int32), ("eps_zero", C.c_double),
-                ("adaptive_restart", C.c_int32), ("pw_update", C.c_int32)]
+                ("adaptive_restart", C.c_int32), ("pw_update", C.c_int32),
+                ("step_policy", C.c_int32), ("omega0", C.c_double)]
 
 
 class Result(C.Structure):
@@ -85,6 +86,8 @@ def lib():
             L.or_solve_traced.argtypes = [C.POINTER(_Lp), C.POINTER(Opts), P, P, P, P, C.POINTER(Result), P,
                                           C.c_int32, C.POINTER(C.c_int32)]
             L.or_pdhg_fixed.argtypes = [C.POINTER(_Lp), C.c_double, C.c_double, C.c_int64, P, P]
+            L.or_power_norm.argtypes = [C.POINTER(_Lp), C.c_int32, C.c_int32]
+            L.or_power_norm.restype = C.c_double
             L.or_unroll_schedule.argtypes = [C.POINTER(_Lp), C.c_int32, C.c_int32, C.c_int64, P, P, P, P, P, P]
             L.or_unroll_forward.argtypes = [C.POINTER(_Lp), C.c_int32, C.c_int32, C.c_int64, P,
                                             C.c_double, P, P, P, P]
@@ -211,6 +214,12 @@ def solve_traced(lp, x0=None, y0=None, ylo=None, trace_cap=256, **opts):
     lib().or_solve_traced(C.byref(pin.s), C.byref(o), _p(x0), _p(y0), _p(x), _p(y), C.byref(r), _p(tr),
                           trace_cap, C.byref(cnt))
     return x, y, r.asdict(), tr[:min(cnt.value, trace_cap)]
+
+
+def power_norm(lp, ruiz_iters=10, pock_chambolle=1):
+    """||K~||_2 of the preconditioned matrix by power iteration (Section 2)."""
+    pin = _Pinned(lp)
+    return float(lib().or_power_norm(C.byref(pin.s), ruiz_iters, pock_chambolle))
 
 
 def pdhg_fixed(lp, eta, omega, T, x0=None, y0=None):

@@ -69,6 +69,8 @@ void or_default_opts(or_opts *o) {
   o->eps_zero = 1e-10;
   o->adaptive_restart = 1;
   o->pw_update = 1;
+  o->step_policy = 0;
+  o->omega0 = 0.0;
 }
 
 /* ---------------------------------------------------------------- basics */
@@ -357,6 +359,31 @@ static void KT_mul(const scaled_lp *s, const double *y, double *out) {
   spmv(s->n, s->trp, s->tci, s->tv, y, out);
 }
 
+/* ||K~||_2 by power iteration on K~^T K~ (Section 2: baseline step size) */
+static double power_norm(const scaled_lp *s) {
+  int32_t m = s->m, n = s->n;
+  double *v = dalloc((size_t)n), *w = dalloc((size_t)m), *u = dalloc((size_t)n);
+  for (int32_t j = 0; j < n; ++j) v[j] = 1.0 / sqrt((double)n);
+  double nu = 0.0;
+  for (int it = 0; it < OR_POWER_ITERS; ++it) {
+    K_mul(s, v, w);
+    KT_mul(s, w, u);
+    nu = norm2(n, u);
+    if (!(nu > 0.0)) break;
+    for (int32_t j = 0; j < n; ++j) v[j] = u[j] / nu;
+  }
+  free(v); free(w); free(u);
+  return sqrt(nu);
+}
+
+double or_power_norm(const or_lp *lp, int32_t ruiz_iters, int32_t pock_chambolle) {
+  scaled_lp s;
+  scaled_build(lp, ruiz_iters, pock_chambolle, &s);
+  double r = power_norm(&s);
+  scaled_free(&s);
+  return r;
+}
+
 /* InitializePrimalWeight (Section 3.3) */
 static double init_primal_weight(const scaled_lp *s, double eps_zero) {
   double nc = norm2(s->n, s->c), nq = norm2(s->m, s->q);
@@ -487,7 +514,11 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
   double kmax = 0.0;
   for (int32_t k = 0; k < nnz; ++k) kmax = fabs(s.v[k]) > kmax ? fabs(s.v[k]) : kmax;
   double eta_hat = kmax > 0.0 ? 1.0 / kmax : 1.0; /* R4 */
-  double omega = init_primal_weight(&s, o->eps_zero);
+  if (o->step_policy == 1) {                        /* constant step 0.9 / ||K~||_2 */
+    double kn = power_norm(&s);
+    eta_hat = kn > 0.0 ? 0.9 / kn : 1.0;
+  }
+  double omega = o->omega0 > 0.0 ? o->omega0 : init_primal_weight(&s, o->eps_zero);
   int64_t k = 0, kkt_passes = 0, restarts = 0;
   int status = OR_RUNNING, ret_avg = 0;
   const iterate *ret = &z;
@@ -515,6 +546,7 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
         if (trace_on() > 1)
           fprintf(stderr, "  attempt k=%lld eta=%.17g eta_bar=%.17g %s\n", (long long)k, eta, eta_bar,
                   eta <= eta_bar ? "accept" : "reject");
+        if (o->step_policy == 1) { eta_next = eta; break; } /* constant step: always accept */
         if (eta <= eta_bar) break;
         eta = eta_next;
         if (kkt_passes >= o->kkt_pass_limit) { status = OR_KKT_PASS_LIMIT; break; }

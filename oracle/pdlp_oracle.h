@@ -45,7 +45,15 @@ typedef struct {
   double eps_zero;         /* Section 3.3 epsilon_zero                           */
   int32_t adaptive_restart;/* 1: restart scheme of Section 3.2; 0: never restart */
   int32_t pw_update;       /* 1: Algorithm 3 at restarts; 0: keep initial omega  */
+  int32_t step_policy;     /* 0: Algorithm 2; 1: constant eta = 0.9 / ||K~||_2,
+                              ||K~||_2 by power iteration (Section 2's baseline
+                              PDHG step; the "fixed step size" ablation)         */
+  double omega0;           /* > 0: initial primal weight; 0: InitializePrimalWeight */
 } or_opts;
+
+/* Iterations of the power iteration for ||K~||_2 (both the oracle and the
+ * library use this count and the start vector 1/sqrt(n)). */
+#define OR_POWER_ITERS 200
 
 typedef struct {
   int32_t status;
@@ -57,6 +65,11 @@ typedef struct {
 } or_result;
 
 void or_default_opts(or_opts *o);
+
+/* ||K~||_2 of the preconditioned K (Ruiz / Pock-Chambolle settings as given)
+ * by OR_POWER_ITERS steps of power iteration on K~^T K~ from v = 1/sqrt(n):
+ * w = K~ v, u = K~^T w, v = u / ||u||; returns sqrt(||u||) of the last step. */
+double or_power_norm(const or_lp *lp, int32_t ruiz_iters, int32_t pock_chambolle);
 
 /* K^T as CSR (n rows), stable in the row index; perm[t] = position in K of
  * the t-th entry of K^T. */

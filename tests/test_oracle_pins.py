@@ -411,3 +411,32 @@ def test_correction_problem_maps_back_to_optimum(oracle_lib):
     assert k["rel_kkt"] <= 1e-9
     ref = lp.c @ lp.x_star
     assert abs(lp.c @ x - ref) <= 1e-8 * (1 + abs(ref))
+
+
+# ------------------------------------------ constant step (baseline PDHG)
+
+@pytest.mark.parametrize("ruiz,pc", [(0, 0), (10, 1)])
+def test_power_norm_is_the_spectral_norm(oracle_lib, ruiz, pc):
+    # Section 2: ||K||_2 by power iteration; against the dense SVD
+    lp = lpgen.planted_uniform(40, 70, 0.15, seed_key=(90,))
+    est = oracle.power_norm(lp, ruiz, pc)
+    v, D1, D2 = oracle.precondition(lp, ruiz, pc)
+    Ks = sp.csr_matrix((v, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).toarray()
+    true = np.linalg.norm(Ks, 2)
+    # from below, error ~ (s2/s1)^(2 iters); after scaling s2/s1 ~ 0.987 here
+    assert est <= true * (1 + 1e-12)
+    assert est >= true * (1 - 1e-5)
+
+
+def test_constant_step_solve_is_plain_pdhg(oracle_lib):
+    # step_policy 1 without restarts, primal-weight updates or scaling is
+    # PDHG of Eq. (3) with eta = 0.9 / ||K||_2 at every step
+    lp = lpgen.planted_uniform(30, 50, 0.2, seed_key=(91,))
+    T = 150
+    kw = dict(ruiz_iters=0, pock_chambolle=0, adaptive_restart=0, pw_update=0, step_policy=1, omega0=1.0)
+    x, y, r = oracle.solve(lp, iter_limit=T, eps=0.0, **kw)
+    eta = 0.9 / oracle.power_norm(lp, 0, 0)
+    assert r["iters"] == T and r["kkt_passes"] == T
+    assert r["eta"] == pytest.approx(eta, rel=1e-15) and r["omega"] == 1.0
+    x2, y2 = oracle.pdhg_fixed(lp, eta, 1.0, T)
+    assert np.allclose(x, x2, rtol=1e-11, atol=1e-12) and np.allclose(y, y2, rtol=1e-11, atol=1e-12)
