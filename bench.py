@@ -196,6 +196,30 @@ def _batch_line(P):
     return out
 
 
+def _ablation_line(P):
+    """KKT passes to 1e-8 on the 200 x 500 planted LP with each enhancement of
+    Section 3 switched off in turn, and Section 2's baseline PDHG (constant
+    eta = 0.9 / ||K||_2, omega = 1, no restarts, no scaling): the axes of the
+    paper's ablation study and of its Figure 1 comparison."""
+    import lpgen
+    lp = lpgen.small_planted()
+    cap = 200000
+    variants = {
+        "pdlp": {},
+        "no_restarts": {"adaptive_restart": 0},
+        "fixed_primal_weight": {"pw_update": 0},
+        "no_preconditioning": {"ruiz_iters": 0, "pock_chambolle": 0},
+        "constant_step": {"step_policy": 1},
+        "baseline_pdhg": {"step_policy": 1, "omega0": 1.0, "adaptive_restart": 0, "pw_update": 0,
+                          "ruiz_iters": 0, "pock_chambolle": 0},
+    }
+    out = {"workload": "planted_200x500", "rel_tol": 1e-8, "iter_cap": cap}
+    for name, kw in variants.items():
+        _, _, r = P.solve(lp, rel_tol=1e-8, iter_limit=cap, **kw)
+        out[name] = {"kkt_passes": r["kkt_passes"], "status": r["status_name"], "seconds": r["seconds"]}
+    return out
+
+
 def _unroll_line(P, dev, sptr):
     """Unrolled map (T = 500, checkpoint every 50) and its adjoint on the
     20k x 50k planted LP with loss 1/2 ||x_T - x_target||^2."""
@@ -398,6 +422,7 @@ def main():
     if not args.no_extra:
         extra["batch"] = _batch_line(P)
         extra["unroll"] = _unroll_line(P, dev, sptr)
+        extra["ablation"] = _ablation_line(P)
 
     # per solve: ~120 create/setup launches, 13 per evaluation (persistent
     # step kernel, 2 evaluation, 6 gap passes, decide, restart, finish) + 8

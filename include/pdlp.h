@@ -97,6 +97,12 @@ typedef struct {
                                (one CTA per SM); 0: one launch per half-step (primal,
                                dual).  Where the kernel's layout does not fit, 1 runs
                                as 0.                                                     */
+  int32_t step_policy;      /* 0 (default): Algorithm 2's adaptive step; 1: constant
+                               step eta = 0.9 / ||K~||_2 with ||K~||_2 estimated by 200
+                               power iterations (Section 2's baseline PDHG step)      */
+  int32_t pad2_;
+  double omega0;            /* > 0: initial primal weight (Section 2's baseline PDHG
+                               uses 1); 0 (default): InitializePrimalWeight          */
   void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
 } pdlp_options;
 
@@ -110,6 +116,7 @@ typedef struct {
   double gap, pres, dres;         /* absolute left-hand sides of Eq. (15a-c)              */
   double rel_gap, rel_pres, rel_dres; /* each divided by its right-hand factor            */
   double seconds;                 /* device wall time of the solve                        */
+  double step_size, primal_weight; /* eta and omega at the end of the solve              */
 } pdlp_result;
 
 /* ---------------------------------------------------------------- calls */
@@ -183,7 +190,8 @@ int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double *y, double 
  * nullable) receive the solutions, res[count] (nullable) the outcomes.
  * Uses opts.precision (PDLP_FP64 or PDLP_FP32 arithmetic in the SpMVs),
  * rel_tol, iter_limit, kkt_pass_limit, the preconditioner, restart, primal
- * weight and step settings, and opts.stream.  Each LP needs m + n <= 4096;
+ * weight and step settings, and opts.stream (step_policy must be 0 and omega0
+ * 0: Algorithm 2 and InitializePrimalWeight).  Each LP needs m + n <= 4096;
  * invalid data (column index out of range or not increasing within a row,
  * non-finite value, l > u) returns PDLP_ERR_INVALID_ARG naming the first such
  * LP.  All arrays may be host or device memory. */

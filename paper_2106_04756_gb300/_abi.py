@@ -42,7 +42,8 @@ class pdlp_options(C.Structure):
                 ("beta_suff", C.c_double), ("beta_nec", C.c_double), ("beta_art", C.c_double),
                 ("eps_zero", C.c_double), ("inner_tol", C.c_double), ("refine_rounds", C.c_int32),
                 ("unroll_T", C.c_int32), ("ckpt_every", C.c_int32), ("use_graph", C.c_int32),
-                ("persistent", C.c_int32), ("stream", C.c_void_p)]
+                ("persistent", C.c_int32), ("step_policy", C.c_int32), ("pad2_", C.c_int32),
+                ("omega0", C.c_double), ("stream", C.c_void_p)]
 
 
 class pdlp_result(C.Structure):
@@ -51,7 +52,7 @@ class pdlp_result(C.Structure):
                 ("pad_", C.c_int32), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("gap", C.c_double), ("pres", C.c_double), ("dres", C.c_double),
                 ("rel_gap", C.c_double), ("rel_pres", C.c_double), ("rel_dres", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("step_size", C.c_double), ("primal_weight", C.c_double)]
 
     def asdict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}

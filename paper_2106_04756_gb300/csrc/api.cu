@@ -211,6 +211,13 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   in.eval_every = o.eval_every;
   in.adaptive_restart = o.adaptive_restart;
   in.pw_update = o.pw_update;
+  in.const_step = o.step_policy == 1 ? 1 : 0;
+  in.omega0 = o.omega0;
+  if (in.const_step) {  // eta = 0.9 / ||K~||_2 (power iteration; the state vectors are scratch here)
+    double kn = 0.0;
+    CK(power_norm<T>(pr.K, pr.KT, 200, S.xs[0], S.Kx[1], S.xs[1], normpart, ctx->st, &kn), "power iteration");
+    in.eta0 = kn > 0.0 ? 0.9 / kn : 1.0;
+  }
   pr.init = in;
   pr.normpart_ptr = normpart;
   if (!o.use_graph) {
@@ -327,6 +334,8 @@ void read_result(const Scalars &s, double seconds, pdlp_result *res) {
   res->rel_pres = k[6];
   res->rel_dres = k[7];
   res->seconds = seconds;
+  res->step_size = s.eta;
+  res->primal_weight = s.omega;
 }
 
 // Launches one precision's solve graph from the staged start point.
@@ -361,6 +370,8 @@ int check_options(const pdlp_options *o, std::string &why) {
   if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
   if (o->eval_every < 1 || o->eval_every > kMaxEval) { why = "eval_every must be in [1, 256]"; return 0; }
   if (o->persistent < 0 || o->persistent > 1) { why = "persistent must be 0 or 1"; return 0; }
+  if (o->step_policy < 0 || o->step_policy > 1) { why = "step_policy must be 0 or 1"; return 0; }
+  if (!(o->omega0 >= 0.0) || !isfinite(o->omega0)) { why = "omega0 must be finite and >= 0"; return 0; }
   if (o->ruiz_iters < 0) { why = "ruiz_iters must be >= 0"; return 0; }
   if (o->iter_limit < 0 || o->kkt_pass_limit < 0) { why = "limits must be >= 0"; return 0; }
   if (!(o->primal_importance > 0.0)) { why = "primal_importance must be > 0"; return 0; }
@@ -397,6 +408,8 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->ckpt_every = 50;
   o->use_graph = 1;
   o->persistent = 1;
+  o->step_policy = 0;
+  o->omega0 = 0.0;
   o->stream = nullptr;
   return PDLP_OK;
 }

@@ -1018,6 +1018,8 @@ extern "C" int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *
     return bfail(PDLP_ERR_INVALID_ARG, "batch precision must be PDLP_FP64 or PDLP_FP32");
   if (opts->eval_every < 1 || !(opts->rel_tol >= 0.0) || opts->ruiz_iters < 0)
     return bfail(PDLP_ERR_INVALID_ARG, "bad options");
+  if (opts->step_policy != 0 || opts->omega0 != 0.0)
+    return bfail(PDLP_ERR_INVALID_ARG, "the batched solve uses Algorithm 2 and InitializePrimalWeight only");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(opts->stream);
   cudaError_t e = cudaSuccess;
   std::vector<int32_t> hm(count), hn(count);

@@ -116,6 +116,7 @@ struct Scalars {
   int adaptive_restart, pw_update;
   int avg_valid;
   int err;        // bounded-wait failures (device-side timeouts)
+  int const_step; // 1: constant step size (every attempt accepted)
   int trace_n;    // restart evaluations recorded so far (ring of kTraceCap)
 };
 
@@ -500,7 +501,7 @@ struct StepCtl {
   double eta, omega, inv_omega, tau, sigma, sum_eta;
   double dx2, dy2, inter, eta_bar;
   long long k, t, attempts;
-  int cur, chunk_acc, status, pad;
+  int cur, chunk_acc, status, const_step;
 };
 
 // Algorithm 2's test on the reductions of one attempt: eta_bar from the
@@ -522,6 +523,14 @@ __device__ __forceinline__ void step_update(StepCtl &c, double dx2, double dy2, 
   c.attempts += 1;
   if (!isfinite(num) || isnan(eta_bar) || isnan(inter)) {
     c.status = kNumErr;
+    return;
+  }
+  if (c.const_step) {  // Section 2's baseline: a fixed eta, every step taken
+    c.cur ^= 1;
+    c.sum_eta += c.eta;
+    c.k += 1;
+    c.t += 1;
+    c.chunk_acc += 1;
     return;
   }
   if (c.eta <= eta_bar) {
@@ -553,6 +562,7 @@ __device__ __forceinline__ void load_step(const Scalars *s, StepCtl &c) {
   c.cur = s->cur;
   c.chunk_acc = s->chunk_acc;
   c.status = s->status;
+  c.const_step = s->const_step;
 }
 
 __device__ __forceinline__ void store_step(Scalars *s, const StepCtl &c) {

@@ -777,7 +777,9 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Mat<T> A, const T *v, T *out)
 
 __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->eta = in.eta0;
-  s->inv_omega = 1.0 / s->omega;  // omega^0 was set by k_problem_norms
+  if (in.omega0 > 0.0) s->omega = in.omega0;  // else omega^0 as set by k_problem_norms
+  s->inv_omega = 1.0 / s->omega;
+  s->const_step = in.const_step;
   s->tau = in.eta0 * s->inv_omega;
   s->sigma = in.eta0 * s->omega;
   s->sum_eta = 0.0;
@@ -884,6 +886,53 @@ template cudaError_t launch_step_pair<double>(const Mat<double> &, const Mat<dou
                                               const State<double> &, cudaStream_t);
 template cudaError_t launch_step_pair<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                              const State<float> &, cudaStream_t);
+
+template <typename T>
+__global__ void k_pow_fill(T *v, int n) {
+  const T val = (T)(1.0 / sqrt((double)n));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = val;
+}
+
+// ||u||_2 by one CTA in fixed order -> nrm[0]; v = u / ||u|| by the grid.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_pow_norm(const T *u, int n, double *nrm) {
+  __shared__ double red[1024 / 32];
+  double a[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[0] += (double)u[i] * (double)u[i];
+  block_sum<1>(a, red);
+  if (threadIdx.x == 0) nrm[0] = sqrt(a[0]);
+}
+
+template <typename T>
+__global__ void k_pow_scale(const T *u, int n, const double *nrm, T *v) {
+  const double s = nrm[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v[i] = s > 0.0 ? (T)((double)u[i] / s) : u[i];
+}
+
+template <typename T>
+cudaError_t power_norm(const Mat<T> &A, const Mat<T> &AT, int iters, T *v, T *w, T *u, double *nrm,
+                       cudaStream_t st, double *out) {
+  const int n = A.cols;
+  const int g = (n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216;
+  k_pow_fill<T><<<g, 256, 0, st>>>(v, n);
+  for (int it = 0; it < iters; ++it) {
+    launch_spmv<T>(A, v, w, st);
+    launch_spmv<T>(AT, w, u, st);
+    k_pow_norm<T><<<1, 1024, 0, st>>>(u, n, nrm);
+    k_pow_scale<T><<<g, 256, 0, st>>>(u, n, nrm, v);
+  }
+  cudaError_t e;
+  double h = 0.0;
+  if ((e = cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  *out = sqrt(h);
+  return cudaGetLastError();
+}
+template cudaError_t power_norm<double>(const Mat<double> &, const Mat<double> &, int, double *, double *,
+                                        double *, double *, cudaStream_t, double *);
+template cudaError_t power_norm<float>(const Mat<float> &, const Mat<float> &, int, float *, float *, float *,
+                                       double *, cudaStream_t, double *);
 
 template <typename T>
 void launch_spmv(const Mat<T> &A, const T *v, T *out, cudaStream_t st) {

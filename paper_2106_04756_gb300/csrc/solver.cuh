@@ -12,7 +12,8 @@ struct ScalarInit {
   double eta0, rel_tol, beta_suff, beta_nec, beta_art, pw_theta, eps_zero;
   long long iter_limit, attempt_limit;
   unsigned long long time_limit_ns;
-  int eval_every, adaptive_restart, pw_update, pad;
+  int eval_every, adaptive_restart, pw_update, const_step;
+  double omega0;  // > 0: initial primal weight instead of InitializePrimalWeight
 };
 
 template <typename T> cudaError_t set_kernel_attributes();
@@ -23,6 +24,11 @@ template <typename T>
 cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               int reps, cudaStream_t st, float *ms_primal, float *ms_dual);
 template <typename T> void launch_spmv(const Mat<T> &A, const T *v, T *out, cudaStream_t st);
+// ||A||_2 by power iteration on A^T A (A = K with its transpose AT): `iters`
+// steps from v = 1/sqrt(n); scratch v (n), w (m), u (n) and 2 doubles.
+template <typename T>
+cudaError_t power_norm(const Mat<T> &A, const Mat<T> &AT, int iters, T *v, T *w, T *u, double *nrm,
+                       cudaStream_t st, double *out);
 // One step attempt (k_primal, k_dual with the step test) outside any graph.
 template <typename T>
 cudaError_t launch_step_pair(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,

@@ -290,3 +290,39 @@ def test_step_kernel_timing_reports_the_persistent_attempt(gpu_lib):
     with P.Context.from_lp(lp, iter_limit=100, persistent=0) as ctx:
         ctx.solve()
         assert ctx.time_step_kernels(5)[2] == 0.0
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_constant_step_policy_matches_oracle(gpu_lib, oracle_lib, persistent):
+    """step_policy 1: eta = 0.9 / ||K~||_2 by power iteration (Section 2's
+    baseline step), every attempt accepted, restarts as configured."""
+    lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
+    x_g, y_g, r_g = P.solve(lp, iter_limit=120, step_policy=1, persistent=persistent)
+    x_o, y_o, r_o = oracle.solve(lp, iter_limit=120, step_policy=1)
+    assert r_g["step_size"] == pytest.approx(r_o["eta"], rel=1e-12)
+    assert r_g["iters"] == r_g["kkt_passes"] == r_o["iters"] == 120
+    assert r_g["restarts"] == r_o["restarts"]
+    assert np.abs(x_g - x_o).max() <= 1e-8 * max(1.0, np.abs(x_o).max())
+    assert np.abs(y_g - y_o).max() <= 1e-8 * max(1.0, np.abs(y_o).max())
+
+
+def test_baseline_pdhg_is_plain_fixed_step_pdhg(gpu_lib, oracle_lib):
+    """Section 2's baseline PDHG: constant eta = 0.9 / ||K||_2, omega = 1, no
+    restarts, no scaling: the iterates of Eq. (3) with that eta."""
+    lp = lpgen.planted_uniform(200, 500, 0.02, seed_key=(73,))
+    kw = dict(step_policy=1, omega0=1.0, adaptive_restart=0, pw_update=0, ruiz_iters=0, pock_chambolle=0)
+    x, y, r = P.solve(lp, iter_limit=200, rel_tol=0.0, **kw)
+    assert r["primal_weight"] == 1.0 and r["iters"] == 200
+    x2, y2 = oracle.pdhg_fixed(lp, r["step_size"], 1.0, 200)
+    assert np.abs(x - x2).max() <= 1e-10 * max(1.0, np.abs(x2).max())
+    assert np.abs(y - y2).max() <= 1e-10 * max(1.0, np.abs(y2).max())
+
+
+def test_pdlp_takes_fewer_kkt_passes_than_baseline_pdhg(gpu_lib):
+    # the comparison of the paper's Figure 1 on one synthetic LP, to 1e-6
+    lp = lpgen.small_planted()
+    _, _, rb = P.solve(lp, rel_tol=1e-6, iter_limit=200000, step_policy=1, omega0=1.0, adaptive_restart=0,
+                       pw_update=0, ruiz_iters=0, pock_chambolle=0)
+    _, _, rp = P.solve(lp, rel_tol=1e-6)
+    assert rp["status_name"] == "OPTIMAL"
+    assert rp["kkt_passes"] < rb["kkt_passes"], (rp["kkt_passes"], rb["kkt_passes"], rb["status_name"])
