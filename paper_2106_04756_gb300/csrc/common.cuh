@@ -10,10 +10,10 @@
 // each warp stages its chunk's values and gathered vector entries in its own
 // shared-memory slice with coalesced loads, reduces each row with a
 // power-of-two group of lanes and runs the fused epilogue one lane per row.
-// Longer rows are looped over by one warp; rows longer than kSegNnz are split
-// into segments whose partial sums are combined, in segment order, by the
-// last segment warp to finish.  All reductions are deterministic: fixed
-// thread-to-data assignment and fixed combination order.
+// Rows longer than kSegNnz are split into segments of kSegNnz nonzeros whose
+// partial sums are combined, in segment order, by the last segment warp to
+// finish.  All reductions are deterministic: fixed thread-to-data assignment
+// and fixed combination order.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,10 +35,11 @@ constexpr int kGapSlots = 3;           // current, average, restart point
 constexpr int kMaxEval = 256;          // largest eval_every (step-factor table size)
 constexpr int kLrAcc = 8;              // epilogue sums kept per long row
 
-// One warp's share of a CSR matrix.  Three kinds:
+// One warp's share of a CSR matrix.  Two kinds (with kSegNnz == kChunkNnz):
 //   rows [row_begin, row_end) with at most kChunkNnz nonzeros and kChunkRows rows;
-//   one row (row_end = row_begin + 1) longer than kChunkNnz, looped over by the warp;
 //   row_end < 0: a segment [nnz_begin, nnz_end) of long row -(row_end + 1).
+// (A single row longer than kChunkNnz but not than kSegNnz would be a third
+// kind, looped over by one warp; spmv_chunk still handles it.)
 struct Chunk {
   int32_t row_begin, row_end, nnz_begin, nnz_end;
 };

@@ -470,7 +470,7 @@ void build_schedule(int32_t rows, const int32_t *rp, std::vector<Chunk> &chunks,
       ++r;
       continue;
     }
-    if (len > kChunkNnz) {  // one warp loops over the row
+    if (len > kChunkNnz) {  // one warp loops over the row (only if kSegNnz > kChunkNnz)
       chunks.push_back(Chunk{r, r + 1, rp[r], rp[r + 1]});
       ++r;
       continue;
