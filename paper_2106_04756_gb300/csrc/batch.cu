@@ -148,6 +148,37 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double *red) {
   __syncthreads();
 }
 
+// The same sum for NV <= 3 with few float64 adds (float64 is slow on this
+// part): values to shared memory, warp 0 adds kBThreads / 32 per lane, then a
+// 5-step shuffle; the result is returned in every thread.
+template <int NV>
+__device__ __forceinline__ void cta_sum_lean(double (&v)[NV], double *red) {
+  static_assert(NV <= 3, "red holds 3 x kBThreads doubles");
+  const int lane = threadIdx.x & 31;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) red[a * kBThreads + threadIdx.x] = v[a];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double t = 0.0;
+      for (int k = lane; k < kBThreads; k += 32) t += red[a * kBThreads + k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[a] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[3 * kBThreads + a] = v[a];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = red[3 * kBThreads + a];
+}
+
 __device__ __forceinline__ double cta_max(double v, double *red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -776,7 +807,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           s3[1] += (double)(dy * dy);
           s3[2] += (double)dy * (double)dk;
         });
-        cta_sum<3>(s3, red);
+        cta_sum_lean<3>(s3, red);
         passes_used += 1;
         // Algorithm 2's test, in one thread
         if (threadIdx.x == 0) {
