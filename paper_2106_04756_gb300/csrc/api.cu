@@ -55,7 +55,7 @@ struct pdlp_ctx {
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams (library-owned)
   std::string err;
   // matrix (float64 master copy, preconditioned in place)
-  DevBuf rp, ci, val, trp, tci, tval, perm;
+  DevBuf rp, ci, val, trp, tci, tval, perm, rowid;  // rowid: row of every nonzero of K
   DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT, lraccK, lraccKT;
   int32_t nlongK = 0, nlongKT = 0;
   int32_t nblocksK = 0, nblocksKT = 0;
@@ -461,9 +461,10 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
   // validation on the device
   DevBuf errbuf;
   unsigned *derr = dalloc<unsigned>(errbuf, 1);
+  int32_t *rowid = dalloc<int32_t>(ctx->rowid, nnz);
   unsigned herr = 0;
-  if (!derr) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
-  CK(validate(m, n, nnz, rp, ci, val, dc, dq, dl, du, derr, &herr, st), "validate");
+  if (!derr || !rowid) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+  CK(validate(m, n, nnz, rp, ci, val, dc, dq, dl, du, rowid, derr, &herr, st), "validate");
   if (herr) return fail(ctx, PDLP_ERR_INVALID_ARG, validate_message(herr));
   CK(ylo_from_mask(m, mask, dylo, st), "ylo");
   // K^T
@@ -483,7 +484,8 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
   double *rb = dalloc<double>(rbuf, m), *cb = dalloc<double>(cbuf, n);
   if (!D1 || !D2 || !cs || !qs || !ls || !us || !ylos || !rb || !cb)
     return fail(ctx, PDLP_ERR_OOM, "allocation failed");
-  CK(precondition(m, n, nnz, rp, ci, val, trp, tval, perm, o.ruiz_iters, o.pock_chambolle, D1, D2, rb, cb, st),
+  CK(precondition(m, n, nnz, rp, ci, rowid, val, trp, tval, perm, o.ruiz_iters, o.pock_chambolle, D1, D2, rb, cb,
+                  st),
      "precondition");
   CK(transform(m, n, D1, D2, dc, dq, dl, du, dylo, cs, qs, ls, us, ylos, st), "transform");
   // step size 1 / max |K~_ij| (Algorithm 1 initialisation)
@@ -738,6 +740,7 @@ extern "C" int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const d
   if (rc) return rc;
   UnrollBuffers &U = ctx->unr;
   U.nnz = ctx->nnz;
+  U.row = reinterpret_cast<const int32_t *>(ctx->rowid.ptr());
   const double *xin = reinterpret_cast<const double *>(ctx->xin.ptr());
   const double *yin = reinterpret_cast<const double *>(ctx->yin.ptr());
   cudaError_t e;

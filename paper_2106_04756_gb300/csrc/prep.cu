@@ -46,13 +46,23 @@ __global__ void k_validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp,
   if (bad) atomicOr(err, bad);
 }
 
-// Sortedness needs a valid row_ptr; run after k_validate reported none of kBadRowPtr.
-__global__ void k_validate_sorted(int32_t m, const int32_t *rp, const int32_t *ci, unsigned *err) {
+// Row index of every nonzero (one warp per row, lanes strided: a long row
+// is written by its warp with coalesced stores).  Needs a valid row_ptr.
+__global__ void k_row_ids(int32_t m, const int32_t *rp, int32_t *rowid) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < m; i += nw)
+    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) rowid[k] = (int32_t)i;
+}
+
+// Column indices strictly increasing within each row: one check per nonzero.
+__global__ void k_validate_sorted(int64_t nnz, const int32_t *rowid, const int32_t *ci, unsigned *err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    for (int32_t k = rp[i] + 1; k < rp[i + 1]; ++k)
-      if (ci[k] <= ci[k - 1]) { atomicOr(err, (unsigned)kUnsorted); break; }
-  }
+  unsigned bad = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k < nnz; k += stride)
+    if (rowid[k] == rowid[k - 1] && ci[k] <= ci[k - 1]) bad = kUnsorted;
+  if (bad) atomicOr(err, bad);
 }
 
 const char *validate_message(unsigned bits) {
@@ -330,16 +340,12 @@ __global__ void k_norm_to_div(int32_t len, double *nrm, double *D) {
   }
 }
 
-// K~_ij <- (K~_ij / a_i) / b_j, one warp per row.
-__global__ void k_scale_rows(int32_t rows, const int32_t *rp, const int32_t *ci, double *val,
-                             const double *a, const double *b) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < rows; i += nw) {
-    const double ai = a[i];
-    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) val[k] = __ddiv_rn(__ddiv_rn(val[k], ai), b[ci[k]]);
-  }
+// K~_ij <- (K~_ij / a_i) / b_j, one thread per nonzero (rowid: row of each).
+__global__ void k_scale_nnz(int64_t nnz, const int32_t *rowid, const int32_t *ci, double *val, const double *a,
+                            const double *b) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride)
+    val[k] = __ddiv_rn(__ddiv_rn(val[k], a[rowid[k]]), b[ci[k]]);
 }
 
 __global__ void k_fill(double *v, int64_t n, double x) {
@@ -348,9 +354,10 @@ __global__ void k_fill(double *v, int64_t n, double x) {
 }
 
 cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                         double *val, const int32_t *trp, double *tval, const int32_t *perm,
-                         int ruiz_iters, int pock_chambolle, double *D1, double *D2, double *rbuf,
-                         double *cbuf, cudaStream_t st) {
+                         const int32_t *rowid, double *val, const int32_t *trp, double *tval,
+                         const int32_t *perm, int ruiz_iters, int pock_chambolle, double *D1, double *D2,
+                         double *rbuf, double *cbuf, cudaStream_t st) {
+  const int gz = grid_for(nnz, 256);
   const int gm = grid_for(m, 256), gn = grid_for(n, 256);
   const int gmw = grid_for((int64_t)m * 32, 256), gnw = grid_for((int64_t)n * 32, 256);
   k_fill<<<gm, 256, 0, st>>>(D1, m, 1.0);
@@ -362,7 +369,7 @@ cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, c
     k_row_absmax<<<gnw, 256, 0, st>>>(n, trp, tval, cbuf);
     k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
     k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
-    k_scale_rows<<<gmw, 256, 0, st>>>(m, rp, ci, val, rbuf, cbuf);
+    if (nnz > 0) k_scale_nnz<<<gz, 256, 0, st>>>(nnz, rowid, ci, val, rbuf, cbuf);
     sync_t();
   }
   if (pock_chambolle) {
@@ -370,7 +377,7 @@ cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, c
     k_row_abssum_seq<<<gn, 256, 0, st>>>(n, trp, tval, cbuf);
     k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
     k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
-    k_scale_rows<<<gmw, 256, 0, st>>>(m, rp, ci, val, rbuf, cbuf);
+    if (nnz > 0) k_scale_nnz<<<gz, 256, 0, st>>>(nnz, rowid, ci, val, rbuf, cbuf);
     sync_t();
   }
   return cudaGetLastError();
@@ -427,7 +434,7 @@ cudaError_t to_float(const double *src, int64_t n, float *dst, cudaStream_t st) 
 
 cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
                      const double *val, const double *c, const double *q, const double *l,
-                     const double *u, unsigned *derr, unsigned *herr, cudaStream_t st) {
+                     const double *u, int32_t *rowid, unsigned *derr, unsigned *herr, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(derr, 0, sizeof(unsigned), st))) return e;
   const int64_t big = std::max<int64_t>(std::max<int64_t>(m, n), nnz);
@@ -435,7 +442,8 @@ cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const
   if ((e = cudaMemcpyAsync(herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
   if ((e = cudaStreamSynchronize(st))) return e;
   if (*herr & kBadRowPtr) return cudaSuccess;
-  k_validate_sorted<<<grid_for(m, 256), 256, 0, st>>>(m, rp, ci, derr);
+  k_row_ids<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(m, rp, rowid);
+  if (nnz > 1) k_validate_sorted<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, rowid, ci, derr);
   if ((e = cudaMemcpyAsync(herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
   return cudaStreamSynchronize(st);
 }

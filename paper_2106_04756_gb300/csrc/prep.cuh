@@ -37,17 +37,19 @@ class DevBuf {
 };
 
 const char *validate_message(unsigned bits);
+// Checks the input (row_ptr, column range and order, finite data, bounds);
+// on a valid row_ptr also fills rowid[nnz] with the row of every nonzero.
 cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
                      const double *val, const double *c, const double *q, const double *l,
-                     const double *u, unsigned *derr, unsigned *herr, cudaStream_t st);
+                     const double *u, int32_t *rowid, unsigned *derr, unsigned *herr, cudaStream_t st);
 cudaError_t exclusive_scan(const int *in, int64_t n, int *out, int *total, int *tmp, cudaStream_t st);
 int64_t scan_tmp_ints(int64_t n);
 cudaError_t build_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
                             int32_t *trp, int32_t *tci, int32_t *perm, DevBuf &tmp, cudaStream_t st);
 cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                         double *val, const int32_t *trp, double *tval, const int32_t *perm,
-                         int ruiz_iters, int pock_chambolle, double *D1, double *D2, double *rbuf,
-                         double *cbuf, cudaStream_t st);
+                         const int32_t *rowid, double *val, const int32_t *trp, double *tval,
+                         const int32_t *perm, int ruiz_iters, int pock_chambolle, double *D1, double *D2,
+                         double *rbuf, double *cbuf, cudaStream_t st);
 cudaError_t transform(int32_t m, int32_t n, const double *D1, const double *D2, const double *c,
                       const double *q, const double *l, const double *u, const double *ylo,
                       double *cs, double *qs, double *ls, double *us, double *ylos, cudaStream_t st);

@@ -155,11 +155,6 @@ __global__ void k_adj_final_K(int64_t nnz, const int32_t *row, const int32_t *ci
     dK[k] = D1[row[k]] * D2[ci[k]] * dKs[k];
 }
 
-__global__ void k_row_index(int m, const int32_t *rp, int32_t *row) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    for (int k = rp[i]; k < rp[i + 1]; ++k) row[k] = i;
-}
-
 template <typename T>
 size_t spmv_bytes() {
   return spmv_smem_bytes<T>(1);
@@ -249,7 +244,7 @@ cudaError_t unroll_backward(UnrollBuffers &U, const Mat<F> &Kf, const Mat<F> &KT
   double *work = reinterpret_cast<double *>(U.work.get(sizeof(double) * (size_t)(6 * n + 8 * m)));
   F *fwork = reinterpret_cast<F *>(U.fwork.get(sizeof(F) * (size_t)(2 * n + 4 * m)));
   double *grads = reinterpret_cast<double *>(U.grads.get(sizeof(double) * (size_t)(2 * (n + m) + 2 * nnz)));
-  int32_t *row = reinterpret_cast<int32_t *>(U.rowidx.get(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)));
+  const int32_t *row = U.row;
   if (!seg || !work || !fwork || !grads || !row) return cudaErrorMemoryAllocation;
   double *XE = reinterpret_cast<double *>(seg);
   double *YS = XE + (size_t)L * n;
@@ -263,7 +258,6 @@ cudaError_t unroll_backward(UnrollBuffers &U, const Mat<F> &Kf, const Mat<F> &KT
   U.dc = dKs + nnz;
   U.dq = U.dc + n;
   U.dK = U.dq + m;
-  k_row_index<<<ew_grid(m), kEw, 0, st>>>(m, K.rp, row);
   if ((e = cudaMemcpyAsync(gx, dL_dx, sizeof(double) * n, cudaMemcpyDefault, st))) return e;
   if (dL_dy && (e = cudaMemcpyAsync(gy, dL_dy, sizeof(double) * m, cudaMemcpyDefault, st))) return e;
   k_adj_init<<<ew_grid(n + m), kEw, 0, st>>>(n, m, gx, dL_dy ? gy : nullptr, P.D2, P.D1, xbar, ybar);

@@ -18,8 +18,9 @@ struct UnrollBuffers {
   int32_t status = 0;  // kOptimal: the map ran to T steps; else why it stopped
   bool fp32 = false;   // forward map in float32 (adjoint in float64)
   int64_t nnz = 0;
+  const int32_t *row = nullptr;  // row of every nonzero of K (the context's)
   double omega = 1.0, inv_omega = 1.0;
-  DevBuf ckpts, etab, outs, seg, work, fwork, grads, rowidx;
+  DevBuf ckpts, etab, outs, seg, work, fwork, grads;
   std::vector<double> eta_host;
   double *eta = nullptr, *xo = nullptr, *yo = nullptr;
   double *dc = nullptr, *dq = nullptr, *dK = nullptr;
