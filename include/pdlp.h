@@ -53,6 +53,9 @@ extern "C" {
 #define PDLP_KKT_PASS_LIMIT 3   /* one pass = one product with K and one with K^T   */
 #define PDLP_TIME_LIMIT 4
 #define PDLP_NUMERICAL_ERROR 5  /* a step produced NaN / Inf                        */
+#define PDLP_PRIMAL_INFEASIBLE 7 /* presolve: a row without free variables that 0 cannot satisfy */
+#define PDLP_DUAL_INFEASIBLE 8   /* presolve: an empty column whose cost points to an infinite bound
+                                    (the LP is unbounded when it is feasible)            */
 
 /* arithmetic of the iteration */
 #define PDLP_FP64 0         /* K, x, y and all reductions in float64                      */
@@ -100,7 +103,11 @@ typedef struct {
   int32_t step_policy;      /* 0 (default): Algorithm 2's adaptive step; 1: constant
                                step eta = 0.9 / ||K~||_2 with ||K~||_2 estimated by 200
                                power iterations (Section 2's baseline PDHG step)      */
-  int32_t pad2_;
+  int32_t presolve;         /* 1: presolve-lite before the solve (fixed variables l = u
+                               substituted, rows left empty dropped, empty columns set
+                               at the bound their cost points to); the solution and
+                               Eq. (15) are reported on the original LP.  0 (default):
+                               none.  Not with unroll_T > 0.                            */
   double omega0;            /* > 0: initial primal weight (Section 2's baseline PDHG
                                uses 1); 0 (default): InitializePrimalWeight          */
   void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
@@ -129,7 +136,14 @@ int pdlp_default_options(pdlp_options *opts);
  * transpose), applies `ruiz_iters` Ruiz steps and one Pock-Chambolle step
  * (Section 3.5) to K and K^T, transforms c, q, l, u, and captures the CUDA
  * graphs of the iteration.  Returns PDLP_ERR_INVALID_ARG for malformed input
- * (nothing is allocated then).  *out receives the context. */
+ * (nothing is allocated then).  *out receives the context.
+ * With opts.presolve = 1 the reductions run first on the device and the rest
+ * is built for the reduced LP (nothing when the presolve alone decides the
+ * LP: solved, PDLP_PRIMAL_INFEASIBLE or PDLP_DUAL_INFEASIBLE, reported by
+ * pdlp_solve).  A presolved context answers pdlp_solve, pdlp_get_trace and
+ * pdlp_time_step_kernels; the calls that work in the scaled space of one LP
+ * (pdlp_get_scaled, pdlp_normalized_gap, pdlp_unroll, pdlp_grad) return
+ * PDLP_ERR_STATE. */
 int pdlp_create(const pdlp_csr *K, const double *c, const double *q, const double *l,
                 const double *u, const uint8_t *ineq_mask, const pdlp_options *opts,
                 pdlp_ctx **out);

@@ -14,13 +14,14 @@ from typing import Optional
 import numpy as np
 
 from . import _abi
-from ._abi import (PDLP_ERR_CUDA, PDLP_ERR_INVALID_ARG, PDLP_ERR_OOM, PDLP_ERR_STATE, PDLP_ERR_TIMEOUT,
-                   PDLP_FP32, PDLP_FP32_REFINE, PDLP_FP64, PDLP_OK, STATUS_NAMES, PdlpError, check, pdlp_csr,
-                   pdlp_options, pdlp_result)
+from ._abi import (PDLP_DUAL_INFEASIBLE, PDLP_ERR_CUDA, PDLP_ERR_INVALID_ARG, PDLP_ERR_OOM, PDLP_ERR_STATE,
+                   PDLP_ERR_TIMEOUT, PDLP_FP32, PDLP_FP32_REFINE, PDLP_FP64, PDLP_OK, PDLP_PRIMAL_INFEASIBLE,
+                   STATUS_NAMES, PdlpError, check, pdlp_csr, pdlp_options, pdlp_result)
 
 __all__ = ["Context", "default_options", "pdlp_create", "solve", "solve_batch", "batch_lanes", "PdlpError",
            "PDLP_FP64", "PDLP_FP32", "PDLP_FP32_REFINE", "STATUS_NAMES", "PDLP_OK", "PDLP_ERR_INVALID_ARG",
-           "PDLP_ERR_CUDA", "PDLP_ERR_OOM", "PDLP_ERR_TIMEOUT", "PDLP_ERR_STATE"]
+           "PDLP_ERR_CUDA", "PDLP_ERR_OOM", "PDLP_ERR_TIMEOUT", "PDLP_ERR_STATE", "PDLP_PRIMAL_INFEASIBLE",
+           "PDLP_DUAL_INFEASIBLE"]
 
 
 def _is_torch(a) -> bool:

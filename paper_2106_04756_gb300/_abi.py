@@ -22,8 +22,9 @@ PDLP_ERR_TIMEOUT = -4
 PDLP_ERR_STATE = -5
 
 PDLP_RUNNING, PDLP_OPTIMAL, PDLP_ITER_LIMIT, PDLP_KKT_PASS_LIMIT, PDLP_TIME_LIMIT, PDLP_NUMERICAL_ERROR = range(6)
+PDLP_PRIMAL_INFEASIBLE, PDLP_DUAL_INFEASIBLE = 7, 8
 STATUS_NAMES = {0: "RUNNING", 1: "OPTIMAL", 2: "ITER_LIMIT", 3: "KKT_PASS_LIMIT", 4: "TIME_LIMIT",
-                5: "NUMERICAL_ERROR"}
+                5: "NUMERICAL_ERROR", 7: "PRIMAL_INFEASIBLE", 8: "DUAL_INFEASIBLE"}
 
 PDLP_FP64, PDLP_FP32, PDLP_FP32_REFINE = 0, 1, 2
 
@@ -42,7 +43,7 @@ class pdlp_options(C.Structure):
                 ("beta_suff", C.c_double), ("beta_nec", C.c_double), ("beta_art", C.c_double),
                 ("eps_zero", C.c_double), ("inner_tol", C.c_double), ("refine_rounds", C.c_int32),
                 ("unroll_T", C.c_int32), ("ckpt_every", C.c_int32), ("use_graph", C.c_int32),
-                ("persistent", C.c_int32), ("step_policy", C.c_int32), ("pad2_", C.c_int32),
+                ("persistent", C.c_int32), ("step_policy", C.c_int32), ("presolve", C.c_int32),
                 ("omega0", C.c_double), ("stream", C.c_void_p)]
 
 

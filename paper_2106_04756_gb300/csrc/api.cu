@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "prep.cuh"
+#include "presolve.cuh"
 #include "refine.cuh"
 #include "solver.cuh"
 #include "unroll.cuh"
@@ -73,9 +74,12 @@ struct pdlp_ctx {
   Precision<float> pc32;             // float32 solves of refinement corrections
   RefineBuffers ref;
   UnrollBuffers unr;
+  std::unique_ptr<Presolve> pre;     // presolve = 1: the original LP and the maps
+  pdlp_ctx *inner = nullptr;         // presolve = 1: context of the reduced LP (null if none is left)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ~pdlp_ctx() {
     if (st) cudaStreamSynchronize(st);
+    delete inner;
     for (auto &s : cap)
       if (s) cudaStreamDestroy(s);
     if (ev0) cudaEventDestroy(ev0);
@@ -372,11 +376,123 @@ int check_options(const pdlp_options *o, std::string &why) {
   if (o->persistent < 0 || o->persistent > 1) { why = "persistent must be 0 or 1"; return 0; }
   if (o->step_policy < 0 || o->step_policy > 1) { why = "step_policy must be 0 or 1"; return 0; }
   if (!(o->omega0 >= 0.0) || !isfinite(o->omega0)) { why = "omega0 must be finite and >= 0"; return 0; }
+  if (o->presolve < 0 || o->presolve > 1) { why = "presolve must be 0 or 1"; return 0; }
+  if (o->presolve && o->unroll_T > 0) { why = "presolve does not combine with unroll_T > 0"; return 0; }
   if (o->ruiz_iters < 0) { why = "ruiz_iters must be >= 0"; return 0; }
   if (o->iter_limit < 0 || o->kkt_pass_limit < 0) { why = "limits must be >= 0"; return 0; }
   if (!(o->primal_importance > 0.0)) { why = "primal_importance must be > 0"; return 0; }
   if (!(o->pw_smoothing >= 0.0 && o->pw_smoothing <= 1.0)) { why = "pw_smoothing must be in [0, 1]"; return 0; }
   return 1;
+}
+
+// presolve = 1: the reductions of presolve.cu on the original LP, then an
+// inner context (presolve = 0) for what is left.
+int create_presolved(const pdlp_csr *K, const double *c, const double *q, const double *l, const double *u,
+                     const uint8_t *ineq_mask, const pdlp_options &o, pdlp_ctx **out) {
+  std::unique_ptr<pdlp_ctx> hold(new pdlp_ctx());
+  pdlp_ctx *ctx = hold.get();
+  const int m = K->m, n = K->n;
+  const int64_t nnz = K->nnz;
+  ctx->m = m;
+  ctx->n = n;
+  ctx->nnz = nnz;
+  ctx->opts = o;
+  ctx->st = reinterpret_cast<cudaStream_t>(o.stream);
+  cudaStream_t st = ctx->st;
+  CK(cudaEventCreate(&ctx->ev0), "event");
+  CK(cudaEventCreate(&ctx->ev1), "event");
+  ctx->pre.reset(new Presolve());
+  Presolve &pre = *ctx->pre;
+  pre.m0 = m;
+  pre.n0 = n;
+  pre.nnz0 = nnz;
+  int32_t *rp = dalloc<int32_t>(pre.rp0, (size_t)m + 1), *ci = dalloc<int32_t>(pre.ci0, nnz);
+  int32_t *rowid = dalloc<int32_t>(pre.rowid0, nnz);
+  double *val = dalloc<double>(pre.val0, nnz), *dc = dalloc<double>(pre.c0, n), *dq = dalloc<double>(pre.q0, m),
+         *dl = dalloc<double>(pre.l0, n), *du = dalloc<double>(pre.u0, n);
+  uint8_t *mask = dalloc<uint8_t>(pre.ineq0, m);
+  double *xin = dalloc<double>(ctx->xin, n), *yin = dalloc<double>(ctx->yin, m);
+  DevBuf errbuf;
+  unsigned *derr = dalloc<unsigned>(errbuf, 1), herr = 0;
+  if (!rp || !ci || !rowid || !val || !dc || !dq || !dl || !du || !mask || !xin || !yin || !derr)
+    return fail(ctx, PDLP_ERR_OOM, "input allocation failed");
+  CK(cudaMemcpyAsync(rp, K->row_ptr, sizeof(int32_t) * ((size_t)m + 1), cudaMemcpyDefault, st), "copy row_ptr");
+  if (nnz > 0) {
+    CK(cudaMemcpyAsync(ci, K->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDefault, st), "copy col_idx");
+    CK(cudaMemcpyAsync(val, K->val, sizeof(double) * nnz, cudaMemcpyDefault, st), "copy val");
+  }
+  CK(cudaMemcpyAsync(dc, c, sizeof(double) * n, cudaMemcpyDefault, st), "copy c");
+  CK(cudaMemcpyAsync(dq, q, sizeof(double) * m, cudaMemcpyDefault, st), "copy q");
+  CK(cudaMemcpyAsync(dl, l, sizeof(double) * n, cudaMemcpyDefault, st), "copy l");
+  CK(cudaMemcpyAsync(du, u, sizeof(double) * n, cudaMemcpyDefault, st), "copy u");
+  CK(cudaMemcpyAsync(mask, ineq_mask, sizeof(uint8_t) * m, cudaMemcpyDefault, st), "copy ineq_mask");
+  CK(validate(m, n, nnz, rp, ci, val, dc, dq, dl, du, rowid, derr, &herr, st), "validate");
+  if (herr) return fail(ctx, PDLP_ERR_INVALID_ARG, validate_message(herr));
+  CK(presolve_run(pre, st), "presolve");
+  pre.rowid0.reset();
+  pre.ttmp.reset();
+  if (pre.status == kPreReduced) {
+    pdlp_csr K1{pre.m1, pre.n1, pre.nnz1, reinterpret_cast<const int32_t *>(pre.rp1.ptr()),
+                reinterpret_cast<const int32_t *>(pre.ci1.ptr()), reinterpret_cast<const double *>(pre.val1.ptr())};
+    pdlp_options oi = o;
+    oi.presolve = 0;
+    const int rc = pdlp_create(&K1, reinterpret_cast<const double *>(pre.c1.ptr()),
+                               reinterpret_cast<const double *>(pre.q1.ptr()),
+                               reinterpret_cast<const double *>(pre.l1.ptr()),
+                               reinterpret_cast<const double *>(pre.u1.ptr()),
+                               reinterpret_cast<const uint8_t *>(pre.ineq1.ptr()), &oi, &ctx->inner);
+    if (rc) return fail(ctx, rc, std::string("reduced LP: ") + pdlp_last_error(nullptr));
+    for (DevBuf *b : {&pre.rp1, &pre.ci1, &pre.val1, &pre.c1, &pre.q1, &pre.l1, &pre.u1, &pre.ineq1}) b->reset();
+  }
+  *out = hold.release();
+  return PDLP_OK;
+}
+
+int solve_presolved(pdlp_ctx *ctx, const double *x0, const double *y0, double *x_out, double *y_out,
+                    pdlp_result *res) {
+  Presolve &pre = *ctx->pre;
+  cudaStream_t st = ctx->st;
+  const int m = ctx->m, n = ctx->n;
+  double *xin = reinterpret_cast<double *>(ctx->xin.ptr()), *yin = reinterpret_cast<double *>(ctx->yin.ptr());
+  double *x1 = reinterpret_cast<double *>(pre.x1.ptr()), *y1 = reinterpret_cast<double *>(pre.y1.ptr());
+  pdlp_result r;
+  memset(&r, 0, sizeof(r));
+  CK(cudaEventRecord(ctx->ev0, st), "event");
+  if (pre.status == kPreReduced) {
+    const double *sx = nullptr, *sy = nullptr;
+    if (x0 || y0) {
+      if (x0) CK(cudaMemcpyAsync(xin, x0, sizeof(double) * n, cudaMemcpyDefault, st), "x0");
+      if (y0) CK(cudaMemcpyAsync(yin, y0, sizeof(double) * m, cudaMemcpyDefault, st), "y0");
+      CK(presolve_map_start(pre, x0 ? xin : nullptr, y0 ? yin : nullptr, st), "start");
+      sx = x1;
+      sy = y1;
+    }
+    const int rc = pdlp_solve(ctx->inner, sx, sy, x1, y1, &r);
+    if (rc) return fail(ctx, rc, std::string("reduced LP: ") + pdlp_last_error(ctx->inner));
+  } else {
+    CK(cudaMemsetAsync(x1, 0, sizeof(double) * pre.n1, st), "x1");
+    CK(cudaMemsetAsync(y1, 0, sizeof(double) * pre.m1, st), "y1");
+    r.status = pre.status;
+  }
+  double kkt[8];
+  CK(postsolve(pre, x1, y1, xin, yin, kkt, st), "postsolve");
+  CK(cudaEventRecord(ctx->ev1, st), "event");
+  r.primal_obj = kkt[0];
+  r.dual_obj = kkt[1];
+  r.gap = kkt[2];
+  r.pres = kkt[3];
+  r.dres = kkt[4];
+  r.rel_gap = kkt[5];
+  r.rel_pres = kkt[6];
+  r.rel_dres = kkt[7];
+  if (x_out) CK(cudaMemcpyAsync(x_out, xin, sizeof(double) * n, cudaMemcpyDefault, st), "x_out");
+  if (y_out) CK(cudaMemcpyAsync(y_out, yin, sizeof(double) * m, cudaMemcpyDefault, st), "y_out");
+  CK(cudaStreamSynchronize(st), "solve");
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
+  r.seconds = ms * 1e-3;
+  if (res) *res = r;
+  return PDLP_OK;
 }
 
 }  // namespace
@@ -410,6 +526,7 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->persistent = 1;
   o->step_policy = 0;
   o->omega0 = 0.0;
+  o->presolve = 0;
   o->stream = nullptr;
   return PDLP_OK;
 }
@@ -427,6 +544,7 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
   if (opts) o = *opts; else pdlp_default_options(&o);
   std::string why;
   if (!check_options(&o, why)) return fail(nullptr, PDLP_ERR_INVALID_ARG, why);
+  if (o.presolve) return create_presolved(K, c, q, l, u, ineq_mask, o, out);
   std::unique_ptr<pdlp_ctx> hold(new pdlp_ctx());
   pdlp_ctx *ctx = hold.get();
   ctx->m = K->m;
@@ -548,6 +666,7 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
 extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, double *x_out, double *y_out,
                           pdlp_result *res) {
   if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->pre) return solve_presolved(ctx, x0, y0, x_out, y_out, res);
   if (ctx->opts.unroll_T > 0)
     return pdlp_unroll(ctx, ctx->opts.unroll_T, ctx->opts.ckpt_every, x0, y0, x_out, y_out, nullptr);
   int rc = stage_start(ctx, x0, y0);
@@ -612,6 +731,7 @@ extern "C" int pdlp_get_scaled(pdlp_ctx *ctx, double *Kval, int32_t *KT_row_ptr,
                                double *KTval, int32_t *KT_perm, double *D1, double *D2, double *cs,
                                double *qs, double *ls, double *us) {
   if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->pre) return fail(ctx, PDLP_ERR_STATE, "pdlp_get_scaled: not available on a presolved context");
   const size_t n = ctx->n, m = ctx->m, nnz = ctx->nnz;
   cudaStream_t st = ctx->st;
   auto cp = [&](void *dst, const DevBuf &src, size_t bytes) -> cudaError_t {
@@ -636,6 +756,7 @@ extern "C" int pdlp_get_scaled(pdlp_ctx *ctx, double *Kval, int32_t *KT_row_ptr,
 extern "C" int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double *y, double omega, double r,
                                    double *mu, double *value) {
   if (!ctx || !x || !y) return fail(ctx, PDLP_ERR_INVALID_ARG, "NULL argument");
+  if (ctx->pre) return fail(ctx, PDLP_ERR_STATE, "pdlp_normalized_gap: not available on a presolved context");
   if (!(r > 0.0) || !(omega > 0.0)) return fail(ctx, PDLP_ERR_INVALID_ARG, "r and omega must be > 0");
   int rc = setup_fp64(ctx);
   if (rc) return rc;
@@ -673,6 +794,11 @@ extern "C" int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double 
 
 extern "C" int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *count) {
   if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->pre) {
+    if (!ctx->inner) return fail(ctx, PDLP_ERR_STATE, "the presolve decided the LP: nothing was iterated");
+    const int rc = pdlp_get_trace(ctx->inner, out, max_records, count);
+    return rc ? fail(ctx, rc, pdlp_last_error(ctx->inner)) : rc;
+  }
   const double *tr = nullptr;
   if (ctx->opts.precision == PDLP_FP64 && ctx->p64.ready) tr = ctx->p64.S.trace;
   else if (ctx->opts.precision == PDLP_FP32 && ctx->p32.ready) tr = ctx->p32.S.trace;
@@ -696,6 +822,11 @@ extern "C" int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, i
 
 extern "C" int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms) {
   if (!ctx || !ms || reps < 1) return fail(ctx, PDLP_ERR_INVALID_ARG, "bad argument");
+  if (ctx->pre) {
+    if (!ctx->inner) return fail(ctx, PDLP_ERR_STATE, "the presolve decided the LP: nothing was iterated");
+    const int rc = pdlp_time_step_kernels(ctx->inner, reps, ms);
+    return rc ? fail(ctx, rc, pdlp_last_error(ctx->inner)) : rc;
+  }
   cudaError_t e;
   const int prec = ctx->opts.precision;
   if (prec == PDLP_FP64 && ctx->p64.ready)
@@ -730,6 +861,7 @@ extern "C" void pdlp_destroy(pdlp_ctx *ctx) { delete ctx; }
 extern "C" int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const double *x0, const double *y0,
                            double *x_out, double *y_out, double *eta_out) {
   if (!ctx) return fail(nullptr, PDLP_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->pre) return fail(ctx, PDLP_ERR_STATE, "pdlp_unroll: not available on a presolved context");
   if (T < 1 || ckpt_every < 1 || ckpt_every > kMaxEval)
     return fail(ctx, PDLP_ERR_INVALID_ARG, "need T >= 1 and 1 <= ckpt_every <= 256");
   const bool f32 = ctx->opts.precision == PDLP_FP32;
@@ -769,6 +901,7 @@ extern "C" int pdlp_unroll(pdlp_ctx *ctx, int32_t T, int32_t ckpt_every, const d
 extern "C" int pdlp_grad(pdlp_ctx *ctx, const double *dL_dx, const double *dL_dy, double *dc, double *dq,
                          double *dK_val) {
   if (!ctx || !dL_dx) return fail(ctx, PDLP_ERR_INVALID_ARG, "NULL argument");
+  if (ctx->pre) return fail(ctx, PDLP_ERR_STATE, "pdlp_grad: not available on a presolved context");
   if (!ctx->unr.ready) return fail(ctx, PDLP_ERR_STATE, "pdlp_grad needs a preceding unrolled solve");
   cudaError_t e =
       ctx->unr.fp32 ? unroll_backward<float>(ctx->unr, ctx->p32.K, ctx->p32.KT, ctx->p32.P, ctx->p64.K, ctx->p64.KT,

@@ -85,3 +85,34 @@ def test_create_rejects_bad_arguments_before_any_device_work(lib):
     rc = _abi.load().pdlp_create(C.byref(csr), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
                                  np.zeros(3, np.uint8).ctypes.data, C.byref(o), C.byref(out))
     assert rc == _abi.PDLP_ERR_INVALID_ARG
+
+
+def test_binding_struct_layout_matches_the_header(tmp_path):
+    """Field offsets and sizes of pdlp_options / pdlp_result / pdlp_csr as the
+    C compiler lays them out from include/pdlp.h, against the ctypes mirrors."""
+    import shutil
+    import subprocess
+    from paper_2106_04756_gb300 import _abi
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"pdlp_options": _abi.pdlp_options, "pdlp_result": _abi.pdlp_result, "pdlp_csr": _abi.pdlp_csr}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdlp.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'  printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = {}
+    for line in got:
+        if line:
+            s, f, v = line.split()
+            want[(s, f)] = int(v)
+    for sname, cls in structs.items():
+        assert C.sizeof(cls) == want[(sname, "size")], sname
+        for fname, _ in cls._fields_:
+            assert getattr(cls, fname).offset == want[(sname, fname)], (sname, fname)
