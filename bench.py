@@ -198,7 +198,9 @@ def _batch_line(P):
 
 def _ablation_line(P):
     """KKT passes to 1e-8 on the 200 x 500 planted LP with each enhancement of
-    Section 3 switched off in turn, and Section 2's baseline PDHG (constant
+    Section 3 switched off in turn, the alternatives of Appendix C (the
+    Malitsky-Pock line search at the paper's best setting, the "theory"
+    restart mode, presolve-lite), and Section 2's baseline PDHG (constant
     eta = 0.9 / ||K||_2, omega = 1, no restarts, no scaling): the axes of the
     paper's ablation study and of its Figure 1 comparison."""
     import lpgen
@@ -210,6 +212,9 @@ def _ablation_line(P):
         "fixed_primal_weight": {"pw_update": 0},
         "no_preconditioning": {"ruiz_iters": 0, "pock_chambolle": 0},
         "constant_step": {"step_policy": 1},
+        "malitsky_pock": {"step_policy": 2, "mp_breaking": 1.0, "mp_downscaling": 0.5, "mp_interpolation": 0.4},
+        "restart_theory": {"restart_to_current": 0, "beta_suff": 0.37, "beta_nec": 0.37},
+        "presolve_lite": {"presolve": 1},
         "baseline_pdhg": {"step_policy": 1, "omega0": 1.0, "adaptive_restart": 0, "pw_update": 0,
                           "ruiz_iters": 0, "pock_chambolle": 0},
     }

@@ -102,7 +102,9 @@ typedef struct {
                                as 0.                                                     */
   int32_t step_policy;      /* 0 (default): Algorithm 2's adaptive step; 1: constant
                                step eta = 0.9 / ||K~||_2 with ||K~||_2 estimated by 200
-                               power iterations (Section 2's baseline PDHG step)      */
+                               power iterations (Section 2's baseline PDHG step); 2:
+                               the Malitsky-Pock line search of Appendix C.1 (runs
+                               on the per-launch engine; not with unroll_T > 0)     */
   int32_t presolve;         /* 1: presolve-lite before the solve (fixed variables l = u
                                substituted, rows left empty dropped, empty columns set
                                at the bound their cost points to); the solution and
@@ -110,6 +112,17 @@ typedef struct {
                                none.  Not with unroll_T > 0.                            */
   double omega0;            /* > 0: initial primal weight (Section 2's baseline PDHG
                                uses 1); 0 (default): InitializePrimalWeight          */
+  int32_t restart_to_current; /* 1 (default): GetRestartCandidate of Section 3.2; 0: the
+                               restart candidate is always the average (Appendix C.2,
+                               "adaptive restart (theory)" with beta_suff = beta_nec =
+                               0.37).  With adaptive_restart = 0 and pw_update = 1 the
+                               primal weight is still updated at the evaluations where
+                               the artificial criterion would restart (k = 40, 80, 160,
+                               ... with the defaults; Appendix C.2 "no restart").     */
+  int32_t pad3_;
+  double mp_breaking;       /* step_policy 2: breaking factor, 1.0 (Appendix C.1)      */
+  double mp_downscaling;    /* step_policy 2: downscaling factor in (0, 1), 0.5        */
+  double mp_interpolation;  /* step_policy 2: interpolation coefficient in [0, 1], 0.4 */
   void *stream;             /* cudaStream_t for all work; NULL = legacy default stream   */
 } pdlp_options;
 

@@ -52,7 +52,9 @@ class Opts(C.Structure):
                 ("pw_theta", C.c_double), ("beta_suff", C.c_double), ("beta_nec", C.c_double),
                 ("beta_art", C.c_double), ("eval_every", C.c_int32), ("eps_zero", C.c_double),
                 ("adaptive_restart", C.c_int32), ("pw_update", C.c_int32),
-                ("step_policy", C.c_int32), ("omega0", C.c_double)]
+                ("step_policy", C.c_int32), ("omega0", C.c_double),
+                ("restart_to_current", C.c_int32), ("mp_breaking", C.c_double),
+                ("mp_downscaling", C.c_double), ("mp_interpolation", C.c_double)]
 
 
 class Result(C.Structure):

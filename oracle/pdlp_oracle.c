@@ -71,6 +71,10 @@ void or_default_opts(or_opts *o) {
   o->pw_update = 1;
   o->step_policy = 0;
   o->omega0 = 0.0;
+  o->restart_to_current = 1;
+  o->mp_breaking = 1.0;
+  o->mp_downscaling = 0.5;
+  o->mp_interpolation = 0.4;
 }
 
 /* ---------------------------------------------------------------- basics */
@@ -428,6 +432,47 @@ static void pdhg_attempt(const scaled_lp *s, const iterate *z, iterate *zp, doub
   *bad = !isfinite(num) || isnan(eb) || isnan(inter);
 }
 
+/* Appendix C.1, one iteration of the Malitsky-Pock line search from z:
+ * the primal step x' = proj_X(x - (eta_k / omega)(c - K^T y)) is taken once;
+ * each trial picks eta_hat (first eta_k + interpolation (sqrt(1 + theta_k) - 1)
+ * eta_k, then times the downscaling factor), theta_hat = eta_k / eta_hat,
+ * y_hat = proj_Y(y + omega eta_hat (q - K(x' + theta_hat (x' - x)))), and
+ * stops when eta_hat ||K^T (y_hat - y)|| <= breaking ||y_hat - y||.  Each trial
+ * adds one to *passes (its K^T product; the K product of x' belongs to the
+ * first).  Writes zp, returns the accepted eta_hat and *theta_out; *accepted
+ * is 0 when *passes reached pass_cap first or a value was not finite. */
+static double mp_iteration(const scaled_lp *s, const or_opts *o, const iterate *z, iterate *zp,
+                           double eta_k, double theta_k, double omega, double *theta_out,
+                           int64_t *passes, int64_t pass_cap, int *accepted, int *bad) {
+  int32_t m = s->m, n = s->n;
+  for (int32_t j = 0; j < n; ++j)
+    zp->x[j] = clip(z->x[j] - (eta_k / omega) * (s->c[j] - z->KTy[j]), s->l[j], s->u[j]);
+  K_mul(s, zp->x, zp->Kx);
+  double eh = eta_k + o->mp_interpolation * (sqrt(1.0 + theta_k) - 1.0) * eta_k;
+  double th = eta_k / eh;
+  *accepted = 0;
+  *bad = 0;
+  for (;;) {
+    for (int32_t i = 0; i < m; ++i) {
+      double xbar_k = zp->Kx[i] + th * (zp->Kx[i] - z->Kx[i]); /* K (x' + th (x' - x)) */
+      double v = z->y[i] + omega * eh * (s->q[i] - xbar_k);
+      zp->y[i] = v > s->ylo[i] ? v : s->ylo[i];
+    }
+    KT_mul(s, zp->y, zp->KTy);
+    *passes += 1;
+    double dy2 = 0.0, dk2 = 0.0;
+    for (int32_t i = 0; i < m; ++i) dy2 += (zp->y[i] - z->y[i]) * (zp->y[i] - z->y[i]);
+    for (int32_t j = 0; j < n; ++j) dk2 += (zp->KTy[j] - z->KTy[j]) * (zp->KTy[j] - z->KTy[j]);
+    if (!isfinite(dy2) || !isfinite(dk2) || !isfinite(eh)) { *bad = 1; break; }
+    if (eh * sqrt(dk2) <= o->mp_breaking * sqrt(dy2)) { *accepted = 1; break; }
+    if (*passes >= pass_cap) break;
+    eh *= o->mp_downscaling;
+    th = eta_k / eh;
+  }
+  *theta_out = th;
+  return eh;
+}
+
 static void copy_iterate(const scaled_lp *s, iterate *dst, const iterate *src) {
   memcpy(dst->x, src->x, sizeof(double) * (size_t)s->n);
   memcpy(dst->y, src->y, sizeof(double) * (size_t)s->m);
@@ -528,6 +573,8 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
   memcpy(x0r, z.x, sizeof(double) * (size_t)n);
   memcpy(y0r, z.y, sizeof(double) * (size_t)m);
   double mu0 = INFINITY; /* R6 */
+  double mp_theta = 1.0; /* Appendix C.1 theta_0 (R22) */
+  int64_t k_virt = 0;    /* no-restart mode: iteration of the last primal weight update */
 
   while (status == OR_RUNNING) {            /* outer loop */
     int64_t t = 0;
@@ -539,7 +586,16 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       /* Algorithm 2 */
       double eta = eta_hat, eta_bar, eta_next;
       int bad = 0;
-      for (;;) {
+      if (o->step_policy == 2) { /* Appendix C.1 */
+        int accepted = 0;
+        double th = 1.0;
+        eta = mp_iteration(&s, o, &z, &zp, eta_hat, mp_theta, omega, &th, &kkt_passes, o->kkt_pass_limit,
+                           &accepted, &bad);
+        if (bad) status = OR_NUMERICAL_ERROR;
+        else if (!accepted) status = OR_KKT_PASS_LIMIT;
+        mp_theta = th;
+        eta_next = eta;
+      } else for (;;) {
         pdhg_attempt(&s, &z, &zp, eta, omega, k, &eta_bar, &eta_next, &bad);
         kkt_passes += 1; /* R10 */
         if (bad) { status = OR_NUMERICAL_ERROR; break; }
@@ -574,7 +630,33 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       }
       if (k >= o->iter_limit) { status = OR_ITER_LIMIT; break; }
       if (kkt_passes >= o->kkt_pass_limit) { status = OR_KKT_PASS_LIMIT; break; }
-      if (!o->adaptive_restart) continue;
+      if (!o->adaptive_restart) {
+        /* Appendix C.2 "no restart": the primal weight is still updated where
+         * the artificial criterion (iii) would have restarted, measured from
+         * the point of the previous update (R23) */
+        if (o->pw_update && (double)(k - k_virt) >= o->beta_art * (double)k) {
+          double dx2 = 0.0, dy2 = 0.0;
+          for (int32_t j = 0; j < n; ++j) dx2 += (z.x[j] - x0r[j]) * (z.x[j] - x0r[j]);
+          for (int32_t i = 0; i < m; ++i) dy2 += (z.y[i] - y0r[i]) * (z.y[i] - y0r[i]);
+          double Dx = sqrt(dx2), Dy = sqrt(dy2);
+          if (Dx > o->eps_zero && Dy > o->eps_zero)
+            omega = exp(o->pw_theta * log(Dy / Dx) + (1.0 - o->pw_theta) * log(omega));
+          memcpy(x0r, z.x, sizeof(double) * (size_t)n);
+          memcpy(y0r, z.y, sizeof(double) * (size_t)m);
+          k_virt = k;
+          if (trace && ntr < trace_cap) {
+            double *rec = trace + (size_t)ntr * 8;
+            rec[0] = (double)k;
+            rec[1] = (double)t;
+            rec[2] = rec[3] = rec[4] = NAN;
+            rec[5] = 0.0;
+            rec[6] = 2.0;
+            rec[7] = omega;
+          }
+          ntr += 1;
+        }
+        continue;
+      }
 
       /* GetRestartCandidate (Section 3.2) */
       double mu_cur = mu_of(&s, &z, x0r, y0r, omega);
@@ -585,8 +667,10 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
         terminated(lp, &s, &zbar, o->eps, ka, xo, yo);
         fprintf(stderr, "  kkt cur %.6e %.6e %.6e avg %.6e %.6e %.6e\n", kc[5], kc[6], kc[7], ka[5], ka[6], ka[7]);
       }
-      const iterate *cand = mu_cur < mu_avg ? &z : &zbar;
-      double muc = mu_cur < mu_avg ? mu_cur : mu_avg;
+      /* restart_to_current = 0: always the average (Appendix C.2, theory mode) */
+      const int to_cur = o->restart_to_current ? mu_cur < mu_avg : 0;
+      const iterate *cand = to_cur ? &z : &zbar;
+      double muc = to_cur ? mu_cur : mu_avg;
       /* restart criteria (i), (ii), (iii) */
       if (muc <= o->beta_suff * mu0) restart = 1;
       else if (muc <= o->beta_nec * mu0 && muc > muc_prev) restart = 1;

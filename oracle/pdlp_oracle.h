@@ -43,12 +43,20 @@ typedef struct {
   double beta_suff, beta_nec, beta_art;  /* Section 3.2: 0.9, 0.1, 0.5           */
   int32_t eval_every;      /* Section 3: restart / termination check every 40    */
   double eps_zero;         /* Section 3.3 epsilon_zero                           */
-  int32_t adaptive_restart;/* 1: restart scheme of Section 3.2; 0: never restart */
+  int32_t adaptive_restart;/* 1: restart scheme of Section 3.2; 0: never restart
+                              (Appendix C.2 "no restart": with pw_update, the
+                              primal weight is still updated at the evaluations
+                              where an artificial restart would have fired)     */
   int32_t pw_update;       /* 1: Algorithm 3 at restarts; 0: keep initial omega  */
   int32_t step_policy;     /* 0: Algorithm 2; 1: constant eta = 0.9 / ||K~||_2,
                               ||K~||_2 by power iteration (Section 2's baseline
-                              PDHG step; the "fixed step size" ablation)         */
+                              PDHG step; the "fixed step size" ablation);
+                              2: Malitsky-Pock line search (Appendix C.1)        */
   double omega0;           /* > 0: initial primal weight; 0: InitializePrimalWeight */
+  int32_t restart_to_current; /* 1: GetRestartCandidate (Section 3.2); 0: the
+                              restart candidate is always the average (Appendix
+                              C.2 "adaptive restart (theory)")                    */
+  double mp_breaking, mp_downscaling, mp_interpolation; /* Appendix C.1: 1, 0.5, 0.4 */
 } or_opts;
 
 /* Iterations of the power iteration for ||K~||_2 (both the oracle and the
@@ -110,7 +118,8 @@ void or_solve(const or_lp *lp, const or_opts *opts, const double *x0, const doub
 
 /* or_solve that also records each restart evaluation (up to trace_cap) as 8
  * doubles: k, t, mu_current, mu_average, mu_0, candidate (0 current, 1
- * average), restarted (0/1), primal weight after the evaluation.
+ * average), restarted (0/1; 2 = the no-restart mode's primal weight update,
+ * with mu_* and mu_0 NaN), primal weight after the evaluation.
  * *trace_n receives the number of evaluations. */
 void or_solve_traced(const or_lp *lp, const or_opts *opts, const double *x0, const double *y0,
                      double *x_out, double *y_out, or_result *res, double *trace, int32_t trace_cap,

@@ -44,7 +44,9 @@ class pdlp_options(C.Structure):
                 ("eps_zero", C.c_double), ("inner_tol", C.c_double), ("refine_rounds", C.c_int32),
                 ("unroll_T", C.c_int32), ("ckpt_every", C.c_int32), ("use_graph", C.c_int32),
                 ("persistent", C.c_int32), ("step_policy", C.c_int32), ("presolve", C.c_int32),
-                ("omega0", C.c_double), ("stream", C.c_void_p)]
+                ("omega0", C.c_double),
+                ("restart_to_current", C.c_int32), ("pad3_", C.c_int32), ("mp_breaking", C.c_double),
+                ("mp_downscaling", C.c_double), ("mp_interpolation", C.c_double), ("stream", C.c_void_p)]
 
 
 class pdlp_result(C.Structure):

@@ -174,7 +174,9 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   S.KTy_cur = take(n); S.KTys = take(n);
   S.Kxbar = take(m);
   S.eta_log = nullptr;
-  CK(persist_plan<T>(ctx->hblocksKT, ctx->hblocksK, ctx->opts.persistent, &pr.pg), "persistent kernel layout");
+  // the Malitsky-Pock line search runs on the per-launch engine
+  const int persist_mode = ctx->opts.step_policy == 2 ? 0 : ctx->opts.persistent;
+  CK(persist_plan<T>(ctx->hblocksKT, ctx->hblocksK, persist_mode, &pr.pg), "persistent kernel layout");
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
                     8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + 16;
   double *parts = dalloc<double>(pr.parts, np);
@@ -217,6 +219,11 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   in.pw_update = o.pw_update;
   in.const_step = o.step_policy == 1 ? 1 : 0;
   in.omega0 = o.omega0;
+  in.restart_to_current = o.restart_to_current;
+  in.mp = o.step_policy == 2 ? 1 : 0;
+  in.mp_breaking = o.mp_breaking;
+  in.mp_downscaling = o.mp_downscaling;
+  in.mp_interpolation = o.mp_interpolation;
   if (in.const_step) {  // eta = 0.9 / ||K~||_2 (power iteration; the state vectors are scratch here)
     double kn = 0.0;
     CK(power_norm<T>(pr.K, pr.KT, 200, S.xs[0], S.Kx[1], S.xs[1], normpart, ctx->st, &kn), "power iteration");
@@ -374,7 +381,12 @@ int check_options(const pdlp_options *o, std::string &why) {
   if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
   if (o->eval_every < 1 || o->eval_every > kMaxEval) { why = "eval_every must be in [1, 256]"; return 0; }
   if (o->persistent < 0 || o->persistent > 1) { why = "persistent must be 0 or 1"; return 0; }
-  if (o->step_policy < 0 || o->step_policy > 1) { why = "step_policy must be 0 or 1"; return 0; }
+  if (o->step_policy < 0 || o->step_policy > 2) { why = "step_policy must be 0, 1 or 2"; return 0; }
+  if (o->restart_to_current < 0 || o->restart_to_current > 1) { why = "restart_to_current must be 0 or 1"; return 0; }
+  if (o->step_policy == 2 && o->unroll_T > 0) { why = "step_policy 2 does not combine with unroll_T > 0"; return 0; }
+  if (!(o->mp_breaking >= 0.0) || !isfinite(o->mp_breaking)) { why = "mp_breaking must be finite and >= 0"; return 0; }
+  if (!(o->mp_downscaling > 0.0 && o->mp_downscaling < 1.0)) { why = "mp_downscaling must be in (0, 1)"; return 0; }
+  if (!(o->mp_interpolation >= 0.0 && o->mp_interpolation <= 1.0)) { why = "mp_interpolation must be in [0, 1]"; return 0; }
   if (!(o->omega0 >= 0.0) || !isfinite(o->omega0)) { why = "omega0 must be finite and >= 0"; return 0; }
   if (o->presolve < 0 || o->presolve > 1) { why = "presolve must be 0 or 1"; return 0; }
   if (o->presolve && o->unroll_T > 0) { why = "presolve does not combine with unroll_T > 0"; return 0; }
@@ -527,6 +539,10 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->step_policy = 0;
   o->omega0 = 0.0;
   o->presolve = 0;
+  o->restart_to_current = 1;
+  o->mp_breaking = 1.0;
+  o->mp_downscaling = 0.5;
+  o->mp_interpolation = 0.4;
   o->stream = nullptr;
   return PDLP_OK;
 }

@@ -60,6 +60,7 @@ struct BatchOpts {
   double rel_tol, eps_zero, beta_suff, beta_nec, beta_art, pw_theta, primal_importance;
   long long iter_limit, kkt_pass_limit;
   int ruiz_iters, pock_chambolle, eval_every, adaptive_restart, pw_update;
+  int restart_to_current;  // 0: the restart candidate is always the average (Appendix C.2)
 };
 
 struct BatchOut {
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     __syncthreads();
     // ---- Algorithm 1 with evaluations
     int cur = 0;
-    long long k = 0, t = 0, passes_used = 0, restarts = 0;
+    long long k = 0, t = 0, passes_used = 0, restarts = 0, k_virt = 0;
     double sum_eta = 0.0, mu0 = INFINITY, muc_prev = INFINITY;
     int status = kRunning, ret_avg = 0;
     double kkt[2][8];
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           const double rcur = sqrt(omega * d2[0] + d2[1] / omega), ravg = sqrt(omega * d2[2] + d2[3] / omega);
           const double mu_cur = cta_gap<T>(w, n, m, x, y, w.KTy, Kx, omega, rcur, skey, sidx, red);
           const double mu_avg = cta_gap<T>(w, n, m, w.xa, w.ya, w.KTys, w.Kxs, omega, ravg, skey, sidx, red);
-          const int cand = mu_cur < mu_avg ? 0 : 1;
+          const int cand = o.restart_to_current ? (mu_cur < mu_avg ? 0 : 1) : 1;
           const double muc = cand == 0 ? mu_cur : mu_avg;
           bool restart = false;
           if (muc <= o.beta_suff * mu0) restart = true;
@@ -762,6 +763,27 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
             restarts += 1;
             __syncthreads();
           }
+        } else if (!first_eval && !o.adaptive_restart && o.pw_update &&
+                   (double)(k - k_virt) >= o.beta_art * (double)k) {
+          // Appendix C.2 "no restart": Algorithm 3 where the artificial
+          // criterion would restart, measured from the previous update's point
+          double d2[2] = {0.0, 0.0};
+          for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double a = (double)x[j] - (double)w.x0[j];
+            d2[0] += a * a;
+          }
+          for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double a = (double)y[i] - (double)w.y0[i];
+            d2[1] += a * a;
+          }
+          cta_sum<2>(d2, red);
+          const double Dx = sqrt(d2[0]), Dy = sqrt(d2[1]);
+          if (Dx > o.eps_zero && Dy > o.eps_zero)
+            omega = exp(o.pw_theta * log(Dy / Dx) + (1.0 - o.pw_theta) * log(omega));
+          for (int j = threadIdx.x; j < n; j += blockDim.x) w.x0[j] = x[j];
+          for (int i = threadIdx.x; i < m; i += blockDim.x) w.y0[i] = y[i];
+          k_virt = k;
+          __syncthreads();
         }
         first_eval = false;
         // Algorithm 2's factors 1 - (k+1)^-0.3, 1 + (k+1)^-0.6 (k counted from 1)
@@ -1113,6 +1135,7 @@ extern "C" int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *
   o.eval_every = opts->eval_every;
   o.adaptive_restart = opts->adaptive_restart;
   o.pw_update = opts->pw_update;
+  o.restart_to_current = opts->restart_to_current;
   // largest first
   std::vector<int32_t> order(count);
   std::iota(order.begin(), order.end(), 0);

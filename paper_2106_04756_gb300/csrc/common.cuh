@@ -119,6 +119,16 @@ struct Scalars {
   int err;        // bounded-wait failures (device-side timeouts)
   int const_step; // 1: constant step size (every attempt accepted)
   int trace_n;    // restart evaluations recorded so far (ring of kTraceCap)
+  // --- Appendix C.2 restart variants
+  int restart_to_current;  // 0: the restart candidate is always the average
+  int vrestart;            // no-restart mode: primal weight updated at this evaluation
+  long long k_virt;        // no-restart mode: k of the last primal weight update
+  // --- Appendix C.1 Malitsky-Pock line search (mp = 1)
+  int mp;
+  int mp_trial;            // trials of the current iteration so far
+  double mp_eta_k, mp_theta;  // eta_k and theta_k = eta_{k-1} / eta_k of the current iterate
+  double mp_eh, mp_th;        // candidate eta_hat and theta_hat of the next trial
+  double mp_bf, mp_df, mp_ic; // breaking, downscaling, interpolation
 };
 
 // One record per restart evaluation: k, t, mu_cur, mu_avg, mu0, candidate,

@@ -132,6 +132,134 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, Mat<T> KT, Problem<
   }
 }
 
+// -------------------------------------- Malitsky-Pock line search (App. C.1)
+//
+// One trial per pass of the inner loop: k_mp_primal (K^T y, x' =
+// proj_X(x - (eta_k / omega)(c - K^T y))) and k_mp_kx (K x') run in the
+// first trial of an iteration only; k_mp_dual forms y_hat from the stored
+// K x' with the trial's eta_hat, theta_hat; k_mp_cols takes K^T y_hat and
+// ||K^T (y_hat - y)||^2 (and the average sums of the columns); k_mp_test
+// accepts or shrinks eta_hat.  The buffers of index cur ^ 1 hold the trial.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mp_primal(Mat<T> KT, Problem<T> P, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  const Scalars *sc = S.s;
+  if (sc->mp_trial) return;  // uniform over the grid
+  const int cur = sc->cur;
+  const T tau = (T)(sc->mp_eta_k / sc->omega);
+  const T *x = S.x[cur];
+  T *xn = S.x[cur ^ 1], *kty = S.KTy_cur;
+  double acc[1] = {0.0};
+  const T *const vec[1] = {S.y[cur]};
+  spmv_warp<T, 1>(KT, vec, sm, acc, [&](int j, const T(&g)[1], double(&)[1]) {
+    kty[j] = g[0];
+    xn[j] = clampv<T>(x[j] - tau * (P.cs[j] - g[0]), P.ls[j], P.us[j]);
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mp_kx(Mat<T> K, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  const Scalars *sc = S.s;
+  if (sc->mp_trial) return;
+  const int cur = sc->cur;
+  T *kxn = S.Kx[cur ^ 1];
+  double acc[1] = {0.0};
+  const T *const vec[1] = {S.x[cur ^ 1]};
+  spmv_warp<T, 1>(K, vec, sm, acc, [&](int i, const T(&v)[1], double(&)[1]) { kxn[i] = v[0]; });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mp_dual(Problem<T> P, State<T> S) {
+  __shared__ double red[kThreads / 32];
+  const Scalars *sc = S.s;
+  const int cur = sc->cur;
+  const double eh = sc->mp_eh, th = sc->mp_th;
+  const T sg = (T)(sc->omega * eh), tht = (T)th, et = (T)eh;
+  const T *y = S.y[cur], *kx = S.Kx[cur], *kxn = S.Kx[cur ^ 1], *ys = S.ys[cur];
+  T *yn = S.y[cur ^ 1], *ysn = S.ys[cur ^ 1];
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.m; i += gridDim.x * blockDim.x) {
+    const T kb = kxn[i] + tht * (kxn[i] - kx[i]);  // K (x' + theta_hat (x' - x))
+    const T v = y[i] + sg * (P.qs[i] - kb), lo = P.ylos[i];
+    const T yp = v > lo ? v : lo;
+    yn[i] = yp;
+    ysn[i] = ys[i] + et * yp;
+    const double d = (double)yp - (double)y[i];
+    acc[0] += d * d;
+  }
+  block_sum<1>(acc, red);
+  if (threadIdx.x == 0) S.part_d[blockIdx.x] = acc[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mp_cols(Mat<T> KT, State<T> S) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double red[kThreads / 32];
+  const Scalars *sc = S.s;
+  const int cur = sc->cur;
+  const T et = (T)sc->mp_eh;
+  const T *kty = S.KTy_cur, *xn = S.x[cur ^ 1], *xs = S.xs[cur];
+  T *xsn = S.xs[cur ^ 1];
+  double acc[1] = {0.0};
+  const T *const vec[1] = {S.y[cur ^ 1]};
+  spmv_warp<T, 1>(KT, vec, sm, acc, [&](int j, const T(&g)[1], double(&a)[1]) {
+    const double d = (double)g[0] - (double)kty[j];
+    a[0] += d * d;
+    xsn[j] = xs[j] + et * xn[j];
+  });
+  block_sum<1>(acc, red);
+  if (threadIdx.x == 0) S.part_p[blockIdx.x] = acc[0];
+}
+
+// The line-search test of one trial (one CTA): sums the partials in a fixed
+// order, then thread 0 accepts (eta_{k+1} = eta_hat, theta_{k+1} = theta_hat,
+// next candidate from the interpolation coefficient) or shrinks eta_hat.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mp_test(Mat<T> KT, State<T> S, int nparts_p, int nparts_d,
+                                                      cudaGraphConditionalHandle h, int has_cond) {
+  __shared__ double red[kThreads / 32];
+  Scalars *s = S.s;
+  double dk[1], dy[1], lk[1];
+  sum_partials<1>(S.part_p, nparts_p, 1, dk, red);
+  __syncthreads();
+  sum_long_rows<1>(KT, lk, red);
+  __syncthreads();
+  sum_partials<1>(S.part_d, nparts_d, 1, dy, red);
+  if (threadIdx.x != 0) return;
+  const double dk2 = dk[0] + lk[0], dy2 = dy[0];
+  const double eh = s->mp_eh;
+  s->attempts += 1;
+  s->dx2 = dk2;
+  s->dy2 = dy2;
+  if (!isfinite(dk2) || !isfinite(dy2) || !isfinite(eh)) {
+    s->status = kNumErr;
+  } else if (eh * sqrt(dk2) <= s->mp_bf * sqrt(dy2)) {
+    s->cur ^= 1;
+    s->sum_eta += eh;
+    s->k += 1;
+    s->t += 1;
+    s->chunk_acc += 1;
+    s->mp_eta_k = eh;
+    s->mp_theta = s->mp_th;
+    s->mp_trial = 0;
+    s->mp_eh = s->mp_eta_k + s->mp_ic * (sqrt(1.0 + s->mp_theta) - 1.0) * s->mp_eta_k;
+    s->mp_th = s->mp_eta_k / s->mp_eh;
+  } else {
+    s->mp_trial += 1;
+    s->mp_eh = s->mp_eh * s->mp_df;
+    s->mp_th = s->mp_eta_k / s->mp_eh;
+  }
+  s->eta = s->mp_eta_k;
+  s->tau = s->eta * s->inv_omega;
+  s->sigma = s->eta * s->omega;
+  bool go = s->status == kRunning && s->chunk_acc < s->eval_every && s->k < s->iter_limit &&
+            s->attempts < s->attempt_limit;
+  if (go && time_up(s)) go = false;
+  if (has_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // ------------------------------------------------------ evaluation kernels
 
 // Columns: K^T y (current) and K^T ys (sum for the average) in one pass, and
@@ -175,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P,
 }
 
 // Finalisation of one evaluation (thread 0 of the last CTA of k_eval_rows).
-__device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er)[8]) {
+__device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er)[8], double *trace) {
   const bool avg = s->sum_eta > 0.0;
   bool pass[2] = {false, false};
   for (int c = 0; c < 2; ++c) {
@@ -209,6 +337,36 @@ __device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er
   }
   s->do_gap = (s->status == kRunning && s->phase == 1 && s->adaptive_restart) ? 1 : 0;
   s->restart = 0;
+  s->vrestart = 0;
+  if (s->status == kRunning && s->phase == 1 && !s->adaptive_restart && s->pw_update &&
+      (double)(s->k - s->k_virt) >= s->beta_art * (double)s->k) {
+    // Appendix C.2 "no restart": Algorithm 3 where the artificial criterion
+    // would restart, from the point of the previous update (z^{n,0} slots)
+    const double Dx = sqrt(s->cand_dx2[0]), Dy = sqrt(s->cand_dy2[0]);
+    if (Dx > s->eps_zero && Dy > s->eps_zero)
+      s->omega = exp(s->pw_theta * log(Dy / Dx) + (1.0 - s->pw_theta) * log(s->omega));
+    s->inv_omega = 1.0 / s->omega;
+    s->tau = s->eta * s->inv_omega;
+    s->sigma = s->eta * s->omega;
+    s->vrestart = 1;
+    s->k_virt = s->k;
+    double *rec = trace + (size_t)(s->trace_n % kTraceCap) * kTraceLen;
+    s->trace_n += 1;
+    {
+      rec[0] = (double)s->k;
+      rec[1] = (double)s->t;
+      rec[2] = rec[3] = rec[4] = NAN;
+      rec[5] = 0.0;
+      rec[6] = 2.0;
+      rec[7] = s->omega;
+      rec[8] = sqrt(s->omega * s->cand_dx2[0] + s->cand_dy2[0] / s->omega);
+      rec[9] = NAN;
+      for (int a = 0; a < 3; ++a) {
+        rec[10 + a] = s->kkt[0][5 + a];
+        rec[13 + a] = s->kkt[1][5 + a];
+      }
+    }
+  }
   if (s->do_gap) {
     for (int c = 0; c < 2; ++c) {
       const double r2 = (c == 1 && !avg) ? 0.0 : s->omega * s->cand_dx2[c] + s->cand_dy2[c] / s->omega;
@@ -277,7 +435,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
         ec[a] += lc[a];
         er[a] += lr[a];
       }
-      eval_finish(sc, ec, er);
+      eval_finish(sc, ec, er, S.trace);
     }
   }
 }
@@ -583,7 +741,8 @@ __global__ void k_decide(Scalars *s, double *trace) {
   if (!s->do_gap) return;
   const double mu_c = s->mu[0];
   const double mu_a = s->sum_eta > 0.0 ? s->mu[1] : INFINITY;
-  const int cand = mu_c < mu_a ? 0 : 1;
+  // restart_to_current = 0: the average whenever there is one (Appendix C.2)
+  const int cand = s->restart_to_current ? (mu_c < mu_a ? 0 : 1) : (s->sum_eta > 0.0 ? 1 : 0);
   const double muc = cand == 0 ? mu_c : mu_a;
   int restart = 0;
   if (muc <= s->beta_suff * s->mu0) restart = 1;
@@ -634,6 +793,14 @@ __global__ void k_decide(Scalars *s, double *trace) {
 template <typename T>
 __global__ void k_apply_restart(Problem<T> P, State<T> S) {
   const Scalars *sc = S.s;
+  if (sc->vrestart) {  // no-restart mode: only the reference point of the next update moves
+    const int cur = sc->cur, n = P.n, N = P.n + P.m;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+      if (i < n) S.x0[i] = S.x[cur][i];
+      else S.y0[i - n] = S.y[cur][i - n];
+    }
+    return;
+  }
   if (!sc->restart) return;
   const int cur = sc->cur, cand = sc->cand;
   const double inv = sc->inv_avg;
@@ -682,6 +849,7 @@ __device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cud
     s->restart = 0;
   }
   s->do_gap = 0;
+  s->vrestart = 0;
   s->chunk_acc = 0;
   if (s->err) s->status = kWaitTimeout;
   if (s->status == kRunning && time_up(s)) s->status = kTimeLimit;
@@ -812,6 +980,18 @@ __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->err = 0;
   s->trace_n = 0;
   for (int a = 0; a < kGapSlots; ++a) { s->g_active[a] = 0; s->mu[a] = INFINITY; }
+  s->restart_to_current = in.restart_to_current;
+  s->vrestart = 0;
+  s->k_virt = 0;
+  s->mp = in.mp;
+  s->mp_trial = 0;
+  s->mp_bf = in.mp_breaking;
+  s->mp_df = in.mp_downscaling;
+  s->mp_ic = in.mp_interpolation;
+  s->mp_eta_k = in.eta0;
+  s->mp_theta = 1.0;  // theta_0 (no earlier step)
+  s->mp_eh = s->mp_eta_k + s->mp_ic * (sqrt(1.0 + s->mp_theta) - 1.0) * s->mp_eta_k;
+  s->mp_th = s->mp_eta_k / s->mp_eh;
 }
 
 // Returned point in the original space: x = D2 x~, y = D1 y~.
@@ -855,6 +1035,9 @@ cudaError_t set_kernel_attributes() {
   if ((e = cudaFuncSetAttribute(k_eval_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(2)))) return e;
   if ((e = cudaFuncSetAttribute(k_eval_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
   if ((e = cudaFuncSetAttribute(k_spmv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  if ((e = cudaFuncSetAttribute(k_mp_primal<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  if ((e = cudaFuncSetAttribute(k_mp_kx<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
+  if ((e = cudaFuncSetAttribute(k_mp_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spmv_smem<T>(1)))) return e;
   const int gsm = (int)gap_smem(2);
   if ((e = cudaFuncSetAttribute(k_gap_pass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm))) return e;
   return cudaSuccess;
@@ -873,6 +1056,18 @@ cudaError_t launch_gap_slots(const Problem<T> &P, const State<T> &S, int s_begin
                              int grid, cudaStream_t st) {
   launch_gap<T>(P, S, s_begin, s_end, when_restart, grid, st);
   return cudaGetLastError();
+}
+
+// One trial of the Malitsky-Pock line search (k_mp_test sets h when has_cond).
+template <typename T>
+static void launch_mp_trial(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                            cudaGraphConditionalHandle h, int has_cond, cudaStream_t st) {
+  const int gd = K.nblocks > 0 ? K.nblocks : 1;  // part_d holds 2 K.nblocks entries
+  if (KT.nblocks > 0) k_mp_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+  if (K.nblocks > 0) k_mp_kx<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, S);
+  k_mp_dual<T><<<gd, kThreads, 0, st>>>(P, S);
+  if (KT.nblocks > 0) k_mp_cols<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, S);
+  k_mp_test<T><<<1, kThreads, 0, st>>>(KT, S, KT.nblocks, gd, h, has_cond);
 }
 
 template <typename T>
@@ -1047,8 +1242,12 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     if (!e) e = add_while(st2, h_inner, &body_inner);
     if (!e) e = cudaStreamBeginCaptureToGraph(st3, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (!e) {
-      if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
-      k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT, P, S, h_inner, 1);
+      if (in.mp) {
+        launch_mp_trial<T>(K, KT, P, S, h_inner, 1, st3);
+      } else {
+        if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
+        k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT, P, S, h_inner, 1);
+      }
       cudaGraph_t tmp;
       e = cudaStreamEndCapture(st3, &tmp);
     }
@@ -1155,7 +1354,9 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
   if ((e = cudaGetLastError()) || (e = read())) return e;
   while (host->status == kRunning) {
     for (;;) {
-      if (pg.grid > 0) {
+      if (in.mp) {
+        launch_mp_trial<T>(K, KT, P, S, 0, 0, st);
+      } else if (pg.grid > 0) {
         if ((e = launch_persist<T>(K, KT, P, S, pg, st))) return e;
       } else {
         if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);

@@ -14,6 +14,9 @@ struct ScalarInit {
   unsigned long long time_limit_ns;
   int eval_every, adaptive_restart, pw_update, const_step;
   double omega0;  // > 0: initial primal weight instead of InitializePrimalWeight
+  int restart_to_current;  // 0: restart candidate always the average (Appendix C.2)
+  int mp;                  // 1: Malitsky-Pock line search (Appendix C.1)
+  double mp_breaking, mp_downscaling, mp_interpolation;
 };
 
 template <typename T> cudaError_t set_kernel_attributes();

@@ -188,6 +188,8 @@ cudaError_t unroll_forward(UnrollBuffers &U, const Mat<F> &K, const Mat<F> &KT, 
   in2.time_limit_ns = 0ull;
   in2.eval_every = ckpt;
   in2.adaptive_restart = 0;
+  in2.pw_update = 0;  // omega fixed over the unrolled map
+  in2.mp = 0;
   launch_problem_norms<F>(P, S.s, primal_importance, norm_part, 152, st);
   launch_init<F>(P, S2, K, in2, x0, y0, st);
   if ((e = cudaGetLastError())) return e;

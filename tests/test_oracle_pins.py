@@ -440,3 +440,73 @@ def test_constant_step_solve_is_plain_pdhg(oracle_lib):
     assert r["eta"] == pytest.approx(eta, rel=1e-15) and r["omega"] == 1.0
     x2, y2 = oracle.pdhg_fixed(lp, eta, 1.0, T)
     assert np.allclose(x, x2, rtol=1e-11, atol=1e-12) and np.allclose(y, y2, rtol=1e-11, atol=1e-12)
+
+
+def test_malitsky_pock_without_search_is_plain_pdhg(oracle_lib):
+    # Appendix C.1 with interpolation 0 (eta_hat = eta_k, theta_hat = 1) and a
+    # breaking factor no trial can fail is PDHG of Eq. (3) at the initial step
+    # 1 / max |K_ij| (Algorithm 1's eta^0): one trial per iteration
+    lp = lpgen.planted_uniform(30, 50, 0.2, seed_key=(91,))
+    T = 150
+    kw = dict(ruiz_iters=0, pock_chambolle=0, adaptive_restart=0, pw_update=0, step_policy=2, omega0=1.0,
+              mp_interpolation=0.0, mp_breaking=1e300)
+    x, y, r = oracle.solve(lp, iter_limit=T, eps=0.0, **kw)
+    eta = 1.0 / np.max(np.abs(lp.val))
+    assert r["iters"] == T and r["kkt_passes"] == T
+    assert r["eta"] == eta
+    x2, y2 = oracle.pdhg_fixed(lp, eta, 1.0, T)
+    assert np.allclose(x, x2, rtol=1e-11, atol=1e-12) and np.allclose(y, y2, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_malitsky_pock_solves_planted_lp(oracle_lib, seed):
+    # the paper's best setting (breaking 1, downscaling 0.5, interpolation 0.4)
+    # inside PDLP converges to the planted optimum; its trials outnumber its
+    # iterations (some candidate steps are shrunk)
+    lp = lpgen.planted_uniform(60, 150, 0.08, seed_key=(95 + seed,))
+    x, y, r = oracle.solve(lp, step_policy=2, iter_limit=200000)
+    assert r["status_name"] == "OPTIMAL", r
+    k = oracle.kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8
+    ref = lp.c @ lp.x_star
+    assert abs(lp.c @ x - ref) <= 1e-6 * (1 + abs(ref))
+    assert r["kkt_passes"] > r["iters"]
+
+
+def test_malitsky_pock_breaking_factor_zero_never_accepts(oracle_lib):
+    # breaking factor 0 accepts only a trial with K^T(y_hat - y) = 0, which a
+    # dual step that moves y cannot give here: every trial is shrunk until the
+    # pass limit ends the solve
+    lp = lpgen.planted_uniform(30, 50, 0.2, seed_key=(92,))
+    _, _, r = oracle.solve(lp, step_policy=2, mp_breaking=0.0, kkt_pass_limit=25)
+    assert r["status_name"] == "KKT_PASS_LIMIT" and r["iters"] == 0 and r["kkt_passes"] == 25
+
+
+def test_no_restart_mode_updates_primal_weight_at_doubling_iterations(oracle_lib):
+    # Appendix C.2: without restarts the primal weight still changes where the
+    # artificial criterion t >= 0.5 k would fire, i.e. at k = 40, 80, 160, ...
+    lp = lpgen.planted_uniform(80, 200, 0.05, seed_key=(93,))
+    _, _, r, tr = oracle.solve_traced(lp, adaptive_restart=0, iter_limit=1300, eps=0.0)
+    assert r["restarts"] == 0
+    ks = [int(row[0]) for row in tr if row[6] == 2.0]
+    assert ks == [40, 80, 160, 320, 640, 1280]
+    om = [row[7] for row in tr if row[6] == 2.0]
+    assert len(set(om)) > 1
+    _, _, r0, tr0 = oracle.solve_traced(lp, adaptive_restart=0, pw_update=0, iter_limit=1300, eps=0.0)
+    assert len(tr0) == 0 and r0["omega"] == oracle.solve(lp, iter_limit=1)[2]["omega"]
+
+
+def test_theory_restart_mode_restarts_to_average(oracle_lib):
+    # Appendix C.2 theory mode: beta_suff = beta_nec = 0.37 and the average as
+    # the only restart candidate; every restart then has mu <= 0.37 mu_0 or
+    # passes the artificial test
+    lp = lpgen.planted_uniform(80, 200, 0.05, seed_key=(94,))
+    x, y, r, tr = oracle.solve_traced(lp, restart_to_current=0, beta_suff=0.37, beta_nec=0.37,
+                                      iter_limit=200000)
+    assert r["status_name"] == "OPTIMAL" and r["restarts"] > 0
+    assert oracle.kkt(lp, x, y)["rel_kkt"] <= 1e-8
+    rows = [row for row in tr if row[6] == 1.0]
+    assert rows and all(row[5] == 1.0 for row in rows)
+    for row in rows:
+        k, t, mu_avg, mu0 = row[0], row[1], row[3], row[4]
+        assert mu_avg <= 0.37 * mu0 or t >= 0.5 * k
