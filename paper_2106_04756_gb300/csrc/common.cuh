@@ -292,12 +292,92 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
 //            (coalesced, independent), then the gathered entries, into the
 //            warp's shared-memory slice;
 //   rows:    a power-of-two group of L lanes per row (L * rows <= 32) sums the
-//            row from shared memory, then shuffles;
+//            row from shared memory, then shuffles; rows longer than a
+//            threshold the chunk picks from its row lengths are summed by the
+//            whole warp instead (chunk_row_sums);
 //   segments of rows longer than kSegNnz: warp partials combined, in segment
 //            order, by the last segment warp to arrive.
 // All sums have a fixed order (deterministic).  `wsm` is the warp's slice of
 // spmv_warp_smem<T>(NV) bytes.
 constexpr int kLaneItems = kChunkNnz / 32;
+
+// Row sums of one staged chunk of nrows <= 32 rows: values sval[e] and
+// gathered entries sx[a * kChunkNnz + e] for the chunk's nonzeros e; lane r
+// passes its row's local bounds [s_r, e_r) (any values on lanes >= nrows).
+// Rows are summed by power-of-two groups of L lanes (L * nrows <= 32), which
+// costs the warp ceil(max length / L) steps; with power-law row lengths one
+// long row would set that count for the whole chunk, so rows longer than a
+// threshold T are instead summed by the whole warp, one after another
+// (ceil(length / 32) steps and a 5-step shuffle each).  T in {16, 32, 64,
+// 128} or none is chosen per chunk by that integer step count.  Every sum
+// has a fixed order.  Writes srow[a * kChunkRows + r].
+template <typename T, int NV>
+__device__ __forceinline__ void chunk_row_sums(const T *sval, const T *sx, int nrows, int s_r, int e_r, T *srow) {
+  const int lane = threadIdx.x & 31;
+  int L = 32;
+  while (L > 1 && L * nrows > 32) L >>= 1;
+  const int lg = 31 - __clz(L);
+  const bool mine = lane < nrows;
+  const unsigned len = mine ? (unsigned)(e_r - s_r) : 0u;
+  unsigned best = __reduce_max_sync(0xffffffffu, (len + (unsigned)L - 1u) >> lg);
+  unsigned thr = 0xffffffffu;
+#pragma unroll
+  for (unsigned th = 16; th <= 128; th <<= 1) {
+    const bool lng = len > th;
+    const unsigned ms = __reduce_max_sync(0xffffffffu, lng ? 0u : (len + (unsigned)L - 1u) >> lg);
+    const unsigned lc = __reduce_add_sync(0xffffffffu, lng ? ((len + 31u) >> 5) + 5u : 0u);
+    if (ms + lc < best) {
+      best = ms + lc;
+      thr = th;
+    }
+  }
+  // rows up to thr: groups of L lanes
+  const int g = lane >> lg, gl = lane & (L - 1);
+  const int gs = __shfl_sync(0xffffffffu, s_r, g), ge = __shfl_sync(0xffffffffu, e_r, g);
+  const bool short_row = g < nrows && (unsigned)(ge - gs) <= thr;
+  T acc[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) acc[a] = T(0);
+  if (short_row) {
+    for (int k = gs + gl; k < ge; k += L) {
+      const T vv = sval[k];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kChunkNnz + k], acc[a]);
+    }
+  }
+  for (int o = L / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o, L);
+  }
+  if (short_row && gl == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) srow[a * kChunkRows + g] = acc[a];
+  }
+  // longer rows: the whole warp, in row order
+  unsigned lmask = __ballot_sync(0xffffffffu, mine && len > thr);
+  while (lmask) {
+    const int r = __ffs(lmask) - 1;
+    lmask &= lmask - 1u;
+    const int rs = __shfl_sync(0xffffffffu, s_r, r), re = __shfl_sync(0xffffffffu, e_r, r);
+    T w[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) w[a] = T(0);
+    for (int k = rs + lane; k < re; k += 32) {
+      const T vv = sval[k];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) w[a] = fma(vv, sx[a * kChunkNnz + k], w[a]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) w[a] += __shfl_down_sync(0xffffffffu, w[a], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) srow[a * kChunkRows + r] = w[a];
+    }
+  }
+}
 
 template <typename T>
 __host__ __device__ constexpr size_t spmv_warp_smem(int nv) {
@@ -357,29 +437,12 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
     }
     __syncwarp();
     const int nrows = c.row_end - c.row_begin;
-    int L = 32;
-    while (L > 1 && L * nrows > 32) L >>= 1;
-    const int g = lane / L, gl = lane % L;
-    T acc[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = T(0);
-    if (g < nrows) {
-      const int row = c.row_begin + g;
-      const int s = __ldg(A.rp + row) - nb, e = __ldg(A.rp + row + 1) - nb;
-      for (int k = s + gl; k < e; k += L) {
-        const T vv = sval[k];
-#pragma unroll
-        for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kChunkNnz + k], acc[a]);
-      }
+    int s_r = 0, e_r = 0;
+    if (lane < nrows) {
+      s_r = __ldg(A.rp + c.row_begin + lane) - nb;
+      e_r = __ldg(A.rp + c.row_begin + lane + 1) - nb;
     }
-    for (int o = L / 2; o > 0; o >>= 1) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) acc[a] += __shfl_down_sync(0xffffffffu, acc[a], o, L);
-    }
-    if (g < nrows && gl == 0) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) srow[a * kChunkRows + g] = acc[a];
-    }
+    chunk_row_sums<T, NV>(sval, sx, nrows, s_r, e_r, srow);
     __syncwarp();
     if (lane < nrows) {
       T s2[NV];

@@ -144,7 +144,7 @@ __device__ int load_desc(const Mat<T> &A, int gw, int nw, Chunk *desc) {
 }
 
 // Reduces a staged chunk and runs its epilogue: rows of a normal chunk by
-// groups of L lanes (the arithmetic of spmv_chunk), segments of long rows by
+// chunk_row_sums (the arithmetic of spmv_chunk), segments of long rows by
 // a warp sum whose partials the last segment warp combines in segment order
 // (that row's reduction terms go to its slot A.lr_acc).
 template <typename T, typename Ph>
@@ -165,17 +165,12 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
       if (e < cnt) sx[e] = xg[it];
     }
     __syncwarp();
-    int L = 32;
-    while (L > 1 && L * nrows > 32) L >>= 1;
-    const int g = lane / L, gl = lane % L;
-    T acc = T(0);
-    if (g < nrows) {
-      const int s = srp[g] - nb;
-      const int e = g + 1 < nrows ? srp[g + 1] - nb : cnt;
-      for (int k = s + gl; k < e; k += L) acc = fma(sval[k], sx[k], acc);
+    int s_r = 0, e_r = 0;
+    if (lane < nrows) {
+      s_r = srp[lane] - nb;
+      e_r = lane + 1 < nrows ? srp[lane + 1] - nb : cnt;
     }
-    for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, L);
-    if (g < nrows && gl == 0) srow[g] = acc;
+    chunk_row_sums<T, 1>(sval, sx, nrows, s_r, e_r, srow);
     __syncwarp();
     if (lane < nrows) ph.epi(c.row_begin + lane, srow[lane], pre + lane, ph.acc);
     return;
