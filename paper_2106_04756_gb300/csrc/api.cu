@@ -59,6 +59,8 @@ struct pdlp_ctx {
   DevBuf rp, ci, val, trp, tci, tval, perm, rowid;  // rowid: row of every nonzero of K
   DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT, lraccK, lraccKT;
   int32_t nlongK = 0, nlongKT = 0;
+  DevBuf wchunkK, woffK, wchunkKT, woffKT;  // chunk lists of the persistent kernel's warps
+  int32_t cmaxK = 0, cmaxKT = 0, assign_nw = 0;
   int32_t nblocksK = 0, nblocksKT = 0;
   std::vector<Chunk> hblocksK, hblocksKT;  // warp-chunk schedules
   // problem data
@@ -136,6 +138,9 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   K.seg_cnt = reinterpret_cast<unsigned *>(ctx->segcntK.ptr());
   K.lr_acc = reinterpret_cast<double *>(ctx->lraccK.ptr());
   K.nlong = ctx->nlongK;
+  K.wchunk = reinterpret_cast<const int32_t *>(ctx->wchunkK.ptr());
+  K.woff = reinterpret_cast<const int32_t *>(ctx->woffK.ptr());
+  K.assign_nw = ctx->assign_nw;
   KT.rows = ctx->n;
   KT.cols = ctx->m;
   KT.rp = reinterpret_cast<const int32_t *>(ctx->trp.ptr());
@@ -149,6 +154,9 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   KT.seg_cnt = reinterpret_cast<unsigned *>(ctx->segcntKT.ptr());
   KT.lr_acc = reinterpret_cast<double *>(ctx->lraccKT.ptr());
   KT.nlong = ctx->nlongKT;
+  KT.wchunk = reinterpret_cast<const int32_t *>(ctx->wchunkKT.ptr());
+  KT.woff = reinterpret_cast<const int32_t *>(ctx->woffKT.ptr());
+  KT.assign_nw = ctx->assign_nw;
   return PDLP_OK;
 }
 
@@ -176,7 +184,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   S.eta_log = nullptr;
   // the Malitsky-Pock line search runs on the per-launch engine
   const int persist_mode = ctx->opts.step_policy == 2 ? 0 : ctx->opts.persistent;
-  CK(persist_plan<T>(ctx->hblocksKT, ctx->hblocksK, persist_mode, &pr.pg), "persistent kernel layout");
+  CK(persist_plan<T>(ctx->cmaxKT, ctx->cmaxK, ctx->assign_nw, persist_mode, &pr.pg), "persistent kernel layout");
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
                     8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + 16;
   double *parts = dalloc<double>(pr.parts, np);
@@ -663,6 +671,21 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     if (!lKT.empty()) CK(cudaMemcpy(LKT, lKT.data(), sizeof(LongRow) * lKT.size(), cudaMemcpyHostToDevice), "long rows");
     CK(cudaMemset(cK, 0, sizeof(unsigned) * std::max<size_t>(lK.size(), 1)), "memset");
     CK(cudaMemset(cKT, 0, sizeof(unsigned) * std::max<size_t>(lKT.size(), 1)), "memset");
+    // balanced chunk lists for the persistent kernel's warps
+    const int nw = persist_warps();
+    if (nw > 0) {
+      std::vector<int32_t> iK, oK, iKT, oKT;
+      assign_chunks(ctx->hblocksK, hrp.data(), nw, iK, oK, ctx->cmaxK);
+      assign_chunks(ctx->hblocksKT, htrp.data(), nw, iKT, oKT, ctx->cmaxKT);
+      int32_t *wK = dalloc<int32_t>(ctx->wchunkK, iK.size()), *fK = dalloc<int32_t>(ctx->woffK, oK.size());
+      int32_t *wKT = dalloc<int32_t>(ctx->wchunkKT, iKT.size()), *fKT = dalloc<int32_t>(ctx->woffKT, oKT.size());
+      if (!wK || !fK || !wKT || !fKT) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+      CK(cudaMemcpy(wK, iK.data(), sizeof(int32_t) * iK.size(), cudaMemcpyHostToDevice), "chunk lists");
+      CK(cudaMemcpy(fK, oK.data(), sizeof(int32_t) * oK.size(), cudaMemcpyHostToDevice), "chunk lists");
+      CK(cudaMemcpy(wKT, iKT.data(), sizeof(int32_t) * iKT.size(), cudaMemcpyHostToDevice), "chunk lists");
+      CK(cudaMemcpy(fKT, oKT.data(), sizeof(int32_t) * oKT.size(), cudaMemcpyHostToDevice), "chunk lists");
+      ctx->assign_nw = nw;
+    }
   }
   double *xin = dalloc<double>(ctx->xin, n), *yin = dalloc<double>(ctx->yin, m);
   Scalars *sc = dalloc<Scalars>(ctx->scal, 1);

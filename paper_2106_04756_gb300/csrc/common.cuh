@@ -63,6 +63,10 @@ struct Mat {
   unsigned int *seg_cnt;  // arrival counter per long row
   double *lr_acc;         // epilogue sums of each long row [nlong][kLrAcc]
   int32_t nlong;
+  // chunks of each warp of the persistent kernel: wchunk[woff[w] .. woff[w+1])
+  // for its assign_nw warps (a cost-balanced static assignment)
+  const int32_t *wchunk = nullptr, *woff = nullptr;
+  int32_t assign_nw = 0;
 };
 
 // Solver outcome codes (same values as the public PDLP_* status codes).

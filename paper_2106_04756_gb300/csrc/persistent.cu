@@ -11,9 +11,11 @@
 //                 Algorithm 2's test on its own copy of the step control, so all
 //                 CTAs take the same decision without a third barrier.
 //
-// Work placement: warp w of the grid owns the warp chunks w, w + W, w + 2W, ...
-// of K^T and of K (W warps in the grid) for the whole launch; their
-// descriptors are copied into the warp's shared-memory slice once per launch.
+// Work placement: each warp of the grid owns a fixed list of warp chunks of
+// K^T and of K for the whole launch (assign_chunks: a longest-processing-time
+// assignment under a cost model of the chunks, so that the warps, and with
+// them the SMs, reach the grid barriers together); the descriptors are
+// copied into the warp's shared-memory slice once per launch.
 // A warp keeps two chunks in flight: while one is reduced, the loads of the
 // next (column indices, then values, row starts and epilogue operands by
 // cp.async, and the gathered entries through L2) are outstanding.  The
@@ -24,6 +26,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <queue>
 #include <vector>
 
 #include "common.cuh"
@@ -133,12 +136,12 @@ struct DualPhase {
   }
 };
 
-// Copies the descriptors of the warp's chunks (w, w + W, ...) into shared
-// memory; returns their count.
+// Copies the descriptors of the warp's chunks (its list of the balanced
+// assignment) into shared memory; returns their count.
 template <typename T>
-__device__ int load_desc(const Mat<T> &A, int gw, int nw, Chunk *desc) {
-  const int count = gw < A.nchunks ? (A.nchunks - 1 - gw) / nw + 1 : 0;
-  for (int i = threadIdx.x & 31; i < count; i += 32) desc[i] = A.chunks[gw + i * nw];
+__device__ int load_desc(const Mat<T> &A, int gw, Chunk *desc) {
+  const int b = A.woff[gw], count = A.woff[gw + 1] - b;
+  for (int i = threadIdx.x & 31; i < count; i += 32) desc[i] = A.chunks[A.wchunk[b + i]];
   __syncwarp();
   return count;
 }
@@ -309,8 +312,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     fac[0][i] = sc->fac_tab[0][i];
     fac[1][i] = sc->fac_tab[1][i];
   }
-  const int cnt_p = load_desc(KT, gw, nw, dp);
-  const int cnt_d = load_desc(K, gw, nw, dd);
+  const int cnt_p = load_desc(KT, gw, dp);
+  const int cnt_d = load_desc(K, gw, dd);
   __syncthreads();
   unsigned long long target = s_base;
   for (int att = 0; att < kMaxAttemptsPerLaunch; ++att) {
@@ -401,9 +404,75 @@ void layout(PersistGeo &g, int cmax_p, int cmax_d) {
 
 }  // namespace
 
+int persist_warps() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms * kPWarps;
+}
+
+// Cost of one chunk in warp steps, the model behind the assignment:
+// gathered entries per lane, twice the row-sum steps that chunk_row_sums
+// takes (float64 multiply-add plus shared-memory loads), a fixed epilogue,
+// and the combine of a long-row segment.
+static double chunk_cost(const Chunk &c, const int32_t *rp) {
+  const int nnz = c.nnz_end - c.nnz_begin;
+  if (c.row_end < 0) return nnz / 32.0 + 2.0 * 13.0 + 30.0;
+  const int nrows = c.row_end - c.row_begin;
+  int L = 32, lg = 5;
+  while (L > 1 && L * nrows > 32) {
+    L >>= 1;
+    --lg;
+  }
+  unsigned best = 0;
+  for (int r = c.row_begin; r < c.row_end; ++r) best = std::max(best, (unsigned)(rp[r + 1] - rp[r] + L - 1) >> lg);
+  for (unsigned th = 16; th <= 128; th <<= 1) {
+    unsigned ms = 0, lc = 0;
+    for (int r = c.row_begin; r < c.row_end; ++r) {
+      const unsigned len = (unsigned)(rp[r + 1] - rp[r]);
+      if (len > th) lc += ((len + 31u) >> 5) + 5u;
+      else ms = std::max(ms, (len + (unsigned)L - 1u) >> lg);
+    }
+    best = std::min(best, ms + lc);
+  }
+  return nnz / 32.0 + 2.0 * (best + lg) + 10.0;
+}
+
+void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, std::vector<int32_t> &idx,
+                   std::vector<int32_t> &off, int &cmax) {
+  const int n = (int)chunks.size();
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) cost[i] = chunk_cost(chunks[i], rp);
+  std::vector<int32_t> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // least-loaded warp first; equal loads by rank, and rank r is warp
+  // (r % grid) * kPWarps + r / grid, so that ties spread over the SMs
+  const int grid = std::max(nw / kPWarps, 1);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> heap;
+  for (int r = 0; r < nw; ++r) heap.push({0.0, r});
+  std::vector<int32_t> owner(n);
+  for (int i : order) {
+    const auto top = heap.top();
+    heap.pop();
+    const int r = top.second;
+    owner[i] = (r % grid) * kPWarps + r / grid;
+    heap.push({top.first + cost[i], r});
+  }
+  off.assign((size_t)nw + 1, 0);
+  for (int i = 0; i < n; ++i) ++off[owner[i] + 1];
+  cmax = 0;
+  for (int w = 0; w < nw; ++w) {
+    cmax = std::max(cmax, off[w + 1]);
+    off[w + 1] += off[w];
+  }
+  idx.assign((size_t)n, 0);
+  std::vector<int32_t> fill(off.begin(), off.end() - 1);
+  for (int i = 0; i < n; ++i) idx[fill[owner[i]]++] = i;  // each list in chunk order
+}
+
 template <typename T>
-cudaError_t persist_plan(const std::vector<Chunk> &chunks_kt, const std::vector<Chunk> &chunks_k, int mode,
-                         PersistGeo *pg) {
+cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, PersistGeo *pg) {
   *pg = PersistGeo{};
   if (mode == 0) return cudaSuccess;
   cudaError_t e;
@@ -415,10 +484,10 @@ cudaError_t persist_plan(const std::vector<Chunk> &chunks_kt, const std::vector<
   if ((e = cudaFuncGetAttributes(&fa, k_persist<T>))) return e;
   const int budget = optin - (int)fa.sharedSizeBytes;
   const int grid = sms;
-  const int nw = grid * kPWarps;
+  if (grid * kPWarps != assign_nw) return cudaSuccess;  // no assignment for this grid
   PersistGeo g{};
   g.grid = grid;
-  layout<T>(g, (int)((chunks_kt.size() + nw - 1) / nw), (int)((chunks_k.size() + nw - 1) / nw));
+  layout<T>(g, cmax_kt, cmax_k);
   if (g.smem > budget) return cudaSuccess;  // too many chunks per warp: one launch per half-step
   // the attribute is per kernel, shared by every context: set it to the budget
   if ((e = cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
@@ -483,8 +552,7 @@ cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P,
 }
 
 #define PDLP_INST(T)                                                                                        \
-  template cudaError_t persist_plan<T>(const std::vector<Chunk> &, const std::vector<Chunk> &, int,          \
-                                       PersistGeo *);                                                       \
+  template cudaError_t persist_plan<T>(int, int, int, int, PersistGeo *);                                   \
   template cudaError_t launch_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &, \
                                          const PersistGeo &, cudaStream_t);                                 \
   template cudaError_t time_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &,   \

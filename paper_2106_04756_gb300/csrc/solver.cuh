@@ -51,10 +51,16 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
                               const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
                               cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec);
 // Persistent step kernel (persistent.cu).  mode 0: off.  Leaves pg->grid = 0
-// when the kernel's layout does not fit.
+// when the kernel's layout does not fit or no chunk assignment exists for
+// its grid (assign_nw warps).  cmax_*: most chunks of one warp.
+int persist_warps();  // warps of the persistent grid on the current device (0 on error)
+// Balanced static assignment of warp chunks to nw warps (longest processing
+// time first under a cost model of the chunks): warp w runs chunks
+// idx[off[w] .. off[w+1]) in chunk order; cmax = the longest list.
+void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, std::vector<int32_t> &idx,
+                   std::vector<int32_t> &off, int &cmax);
 template <typename T>
-cudaError_t persist_plan(const std::vector<Chunk> &chunks_kt, const std::vector<Chunk> &chunks_k, int mode,
-                         PersistGeo *pg);
+cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, PersistGeo *pg);
 template <typename T>
 cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                            const PersistGeo &pg, cudaStream_t st);
