@@ -163,7 +163,7 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
 // Allocates the iterate state of one precision and captures its solve graph
 // on the problem `P` (already filled in).
 template <typename T>
-int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
+int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_dev = nullptr) {
   const int n = ctx->n, m = ctx->m, N = n + m;
   const size_t nv = 2 * (size_t)n + 2 * (size_t)m + 2 * (size_t)m + 2 * (size_t)n + 2 * (size_t)m +
                     (size_t)n + (size_t)m + 2 * (size_t)n + (size_t)m;
@@ -214,6 +214,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol) {
   ScalarInit in{};
   in.eta0 = ctx->eta0;
   in.rel_tol = tol;
+  in.tol_dev = tol_dev;
   in.beta_suff = o.beta_suff;
   in.beta_nec = o.beta_nec;
   in.beta_art = o.beta_art;
@@ -333,7 +334,9 @@ int setup_refine(pdlp_ctx *ctx) {
   Problem<double> P64;
   fill_problem64(ctx, P64);
   pr.P = refine_problem(ctx->ref, P64);
-  return setup_state<float>(ctx, pr, ctx->opts.inner_tol);
+  double *tol_dev = reinterpret_cast<double *>(ctx->ref.tol.ptr());
+  CK(cudaMemcpy(tol_dev, &ctx->opts.inner_tol, sizeof(double), cudaMemcpyHostToDevice), "tolerance");
+  return setup_state<float>(ctx, pr, ctx->opts.inner_tol, tol_dev);
 }
 
 void read_result(const Scalars &s, double seconds, pdlp_result *res) {
@@ -734,7 +737,7 @@ extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, dou
       return run_graph<float>(ctx, ctx->pc32, h) == PDLP_OK ? cudaSuccess : cudaErrorUnknown;
     };
     cudaError_t e = refine_solve(ctx->ref, ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->pc32.S, run_inner,
-                                 ctx->opts.rel_tol, ctx->opts.refine_rounds,
+                                 ctx->opts.rel_tol, ctx->opts.inner_tol, ctx->opts.refine_rounds,
                                  reinterpret_cast<const double *>(ctx->xin.ptr()),
                                  reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st, &ro);
     if (e) return cuda_fail(ctx, e, "refinement");

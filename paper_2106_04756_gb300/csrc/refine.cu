@@ -193,7 +193,8 @@ cudaError_t refine_alloc(RefineBuffers &R, int32_t m, int32_t n, int32_t nbK, in
   float *f = reinterpret_cast<float *>(R.vec32.get(sizeof(float) * (3 * (size_t)n + 2 * (size_t)m)));
   double *part = reinterpret_cast<double *>(R.part.get(sizeof(double) * 8 * 1024 + 64));
   double *rs = reinterpret_cast<double *>(R.rs.get(sizeof(double) * 16));
-  if (!d || !f || !part || !rs) return cudaErrorMemoryAllocation;
+  double *tl = reinterpret_cast<double *>(R.tol.get(sizeof(double)));
+  if (!d || !f || !part || !rs || !tl) return cudaErrorMemoryAllocation;
   R.v.xh = d; d += n;
   R.v.yh = d; d += m;
   R.v.xt = d; d += n;
@@ -244,10 +245,18 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64) {
   return P;
 }
 
+constexpr double kInnerFloor = 1e-6;  // tightest inner tolerance (float32 arithmetic)
+
+double refine_round_tol(double rel, double tol, double inner_tol) {
+  const double want = 0.1 * tol / rel;
+  if (want >= inner_tol || want < kInnerFloor) return inner_tol;
+  return want;
+}
+
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
                          const State<float> &Sc, const std::function<cudaError_t(Scalars *)> &run_inner,
-                         double tol, int max_rounds, const double *x_stage, const double *y_stage,
-                         cudaStream_t st, RefineOutcome *out) {
+                         double tol, double inner_tol, int max_rounds, const double *x_stage,
+                         const double *y_stage, cudaStream_t st, RefineOutcome *out) {
   cudaError_t e;
   const int N = P.n + P.m, grid = (N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024;
   RefView V = R.v;
@@ -300,6 +309,8 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
     refine_scales(h[8], h[9], 1e12, &dP, &dD);
     k_ref_build<<<grid, 256, 0, st>>>(P, V, dP, dD);
     // inner float32 solve from zero (the staging buffers are the graph's start point)
+    const double round_tol = refine_round_tol(rel, tol, inner_tol);
+    if ((e = cudaMemcpyAsync(R.tol.ptr(), &round_tol, sizeof(double), cudaMemcpyHostToDevice, st))) return e;
     if ((e = cudaMemsetAsync(const_cast<double *>(x_stage), 0, sizeof(double) * P.n, st))) return e;
     if ((e = cudaMemsetAsync(const_cast<double *>(y_stage), 0, sizeof(double) * P.m, st))) return e;
     if ((e = run_inner(&hs))) return e;

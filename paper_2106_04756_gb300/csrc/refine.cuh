@@ -27,6 +27,7 @@ struct RefineBuffers {
   DevBuf vec;    // float64 vectors
   DevBuf vec32;  // float32 correction data
   DevBuf part, rs;
+  DevBuf tol;    // Eq. (15) tolerance of the next inner solve (read by its k_init_scalars)
   RefView v{};
 };
 
@@ -43,11 +44,18 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64);
 // Scales of the correction problem from the violations (see refine.cu).
 void refine_scales(double pv, double dv, double dmax, double *dP, double *dD);
 
+// Tolerance of the next inner solve: inner_tol, or tighter (down to
+// kInnerFloor) when a round at that tolerance is expected to end within 10x
+// of the target: the error after a round is about the current error times
+// the inner tolerance.
+double refine_round_tol(double rel, double tol, double inner_tol);
+
 // run_inner runs one float32 solve of the correction problem held in R (start
-// point: the staging buffers) and returns its final scalars in *hs (host).
+// point: the staging buffers) to the tolerance in R.tol and returns its final
+// scalars in *hs (host).
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
                          const State<float> &Sc, const std::function<cudaError_t(Scalars *)> &run_inner,
-                         double tol, int max_rounds, const double *x_stage, const double *y_stage,
-                         cudaStream_t st, RefineOutcome *out);
+                         double tol, double inner_tol, int max_rounds, const double *x_stage,
+                         const double *y_stage, cudaStream_t st, RefineOutcome *out);
 
 }  // namespace pdlp

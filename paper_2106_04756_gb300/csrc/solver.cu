@@ -954,7 +954,7 @@ __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->mu0 = INFINITY;
   s->muc_prev = INFINITY;
   s->inv_avg = 0.0;
-  s->rel_tol = in.rel_tol;
+  s->rel_tol = in.tol_dev ? *in.tol_dev : in.rel_tol;
   s->beta_suff = in.beta_suff;
   s->beta_nec = in.beta_nec;
   s->beta_art = in.beta_art;

@@ -17,6 +17,7 @@ struct ScalarInit {
   int restart_to_current;  // 0: restart candidate always the average (Appendix C.2)
   int mp;                  // 1: Malitsky-Pock line search (Appendix C.1)
   double mp_breaking, mp_downscaling, mp_interpolation;
+  const double *tol_dev;  // non-null: read rel_tol from this device double at each solve
 };
 
 template <typename T> cudaError_t set_kernel_attributes();
