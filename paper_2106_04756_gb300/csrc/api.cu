@@ -66,7 +66,7 @@ struct pdlp_ctx {
   // problem data
   DevBuf c, q, l, u, ylo;            // original space
   DevBuf cs, qs, ls, us, ylos;       // preconditioned (float64)
-  DevBuf D1, D2;
+  DevBuf D1, D2, D1inv, D2inv;
   DevBuf xin, yin;                   // start point staging (original space)
   DevBuf mask;                       // inequality mask as given
   DevBuf scal;                       // Scalars
@@ -111,6 +111,11 @@ int cuda_fail(pdlp_ctx *ctx, cudaError_t e, const char *where) {
 template <typename T>
 T *dalloc(DevBuf &b, size_t count) {
   return reinterpret_cast<T *>(b.get(sizeof(T) * (count ? count : 1)));
+}
+
+__global__ void k_recip(const double *v, int64_t n, double *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = 1.0 / v[i];
 }
 
 __global__ void k_absmax_bits(const double *v, int64_t n, unsigned long long *out) {
@@ -269,6 +274,8 @@ void fill_problem64(pdlp_ctx *ctx, Problem<double> &P) {
   P.ylo = reinterpret_cast<const double *>(ctx->ylo.ptr());
   P.D1 = reinterpret_cast<const double *>(ctx->D1.ptr());
   P.D2 = reinterpret_cast<const double *>(ctx->D2.ptr());
+  P.D1inv = reinterpret_cast<const double *>(ctx->D1inv.ptr());
+  P.D2inv = reinterpret_cast<const double *>(ctx->D2inv.ptr());
 }
 
 int setup_fp64(pdlp_ctx *ctx) {
@@ -320,6 +327,7 @@ int setup_fp32(pdlp_ctx *ctx) {
   P.cs = cs; P.qs = qs; P.ls = ls; P.us = us; P.ylos = ylos;
   P.c = P64.c; P.q = P64.q; P.l = P64.l; P.u = P64.u; P.ylo = P64.ylo;
   P.D1 = P64.D1; P.D2 = P64.D2;
+  P.D1inv = P64.D1inv; P.D2inv = P64.D2inv;
   return setup_state<float>(ctx, pr, ctx->opts.rel_tol);
 }
 
@@ -633,6 +641,13 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
                   st),
      "precondition");
   CK(transform(m, n, D1, D2, dc, dq, dl, du, dylo, cs, qs, ls, us, ylos, st), "transform");
+  {
+    double *i1 = dalloc<double>(ctx->D1inv, m), *i2 = dalloc<double>(ctx->D2inv, n);
+    if (!i1 || !i2) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+    k_recip<<<std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(D1, m, i1);
+    k_recip<<<std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(D2, n, i2);
+    CK(cudaGetLastError(), "reciprocals");
+  }
   // step size 1 / max |K~_ij| (Algorithm 1 initialisation)
   {
     DevBuf mb;

@@ -151,6 +151,7 @@ struct Problem {
   const T *cs, *qs, *ls, *us, *ylos;
   const double *c, *q, *l, *u, *ylo;  // ylo: 0 / -inf for the paper's Y, general for corrections
   const double *D1, *D2;
+  const double *D1inv, *D2inv;  // 1 / D1, 1 / D2 (the evaluation multiplies instead of dividing)
 };
 
 // Iteration state (ping-pong buffers selected by Scalars::cur).

@@ -242,6 +242,8 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64) {
   P.ylo = R.v.ylo;
   P.D1 = P64.D1;
   P.D2 = P64.D2;
+  P.D1inv = P64.D1inv;
+  P.D2inv = P64.D2inv;
   return P;
 }
 

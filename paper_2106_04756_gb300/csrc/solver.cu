@@ -281,13 +281,13 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P,
   spmv_warp<T, 2>(KT, vec, sm, acc, [&](int j, const T(&g)[2], double(&acc)[8]) {
     S.KTy_cur[j] = g[0];
     S.KTys[j] = g[1];
-    const double D2 = P.D2[j], cj = P.c[j], lj = P.l[j], uj = P.u[j], xr = (double)x0[j];
+    const double D2 = P.D2[j], iD2 = P.D2inv[j], cj = P.c[j], lj = P.l[j], uj = P.u[j], xr = (double)x0[j];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (c == 1 && !avg) break;
       const double xt = c == 0 ? (double)x[j] : (double)xs[j] * inv;
       const double kt = c == 0 ? (double)g[0] : (double)g[1] * inv;
-      const double xo = D2 * xt, rc = cj - kt / D2;
+      const double xo = D2 * xt, rc = cj - kt * iD2;
       const double lam = proj_lambda(rc, lj, uj);
       acc[4 * c + 0] += cj * xo;
       acc[4 * c + 1] += (rc - lam) * (rc - lam);
@@ -399,13 +399,13 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
   const T *const vec[1] = {S.xs[cur]};
   spmv_warp<T, 1>(K, vec, sm, acc, [&](int i, const T(&s)[1], double(&acc)[8]) {
     S.Kxbar[i] = s[0];
-    const double D1 = P.D1[i], qi = P.q[i], lo = P.ylo[i], yr = (double)y0[i];
+    const double D1 = P.D1[i], iD1 = P.D1inv[i], qi = P.q[i], lo = P.ylo[i], yr = (double)y0[i];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (c == 1 && !avg) break;
       const double yt = c == 0 ? (double)y[i] : (double)ys[i] * inv;
       const double kx = c == 0 ? (double)Kx[i] : (double)s[0] * inv;
-      double r = qi - kx / D1;
+      double r = qi - kx * iD1;
       if (lo > -INFINITY) {                      // inequality row
         if (lo != 0.0) acc[4 * c + 3] += lo * r;  // general dual bound only
         r = r > 0.0 ? r : 0.0;
