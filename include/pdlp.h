@@ -88,7 +88,11 @@ typedef struct {
   double primal_importance; /* multiplies InitializePrimalWeight (Section 3.3): 1.0       */
   double beta_suff, beta_nec, beta_art; /* Section 3.2: 0.9, 0.1, 0.5                    */
   double eps_zero;          /* Section 3.3 epsilon_zero: 1e-10                           */
-  double inner_tol;         /* PDLP_FP32_REFINE: Eq. (15) tolerance of each inner solve  */
+  double inner_tol;         /* PDLP_FP32_REFINE: Eq. (15) tolerance of the first inner
+                               solve, 1e-5; a later round that can reach rel_tol uses
+                               the loosest tolerance that should get there (see
+                               refine.cu), and the loop ends when an inner solve stops
+                               at a limit                                               */
   int32_t refine_rounds;    /* PDLP_FP32_REFINE: maximum outer rounds                    */
   int32_t unroll_T;         /* >0: pdlp_solve runs T unrolled steps for pdlp_grad        */
   int32_t ckpt_every;       /* unrolled steps between stored checkpoints                 */

@@ -251,8 +251,8 @@ constexpr double kInnerFloor = 1e-6;  // tightest inner tolerance (float32 arith
 
 double refine_round_tol(double rel, double tol, double inner_tol) {
   const double want = 0.1 * tol / rel;
-  if (want >= inner_tol || want < kInnerFloor) return inner_tol;
-  return want;
+  if (want < kInnerFloor) return inner_tol;  // no single round can finish
+  return want < 0.1 ? want : 0.1;            // the loosest round that finishes
 }
 
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
@@ -280,6 +280,7 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
   out->iters = out->kkt_passes = out->restarts = 0;
   out->rounds = 0;
   double best = INFINITY;
+  int inner_stop = 0;  // an inner solve stopped at a limit: end after evaluating its update
   for (int round = 0;; ++round) {
     k_ref_scale<<<grid, 256, 0, st>>>(P.n, P.m, V.xh, V.yh, P.D1, P.D2, V.xt, V.yt);
     launch_spmv<double>(K, V.xt, V.Kx, st);
@@ -304,6 +305,7 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
     out->rounds = round;
     if (h[5] <= tol && h[6] <= tol && h[7] <= tol) { out->status = kOptimal; break; }
     if (!(isfinite(h[0]) && isfinite(h[1]))) { out->status = kNumErr; break; }
+    if (inner_stop) { out->status = inner_stop; break; }
     if (round >= max_rounds) break;
     if ((e = cudaMemcpyAsync(V.xb, V.xh, sizeof(double) * P.n, cudaMemcpyDeviceToDevice, st))) return e;
     if ((e = cudaMemcpyAsync(V.yb, V.yh, sizeof(double) * P.m, cudaMemcpyDeviceToDevice, st))) return e;
@@ -322,7 +324,7 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
     out->iters += hs.k;
     out->kkt_passes += hs.attempts;
     out->restarts += hs.restarts;
-    if (hs.status == kTimeLimit) out->status = kTimeLimit;
+    if (hs.status == kTimeLimit || hs.status == kIterLimit || hs.status == kKktLimit) inner_stop = hs.status;
   }
   out->x = V.xh;
   out->y = V.yh;
