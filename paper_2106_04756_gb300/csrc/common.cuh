@@ -80,7 +80,6 @@ struct Scalars {
   double omega;     // primal weight omega^n
   double tau, sigma;  // eta / omega and eta * omega of the next attempt (Section 2)
   double inv_omega;   // 1 / omega
-  double fac_red, fac_grow;  // (unused)
   // Algorithm 2 factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 for the steps
   // k = fac_k0 + i of the current chunk (k counted from 1), filled by k_finish
   double fac_tab[2][kMaxEval];
@@ -119,7 +118,6 @@ struct Scalars {
   int restart;    // a restart was decided at this evaluation
   int cand;       // restart candidate: 0 current, 1 average
   int adaptive_restart, pw_update;
-  int avg_valid;
   int err;        // bounded-wait failures (device-side timeouts)
   int const_step; // 1: constant step size (every attempt accepted)
   int trace_n;    // restart evaluations recorded so far (ring of kTraceCap)
