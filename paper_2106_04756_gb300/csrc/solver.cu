@@ -268,7 +268,6 @@ __global__ void __launch_bounds__(kThreads) k_mp_test(Mat<T> KT, State<T> S, int
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[8 * (kThreads / 32)];
   const Scalars *sc = S.s;
   const int cur = sc->cur;
   const bool avg = sc->sum_eta > 0.0;
@@ -295,7 +294,8 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P,
       acc[4 * c + 3] += (xt - xr) * (xt - xr);
     }
   });
-  block_sum<8>(acc, red);
+  // the staging area is free now: few float64 adds (float64 is slow on this part)
+  block_sum_lean<8>(acc, reinterpret_cast<double *>(sm));
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int a = 0; a < 8; ++a) S.part_ec[8 * blockIdx.x + a] = acc[a];
@@ -415,7 +415,8 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
       acc[4 * c + 2] += (yt - yr) * (yt - yr);
     }
   });
-  block_sum<8>(acc, red);
+  // the staging area is free now: few float64 adds (float64 is slow on this part)
+  block_sum_lean<8>(acc, reinterpret_cast<double *>(sm));
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int a = 0; a < 8; ++a) S.part_er[8 * blockIdx.x + a] = acc[a];
