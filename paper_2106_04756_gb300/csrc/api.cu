@@ -693,8 +693,9 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     const int nw = persist_warps();
     if (nw > 0) {
       std::vector<int32_t> iK, oK, iKT, oKT;
-      assign_chunks(ctx->hblocksK, hrp.data(), nw, iK, oK, ctx->cmaxK);
-      assign_chunks(ctx->hblocksKT, htrp.data(), nw, iKT, oKT, ctx->cmaxKT);
+      const int wpc = persist_warps_per_cta();
+      assign_chunks(ctx->hblocksK, hrp.data(), nw, wpc, iK, oK, ctx->cmaxK);
+      assign_chunks(ctx->hblocksKT, htrp.data(), nw, wpc, iKT, oKT, ctx->cmaxKT);
       int32_t *wK = dalloc<int32_t>(ctx->wchunkK, iK.size()), *fK = dalloc<int32_t>(ctx->woffK, oK.size());
       int32_t *wKT = dalloc<int32_t>(ctx->wchunkKT, iKT.size()), *fKT = dalloc<int32_t>(ctx->woffKT, oKT.size());
       if (!wK || !fK || !wKT || !fKT) return fail(ctx, PDLP_ERR_OOM, "allocation failed");

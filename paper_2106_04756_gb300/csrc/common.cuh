@@ -21,33 +21,17 @@
 #include <stdint.h>
 
 #include "pdlp.h"
+#include "schedule.h"
 
 namespace pdlp {
 
 constexpr int kThreads = 256;          // CTA size of the sparse-product kernels
 constexpr int kWarps = kThreads / 32;  // warps per CTA, one chunk per warp
-constexpr int kChunkNnz = 256;         // nonzeros staged per warp chunk
-constexpr int kChunkRows = 32;         // rows per warp chunk (one epilogue lane per row)
-constexpr int kSegNnz = kChunkNnz;     // rows longer than this are split across warps, one chunk each
 constexpr int kGapBuckets = 2048;      // radix digit of the normalized-gap selection
 constexpr int kGapThreads = 512;
 constexpr int kGapSlots = 3;           // current, average, restart point
 constexpr int kMaxEval = 256;          // largest eval_every (step-factor table size)
 constexpr int kLrAcc = 8;              // epilogue sums kept per long row
-
-// One warp's share of a CSR matrix.  Two kinds (with kSegNnz == kChunkNnz):
-//   rows [row_begin, row_end) with at most kChunkNnz nonzeros and kChunkRows rows;
-//   row_end < 0: a segment [nnz_begin, nnz_end) of long row -(row_end + 1).
-// (A single row longer than kChunkNnz but not than kSegNnz would be a third
-// kind, looped over by one warp; spmv_chunk still handles it.)
-struct Chunk {
-  int32_t row_begin, row_end, nnz_begin, nnz_end;
-};
-
-// A row longer than kSegNnz, processed by `nseg` warps (consecutive chunks).
-struct LongRow {
-  int32_t row, nseg, part_off, pad;
-};
 
 // CSR matrix plus its warp-chunk schedule.
 template <typename T>

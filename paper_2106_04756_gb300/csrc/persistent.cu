@@ -404,71 +404,13 @@ void layout(PersistGeo &g, int cmax_p, int cmax_d) {
 
 }  // namespace
 
+int persist_warps_per_cta() { return kPWarps; }
+
 int persist_warps() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   return sms * kPWarps;
-}
-
-// Cost of one chunk in warp steps, the model behind the assignment:
-// gathered entries per lane, twice the row-sum steps that chunk_row_sums
-// takes (float64 multiply-add plus shared-memory loads), a fixed epilogue,
-// and the combine of a long-row segment.
-static double chunk_cost(const Chunk &c, const int32_t *rp) {
-  const int nnz = c.nnz_end - c.nnz_begin;
-  if (c.row_end < 0) return nnz / 32.0 + 2.0 * 13.0 + 30.0;
-  const int nrows = c.row_end - c.row_begin;
-  int L = 32, lg = 5;
-  while (L > 1 && L * nrows > 32) {
-    L >>= 1;
-    --lg;
-  }
-  unsigned best = 0;
-  for (int r = c.row_begin; r < c.row_end; ++r) best = std::max(best, (unsigned)(rp[r + 1] - rp[r] + L - 1) >> lg);
-  for (unsigned th = 16; th <= 128; th <<= 1) {
-    unsigned ms = 0, lc = 0;
-    for (int r = c.row_begin; r < c.row_end; ++r) {
-      const unsigned len = (unsigned)(rp[r + 1] - rp[r]);
-      if (len > th) lc += ((len + 31u) >> 5) + 5u;
-      else ms = std::max(ms, (len + (unsigned)L - 1u) >> lg);
-    }
-    best = std::min(best, ms + lc);
-  }
-  return nnz / 32.0 + 2.0 * (best + lg) + 10.0;
-}
-
-void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, std::vector<int32_t> &idx,
-                   std::vector<int32_t> &off, int &cmax) {
-  const int n = (int)chunks.size();
-  std::vector<double> cost(n);
-  for (int i = 0; i < n; ++i) cost[i] = chunk_cost(chunks[i], rp);
-  std::vector<int32_t> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  // least-loaded warp first; equal loads by rank, and rank r is warp
-  // (r % grid) * kPWarps + r / grid, so that ties spread over the SMs
-  const int grid = std::max(nw / kPWarps, 1);
-  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> heap;
-  for (int r = 0; r < nw; ++r) heap.push({0.0, r});
-  std::vector<int32_t> owner(n);
-  for (int i : order) {
-    const auto top = heap.top();
-    heap.pop();
-    const int r = top.second;
-    owner[i] = (r % grid) * kPWarps + r / grid;
-    heap.push({top.first + cost[i], r});
-  }
-  off.assign((size_t)nw + 1, 0);
-  for (int i = 0; i < n; ++i) ++off[owner[i] + 1];
-  cmax = 0;
-  for (int w = 0; w < nw; ++w) {
-    cmax = std::max(cmax, off[w + 1]);
-    off[w + 1] += off[w];
-  }
-  idx.assign((size_t)n, 0);
-  std::vector<int32_t> fill(off.begin(), off.end() - 1);
-  for (int i = 0; i < n; ++i) idx[fill[owner[i]]++] = i;  // each list in chunk order
 }
 
 template <typename T>

@@ -448,50 +448,4 @@ cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const
   return cudaStreamSynchronize(st);
 }
 
-// ------------------------------------------------------ row-block schedule
-
-void build_schedule(int32_t rows, const int32_t *rp, std::vector<Chunk> &chunks, std::vector<LongRow> &longrows,
-                    int32_t &nseg_total) {
-  chunks.clear();
-  longrows.clear();
-  nseg_total = 0;
-  int32_t r = 0;
-  while (r < rows) {
-    const int32_t len = rp[r + 1] - rp[r];
-    if (len > kSegNnz) {  // split across warps
-      LongRow L;
-      L.row = r;
-      L.nseg = (len + kSegNnz - 1) / kSegNnz;
-      L.part_off = nseg_total;
-      L.pad = 0;
-      const int32_t lr = (int32_t)longrows.size();
-      longrows.push_back(L);
-      for (int32_t s = 0; s < L.nseg; ++s) {
-        Chunk c;
-        c.row_begin = r;
-        c.row_end = -(lr + 1);
-        c.nnz_begin = rp[r] + s * kSegNnz;
-        c.nnz_end = std::min(rp[r + 1], c.nnz_begin + kSegNnz);
-        chunks.push_back(c);
-      }
-      nseg_total += L.nseg;
-      ++r;
-      continue;
-    }
-    if (len > kChunkNnz) {  // one warp loops over the row (only if kSegNnz > kChunkNnz)
-      chunks.push_back(Chunk{r, r + 1, rp[r], rp[r + 1]});
-      ++r;
-      continue;
-    }
-    int32_t e = r;
-    while (e < rows && e - r < kChunkRows) {
-      if (rp[e + 1] - rp[e] > kChunkNnz) break;
-      if (rp[e + 1] - rp[r] > kChunkNnz) break;
-      ++e;
-    }
-    chunks.push_back(Chunk{r, e, rp[r], rp[e]});
-    r = e;
-  }
-}
-
 }  // namespace pdlp

@@ -55,8 +55,5 @@ cudaError_t transform(int32_t m, int32_t n, const double *D1, const double *D2, 
                       double *cs, double *qs, double *ls, double *us, double *ylos, cudaStream_t st);
 cudaError_t ylo_from_mask(int32_t m, const uint8_t *ineq, double *ylo, cudaStream_t st);
 cudaError_t to_float(const double *src, int64_t n, float *dst, cudaStream_t st);
-// Warp-chunk schedule of a CSR matrix (see Chunk in common.cuh).
-void build_schedule(int32_t rows, const int32_t *rp_host, std::vector<Chunk> &chunks,
-                    std::vector<LongRow> &longrows, int32_t &nseg_total);
 
 }  // namespace pdlp

@@ -175,13 +175,6 @@ __global__ void k_ref_start(Problem<double> P, RefView R, const double *x0, cons
 
 }  // namespace
 
-void refine_scales(double pv, double dv, double dmax, double *dP, double *dD) {
-  double P = pv > 1.0 / dmax ? 1.0 / pv : dmax;
-  double D = dv > 1.0 / dmax ? 1.0 / dv : dmax;
-  *dP = P < 1.0 ? 1.0 : P;
-  *dD = D < 1.0 ? 1.0 : D;
-}
-
 cudaError_t refine_alloc(RefineBuffers &R, int32_t m, int32_t n, int32_t nbK, int32_t nbKT) {
   if (R.ready) return cudaSuccess;
   R.m = m;
@@ -245,14 +238,6 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64) {
   P.D1inv = P64.D1inv;
   P.D2inv = P64.D2inv;
   return P;
-}
-
-constexpr double kInnerFloor = 1e-6;  // tightest inner tolerance (float32 arithmetic)
-
-double refine_round_tol(double rel, double tol, double inner_tol) {
-  const double want = 0.1 * tol / rel;
-  if (want < kInnerFloor) return inner_tol;  // no single round can finish
-  return want < 0.1 ? want : 0.1;            // the loosest round that finishes
 }
 
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,

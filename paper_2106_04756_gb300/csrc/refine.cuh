@@ -41,15 +41,7 @@ struct RefineOutcome {
 cudaError_t refine_alloc(RefineBuffers &R, int32_t m, int32_t n, int32_t nbK, int32_t nbKT);
 Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64);
 
-// Scales of the correction problem from the violations (see refine.cu).
-void refine_scales(double pv, double dv, double dmax, double *dP, double *dD);
 
-// Tolerance of the next inner solve.  The error after a round is about the
-// current error times the round's tolerance, so when 0.1 tol / current error
-// is at least kInnerFloor (1e-6, what float32 reaches) the round uses it
-// (capped at 0.1): the loosest solve expected to finish with a 10x margin;
-// otherwise inner_tol.
-double refine_round_tol(double rel, double tol, double inner_tol);
 
 // run_inner runs one float32 solve of the correction problem held in R (start
 // point: the staging buffers) to the tolerance in R.tol and returns its final

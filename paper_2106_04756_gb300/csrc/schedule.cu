@@ -1,0 +1,124 @@
+// Host-side planning (declared in schedule.h): plain C++ with no CUDA
+// headers, compiled into the library and, by the CPU tests, on its own.
+#include "schedule.h"
+
+#include <algorithm>
+#include <functional>
+#include <queue>
+#include <utility>
+#include <vector>
+
+namespace pdlp {
+
+void build_schedule(int32_t rows, const int32_t *rp, std::vector<Chunk> &chunks, std::vector<LongRow> &longrows,
+                    int32_t &nseg_total) {
+  chunks.clear();
+  longrows.clear();
+  nseg_total = 0;
+  int32_t r = 0;
+  while (r < rows) {
+    const int32_t len = rp[r + 1] - rp[r];
+    if (len > kSegNnz) {  // split across warps
+      LongRow L;
+      L.row = r;
+      L.nseg = (len + kSegNnz - 1) / kSegNnz;
+      L.part_off = nseg_total;
+      L.pad = 0;
+      const int32_t lr = (int32_t)longrows.size();
+      longrows.push_back(L);
+      for (int32_t s = 0; s < L.nseg; ++s) {
+        Chunk c;
+        c.row_begin = r;
+        c.row_end = -(lr + 1);
+        c.nnz_begin = rp[r] + s * kSegNnz;
+        c.nnz_end = std::min(rp[r + 1], c.nnz_begin + kSegNnz);
+        chunks.push_back(c);
+      }
+      nseg_total += L.nseg;
+      ++r;
+      continue;
+    }
+    if (len > kChunkNnz) {  // one warp loops over the row (only if kSegNnz > kChunkNnz)
+      chunks.push_back(Chunk{r, r + 1, rp[r], rp[r + 1]});
+      ++r;
+      continue;
+    }
+    int32_t e = r;
+    while (e < rows && e - r < kChunkRows) {
+      if (rp[e + 1] - rp[e] > kChunkNnz) break;
+      if (rp[e + 1] - rp[r] > kChunkNnz) break;
+      ++e;
+    }
+    chunks.push_back(Chunk{r, e, rp[r], rp[e]});
+    r = e;
+  }
+}
+
+double chunk_cost(const Chunk &c, const int32_t *rp) {
+  const int nnz = c.nnz_end - c.nnz_begin;
+  if (c.row_end < 0) return nnz / 32.0 + 2.0 * 13.0 + 30.0;
+  const int nrows = c.row_end - c.row_begin;
+  int L = 32, lg = 5;
+  while (L > 1 && L * nrows > 32) {
+    L >>= 1;
+    --lg;
+  }
+  unsigned best = 0;
+  for (int r = c.row_begin; r < c.row_end; ++r) best = std::max(best, (unsigned)(rp[r + 1] - rp[r] + L - 1) >> lg);
+  for (unsigned th = 16; th <= 128; th <<= 1) {
+    unsigned ms = 0, lc = 0;
+    for (int r = c.row_begin; r < c.row_end; ++r) {
+      const unsigned len = (unsigned)(rp[r + 1] - rp[r]);
+      if (len > th) lc += ((len + 31u) >> 5) + 5u;
+      else ms = std::max(ms, (len + (unsigned)L - 1u) >> lg);
+    }
+    best = std::min(best, ms + lc);
+  }
+  return nnz / 32.0 + 2.0 * (best + lg) + 10.0;
+}
+
+void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, int warps_per_cta,
+                   std::vector<int32_t> &idx, std::vector<int32_t> &off, int &cmax) {
+  const int n = (int)chunks.size();
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) cost[i] = chunk_cost(chunks[i], rp);
+  std::vector<int32_t> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  const int grid = std::max(nw / warps_per_cta, 1);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> heap;
+  for (int r = 0; r < nw; ++r) heap.push({0.0, r});
+  std::vector<int32_t> owner(n);
+  for (int i : order) {
+    const auto top = heap.top();
+    heap.pop();
+    const int r = top.second;
+    owner[i] = (r % grid) * warps_per_cta + r / grid;
+    heap.push({top.first + cost[i], r});
+  }
+  off.assign((size_t)nw + 1, 0);
+  for (int i = 0; i < n; ++i) ++off[owner[i] + 1];
+  cmax = 0;
+  for (int w = 0; w < nw; ++w) {
+    cmax = std::max(cmax, off[w + 1]);
+    off[w + 1] += off[w];
+  }
+  idx.assign((size_t)n, 0);
+  std::vector<int32_t> fill(off.begin(), off.end() - 1);
+  for (int i = 0; i < n; ++i) idx[fill[owner[i]]++] = i;  // each list in chunk order
+}
+
+void refine_scales(double pv, double dv, double dmax, double *dP, double *dD) {
+  double P = pv > 1.0 / dmax ? 1.0 / pv : dmax;
+  double D = dv > 1.0 / dmax ? 1.0 / dv : dmax;
+  *dP = P < 1.0 ? 1.0 : P;
+  *dD = D < 1.0 ? 1.0 : D;
+}
+
+double refine_round_tol(double rel, double tol, double inner_tol) {
+  const double want = 0.1 * tol / rel;
+  if (want < kInnerFloor) return inner_tol;  // no single round can finish
+  return want < 0.1 ? want : 0.1;            // the loosest round that finishes
+}
+
+}  // namespace pdlp

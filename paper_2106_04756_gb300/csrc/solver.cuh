@@ -55,11 +55,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
 // when the kernel's layout does not fit or no chunk assignment exists for
 // its grid (assign_nw warps).  cmax_*: most chunks of one warp.
 int persist_warps();  // warps of the persistent grid on the current device (0 on error)
-// Balanced static assignment of warp chunks to nw warps (longest processing
-// time first under a cost model of the chunks): warp w runs chunks
-// idx[off[w] .. off[w+1]) in chunk order; cmax = the longest list.
-void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, std::vector<int32_t> &idx,
-                   std::vector<int32_t> &off, int &cmax);
+int persist_warps_per_cta();
 template <typename T>
 cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, PersistGeo *pg);
 template <typename T>

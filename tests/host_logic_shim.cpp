@@ -1,0 +1,47 @@
+// C entry points over the library's host-side planning (schedule.h) for the
+// CPU tests; built by tests/test_host_logic.py with the host compiler.
+#include <string.h>
+
+#include <vector>
+
+#include "schedule.h"
+
+using namespace pdlp;
+
+extern "C" int hl_build_schedule(int rows, const int32_t *rp, int32_t *chunks4, int cap_chunks, int32_t *long4,
+                                 int cap_long, int32_t *counts /* nchunks, nlong, nseg_total */) {
+  std::vector<Chunk> ch;
+  std::vector<LongRow> lr;
+  int32_t nseg = 0;
+  build_schedule(rows, rp, ch, lr, nseg);
+  counts[0] = (int32_t)ch.size();
+  counts[1] = (int32_t)lr.size();
+  counts[2] = nseg;
+  if ((int)ch.size() > cap_chunks || (int)lr.size() > cap_long) return -1;
+  memcpy(chunks4, ch.data(), sizeof(Chunk) * ch.size());
+  memcpy(long4, lr.data(), sizeof(LongRow) * lr.size());
+  return 0;
+}
+
+extern "C" double hl_chunk_cost(const int32_t *chunk4, const int32_t *rp) {
+  Chunk c;
+  memcpy(&c, chunk4, sizeof(c));
+  return chunk_cost(c, rp);
+}
+
+extern "C" int hl_assign(int n, const int32_t *chunks4, const int32_t *rp, int nw, int wpc, int32_t *idx,
+                         int32_t *off, int32_t *cmax) {
+  std::vector<Chunk> ch((size_t)n);
+  memcpy(ch.data(), chunks4, sizeof(Chunk) * (size_t)n);
+  std::vector<int32_t> i, o;
+  int cm = 0;
+  assign_chunks(ch, rp, nw, wpc, i, o, cm);
+  memcpy(idx, i.data(), sizeof(int32_t) * i.size());
+  memcpy(off, o.data(), sizeof(int32_t) * o.size());
+  *cmax = cm;
+  return 0;
+}
+
+extern "C" double hl_round_tol(double rel, double tol, double inner) { return refine_round_tol(rel, tol, inner); }
+
+extern "C" void hl_scales(double pv, double dv, double dmax, double *out) { refine_scales(pv, dv, dmax, out, out + 1); }

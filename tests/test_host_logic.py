@@ -1,0 +1,163 @@
+"""Host-side planning of the library (csrc/schedule.h), built here with the
+host compiler alone: the warp-chunk schedule, the balanced assignment of
+chunks to the persistent kernel's warps, and the refinement's tolerance and
+scale rules."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2106_04756_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def hl(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("hl") / "libhl.so")
+    subprocess.run([gxx, "-std=c++17", "-O2", "-shared", "-fPIC", "-I", CSRC, "-x", "c++",
+                    os.path.join(CSRC, "schedule.cu"), "-x", "none",
+                    os.path.join(ROOT, "tests", "host_logic_shim.cpp"), "-o", out], check=True)
+    L = C.CDLL(out)
+    P = C.c_void_p
+    L.hl_build_schedule.argtypes = [C.c_int, P, P, C.c_int, P, C.c_int, P]
+    L.hl_chunk_cost.argtypes = [P, P]
+    L.hl_chunk_cost.restype = C.c_double
+    L.hl_assign.argtypes = [C.c_int, P, P, C.c_int, C.c_int, P, P, P]
+    L.hl_round_tol.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.hl_round_tol.restype = C.c_double
+    L.hl_scales.argtypes = [C.c_double, C.c_double, C.c_double, P]
+    return L
+
+
+def _schedule(hl, rp):
+    rp = np.ascontiguousarray(rp, np.int32)
+    rows = rp.size - 1
+    cap = rows + int(rp[-1]) // 256 + 8
+    ch = np.zeros((cap, 4), np.int32)
+    lr = np.zeros((cap, 4), np.int32)
+    cnt = np.zeros(3, np.int32)
+    assert hl.hl_build_schedule(rows, rp.ctypes.data, ch.ctypes.data, cap, lr.ctypes.data, cap,
+                                cnt.ctypes.data) == 0
+    return ch[:cnt[0]], lr[:cnt[1]], int(cnt[2])
+
+
+def _powerlaw_rp(rng, rows, with_specials=True):
+    lens = np.minimum((rng.pareto(1.1, rows) * 3).astype(np.int64), 2000)
+    if with_specials:
+        lens[:8] = [0, 0, 256, 257, 512, 513, 1, 2000]
+        lens[rng.choice(rows, 20)] = 0
+    rp = np.zeros(rows + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    return rp.astype(np.int32)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_schedule_covers_every_row_and_nonzero_once(hl, seed):
+    rng = np.random.default_rng(seed)
+    rp = _powerlaw_rp(rng, 3000)
+    ch, lr, nseg = _schedule(hl, rp)
+    lens = np.diff(rp)
+    r = 0
+    k = 0
+    nlong = 0
+    while k < len(ch):
+        rb, re_, nb, ne = ch[k]
+        assert rb == r
+        if re_ < 0:  # segments of a long row, in order
+            li = -(re_ + 1)
+            assert li == nlong and lr[li][0] == r
+            L = lr[li]
+            assert L[1] == -(-lens[r] // 256) and lens[r] > 256
+            assert L[2] == sum(x[1] for x in lr[:li])  # part_off: cumulative segment count
+            for s in range(L[1]):
+                rb2, re2, nb2, ne2 = ch[k + s]
+                assert (rb2, re2) == (r, re_)
+                assert nb2 == rp[r] + 256 * s and ne2 == min(rp[r + 1], nb2 + 256)
+            k += L[1]
+            r += 1
+            nlong += 1
+            continue
+        assert re_ > rb and re_ - rb <= 32
+        assert nb == rp[rb] and ne == rp[re_] and ne - nb <= 256
+        assert np.all(lens[rb:re_] <= 256)
+        # greedy: the chunk stops at 32 rows, at the end, before a long row, or
+        # before the row that would take it past 256 nonzeros
+        if re_ - rb < 32 and re_ < len(lens):
+            assert lens[re_] > 256 or rp[re_ + 1] - rp[rb] > 256
+        r = re_
+        k += 1
+    assert r == len(lens) and nlong == len(lr) and nseg == sum(x[1] for x in lr)
+
+
+def test_chunk_cost_closed_forms(hl):
+    # 32 rows of 8 nonzeros: one lane per row, 8 steps, no shuffle
+    rp = np.arange(0, 33 * 8, 8, dtype=np.int32)
+    c = np.array([0, 32, 0, 256], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == 256 / 32 + 2 * 8 + 10
+    # 4 rows of 64: 8 lanes per row, 8 steps + 3 shuffle levels
+    rp = np.arange(0, 5 * 64, 64, dtype=np.int32)
+    c = np.array([0, 4, 0, 256], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == 256 / 32 + 2 * (8 + 3) + 10
+    # one row of 200 among 20 rows of 2: summing the long row with the warp
+    # (7 + 5 steps) plus 2 steps for the rest beats 200 steps at one lane a row
+    lens = np.array([200] + [2] * 20)
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    c = np.array([0, 21, 0, int(rp[-1])], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == rp[-1] / 32 + 2 * (2 + 7 + 5) + 10
+    # a segment of a long row
+    c = np.array([0, -1, 0, 256], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == 256 / 32 + 2 * 13 + 30
+
+
+@pytest.mark.parametrize("nw,wpc", [(64, 16), (2432, 16), (7, 1)])
+def test_assignment_is_a_balanced_partition(hl, nw, wpc):
+    rng = np.random.default_rng(5)
+    rp = _powerlaw_rp(rng, 20000)
+    ch, _, _ = _schedule(hl, rp)
+    n = len(ch)
+    chc = np.ascontiguousarray(ch, np.int32)
+    idx = np.zeros(n, np.int32)
+    off = np.zeros(nw + 1, np.int32)
+    cmax = C.c_int32()
+    hl.hl_assign(n, chc.ctypes.data, rp.ctypes.data, nw, wpc, idx.ctypes.data, off.ctypes.data, C.byref(cmax))
+    assert sorted(idx.tolist()) == list(range(n))  # every chunk once
+    assert off[0] == 0 and off[-1] == n and np.all(np.diff(off) >= 0)
+    assert cmax.value == np.diff(off).max()
+    cost = np.array([hl.hl_chunk_cost(chc[i].ctypes.data, rp.ctypes.data) for i in range(n)])
+    loads = np.array([cost[idx[off[w]:off[w + 1]]].sum() for w in range(nw)])
+    for w in range(nw):
+        lst = idx[off[w]:off[w + 1]]
+        assert np.all(np.diff(lst) > 0)  # each list in chunk order
+    # list scheduling bound: the last chunk went to the least-loaded warp
+    assert loads.max() <= cost.sum() / nw + cost.max() + 1e-9
+    # same input, same assignment
+    idx2 = np.zeros(n, np.int32)
+    off2 = np.zeros(nw + 1, np.int32)
+    hl.hl_assign(n, chc.ctypes.data, rp.ctypes.data, nw, wpc, idx2.ctypes.data, off2.ctypes.data, C.byref(cmax))
+    assert np.array_equal(idx, idx2) and np.array_equal(off, off2)
+
+
+def test_refinement_round_tolerance(hl):
+    # a round that can finish uses the loosest tolerance with a 10x margin
+    assert hl.hl_round_tol(1e-4, 1e-8, 1e-5) == pytest.approx(1e-5)
+    assert hl.hl_round_tol(1e-6, 1e-8, 1e-5) == pytest.approx(1e-3)
+    assert hl.hl_round_tol(1e-12, 1e-8, 1e-5) == 0.1  # capped
+    # no single round can finish: the configured inner tolerance
+    assert hl.hl_round_tol(1.0, 1e-8, 1e-5) == 1e-5
+    assert hl.hl_round_tol(2e-3, 1e-8, 1e-4) == 1e-4
+
+
+def test_refinement_scales(hl):
+    out = np.zeros(2)
+    hl.hl_scales(1e-3, 1e-5, 1e12, out.ctypes.data)
+    assert out[0] == 1e3 and out[1] == pytest.approx(1e5)
+    hl.hl_scales(10.0, 0.5, 1e12, out.ctypes.data)  # violations above 1: no down-scaling
+    assert out[0] == 1.0 and out[1] == 2.0
+    hl.hl_scales(0.0, 1e-20, 1e12, out.ctypes.data)  # clipped at dmax
+    assert out[0] == 1e12 and out[1] == 1e12
