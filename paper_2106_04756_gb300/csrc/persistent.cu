@@ -246,6 +246,36 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
   }
 }
 
+// Fixed-order CTA sum of three values per thread with few float64 adds
+// (float64 is slow on this part): value a's 512 terms go to the staging area
+// of warp a (idle between the phases), which sums them, 16 per lane in a
+// pairwise tree, then in a 5-step shuffle.  tot[0..2] (shared) holds the
+// sums after the call.
+static_assert(kPThreads * sizeof(double) <= 2 * buf_bytes<float>(), "a warp's staging area holds a CTA's terms");
+__device__ __forceinline__ void cta_sum3(const double (&v)[3], char *sm, int warp_bytes, double *tot) {
+  __syncthreads();  // every warp is done with its staging buffers
+#pragma unroll
+  for (int a = 0; a < 3; ++a) reinterpret_cast<double *>(sm + (size_t)a * warp_bytes)[threadIdx.x] = v[a];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < 3) {
+    const double *r = reinterpret_cast<const double *>(sm + (size_t)w * warp_bytes);
+    double p[kPThreads / 32];
+#pragma unroll
+    for (int k = 0; k < kPThreads / 32; ++k) p[k] = r[lane + 32 * k];
+#pragma unroll
+    for (int s = kPThreads / 64; s >= 1; s >>= 1) {
+#pragma unroll
+      for (int k = 0; k < s; ++k) p[k] += p[k + s];
+    }
+    double t = p[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) tot[w] = t;
+  }
+  __syncthreads();
+}
+
 // One phase over the warp's chunks with two chunks in flight (two staging
 // buffers, gathered entries in registers a / b): the loads of chunk i + 2
 // start once chunk i is done.
@@ -282,7 +312,7 @@ template <typename T>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_persist(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S, PersistGeo geo) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[3 * kPWarps];
+  __shared__ double s_tot[3];
   __shared__ double fac[2][kMaxEval];
   __shared__ StepCtl ctl;
   __shared__ long long s_fac_k0, s_iter_limit, s_attempt_limit;
@@ -290,7 +320,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   __shared__ unsigned long long s_base;
   Scalars *sc = S.s;
   const int wid = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kPWarps + wid, nw = gridDim.x * kPWarps;
+  const int gw = blockIdx.x * kPWarps + wid;
   const unsigned long long G = gridDim.x;
   unsigned long long *bar = reinterpret_cast<unsigned long long *>(S.tickets + kTicketBar);
   char *wsm = sm + (size_t)geo.warp_bytes * wid;
@@ -330,12 +360,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                      (T)ctl.sigma, (T)ctl.eta, {0.0, 0.0}};
     run_phase<T>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
     {
-      double v[3] = {pp.acc[0], dph.acc[0], dph.acc[1]};
-      block_sum<3>(v, red);
+      const double v[3] = {pp.acc[0], dph.acc[0], dph.acc[1]};
+      cta_sum3(v, sm, geo.warp_bytes, s_tot);
       if (threadIdx.x == 0) {
-        S.part_cp[3 * blockIdx.x + 0] = v[0];
-        S.part_cp[3 * blockIdx.x + 1] = v[1];
-        S.part_cp[3 * blockIdx.x + 2] = v[2];
+        S.part_cp[3 * blockIdx.x + 0] = s_tot[0];
+        S.part_cp[3 * blockIdx.x + 1] = s_tot[1];
+        S.part_cp[3 * blockIdx.x + 2] = s_tot[2];
       }
     }
     target += G;
@@ -354,8 +384,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
         t[1] += __ldcg(K.lr_acc + (size_t)r * kLrAcc);
         t[2] += __ldcg(K.lr_acc + (size_t)r * kLrAcc + 1);
       }
-      block_sum<3>(t, red);
+      cta_sum3(t, sm, geo.warp_bytes, s_tot);
       if (threadIdx.x == 0) {
+        t[0] = s_tot[0];
+        t[1] = s_tot[1];
+        t[2] = s_tot[2];
         const long long idx = ctl.k - s_fac_k0;
         double fr, fg;
         if (idx >= 0 && idx < ne) {
