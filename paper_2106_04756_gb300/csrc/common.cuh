@@ -287,19 +287,130 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
 // All sums have a fixed order (deterministic).  `wsm` is the warp's slice of
 // spmv_warp_smem<T>(NV) bytes.
 constexpr int kLaneItems = kChunkNnz / 32;
+constexpr unsigned kSegSteps = 16;  // float64 steps above which a chunk takes the segmented row sums
 
-// Row sums of one staged chunk of nrows <= 32 rows: values sval[e] and
-// gathered entries sx[a * kChunkNnz + e] for the chunk's nonzeros e; lane r
-// passes its row's local bounds [s_r, e_r) (any values on lanes >= nrows).
+// Position of a chunk's nonzero e in its staging arrays.  In float64 the
+// 16-byte granules (two entries) of each aligned group of eight are permuted
+// by an XOR with e / 8 mod 8, so that lanes reading eight consecutive entries
+// each (chunk_row_sums_seg) fall on different banks; the permutation stays
+// inside each 128-byte group, so lanes writing consecutive entries stay
+// conflict-free too.  float32: identity.
+template <typename T>
+__device__ __forceinline__ int stg(int e) {
+  if constexpr (sizeof(T) == 8) return (((e >> 1) ^ ((e >> 3) & 7)) << 1) | (e & 1);
+  else return e;
+}
+
+// Position of the n-th (n >= 1) set bit of m.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) {
+    const int c = __popc(m & ((1u << sh) - 1u));
+    if (n > c) {
+      n -= c;
+      m >>= sh;
+      pos += sh;
+    }
+  }
+  return pos;
+}
+
+// Segmented row sums of a float64 chunk (one gathered vector): lane l
+// multiplies its eight consecutive nonzeros [8l, 8l + 8) and adds them by
+// row; a row that crosses lane boundaries is completed by an inclusive
+// segmented scan over the lanes (5 steps) of each lane's last partial sum.
+// 8 multiply-adds and about 6 adds per lane, whatever the row lengths.  Row
+// r's sum goes to srow[r] (0 for an empty row).  Fixed order throughout.
+template <typename T>
+__device__ __forceinline__ void chunk_row_sums_seg(const T *sval, const T *sx, int nrows, int cnt, int s_r,
+                                                   int e_r, T *srow) {
+  const int lane = threadIdx.x & 31;
+  const bool mine = lane < nrows;
+  const bool nonempty_row = mine && e_r > s_r;
+  const unsigned nonempty = __ballot_sync(0xffffffffu, nonempty_row);
+  if (mine && !nonempty_row) srow[lane] = T(0);
+  // bit p of starts[p / 32]: a non-empty row starts at local position p
+  unsigned starts[kChunkNnz / 32];
+#pragma unroll
+  for (int w = 0; w < kChunkNnz / 32; ++w)
+    starts[w] = __reduce_or_sync(0xffffffffu, (nonempty_row && (s_r >> 5) == w) ? (1u << (s_r & 31)) : 0u);
+  const int e0 = 8 * lane;
+  const int nloc = cnt - e0 < 0 ? 0 : (cnt - e0 < 8 ? cnt - e0 : 8);
+  // row of item e0: the rank-th non-empty row, rank = starts at or before e0
+  int rank = 0;
+#pragma unroll
+  for (int w = 0; w < kChunkNnz / 32; ++w) {
+    if (e0 >= 32 * w + 32) rank += __popc(starts[w]);
+    else if (e0 >= 32 * w) rank += __popc(starts[w] & (0xffffffffu >> (31 - (e0 - 32 * w))));
+  }
+  // the word holding this lane's eight items and the next lane's first item
+  // (selected without dynamic indexing, so that starts[] stays in registers)
+  const int w0 = e0 >> 5, en = e0 + 8, w1 = en >> 5;
+  unsigned word = 0u, word_n = 0u;
+#pragma unroll
+  for (int w = 0; w < kChunkNnz / 32; ++w) {
+    if (w == w0) word = starts[w];
+    if (w == w1) word_n = starts[w];
+  }
+  const bool first_is_start = nloc > 0 && ((word >> (e0 & 31)) & 1u);
+  int cur = rank > 0 ? nth_set_bit(nonempty, rank) : 0;
+  const int head_row = cur;
+  T acc = T(0), headv = T(0);
+  bool crossed = false;  // a row start after e0 inside this lane
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    if (it < nloc) {
+      const int e = e0 + it;
+      if (it > 0 && ((word >> (e & 31)) & 1u)) {
+        if (!crossed && !first_is_start) headv = acc;  // continuation of an earlier lane's row
+        else srow[cur] = acc;                          // a row that starts and ends in this lane
+        crossed = true;
+        const int nxt = __ffs(cur < 31 ? nonempty & ~((2u << cur) - 1u) : 0u) - 1;  // next non-empty row
+        cur = nxt >= 0 ? nxt : cur;
+        acc = T(0);
+      }
+      acc = fma(sval[stg<T>(e)], sx[stg<T>(e)], acc);
+    }
+  }
+  // carries of the rows that cross lanes: segmented inclusive scan of the
+  // lanes' last partial sums; a chain starts at a lane whose last partial
+  // begins at a row start
+  T v = acc;
+  int f = (nloc == 0 || crossed || first_is_start) ? 1 : 0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const T tv = __shfl_up_sync(0xffffffffu, v, d);
+    const int tf = __shfl_up_sync(0xffffffffu, f, d);
+    if (lane >= d) {
+      if (!f) v = tv + v;
+      f = f | tf;
+    }
+  }
+  const T carry_prev = __shfl_up_sync(0xffffffffu, v, 1);
+  if (nloc > 0 && !first_is_start && crossed) srow[head_row] = carry_prev + headv;
+  // the last partial's row ends with this lane: the chunk ends, or the next
+  // lane's first item starts a row
+  const bool next_starts = en < cnt && ((word_n >> (en & 31)) & 1u);
+  if (nloc > 0 && (e0 + nloc == cnt || next_starts)) srow[cur] = v;
+}
+
+// Row sums of one staged chunk of nrows <= 32 rows: values sval[stg(e)] and
+// gathered entries sx[a * kChunkNnz + stg(e)] for the chunk's nonzeros e;
+// lane r passes its row's local bounds [s_r, e_r) (any values on lanes >=
+// nrows) and cnt is the chunk's nonzero count.
 // Rows are summed by power-of-two groups of L lanes (L * nrows <= 32), which
 // costs the warp ceil(max length / L) steps; with power-law row lengths one
 // long row would set that count for the whole chunk, so rows longer than a
 // threshold T are instead summed by the whole warp, one after another
 // (ceil(length / 32) steps and a 5-step shuffle each).  T in {16, 32, 64,
-// 128} or none is chosen per chunk by that integer step count.  Every sum
-// has a fixed order.  Writes srow[a * kChunkRows + r].
+// 128} or none is chosen per chunk by that integer step count; in float64
+// with one vector, chunks whose step count stays above the segmented sum's
+// (chunk_row_sums_seg, 8 + 6) take that instead.  Every sum has a fixed
+// order.  Writes srow[a * kChunkRows + r].
 template <typename T, int NV>
-__device__ __forceinline__ void chunk_row_sums(const T *sval, const T *sx, int nrows, int s_r, int e_r, T *srow) {
+__device__ __forceinline__ void chunk_row_sums(const T *sval, const T *sx, int nrows, int cnt, int s_r, int e_r,
+                                               T *srow) {
   const int lane = threadIdx.x & 31;
   int L = 32;
   while (L > 1 && L * nrows > 32) L >>= 1;
@@ -318,6 +429,12 @@ __device__ __forceinline__ void chunk_row_sums(const T *sval, const T *sx, int n
       thr = th;
     }
   }
+  if constexpr (sizeof(T) == 8 && NV == 1) {
+    if (best + (unsigned)lg > kSegSteps) {
+      chunk_row_sums_seg<T>(sval, sx, nrows, cnt, s_r, e_r, srow);
+      return;
+    }
+  }
   // rows up to thr: groups of L lanes
   const int g = lane >> lg, gl = lane & (L - 1);
   const int gs = __shfl_sync(0xffffffffu, s_r, g), ge = __shfl_sync(0xffffffffu, e_r, g);
@@ -327,9 +444,10 @@ __device__ __forceinline__ void chunk_row_sums(const T *sval, const T *sx, int n
   for (int a = 0; a < NV; ++a) acc[a] = T(0);
   if (short_row) {
     for (int k = gs + gl; k < ge; k += L) {
-      const T vv = sval[k];
+      const int q = stg<T>(k);
+      const T vv = sval[q];
 #pragma unroll
-      for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kChunkNnz + k], acc[a]);
+      for (int a = 0; a < NV; ++a) acc[a] = fma(vv, sx[a * kChunkNnz + q], acc[a]);
     }
   }
   for (int o = L / 2; o > 0; o >>= 1) {
@@ -350,9 +468,10 @@ __device__ __forceinline__ void chunk_row_sums(const T *sval, const T *sx, int n
 #pragma unroll
     for (int a = 0; a < NV; ++a) w[a] = T(0);
     for (int k = rs + lane; k < re; k += 32) {
-      const T vv = sval[k];
+      const int q = stg<T>(k);
+      const T vv = sval[q];
 #pragma unroll
-      for (int a = 0; a < NV; ++a) w[a] = fma(vv, sx[a * kChunkNnz + k], w[a]);
+      for (int a = 0; a < NV; ++a) w[a] = fma(vv, sx[a * kChunkNnz + q], w[a]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -416,9 +535,10 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
       for (int it = 0; it < kLaneItems; ++it) {
         const int e = lane + 32 * it;
         if (e < cnt) {
-          sval[e] = v[it];
+          const int q = stg<T>(e);
+          sval[q] = v[it];
 #pragma unroll
-          for (int a = 0; a < NV; ++a) sx[a * kChunkNnz + e] = xv[a][it];
+          for (int a = 0; a < NV; ++a) sx[a * kChunkNnz + q] = xv[a][it];
         }
       }
     }
@@ -429,7 +549,7 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
       s_r = __ldg(A.rp + c.row_begin + lane) - nb;
       e_r = __ldg(A.rp + c.row_begin + lane + 1) - nb;
     }
-    chunk_row_sums<T, NV>(sval, sx, nrows, s_r, e_r, srow);
+    chunk_row_sums<T, NV>(sval, sx, nrows, cnt, s_r, e_r, srow);
     __syncwarp();
     if (lane < nrows) {
       T s2[NV];

@@ -165,7 +165,7 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
 #pragma unroll
     for (int it = 0; it < kLaneItems; ++it) {
       const int e = lane + 32 * it;
-      if (e < cnt) sx[e] = xg[it];
+      if (e < cnt) sx[stg<T>(e)] = xg[it];
     }
     __syncwarp();
     int s_r = 0, e_r = 0;
@@ -173,7 +173,7 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
       s_r = srp[lane] - nb;
       e_r = lane + 1 < nrows ? srp[lane + 1] - nb : cnt;
     }
-    chunk_row_sums<T, 1>(sval, sx, nrows, s_r, e_r, srow);
+    chunk_row_sums<T, 1>(sval, sx, nrows, cnt, s_r, e_r, srow);
     __syncwarp();
     if (lane < nrows) ph.epi(c.row_begin + lane, srow[lane], pre + lane, ph.acc);
     return;
@@ -182,7 +182,7 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
 #pragma unroll
   for (int it = 0; it < kLaneItems; ++it) {
     const int e = lane + 32 * it;
-    if (e < cnt) acc = fma(sval[e], xg[it], acc);
+    if (e < cnt) acc = fma(sval[stg<T>(e)], xg[it], acc);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -232,7 +232,7 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
   for (int it = 0; it < kLaneItems; ++it) {
     const int e = lane + 32 * it;
     cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
-    if (e < cnt) cp_async(sval + e, A.val + nb + e);
+    if (e < cnt) cp_async(sval + stg<T>(e), A.val + nb + e);
   }
   if (lane < nrows) {
     cp_async(srp + lane, A.rp + c.row_begin + lane);
