@@ -168,7 +168,8 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
 // Allocates the iterate state of one precision and captures its solve graph
 // on the problem `P` (already filled in).
 template <typename T>
-int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_dev = nullptr) {
+int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_dev = nullptr,
+                int stall_evals = 0) {
   const int n = ctx->n, m = ctx->m, N = n + m;
   const size_t nv = 2 * (size_t)n + 2 * (size_t)m + 2 * (size_t)m + 2 * (size_t)n + 2 * (size_t)m +
                     (size_t)n + (size_t)m + 2 * (size_t)n + (size_t)m;
@@ -220,6 +221,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   in.eta0 = ctx->eta0;
   in.rel_tol = tol;
   in.tol_dev = tol_dev;
+  in.stall_evals = stall_evals;
   in.beta_suff = o.beta_suff;
   in.beta_nec = o.beta_nec;
   in.beta_art = o.beta_art;
@@ -344,7 +346,11 @@ int setup_refine(pdlp_ctx *ctx) {
   pr.P = refine_problem(ctx->ref, P64);
   double *tol_dev = reinterpret_cast<double *>(ctx->ref.tol.ptr());
   CK(cudaMemcpy(tol_dev, &ctx->opts.inner_tol, sizeof(double), cudaMemcpyHostToDevice), "tolerance");
-  return setup_state<float>(ctx, pr, ctx->opts.inner_tol, tol_dev);
+  // an inner solve that stops improving (the float32 floor of a
+  // correction problem) returns to the outer loop after 250 evaluations
+  // (10,000 iterations) without a 10% gain; windows of 50 cut off plateaus
+  // that restarted PDHG passes through on its way (measured on PageRank)
+  return setup_state<float>(ctx, pr, ctx->opts.inner_tol, tol_dev, 250);
 }
 
 void read_result(const Scalars &s, double seconds, pdlp_result *res) {

@@ -55,7 +55,7 @@ struct Mat {
 
 // Solver outcome codes (same values as the public PDLP_* status codes).
 enum : int { kRunning = 0, kOptimal = 1, kIterLimit = 2, kKktLimit = 3, kTimeLimit = 4, kNumErr = 5,
-             kWaitTimeout = 6 };
+             kWaitTimeout = 6, kStalled = 9 };  // kStalled: refinement inner solves only
 
 // Every scalar of Algorithm 1 / 2 / 3 and of the evaluation, in one block.
 struct Scalars {
@@ -115,6 +115,9 @@ struct Scalars {
   double mp_eta_k, mp_theta;  // eta_k and theta_k = eta_{k-1} / eta_k of the current iterate
   double mp_eh, mp_th;        // candidate eta_hat and theta_hat of the next trial
   double mp_bf, mp_df, mp_ic; // breaking, downscaling, interpolation
+  // --- stall test of refinement inner solves (stall_evals > 0)
+  double stall_best;          // smallest relative Eq. (15) error at an evaluation so far
+  int stall_count, stall_evals;
 };
 
 // One record per restart evaluation: k, t, mu_cur, mu_avg, mu0, candidate,
@@ -287,7 +290,7 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
 // All sums have a fixed order (deterministic).  `wsm` is the warp's slice of
 // spmv_warp_smem<T>(NV) bytes.
 constexpr int kLaneItems = kChunkNnz / 32;
-constexpr unsigned kSegSteps = 16;  // float64 steps above which a chunk takes the segmented row sums
+constexpr unsigned kSegSteps = kSegStepsHost;  // float64 steps above which a chunk takes the segmented row sums
 
 // Position of a chunk's nonzero e in its staging arrays.  In float64 the
 // 16-byte granules (two entries) of each aligned group of eight are permuted

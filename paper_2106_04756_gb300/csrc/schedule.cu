@@ -74,7 +74,9 @@ double chunk_cost(const Chunk &c, const int32_t *rp) {
     }
     best = std::min(best, ms + lc);
   }
-  return nnz / 32.0 + 2.0 * (best + lg) + 10.0;
+  // float64 chunks above 16 steps take the segmented sum (about 16 steps)
+  const unsigned steps = std::min(best + (unsigned)lg, kSegStepsHost);
+  return nnz / 32.0 + 2.0 * steps + 10.0;
 }
 
 void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, int warps_per_cta,

@@ -39,8 +39,9 @@ void build_schedule(int32_t rows, const int32_t *rp, std::vector<Chunk> &chunks,
 
 // Cost of one chunk in warp steps, the model behind the assignment: gathered
 // entries per lane, twice the row-sum steps of the device's chunk_row_sums
-// (float64 multiply-add plus shared-memory loads), a fixed epilogue, and the
-// combine of a long-row segment.
+// (float64 multiply-add plus shared-memory loads; at most kSegStepsHost, the
+// segmented sum's), a fixed epilogue, and the combine of a long-row segment.
+constexpr unsigned kSegStepsHost = 16;
 double chunk_cost(const Chunk &c, const int32_t *rp);
 
 // Balanced static assignment of chunks to nw warps (grids of nw /

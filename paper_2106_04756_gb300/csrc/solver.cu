@@ -335,6 +335,24 @@ __device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er
     else if (s->attempts >= s->attempt_limit) s->status = kKktLimit;
     else if (time_up(s)) s->status = kTimeLimit;
   }
+  if (s->status == kRunning && s->stall_evals > 0 && s->phase == 1) {
+    // the solve has reached what its arithmetic allows when the better
+    // candidate's relative error has not dropped by 10% for stall_evals
+    // evaluations; it stops and returns that candidate.  (A float32
+    // correction problem can keep its relative gap near 1 while its
+    // residuals are tiny: its objective terms cancel to below float32
+    // resolution; the outer update still gains from such a point.)
+    const double e0 = fmax(s->kkt[0][5], fmax(s->kkt[0][6], s->kkt[0][7]));
+    const double e1 = avg ? fmax(s->kkt[1][5], fmax(s->kkt[1][6], s->kkt[1][7])) : INFINITY;
+    const double err = fmin(e0, e1);
+    if (err < 0.9 * s->stall_best) {
+      s->stall_best = err;
+      s->stall_count = 0;
+    } else if (++s->stall_count >= s->stall_evals) {
+      s->status = kStalled;
+      s->ret_which = e1 < e0 ? 1 : 0;
+    }
+  }
   s->do_gap = (s->status == kRunning && s->phase == 1 && s->adaptive_restart) ? 1 : 0;
   s->restart = 0;
   s->vrestart = 0;
@@ -993,6 +1011,9 @@ __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->mp_theta = 1.0;  // theta_0 (no earlier step)
   s->mp_eh = s->mp_eta_k + s->mp_ic * (sqrt(1.0 + s->mp_theta) - 1.0) * s->mp_eta_k;
   s->mp_th = s->mp_eta_k / s->mp_eh;
+  s->stall_best = INFINITY;
+  s->stall_count = 0;
+  s->stall_evals = in.stall_evals;
 }
 
 // Returned point in the original space: x = D2 x~, y = D1 y~.

@@ -18,6 +18,7 @@ struct ScalarInit {
   int mp;                  // 1: Malitsky-Pock line search (Appendix C.1)
   double mp_breaking, mp_downscaling, mp_interpolation;
   const double *tol_dev;  // non-null: read rel_tol from this device double at each solve
+  int stall_evals;        // > 0: stop (kStalled) after this many evaluations without a 10% gain
 };
 
 template <typename T> cudaError_t set_kernel_attributes();

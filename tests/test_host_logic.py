@@ -110,6 +110,24 @@ def test_chunk_cost_closed_forms(hl):
     rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
     c = np.array([0, 21, 0, int(rp[-1])], np.int32)
     assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == rp[-1] / 32 + 2 * (2 + 7 + 5) + 10
+    # 32 rows, one of 40 and 31 of 1: the long row is split off
+    lens = np.array([40] + [1] * 31)
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    c = np.array([0, 32, 0, int(rp[-1])], np.int32)
+    # L = 1: 40 steps; split at 32: 1 + (2 + 5) = 8 -> 8 is below the cap
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == rp[-1] / 32 + 2 * 8 + 10
+    lens = np.array([30] * 8)  # 8 rows of 30: L = 4 -> 8 steps + 2 shuffle levels
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    c = np.array([0, 8, 0, int(rp[-1])], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == rp[-1] / 32 + 2 * 10 + 10
+    lens = np.array([15] * 16 + [1] * 16)  # 32 rows, one lane each: 15 steps
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    c = np.array([0, 32, 0, int(rp[-1])], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == rp[-1] / 32 + 2 * 15 + 10
+    lens = np.array([17] * 8 + [2] * 24)  # 17 steps at one lane a row: capped at 16
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    c = np.array([0, 32, 0, int(rp[-1])], np.int32)
+    assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == rp[-1] / 32 + 2 * 16 + 10
     # a segment of a long row
     c = np.array([0, -1, 0, 256], np.int32)
     assert hl.hl_chunk_cost(c.ctypes.data, rp.ctypes.data) == 256 / 32 + 2 * 13 + 30
