@@ -46,7 +46,7 @@ METRIC = "time-to-1e-8 rel KKT & PDHG iter/s (HBM GB/s vs peak); FP32+refine vs 
 # dram__bytes_read.sum + dram__bytes_write.sum per step attempt of k_persist<double>
 # from one ncu capture (one launch = 40 attempts; see profiles/); reset to
 # None whenever the kernel changes
-CAPTURED_TRAFFIC = {}
+CAPTURED_TRAFFIC = {"mip_100k": 1.341e6, "pagerank_1m": 3.275e8}
 WORKLOADS = ("mip_100k", "pagerank_1m", "planted_200x500")
 
 
