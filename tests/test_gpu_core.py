@@ -326,3 +326,38 @@ def test_pdlp_takes_fewer_kkt_passes_than_baseline_pdhg(gpu_lib):
     _, _, rp = P.solve(lp, rel_tol=1e-6)
     assert rp["status_name"] == "OPTIMAL"
     assert rp["kkt_passes"] < rb["kkt_passes"], (rp["kkt_passes"], rb["kkt_passes"], rb["status_name"])
+
+
+def _lp_midsize_rows(m=3000, n=6000, seed=74):
+    """Row lengths cycling through empty, short and 17-120 nonzeros, so that
+    float64 chunks take the segmented row sums with empty rows and rows that
+    cross lane boundaries."""
+    rng = np.random.default_rng(seed)
+    cycle = [0, 19, 3, 0, 40, 1, 17, 0, 66, 2, 25, 120, 0, 5, 33]
+    lens = np.array([cycle[i % len(cycle)] for i in range(m)])
+    rows, cols = [], []
+    for i, L in enumerate(lens):
+        if L:
+            cols.append(np.sort(rng.choice(n, L, replace=False)))
+            rows.append(np.full(L, i))
+    A = sp.csr_matrix((rng.standard_normal(int(lens.sum())), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(m, n))
+    A.sort_indices()
+    base = lpgen.planted_uniform(m, n, 0.001, frac_boxed=0.8, seed_key=(seed,))
+    return lpgen._plant(lpgen.rng_for(seed, 2), m, n, A.indptr.astype(np.int32), A.indices.astype(np.int32),
+                        A.data, base.ineq, base.l, base.u, "midsize_rows")
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_segmented_row_sums_match_oracle(gpu_lib, oracle_lib, persistent):
+    """First iterates on rows that exercise the segmented float64 row sums
+    (empty rows, rows across lanes, a full lane of one row), through one
+    restart evaluation and beyond."""
+    lp = _lp_midsize_rows()
+    for iters in (39, 120):
+        x_g, y_g, r_g = P.solve(lp, iter_limit=iters, persistent=persistent)
+        x_o, y_o, r_o = oracle.solve(lp, iter_limit=iters)
+        assert r_g["iters"] == r_o["iters"] == iters and r_g["kkt_passes"] == r_o["kkt_passes"]
+        assert r_g["restarts"] == r_o["restarts"]
+        assert np.abs(x_g - x_o).max() <= TRAJ_TOL[iters] * max(1.0, np.abs(x_o).max())
+        assert np.abs(y_g - y_o).max() <= TRAJ_TOL[iters] * max(1.0, np.abs(y_o).max())
