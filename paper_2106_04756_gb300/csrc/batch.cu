@@ -851,13 +851,13 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           s_step[3] = (!isfinite(num) || isnan(eta_bar) || isnan(s3[2])) ? -1.0 : (eta <= eta_bar ? 1.0 : 0.0);
         }
         __syncthreads();
-        const double eta_next = s_step[2], verdict = s_step[3];
+        const double eta_next = s_step[2], decision = s_step[3];
         __syncthreads();
-        if (verdict < 0.0) {
+        if (decision < 0.0) {
           status = kNumErr;
           break;
         }
-        if (verdict > 0.0) {
+        if (decision > 0.0) {
           accepted = true;
           cur ^= 1;
           sum_eta += eta;
