@@ -268,6 +268,23 @@ __device__ __forceinline__ bool last_block(unsigned int *ticket) {
   return s_last != 0;
 }
 
+// last_block over several launches sharing `ticket`: true in the CTA that
+// arrives last among `total` CTAs (which may belong to kernels running
+// concurrently); that CTA resets the ticket.
+__device__ __forceinline__ bool last_of(unsigned int *ticket, unsigned int total) {
+  __shared__ int s_last_of;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(ticket, 1u);
+    s_last_of = (prev == total - 1u);
+    if (s_last_of) *ticket = 0u;
+  }
+  __syncthreads();
+  if (s_last_of) __threadfence();
+  return s_last_of != 0;
+}
+
 // ------------------------------------------------------- CSR-stream engine
 //
 // spmv_warp computes, for the calling warp's chunk of `A`, the row sums

@@ -265,9 +265,40 @@ __global__ void __launch_bounds__(kThreads) k_mp_test(Mat<T> KT, State<T> S, int
 // Columns: K^T y (current) and K^T ys (sum for the average) in one pass, and
 // the column terms of Eq. (15) for both candidates.
 // Partial layout per CTA (8): [cand][pobj, dres^2, dobj(lambda), |x - x0|^2].
+__device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er)[8], double *trace);
+
+// The column and row kernels of an evaluation may run concurrently; the last
+// of their CTAs sums both sets of partials and the long-row slots in a fixed
+// order and finishes the evaluation.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P, State<T> S) {
+__device__ void eval_finalize(const Mat<T> &K, const Mat<T> &KT, const State<T> &S, double *red) {
+  double ec[8], er[8], lc[8], lr[8];
+  sum_partials<8>(S.part_ec, KT.nblocks, 8, ec, red);
+  __syncthreads();
+  sum_partials<8>(S.part_er, K.nblocks, 8, er, red);
+  __syncthreads();
+  sum_long_rows<8>(KT, lc, red);
+  __syncthreads();
+  sum_long_rows<8>(K, lr, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      ec[a] += lc[a];
+      er[a] += lr[a];
+    }
+    eval_finish(S.s, ec, er, S.trace);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned eval_ctas(const Mat<T> &K, const Mat<T> &KT) {
+  return (unsigned)((KT.nblocks > 0 ? KT.nblocks : 0) + K.nblocks);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
+  __shared__ double red[8 * (kThreads / 32)];
   const Scalars *sc = S.s;
   const int cur = sc->cur;
   const bool avg = sc->sum_eta > 0.0;
@@ -300,6 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> KT, Problem<T> P,
 #pragma unroll
     for (int a = 0; a < 8; ++a) S.part_ec[8 * blockIdx.x + a] = acc[a];
   }
+  if (last_of(S.tickets + kTicketEvalRows, eval_ctas(K, KT))) eval_finalize(K, KT, S, red);
 }
 
 // Finalisation of one evaluation (thread 0 of the last CTA of k_eval_rows).
@@ -439,24 +471,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
 #pragma unroll
     for (int a = 0; a < 8; ++a) S.part_er[8 * blockIdx.x + a] = acc[a];
   }
-  if (last_block(S.tickets + kTicketEvalRows)) {
-    double ec[8], er[8], lc[8], lr[8];
-    sum_partials<8>(S.part_ec, KT.nblocks, 8, ec, red);
-    __syncthreads();
-    sum_partials<8>(S.part_er, gridDim.x, 8, er, red);
-    __syncthreads();
-    sum_long_rows<8>(KT, lc, red);
-    __syncthreads();
-    sum_long_rows<8>(K, lr, red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        ec[a] += lc[a];
-        er[a] += lr[a];
-      }
-      eval_finish(sc, ec, er, S.trace);
-    }
-  }
+  if (last_of(S.tickets + kTicketEvalRows, eval_ctas(K, KT))) eval_finalize(K, KT, S, red);
 }
 
 // --------------------------------------------- normalized gap (Section 3.2)
@@ -1173,8 +1188,22 @@ void launch_init(const Problem<T> &P, const State<T> &S, const Mat<T> &K, const 
 
 template <typename T>
 void launch_eval(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, cudaStream_t st) {
-  if (KT.nblocks > 0) k_eval_cols<T><<<KT.nblocks, kThreads, spmv_smem<T>(2), st>>>(KT, P, S);
+  if (KT.nblocks > 0) k_eval_cols<T><<<KT.nblocks, kThreads, spmv_smem<T>(2), st>>>(K, KT, P, S);
   k_eval_rows<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S);
+}
+
+// The evaluation with its column kernel on a side stream, so that the two
+// kernels run concurrently (their float64 pipes are each about half busy);
+// `st` waits for both.
+template <typename T>
+static void launch_eval_fork(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                             cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
+  cudaEventRecord(ev_fork, st);
+  cudaStreamWaitEvent(side, ev_fork, 0);
+  if (KT.nblocks > 0) k_eval_cols<T><<<KT.nblocks, kThreads, spmv_smem<T>(2), side>>>(K, KT, P, S);
+  k_eval_rows<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S);
+  cudaEventRecord(ev_join, side);
+  cudaStreamWaitEvent(st, ev_join, 0);
 }
 
 template <typename T>
@@ -1229,6 +1258,20 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   cudaError_t e;
   cudaGraph_t graph = nullptr;
   *exec = nullptr;
+  // fork / join of the evaluation's two kernels inside the loop body
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  if ((e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming))) return e;
+  if ((e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming))) {
+    cudaEventDestroy(ev_fork);
+    return e;
+  }
+  struct EventPair {
+    cudaEvent_t a, b;
+    ~EventPair() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } events{ev_fork, ev_join};
   if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal))) return e;
   const int N = P.n + P.m;
   launch_problem_norms<T>(P, S.s, primal_importance, norm_part, 152, st);
@@ -1249,7 +1292,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     // one persistent cooperative kernel per chunk of step attempts
     e = launch_persist<T>(K, KT, P, S, pg, st2);
     if (!e) {
-      launch_eval<T>(K, KT, P, S, st2);
+      launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
       launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
       k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
       k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
@@ -1274,7 +1317,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
       e = cudaStreamEndCapture(st3, &tmp);
     }
     if (!e) {
-      launch_eval<T>(K, KT, P, S, st2);
+      launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
       launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
       k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
       k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
