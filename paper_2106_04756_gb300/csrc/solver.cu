@@ -38,7 +38,7 @@ __device__ __forceinline__ bool time_up(const Scalars *s) {
 
 // Algorithm 2's test and step-size update (step_update), run by one thread
 // after the reductions of an attempt, on the scalars in global memory; the
-// factors come from the table k_finish fills for the current chunk.
+// factors come from the table k_eval_rows fills for the current chunk.
 __device__ void accept_step(Scalars *s, double dx2, double dy2, double inter,
                             cudaGraphConditionalHandle h, int has_cond, double *eta_log) {
   StepCtl c;
@@ -443,6 +443,19 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
   const bool avg = sc->sum_eta > 0.0;
   const double inv = avg ? 1.0 / sc->sum_eta : 0.0;
   const T *y = S.y[cur], *ys = S.ys[cur], *Kx = S.Kx[cur], *y0 = S.y0;
+  if (blockIdx.x == 0) {
+    // Algorithm 2's factors for the next chunk's steps (k does not change
+    // until then), computed here where their float64 pow overlaps the
+    // products instead of in k_finish's serial tail
+    const long long k0 = sc->k;
+    const int ne = sc->eval_every < kMaxEval ? sc->eval_every : kMaxEval;
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+      const double kk = (double)(k0 + i + 1);
+      sc->fac_tab[0][i] = 1.0 - pow(kk + 1.0, -0.3);
+      sc->fac_tab[1][i] = 1.0 + pow(kk + 1.0, -0.6);
+    }
+    if (threadIdx.x == 0) sc->fac_k0 = k0;
+  }
   double acc[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) acc[a] = 0.0;
@@ -860,16 +873,11 @@ __global__ void k_apply_restart(Problem<T> P, State<T> S) {
 __device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
                              int has_inner, int has_cond);
 
-// End of an evaluation: book-keeping of the restart and the loop conditions,
-// and the Algorithm 2 factors of the next chunk.
+// End of an evaluation: book-keeping of the restart and the loop conditions
+// (the Algorithm 2 factors of the next chunk are filled by k_eval_rows).
 __global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
                          int has_inner, int has_cond = 1) {
-  if (threadIdx.x == 0) {
-    finish_state(s, h_outer, h_inner, has_inner, has_cond);
-    s->fac_k0 = s->k;
-  }
-  __syncthreads();
-  fill_step_factors(s);  // for the next chunk's steps
+  if (threadIdx.x == 0) finish_state(s, h_outer, h_inner, has_inner, has_cond);
 }
 
 __device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
