@@ -707,9 +707,11 @@ __device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *s
   (void)sh;
 }
 
+__device__ void decide(Scalars *s, double *trace);
+
 template <typename T>
 __global__ void __launch_bounds__(kGapThreads) k_gap_pass(Problem<T> P, State<T> S, int pass, int s_begin,
-                                                          int s_end, int when_restart) {
+                                                          int s_end, int when_restart, int with_decide) {
   extern __shared__ __align__(16) double hist[];  // [slots][3][kGapBuckets]
   Scalars *sc = S.s;
   if (when_restart ? !sc->restart : !sc->do_gap) return;  // uniform over the grid
@@ -778,13 +780,16 @@ __global__ void __launch_bounds__(kGapThreads) k_gap_pass(Problem<T> P, State<T>
       if (!act[s]) continue;
       gap_select(sc, s, pass, S.ghist + (size_t)s * kGapBuckets * 3, hist);
     }
+    // the restart decision as soon as the candidates' gaps are known
+    if (pass == 2 && with_decide && threadIdx.x == 0) decide(sc, S.trace);
   }
 }
 
 // --------------------------------------------------- restart (Section 3.2)
 
-// GetRestartCandidate, criteria (i)-(iii) and Algorithm 3.  One thread.
-__global__ void k_decide(Scalars *s, double *trace) {
+// GetRestartCandidate, criteria (i)-(iii) and Algorithm 3.  One thread (of
+// the last CTA of the candidates' final gap pass).
+__device__ void decide(Scalars *s, double *trace) {
   if (!s->do_gap) return;
   const double mu_c = s->mu[0];
   const double mu_a = s->sum_eta > 0.0 ? s->mu[1] : INFINITY;
@@ -1090,10 +1095,10 @@ cudaError_t set_kernel_attributes() {
 
 template <typename T>
 static void launch_gap(const Problem<T> &P, const State<T> &S, int s_begin, int s_end, int when_restart,
-                       int grid, cudaStream_t st) {
+                       int grid, cudaStream_t st, int with_decide = 0) {
   const size_t smem = gap_smem(s_end - s_begin);
   for (int pass = 0; pass < 3; ++pass)
-    k_gap_pass<T><<<grid, kGapThreads, smem, st>>>(P, S, pass, s_begin, s_end, when_restart);
+    k_gap_pass<T><<<grid, kGapThreads, smem, st>>>(P, S, pass, s_begin, s_end, when_restart, with_decide);
 }
 
 template <typename T>
@@ -1301,8 +1306,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     e = launch_persist<T>(K, KT, P, S, pg, st2);
     if (!e) {
       launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
-      launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
-      k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
+      launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2, 1);  // with the restart decision
       k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
       launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
       k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_outer, 0);
@@ -1326,8 +1330,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     }
     if (!e) {
       launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
-      launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2);
-      k_decide<<<1, 1, 0, st2>>>(S.s, S.trace);
+      launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2, 1);  // with the restart decision
       k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
       launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
       k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_inner, 1);
@@ -1441,8 +1444,7 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
       if (!go) break;
     }
     launch_eval<T>(K, KT, P, S, st);
-    launch_gap<T>(P, S, 0, 2, 0, gap_grid, st);
-    k_decide<<<1, 1, 0, st>>>(S.s, S.trace);
+    launch_gap<T>(P, S, 0, 2, 0, gap_grid, st, 1);  // with the restart decision
     k_apply_restart<T><<<(N + 255) / 256, 256, 0, st>>>(P, S);
     launch_gap<T>(P, S, 2, 3, 1, gap_grid, st);
     k_finish<<<1, 64, 0, st>>>(S.s, 0, 0, 0, 0);
