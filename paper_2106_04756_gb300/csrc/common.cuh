@@ -65,7 +65,8 @@ struct Scalars {
   double tau, sigma;  // eta / omega and eta * omega of the next attempt (Section 2)
   double inv_omega;   // 1 / omega
   // Algorithm 2 factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 for the steps
-  // k = fac_k0 + i of the current chunk (k counted from 1), filled by k_finish
+  // k = fac_k0 + i of the current chunk (k counted from 1), filled by block 0
+  // of each evaluation's row kernel (k_eval_rows) and by fill_step_factors
   double fac_tab[2][kMaxEval];
   long long fac_k0;
   double sum_eta;   // sum of accepted step sizes of this outer loop

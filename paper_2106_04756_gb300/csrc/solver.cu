@@ -445,8 +445,8 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
   const T *y = S.y[cur], *ys = S.ys[cur], *Kx = S.Kx[cur], *y0 = S.y0;
   if (blockIdx.x == 0) {
     // Algorithm 2's factors for the next chunk's steps (k does not change
-    // until then), computed here where their float64 pow overlaps the
-    // products instead of in k_finish's serial tail
+    // until then), computed here, where their float64 pow overlaps the
+    // products, rather than in the one-CTA k_finish
     const long long k0 = sc->k;
     const int ne = sc->eval_every < kMaxEval ? sc->eval_every : kMaxEval;
     for (int i = threadIdx.x; i < ne; i += blockDim.x) {
