@@ -116,3 +116,21 @@ def test_binding_struct_layout_matches_the_header(tmp_path):
         assert C.sizeof(cls) == want[(sname, "size")], sname
         for fname, _ in cls._fields_:
             assert getattr(cls, fname).offset == want[(sname, fname)], (sname, fname)
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    """Without a CUDA device every compute entry point raises PdlpError
+    (PDLP_ERR_CUDA) instead of returning a result computed some other way."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import lpgen
+    import paper_2106_04756_gb300 as P
+    lp = lpgen.small_planted()
+    calls = [lambda: P.solve(lp), lambda: P.solve(lp, precision=P.PDLP_FP32_REFINE),
+             lambda: P.solve(lp, presolve=1), lambda: P.Context.from_lp(lp, unroll_T=5),
+             lambda: P.solve_batch([lp, lpgen.small_planted()])]
+    for call in calls:
+        with pytest.raises(P.PdlpError) as e:
+            call()
+        assert e.value.code == P.PDLP_ERR_CUDA, e.value
