@@ -28,8 +28,10 @@ def _is_torch(a) -> bool:
     return type(a).__module__.startswith("torch")
 
 
-def _in(a, dtype):
-    """(pointer, keep-alive) for an input array; None passes through."""
+def _in(a, dtype, size=None):
+    """(pointer, keep-alive) for an input array of `size` elements (any size
+    when None); None passes through.  The C ABI takes bare pointers, so a
+    wrong length is caught here, before the library reads past the array."""
     if a is None:
         return None, None
     if _is_torch(a):
@@ -37,9 +39,13 @@ def _in(a, dtype):
         tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
                np.int64: torch.int64}[dtype]
         t = a.to(tdt).contiguous()
-        return t.data_ptr(), t
-    arr = np.ascontiguousarray(a, dtype=dtype)
-    return arr.ctypes.data, arr
+        ptr, keep, count = t.data_ptr(), t, t.numel()
+    else:
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        ptr, keep, count = arr.ctypes.data, arr, arr.size
+    if size is not None and count != size:
+        raise ValueError(f"input array has {count} elements, expected {size}")
+    return ptr, keep
 
 
 def _out(a, size, dtype=np.float64):
@@ -48,8 +54,10 @@ def _out(a, size, dtype=np.float64):
         arr = np.empty(size, dtype=dtype)
         return arr.ctypes.data, arr
     if _is_torch(a):
-        if not a.is_contiguous() or a.numel() != size:
-            raise ValueError("output tensor must be contiguous with the right size")
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if not a.is_contiguous() or a.numel() != size or a.dtype != tdt:
+            raise ValueError("output tensor must be contiguous with the right size and dtype")
         return a.data_ptr(), a
     if not a.flags.c_contiguous or a.size != size or a.dtype != dtype:
         raise ValueError("output array must be contiguous with the right size and dtype")
@@ -78,14 +86,15 @@ class Context:
         opts = options if options is not None else default_options(**kw)
         self.options = opts
         keep = []
-        p_rp, k = _in(row_ptr, np.int32); keep.append(k)
-        p_ci, k = _in(col_idx, np.int32); keep.append(k)
         p_v, k = _in(val, np.float64); keep.append(k)
         self.nnz = int(k.numel() if _is_torch(k) else k.size)
+        p_rp, k = _in(row_ptr, np.int32, self.m + 1); keep.append(k)
+        p_ci, k = _in(col_idx, np.int32, self.nnz); keep.append(k)
         csr = pdlp_csr(self.m, self.n, self.nnz, p_rp, p_ci, p_v)
         ptrs = []
-        for arr, dt in ((c, np.float64), (q, np.float64), (l, np.float64), (u, np.float64), (ineq, np.uint8)):
-            p, k = _in(arr, dt)
+        for arr, dt, size in ((c, np.float64, self.n), (q, np.float64, self.m), (l, np.float64, self.n),
+                              (u, np.float64, self.n), (ineq, np.uint8, self.m)):
+            p, k = _in(arr, dt, size)
             ptrs.append(p)
             keep.append(k)
         h = C.c_void_p()
@@ -118,8 +127,8 @@ class Context:
 
     def pdlp_solve(self, x0=None, y0=None, x_out=None, y_out=None):
         """pdlp_solve: returns (x, y, result dict) in the original space."""
-        p_x0, k0 = _in(x0, np.float64)
-        p_y0, k1 = _in(y0, np.float64)
+        p_x0, k0 = _in(x0, np.float64, self.n)
+        p_y0, k1 = _in(y0, np.float64, self.m)
         px, x = _out(x_out, self.n)
         py, y = _out(y_out, self.m)
         r = pdlp_result()
@@ -130,8 +139,8 @@ class Context:
 
     def pdlp_unroll(self, T: int, ckpt_every: int = 50, x0=None, y0=None, x_out=None, y_out=None):
         """pdlp_unroll: T unrolled steps -> (x_T, y_T, eta[T])."""
-        p_x0, k0 = _in(x0, np.float64)
-        p_y0, k1 = _in(y0, np.float64)
+        p_x0, k0 = _in(x0, np.float64, self.n)
+        p_y0, k1 = _in(y0, np.float64, self.m)
         px, x = _out(x_out, self.n)
         py, y = _out(y_out, self.m)
         pe, eta = _out(None, int(T))
@@ -142,8 +151,8 @@ class Context:
 
     def pdlp_grad(self, dL_dx, dL_dy=None, dc=None, dq=None, dK=None):
         """pdlp_grad: VJP of the last unrolled map -> (dL/dc, dL/dq, dL/dK values)."""
-        p_gx, k0 = _in(dL_dx, np.float64)
-        p_gy, k1 = _in(dL_dy, np.float64)
+        p_gx, k0 = _in(dL_dx, np.float64, self.n)
+        p_gy, k1 = _in(dL_dy, np.float64, self.m)
         pc, oc = _out(dc, self.n)
         pq, oq = _out(dq, self.m)
         pk, ok = _out(dK, self.nnz)
@@ -167,8 +176,8 @@ class Context:
 
     def pdlp_normalized_gap(self, x, y, omega: float, r: float):
         """pdlp_normalized_gap on the scaled problem -> (mu, maximised gap)."""
-        px, k0 = _in(x, np.float64)
-        py, k1 = _in(y, np.float64)
+        px, k0 = _in(x, np.float64, self.n)
+        py, k1 = _in(y, np.float64, self.m)
         mu = C.c_double()
         val = C.c_double()
         check(self._lib.pdlp_normalized_gap(self._h, px, py, float(omega), float(r), C.byref(mu),

@@ -134,3 +134,28 @@ def test_no_cpu_fallback_without_a_gpu(lib):
         with pytest.raises(P.PdlpError) as e:
             call()
         assert e.value.code == P.PDLP_ERR_CUDA, e.value
+
+
+def test_binding_checks_array_lengths_before_the_library_reads_them(lib):
+    """The C ABI takes bare pointers; the binding rejects an input of the
+    wrong length (which the library would read past) and an output of the
+    wrong length or dtype (which it would write past) with ValueError."""
+    import copy
+    import torch
+    import lpgen
+    import paper_2106_04756_gb300 as P
+    base = lpgen.small_planted()
+    for field, cut in (("row_ptr", 1), ("col_idx", 1), ("c", 1), ("q", 1), ("l", 1), ("u", 1), ("ineq", 1)):
+        lp = copy.deepcopy(base)
+        setattr(lp, field, getattr(lp, field)[:-cut])
+        with pytest.raises(ValueError):
+            P.Context.from_lp(lp)
+    lp = copy.deepcopy(base)
+    lp.c = torch.as_tensor(lp.c[:-1])
+    with pytest.raises(ValueError):
+        P.Context.from_lp(lp)
+    with pytest.raises(ValueError):
+        P._out(torch.zeros(base.n, dtype=torch.float32), base.n)
+    with pytest.raises(ValueError):
+        P._out(np.zeros(base.n - 1), base.n)
+    assert P._in(np.zeros(4), np.float64, 4)[1].size == 4
