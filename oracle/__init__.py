@@ -96,6 +96,13 @@ def lib():
             L.or_unroll_vjp.argtypes = [C.POINTER(_Lp), C.c_int32, C.c_int32, C.c_int64, P,
                                         C.c_double, P, P, P, P, P, P, P]
             L.or_correction_lp.argtypes = [C.POINTER(_Lp), P, P, C.c_double, P, P, P, P, P, P, P]
+            L.or_step_sizes.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.or_primal_weight.argtypes = [C.c_double] * 5
+            L.or_primal_weight.restype = C.c_double
+            L.or_restart_check.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int64, C.c_int64,
+                                           C.c_double, C.c_double, C.c_double]
+            L.or_restart_check.restype = C.c_int32
             _lib = L
     return _lib
 
@@ -281,3 +288,26 @@ def correction_lp(lp, xh, yh, dmax=1e12, ylo=None):
     lib().or_correction_lp(C.byref(pin.s), _p(xh), _p(yh), float(dmax), _p(cp), _p(qp), _p(lp_),
                            _p(up), _p(yl), _p(dP), _p(dD))
     return dict(c=cp, q=qp, l=lp_, u=up, ylo=yl, dP=float(dP[0]), dD=float(dD[0]))
+
+
+def step_sizes(omega, dx2, dy2, inter, eta, k):
+    """Algorithm 2's (eta_bar, eta') for an attempt at eta after k accepted steps."""
+    eb, en = C.c_double(), C.c_double()
+    lib().or_step_sizes(float(omega), float(dx2), float(dy2), float(inter), float(eta), int(k),
+                        C.byref(eb), C.byref(en))
+    return eb.value, en.value
+
+
+def primal_weight(omega, Dx, Dy, theta=0.5, eps_zero=1e-10):
+    """Algorithm 3's primal weight update."""
+    return float(lib().or_primal_weight(float(omega), float(Dx), float(Dy), float(theta), float(eps_zero)))
+
+
+RESTART_REASON = {0: None, 1: "sufficient", 2: "necessary", 3: "artificial"}
+
+
+def restart_check(muc, mu0, muc_prev, t, k, beta_suff=0.9, beta_nec=0.1, beta_art=0.5):
+    """Section 3.2 restart criteria -> None or the name of the first that holds."""
+    r = lib().or_restart_check(float(muc), float(mu0), float(muc_prev), int(t), int(k),
+                               float(beta_suff), float(beta_nec), float(beta_art))
+    return RESTART_REASON[int(r)]

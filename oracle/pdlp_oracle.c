@@ -398,6 +398,46 @@ static double init_primal_weight(const scaled_lp *s, double eps_zero) {
 /* ||(dx, dy)||_omega^2 */
 static double wnorm2(double omega, double dx2, double dy2) { return omega * dx2 + dy2 / omega; }
 
+/* Algorithm 2's two step sizes for an attempt at step size eta, with k
+ * accepted steps taken before it:
+ *   eta_bar = ||z' - z||_omega^2 / (2 |(y' - y)^T K (x' - x)|)   (R5; a zero
+ *             denominator gives +inf),
+ *   eta'    = min((1 - (k' + 1)^-0.3) eta_bar, (1 + (k' + 1)^-0.6) eta)
+ * with k' = k + 1 the number of the step being taken (R11). */
+void or_step_sizes(double omega, double dx2, double dy2, double inter, double eta, int64_t k,
+                   double *eta_bar, double *eta_next) {
+  double num = wnorm2(omega, dx2, dy2);
+  double den = 2.0 * fabs(inter);                           /* R5 */
+  double eb = den > 0.0 ? num / den : INFINITY;
+  double kk = (double)(k + 1);                              /* R11 */
+  double e1 = (1.0 - pow(kk + 1.0, -0.3)) * eb;
+  double e2 = (1.0 + pow(kk + 1.0, -0.6)) * eta;
+  *eta_bar = eb;
+  *eta_next = e1 < e2 ? e1 : e2;
+}
+
+/* Algorithm 3 (PrimalWeightUpdate): with Delta_x = ||x^{n,0} - x^{n-1,0}||_2
+ * and Delta_y likewise, omega <- exp(theta log(Delta_y / Delta_x) +
+ * (1 - theta) log(omega)) when both exceed epsilon_zero, else unchanged. */
+double or_primal_weight(double omega, double Dx, double Dy, double theta, double eps_zero) {
+  if (Dx > eps_zero && Dy > eps_zero) return exp(theta * log(Dy / Dx) + (1.0 - theta) * log(omega));
+  return omega;
+}
+
+/* Section 3.2 restart criteria at an evaluation: muc = mu of the restart
+ * candidate, mu0 = mu_n(z^{n,0}, z^{n-1,0}), muc_prev = the candidate's mu at
+ * the previous evaluation of this outer loop (R6), t inner and k total
+ * iterations.  Returns 1 for (i) sufficient decay, 2 for (ii) necessary decay
+ * without local progress, 3 for (iii) artificial restart, 0 for none (the
+ * first that holds, in that order). */
+int32_t or_restart_check(double muc, double mu0, double muc_prev, int64_t t, int64_t k,
+                         double beta_suff, double beta_nec, double beta_art) {
+  if (muc <= beta_suff * mu0) return 1;
+  if (muc <= beta_nec * mu0 && muc > muc_prev) return 2;
+  if ((double)t >= beta_art * (double)k) return 3;
+  return 0;
+}
+
 /* One attempt of Algorithm 2's loop body at step size eta: writes x', y',
  * K x', K^T y' and returns eta_bar and the next eta'. */
 typedef struct { double *x, *y, *Kx, *KTy; } iterate;
@@ -422,14 +462,8 @@ static void pdhg_attempt(const scaled_lp *s, const iterate *z, iterate *zp, doub
     inter += dy * (zp->Kx[i] - z->Kx[i]);
   }
   double num = wnorm2(omega, dx2, dy2);
-  double den = 2.0 * fabs(inter);                           /* R5 */
-  double eb = den > 0.0 ? num / den : INFINITY;
-  double kk = (double)(k + 1);                              /* R11 */
-  double e1 = (1.0 - pow(kk + 1.0, -0.3)) * eb;
-  double e2 = (1.0 + pow(kk + 1.0, -0.6)) * eta;
-  *eta_bar = eb;
-  *eta_next = e1 < e2 ? e1 : e2;
-  *bad = !isfinite(num) || isnan(eb) || isnan(inter);
+  or_step_sizes(omega, dx2, dy2, inter, eta, k, eta_bar, eta_next);
+  *bad = !isfinite(num) || isnan(*eta_bar) || isnan(inter);
 }
 
 /* Appendix C.1, one iteration of the Malitsky-Pock line search from z:
@@ -639,8 +673,7 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
           for (int32_t j = 0; j < n; ++j) dx2 += (z.x[j] - x0r[j]) * (z.x[j] - x0r[j]);
           for (int32_t i = 0; i < m; ++i) dy2 += (z.y[i] - y0r[i]) * (z.y[i] - y0r[i]);
           double Dx = sqrt(dx2), Dy = sqrt(dy2);
-          if (Dx > o->eps_zero && Dy > o->eps_zero)
-            omega = exp(o->pw_theta * log(Dy / Dx) + (1.0 - o->pw_theta) * log(omega));
+          omega = or_primal_weight(omega, Dx, Dy, o->pw_theta, o->eps_zero);
           memcpy(x0r, z.x, sizeof(double) * (size_t)n);
           memcpy(y0r, z.y, sizeof(double) * (size_t)m);
           k_virt = k;
@@ -672,9 +705,7 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       const iterate *cand = to_cur ? &z : &zbar;
       double muc = to_cur ? mu_cur : mu_avg;
       /* restart criteria (i), (ii), (iii) */
-      if (muc <= o->beta_suff * mu0) restart = 1;
-      else if (muc <= o->beta_nec * mu0 && muc > muc_prev) restart = 1;
-      else if ((double)t >= o->beta_art * (double)k) restart = 1;
+      restart = or_restart_check(muc, mu0, muc_prev, t, k, o->beta_suff, o->beta_nec, o->beta_art) != 0;
       if (trace_on())
         fprintf(stderr, "k=%lld t=%lld mu_cur=%.3e mu_avg=%.3e mu0=%.3e muc_prev=%.3e restart=%d omega=%.4g eta=%.4g\n",
                 (long long)k, (long long)t, mu_cur, mu_avg, mu0, muc_prev, restart, omega, eta_hat);
@@ -700,8 +731,7 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       double Dx = sqrt(dx2), Dy = sqrt(dy2);
       if (cand != &z) copy_iterate(&s, &z, cand);
       if (trace_on()) fprintf(stderr, "  restart to %s: Dx=%.4e Dy=%.4e\n", cand == &z ? "current" : "average", Dx, Dy);
-      if (o->pw_update && Dx > o->eps_zero && Dy > o->eps_zero)
-        omega = exp(o->pw_theta * log(Dy / Dx) + (1.0 - o->pw_theta) * log(omega));
+      if (o->pw_update) omega = or_primal_weight(omega, Dx, Dy, o->pw_theta, o->eps_zero);
       if (trace && ntr - 1 < trace_cap) trace[(size_t)(ntr - 1) * 8 + 7] = omega;
       /* mu_0 of the new outer loop: mu_n(z^{n,0}, z^{n-1,0}) under the new omega */
       mu0 = mu_of(&s, &z, x0r, y0r, omega);

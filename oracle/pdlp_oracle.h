@@ -110,6 +110,22 @@ double or_normalized_gap(int32_t n, int32_t m, const double *x, const double *y,
                          const double *u, const double *ylo, double omega, double r,
                          double *value);
 
+/* Algorithm 2's step sizes for one attempt at step size eta after k accepted
+ * steps: *eta_bar = (omega dx2 + dy2 / omega) / (2 |inter|) (+inf for a zero
+ * denominator), *eta_next = min((1 - (k+2)^-0.3) eta_bar, (1 + (k+2)^-0.6) eta)
+ * (the step being taken is number k + 1).  dx2 = ||x'-x||^2, dy2 = ||y'-y||^2,
+ * inter = (y'-y)^T K (x'-x).  The solver accepts the attempt iff eta <= eta_bar. */
+void or_step_sizes(double omega, double dx2, double dy2, double inter, double eta, int64_t k,
+                   double *eta_bar, double *eta_next);
+
+/* Algorithm 3: the new primal weight from Delta_x, Delta_y (2-norm distances
+ * between consecutive restart points) and the smoothing theta. */
+double or_primal_weight(double omega, double Dx, double Dy, double theta, double eps_zero);
+
+/* Section 3.2 restart criteria: 1 (i), 2 (ii), 3 (iii) or 0 (no restart). */
+int32_t or_restart_check(double muc, double mu0, double muc_prev, int64_t t, int64_t k,
+                         double beta_suff, double beta_nec, double beta_art);
+
 /* Algorithm 1 with Algorithm 2 steps, Section 3.2 restarts and Algorithm 3
  * primal weights, after the Section 3.5 preconditioning.  x0, y0 nullable
  * (zero start).  Outputs are in the original space. */
