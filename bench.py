@@ -63,6 +63,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and unroll lines")
     ap.add_argument("--stepped", action="store_true", help="host-stepped kernels instead of one graph per solve")
+    ap.add_argument("--mip-cap-s", type=float, default=20.0,
+                    help="time cap of each time-to-1e-8 solve of the MIP-shaped LP")
     return ap.parse_args()
 
 
@@ -155,6 +157,17 @@ def _alg_bytes(lp, fp):
     return primal, dual
 
 
+def _survey_bytes(m, n, nnz, fp):
+    """Algorithmic bytes of one step attempt by the per-unit figure of the
+    measurement plan: both matrices' values and indices (2 nnz (v + 4)), row
+    starts 4 (m + n), one read of each gathered vector v (m + n), and the
+    vector streams of the two epilogues v (10 n + 9 m), with v the element
+    size of the iteration (8 for float64; 4 for float32, whose iterate and
+    running-sum vectors are float32 here)."""
+    v = 8 if fp == 64 else 4
+    return 2 * nnz * (v + 4) + 4 * (m + n) + v * (m + n) + v * (10 * n + 9 * m)
+
+
 def aggregate_over_ranks(elapsed, iters, device=None):
     """Whole-job figures of N replicas: the slowest rank's timed seconds and
     the iterations of all ranks (torch.distributed, any backend; one process
@@ -244,6 +257,93 @@ def _unroll_line(P, dev, sptr):
         t2 = time.perf_counter()
     return {"workload": "mip_20k_50k (m=20,000, n=50,000, nnz=%d)" % lp.nnz, "T": 500, "ckpt_every": 50,
             "forward_s": t1 - t0, "backward_s": t2 - t1, "backward_over_forward": (t2 - t1) / (t1 - t0)}
+
+
+def _attempt_ms(ctx, reps=30):
+    """Mean CUDA-event time of one step attempt on the context's step engine
+    (the persistent kernel's per-attempt time, or the two launches of the
+    per-launch engines) and the engine's name."""
+    kp, kd, kc = ctx.time_step_kernels(reps)
+    if kc > 0:
+        return kc, "k_persist (persistent warp-chunk kernel)"
+    slab = ctx.last_engine == 2
+    return kp + kd, ("k_primal_slab + k_dual_slab (slab kernels)" if slab else "k_primal + k_dual (warp chunks)")
+
+
+def _pagerank_lines(P, T, dev, sptr, flush, peak, peak_src, reps=3):
+    """On the 1M-node PageRank LP (working set far above L2): the HBM roofline
+    of the step attempt in float64 and float32, and the time to 1e-8 relative
+    KKT error (Eq. (15)) in float64 against float32 + refinement, `reps`
+    times each; the same times on the 100k-node PageRank LP (Table 2's
+    family)."""
+    import lpgen
+    import torch
+    out = {}
+    pr = lpgen.pagerank_1m()
+    pin = [T(pr.row_ptr), T(pr.col_idx), T(pr.val), T(pr.c), T(pr.q), T(pr.l), T(pr.u), T(pr.ineq)]
+    roof = {}
+    for name, prec, fp in (("fp64", P.PDLP_FP64, 64), ("fp32", P.PDLP_FP32, 32)):
+        c = P.Context(*pin, pr.m, pr.n, precision=prec, stream=sptr, iter_limit=400)
+        c.solve()
+        ms, eng = _attempt_ms(c)
+        c.close()
+        b = _survey_bytes(pr.m, pr.n, pr.nnz, fp)
+        ach = b / (ms * 1e-3) / 1e9
+        roof[name] = {"bound": "hbm", "kernel": eng, "achieved": ach, "peak": peak, "unit": "GB/s",
+                      "frac": ach / peak, "peak_source": peak_src + " burst copy (MEASURED_PEAKS.json hbm_gbs)",
+                      "traffic": CAPTURED_TRAFFIC.get(f"pagerank_1m_{name}"),
+                      "algorithmic_bytes_per_attempt": b, "attempt_ms": ms,
+                      "note": _roofline_note(b)}
+    out["roofline_hbm"] = {"workload": "pagerank_1m (n=1,000,000, nnz=7,999,982)", **roof}
+
+    def to_tol(lp, pins, label):
+        res = {"workload": label, "rel_tol": 1e-8, "repeats": reps}
+        for name, prec in (("fp64", P.PDLP_FP64), ("fp32_refine", P.PDLP_FP32_REFINE)):
+            runs = []
+            for _ in range(reps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                c3 = P.Context(*pins, lp.m, lp.n, precision=prec, stream=sptr, time_limit_s=120.0)
+                _, _, r3 = c3.solve()
+                torch.cuda.synchronize(dev)
+                runs.append({"seconds": time.perf_counter() - t0, "status": r3["status_name"],
+                             "iters": r3["iters"], "rel_kkt": r3["rel_kkt"], "refine_rounds": r3["refine_rounds"]})
+                c3.close()
+            secs = [r["seconds"] for r in runs]
+            res[name] = {"median_seconds": float(np.median(secs)), "min_seconds": min(secs),
+                         "max_seconds": max(secs), "iters": [r["iters"] for r in runs],
+                         "status": [r["status"] for r in runs], "rel_kkt": [r["rel_kkt"] for r in runs],
+                         "refine_rounds": [r["refine_rounds"] for r in runs]}
+        return res
+
+    out["time_to_tol"] = to_tol(pr, pin, "pagerank_1m (n=1,000,000, nnz=7,999,982)")
+    del pin
+    p1 = lpgen.pagerank(100_000, seed_key=(2, 1), name="pagerank_100k")
+    pin = [T(p1.row_ptr), T(p1.col_idx), T(p1.val), T(p1.c), T(p1.q), T(p1.l), T(p1.u), T(p1.ineq)]
+    out["time_to_tol_pagerank_100k"] = to_tol(p1, pin, f"pagerank_100k (n=100,000, nnz={p1.nnz})")
+    return out
+
+
+def _mip_time_to_tol(P, inputs, lp, dev, sptr, flush, cap_s):
+    """Time to 1e-8 on the 100k x 250k MIP-shaped LP, float64 against float32
+    + refinement, each stopped at cap_s seconds of solve time: status, accepted
+    iterations and the relative KKT error reached."""
+    import torch
+    res = {"workload": "mip_100k", "rel_tol": 1e-8, "time_cap_s": cap_s}
+    for name, prec in (("fp64", P.PDLP_FP64), ("fp32_refine", P.PDLP_FP32_REFINE)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        c = P.Context(*inputs, lp.m, lp.n, precision=prec, stream=sptr, time_limit_s=cap_s, iter_limit=10 ** 9,
+                      kkt_pass_limit=10 ** 9)
+        _, _, r = c.solve()
+        torch.cuda.synchronize(dev)
+        res[name] = {"seconds": time.perf_counter() - t0, "status": r["status_name"], "iters": r["iters"],
+                     "rel_kkt": r["rel_kkt"], "rel_gap": r["rel_gap"], "rel_pres": r["rel_pres"],
+                     "rel_dres": r["rel_dres"], "refine_rounds": r["refine_rounds"]}
+        c.close()
+    return res
 
 
 def _roofline_note(ws_bytes):
@@ -400,24 +500,17 @@ def main():
     d2h = 8 * (lp.n + lp.m) + 2 * 8 * 16
     e2e = {"value": e2e_iters / e2e_t, "unit": "PDHG iter/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # ---- time to 1e-8 (Eq. (15)) on the PageRank LP: float64 vs float32 + refinement
+    # ---- PageRank: HBM roofline of the step attempt, time to 1e-8 (3 repeats,
+    # float64 vs float32 + refinement, 1M and 100k nodes); the MIP-shaped LP
+    # itself solved under a time cap in both precisions
     tol = None
-    if not args.no_tol and args.workload != "pagerank_1m":
-        import lpgen
-        pr = lpgen.pagerank_1m()
-        pin = [T(pr.row_ptr), T(pr.col_idx), T(pr.val), T(pr.c), T(pr.q), T(pr.l), T(pr.u), T(pr.ineq)]
-        tol = {"workload": "pagerank_1m (n=1,000,000, nnz=7,999,982)", "rel_tol": 1e-8}
-        for name, prec in (("fp64", P.PDLP_FP64), ("fp32_refine", P.PDLP_FP32_REFINE)):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            c3 = P.Context(*pin, pr.m, pr.n, precision=prec, stream=sptr, time_limit_s=120.0)
-            _, _, r3 = c3.solve()
-            torch.cuda.synchronize(dev)
-            tol[name] = {"seconds": time.perf_counter() - t0, "status": r3["status_name"], "iters": r3["iters"],
-                         "rel_kkt": r3["rel_kkt"], "refine_rounds": r3["refine_rounds"]}
-            c3.close()
-        del pin
+    pagerank = {}
+    if not args.no_tol:
+        if args.workload != "pagerank_1m":
+            pagerank = _pagerank_lines(P, T, dev, sptr, flush, peak, peak_src)
+        if args.workload == "mip_100k":
+            pagerank["time_to_tol_mip_100k"] = _mip_time_to_tol(P, inputs, lp, dev, sptr, flush, args.mip_cap_s)
+        tol = pagerank.pop("time_to_tol", None)
 
     # ---- CPU oracle on a bounded sample of the same workload
     cpu = None
@@ -448,7 +541,12 @@ def main():
                       "l2": "flushed between steps (256 MiB write)",
                       "rel_kkt_at_cap": float(np.median([r["rel_kkt"] for r in results]))},
            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-           "gpu_launches": int(launches_per_step * args.steps), "clocks": clk, "time_to_tol": tol, **extra}
+           "gpu_launches": int(launches_per_step * args.steps),
+           "gpu_launches_basis": ("not a profiler count: kernel nodes the solve graph executes per create + solve "
+                                  "(about 120 set-up launches, 13 per evaluation: persistent step kernel, two "
+                                  "evaluation kernels, six gap passes, decision, restart, finish; 8 at the end), "
+                                  "times the evaluations the device counted"),
+           "clocks": clk, "time_to_tol": tol, **pagerank, **extra}
     print(json.dumps(out), flush=True)
 
 

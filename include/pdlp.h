@@ -123,7 +123,15 @@ typedef struct {
                                primal weight is still updated at the evaluations where
                                the artificial criterion would restart (k = 40, 80, 160,
                                ... with the defaults; Appendix C.2 "no restart").     */
-  int32_t pad3_;
+  int32_t wait_limit_us;    /* bound of every device-side wait (the grid-wide barriers of
+                               the persistent step kernel), microseconds; 0 (default):
+                               2 s.  A wait that runs out records the failure, the
+                               kernel returns, and pdlp_solve returns PDLP_ERR_TIMEOUT
+                               with the context still usable.  A negative value -N
+                               bounds the waits at N us AND makes the first barrier of
+                               each persistent launch wait for one arrival more than
+                               the grid has, so that it always runs out: a test of
+                               that path that faults and hangs nothing.              */
   double mp_breaking;       /* step_policy 2: breaking factor, 1.0 (Appendix C.1)      */
   double mp_downscaling;    /* step_policy 2: downscaling factor in (0, 1), 0.5        */
   double mp_interpolation;  /* step_policy 2: interpolation coefficient in [0, 1], 0.4 */
@@ -135,7 +143,8 @@ typedef struct {
   int32_t returned_average;       /* 1 if the returned point is the step-weighted average */
   int64_t iters, kkt_passes, restarts;
   int32_t refine_rounds;          /* outer rounds used by PDLP_FP32_REFINE                 */
-  int32_t pad_;
+  int32_t engine;                 /* step engine that ran the attempts: 0 warp chunks, one launch per
+                                     half-step; 1 persistent warp-chunk kernel; 2 slab kernels  */
   double primal_obj, dual_obj;    /* Eq. (15) at the returned point, original problem     */
   double gap, pres, dres;         /* absolute left-hand sides of Eq. (15a-c)              */
   double rel_gap, rel_pres, rel_dres; /* each divided by its right-hand factor            */
@@ -242,13 +251,13 @@ int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *n, const in
 int pdlp_batch_lanes(int32_t precision, int32_t *lanes_k, int32_t *lanes_kt, int32_t nbuckets);
 
 /* Restart evaluations of the last solve on ctx, oldest first (a ring keeps
- * the last 256).  Each record is 16 float64: k, t, mu(current), mu(average),
+ * the last 2048).  Each record is 16 float64: k, t, mu(current), mu(average),
  * mu_0, candidate (0 current, 1 average), restarted (0/1), primal weight
  * after the evaluation (Section 3.2 and Algorithm 3), the radii
  * ||z - z^{n,0}||_omega of the current and the average iterate, and the
  * relative gap, primal and dual residuals of Eq. (15) of the current, then
  * the average iterate.  out holds 16 * max_records doubles (host or device);
- * *count receives the number of evaluations of the solve (may exceed 256). */
+ * *count receives the number of evaluations of the solve (may exceed 2048). */
 int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *count);
 
 /* Measures the two kernels of one step attempt of Algorithm 2 (the fused

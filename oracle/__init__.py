@@ -210,15 +210,17 @@ def solve(lp, x0=None, y0=None, ylo=None, **opts):
 
 
 def solve_traced(lp, x0=None, y0=None, ylo=None, trace_cap=256, **opts):
-    """solve() plus the restart evaluations: (x, y, result, trace[records, 8]) with
-    columns k, t, mu_cur, mu_avg, mu0, candidate, restarted, omega."""
+    """solve() plus the restart evaluations: (x, y, result, trace[records, 16]) with
+    columns k, t, mu_cur, mu_avg, mu0, candidate, restarted, omega, r_cur, r_avg,
+    then the relative Eq. (15) gap / primal / dual terms of the current and of
+    the average iterate (the layout of the library's pdlp_get_trace)."""
     o = default_opts(**opts)
     pin = _Pinned(lp, ylo)
     x0, y0 = _f64(x0), _f64(y0)
     x = np.zeros(lp.n)
     y = np.zeros(lp.m)
     r = Result()
-    tr = np.zeros((trace_cap, 8))
+    tr = np.zeros((trace_cap, 16))
     cnt = C.c_int32()
     lib().or_solve_traced(C.byref(pin.s), C.byref(o), _p(x0), _p(y0), _p(x), _p(y), C.byref(r), _p(tr),
                           trace_cap, C.byref(cnt))

@@ -522,14 +522,16 @@ static void alloc_iterate(const scaled_lp *s, iterate *z) {
 }
 static void free_iterate(iterate *z) { free(z->x); free(z->y); free(z->Kx); free(z->KTy); }
 
-/* mu_n(z, z_ref): normalized gap at z with radius ||z - z_ref||_omega */
+/* mu_n(z, z_ref): normalized gap at z with radius r = ||z - z_ref||_omega
+ * (*r_out, nullable, receives r) */
 static double mu_of(const scaled_lp *s, const iterate *z, const double *xr, const double *yr,
-                    double omega) {
+                    double omega, double *r_out) {
   int32_t m = s->m, n = s->n;
   double dx2 = 0.0, dy2 = 0.0;
   for (int32_t j = 0; j < n; ++j) dx2 += (z->x[j] - xr[j]) * (z->x[j] - xr[j]);
   for (int32_t i = 0; i < m; ++i) dy2 += (z->y[i] - yr[i]) * (z->y[i] - yr[i]);
   double r = sqrt(wnorm2(omega, dx2, dy2));
+  if (r_out) *r_out = r;
   double *gx = dalloc((size_t)n), *gy = dalloc((size_t)m);
   for (int32_t j = 0; j < n; ++j) gx[j] = z->KTy[j] - s->c[j];
   for (int32_t i = 0; i < m; ++i) gy[i] = s->q[i] - z->Kx[i];
@@ -658,8 +660,9 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       for (int32_t i = 0; i < m; ++i) zbar.y[i] = sy[i] / sum_eta;
       K_mul(&s, zbar.x, zbar.Kx);
       KT_mul(&s, zbar.y, zbar.KTy);
-      if (terminated(lp, &s, &z, o->eps, kkt, xo, yo)) { status = OR_OPTIMAL; ret = &z; break; }
-      if (terminated(lp, &s, &zbar, o->eps, kkt, xo, yo)) {
+      double kc[8], ka[8]; /* Eq. (15) at the current and the average iterate */
+      if (terminated(lp, &s, &z, o->eps, kc, xo, yo)) { status = OR_OPTIMAL; ret = &z; break; }
+      if (terminated(lp, &s, &zbar, o->eps, ka, xo, yo)) {
         status = OR_OPTIMAL; ret = &zbar; ret_avg = 1; break;
       }
       if (k >= o->iter_limit) { status = OR_ITER_LIMIT; break; }
@@ -678,13 +681,15 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
           memcpy(y0r, z.y, sizeof(double) * (size_t)m);
           k_virt = k;
           if (trace && ntr < trace_cap) {
-            double *rec = trace + (size_t)ntr * 8;
+            double *rec = trace + (size_t)ntr * OR_TRACE_LEN;
             rec[0] = (double)k;
             rec[1] = (double)t;
             rec[2] = rec[3] = rec[4] = NAN;
             rec[5] = 0.0;
             rec[6] = 2.0;
             rec[7] = omega;
+            rec[8] = rec[9] = NAN;
+            for (int a = 0; a < 3; ++a) { rec[10 + a] = kc[5 + a]; rec[13 + a] = ka[5 + a]; }
           }
           ntr += 1;
         }
@@ -692,14 +697,11 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       }
 
       /* GetRestartCandidate (Section 3.2) */
-      double mu_cur = mu_of(&s, &z, x0r, y0r, omega);
-      double mu_avg = mu_of(&s, &zbar, x0r, y0r, omega);
-      if (trace_on()) {
-        double kc[8], ka[8];
-        terminated(lp, &s, &z, o->eps, kc, xo, yo);
-        terminated(lp, &s, &zbar, o->eps, ka, xo, yo);
+      double r_cur, r_avg;
+      double mu_cur = mu_of(&s, &z, x0r, y0r, omega, &r_cur);
+      double mu_avg = mu_of(&s, &zbar, x0r, y0r, omega, &r_avg);
+      if (trace_on())
         fprintf(stderr, "  kkt cur %.6e %.6e %.6e avg %.6e %.6e %.6e\n", kc[5], kc[6], kc[7], ka[5], ka[6], ka[7]);
-      }
       /* restart_to_current = 0: always the average (Appendix C.2, theory mode) */
       const int to_cur = o->restart_to_current ? mu_cur < mu_avg : 0;
       const iterate *cand = to_cur ? &z : &zbar;
@@ -711,7 +713,7 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
                 (long long)k, (long long)t, mu_cur, mu_avg, mu0, muc_prev, restart, omega, eta_hat);
       muc_prev = muc;
       if (trace && ntr < trace_cap) {
-        double *rec = trace + (size_t)ntr * 8;
+        double *rec = trace + (size_t)ntr * OR_TRACE_LEN;
         rec[0] = (double)k;
         rec[1] = (double)t;
         rec[2] = mu_cur;
@@ -720,6 +722,9 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
         rec[5] = cand == &z ? 0.0 : 1.0;
         rec[6] = (double)restart;
         rec[7] = omega;
+        rec[8] = r_cur;
+        rec[9] = r_avg;
+        for (int a = 0; a < 3; ++a) { rec[10 + a] = kc[5 + a]; rec[13 + a] = ka[5 + a]; }
       }
       ntr += 1;
       if (!restart) continue;
@@ -732,9 +737,9 @@ void or_solve_traced(const or_lp *lp, const or_opts *o, const double *x0, const 
       if (cand != &z) copy_iterate(&s, &z, cand);
       if (trace_on()) fprintf(stderr, "  restart to %s: Dx=%.4e Dy=%.4e\n", cand == &z ? "current" : "average", Dx, Dy);
       if (o->pw_update) omega = or_primal_weight(omega, Dx, Dy, o->pw_theta, o->eps_zero);
-      if (trace && ntr - 1 < trace_cap) trace[(size_t)(ntr - 1) * 8 + 7] = omega;
+      if (trace && ntr - 1 < trace_cap) trace[(size_t)(ntr - 1) * OR_TRACE_LEN + 7] = omega;
       /* mu_0 of the new outer loop: mu_n(z^{n,0}, z^{n-1,0}) under the new omega */
-      mu0 = mu_of(&s, &z, x0r, y0r, omega);
+      mu0 = mu_of(&s, &z, x0r, y0r, omega, NULL);
       memcpy(x0r, z.x, sizeof(double) * (size_t)n);
       memcpy(y0r, z.y, sizeof(double) * (size_t)m);
       restarts += 1;

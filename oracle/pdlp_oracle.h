@@ -132,11 +132,15 @@ int32_t or_restart_check(double muc, double mu0, double muc_prev, int64_t t, int
 void or_solve(const or_lp *lp, const or_opts *opts, const double *x0, const double *y0,
               double *x_out, double *y_out, or_result *res);
 
-/* or_solve that also records each restart evaluation (up to trace_cap) as 8
- * doubles: k, t, mu_current, mu_average, mu_0, candidate (0 current, 1
- * average), restarted (0/1; 2 = the no-restart mode's primal weight update,
- * with mu_* and mu_0 NaN), primal weight after the evaluation.
+/* or_solve that also records each restart evaluation (up to trace_cap) as
+ * OR_TRACE_LEN doubles: k, t, mu_current, mu_average, mu_0, candidate (0
+ * current, 1 average), restarted (0/1; 2 = the no-restart mode's primal
+ * weight update, with mu_*, mu_0 and the radii NaN), primal weight after the
+ * evaluation, the radii ||z - z^{n,0}||_omega of the current and the average
+ * iterate, then the relative Eq. (15) terms (gap, primal, dual) of the
+ * current and of the average iterate on the original problem.
  * *trace_n receives the number of evaluations. */
+#define OR_TRACE_LEN 16
 void or_solve_traced(const or_lp *lp, const or_opts *opts, const double *x0, const double *y0,
                      double *x_out, double *y_out, or_result *res, double *trace, int32_t trace_cap,
                      int32_t *trace_n);

@@ -133,6 +133,7 @@ class Context:
         py, y = _out(y_out, self.m)
         r = pdlp_result()
         check(self._lib.pdlp_solve(self._h, p_x0, p_y0, px, py, C.byref(r)), self._h)
+        self.last_engine = int(r.engine)
         return x, y, r.asdict()
 
     solve = pdlp_solve
@@ -145,6 +146,7 @@ class Context:
         py, y = _out(y_out, self.m)
         pe, eta = _out(None, int(T))
         check(self._lib.pdlp_unroll(self._h, int(T), int(ckpt_every), p_x0, p_y0, px, py, pe), self._h)
+        self.unroll_generation = getattr(self, "unroll_generation", 0) + 1
         return x, y, eta
 
     unroll = pdlp_unroll
@@ -186,7 +188,7 @@ class Context:
 
     normalized_gap = pdlp_normalized_gap
 
-    def pdlp_get_trace(self, max_records: int = 256):
+    def pdlp_get_trace(self, max_records: int = 2048):
         """Restart evaluations of the last solve: array [records, 16] with columns
         k, t, mu_cur, mu_avg, mu0, candidate, restarted, omega, r_cur, r_avg,
         rel gap / primal / dual of the current, then of the average iterate."""

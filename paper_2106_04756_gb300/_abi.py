@@ -45,20 +45,20 @@ class pdlp_options(C.Structure):
                 ("unroll_T", C.c_int32), ("ckpt_every", C.c_int32), ("use_graph", C.c_int32),
                 ("persistent", C.c_int32), ("step_policy", C.c_int32), ("presolve", C.c_int32),
                 ("omega0", C.c_double),
-                ("restart_to_current", C.c_int32), ("pad3_", C.c_int32), ("mp_breaking", C.c_double),
+                ("restart_to_current", C.c_int32), ("wait_limit_us", C.c_int32), ("mp_breaking", C.c_double),
                 ("mp_downscaling", C.c_double), ("mp_interpolation", C.c_double), ("stream", C.c_void_p)]
 
 
 class pdlp_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("returned_average", C.c_int32), ("iters", C.c_int64),
                 ("kkt_passes", C.c_int64), ("restarts", C.c_int64), ("refine_rounds", C.c_int32),
-                ("pad_", C.c_int32), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
+                ("engine", C.c_int32), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("gap", C.c_double), ("pres", C.c_double), ("dres", C.c_double),
                 ("rel_gap", C.c_double), ("rel_pres", C.c_double), ("rel_dres", C.c_double),
                 ("seconds", C.c_double), ("step_size", C.c_double), ("primal_weight", C.c_double)]
 
     def asdict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ }
         d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
         d["rel_kkt"] = max(self.rel_gap, self.rel_pres, self.rel_dres)
         return d

@@ -12,6 +12,7 @@
 #include "prep.cuh"
 #include "presolve.cuh"
 #include "refine.cuh"
+#include "slab.cuh"
 #include "solver.cuh"
 #include "unroll.cuh"
 
@@ -61,6 +62,9 @@ struct pdlp_ctx {
   int32_t nlongK = 0, nlongKT = 0;
   DevBuf wchunkK, woffK, wchunkKT, woffKT;  // chunk lists of the persistent kernel's warps
   int32_t cmaxK = 0, cmaxKT = 0, assign_nw = 0;
+  // fixed-size slabs of K and K^T (the slab step kernels)
+  DevBuf slabK, slabKT, splitK, splitKT, spartK, spartKT, scntK, scntKT, saccK, saccKT;
+  int32_t nslabK = 0, nslabKT = 0, nsplitK = 0, nsplitKT = 0;
   int32_t nblocksK = 0, nblocksKT = 0;
   std::vector<Chunk> hblocksK, hblocksKT;  // warp-chunk schedules
   // problem data
@@ -146,6 +150,18 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   K.wchunk = reinterpret_cast<const int32_t *>(ctx->wchunkK.ptr());
   K.woff = reinterpret_cast<const int32_t *>(ctx->woffK.ptr());
   K.assign_nw = ctx->assign_nw;
+  {
+    const int32_t *meta = reinterpret_cast<const int32_t *>(ctx->slabK.ptr());
+    K.nslab = ctx->nslabK;
+    K.nsplit = ctx->nsplitK;
+    K.slab_first = meta;
+    K.slab_head = meta + K.nslab + 1;
+    K.slab_tail = meta + 2 * K.nslab + 1;
+    K.splits = reinterpret_cast<const SplitRow *>(ctx->splitK.ptr());
+    K.split_part = reinterpret_cast<double *>(ctx->spartK.ptr());
+    K.split_cnt = reinterpret_cast<unsigned *>(ctx->scntK.ptr());
+    K.split_acc = reinterpret_cast<double *>(ctx->saccK.ptr());
+  }
   KT.rows = ctx->n;
   KT.cols = ctx->m;
   KT.rp = reinterpret_cast<const int32_t *>(ctx->trp.ptr());
@@ -162,7 +178,34 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
   KT.wchunk = reinterpret_cast<const int32_t *>(ctx->wchunkKT.ptr());
   KT.woff = reinterpret_cast<const int32_t *>(ctx->woffKT.ptr());
   KT.assign_nw = ctx->assign_nw;
+  {
+    const int32_t *meta = reinterpret_cast<const int32_t *>(ctx->slabKT.ptr());
+    KT.nslab = ctx->nslabKT;
+    KT.nsplit = ctx->nsplitKT;
+    KT.slab_first = meta;
+    KT.slab_head = meta + KT.nslab + 1;
+    KT.slab_tail = meta + 2 * KT.nslab + 1;
+    KT.splits = reinterpret_cast<const SplitRow *>(ctx->splitKT.ptr());
+    KT.split_part = reinterpret_cast<double *>(ctx->spartKT.ptr());
+    KT.split_cnt = reinterpret_cast<unsigned *>(ctx->scntKT.ptr());
+    KT.split_acc = reinterpret_cast<double *>(ctx->saccKT.ptr());
+  }
   return PDLP_OK;
+}
+
+// The step engine of a context (option `persistent`): 2 = slab kernels;
+// 0 and 3 = warp-chunk kernels (per launch / persistent); 1 = slab kernels
+// when one attempt's matrix streams (indices, values and row starts of K and
+// K^T in the arithmetic type) exceed kSlabAutoBytes, where the working set
+// no longer stays in L2 and the products run at the gather rate, else the
+// persistent warp-chunk kernel.
+constexpr double kSlabAutoBytes = 96e6;
+int use_slab_engine(const pdlp_ctx *ctx, int elem_bytes) {
+  const int p = ctx->opts.persistent;
+  if (p == 2) return 1;
+  if (p != 1) return 0;
+  const double bytes = 2.0 * (double)ctx->nnz * (4.0 + elem_bytes) + 4.0 * ((double)ctx->m + ctx->n + 2);
+  return bytes > kSlabAutoBytes;
 }
 
 // Allocates the iterate state of one precision and captures its solve graph
@@ -188,11 +231,16 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   S.KTy_cur = take(n); S.KTys = take(n);
   S.Kxbar = take(m);
   S.eta_log = nullptr;
-  // the Malitsky-Pock line search runs on the per-launch engine
-  const int persist_mode = ctx->opts.step_policy == 2 ? 0 : ctx->opts.persistent;
+  // step engine: the slab kernels, the persistent warp-chunk kernel or the
+  // per-launch warp-chunk kernels (the Malitsky-Pock line search runs on the
+  // last)
+  const int slab = ctx->opts.step_policy != 2 && use_slab_engine(ctx, (int)sizeof(T));
+  pr.K.slab_on = pr.KT.slab_on = slab;
+  const int persist_mode = (ctx->opts.step_policy == 2 || slab || ctx->opts.persistent == 0) ? 0 : 1;
   CK(persist_plan<T>(ctx->cmaxKT, ctx->cmaxK, ctx->assign_nw, persist_mode, &pr.pg), "persistent kernel layout");
+  const size_t nsp = (size_t)slab_ctas(ctx->nslabKT), nsd = 2 * (size_t)slab_ctas(ctx->nslabK);
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
-                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + 16;
+                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + nsp + nsd + 16;
   double *parts = dalloc<double>(pr.parts, np);
   if (!parts) return fail(ctx, PDLP_ERR_OOM, "partials allocation failed");
   S.part_p = parts;
@@ -200,6 +248,8 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   S.part_ec = S.part_d + 2 * (size_t)ctx->nblocksK;
   S.part_er = S.part_ec + 8 * (size_t)ctx->nblocksKT;
   S.part_cp = S.part_er + 8 * (size_t)ctx->nblocksK;
+  S.part_sp = S.part_cp + 3 * (size_t)pr.pg.grid;
+  S.part_sd = S.part_sp + nsp;
   S.tickets = dalloc<unsigned>(pr.tickets, kNumTickets);
   S.gkeys = dalloc<unsigned>(pr.gkeys, (size_t)kGapSlots * N);
   S.ghist = dalloc<double>(pr.ghist, (size_t)kGapSlots * kGapBuckets * 3);
@@ -230,6 +280,10 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   in.iter_limit = o.iter_limit;
   in.attempt_limit = o.kkt_pass_limit;
   in.time_limit_ns = o.time_limit_s > 0 ? (unsigned long long)(o.time_limit_s * 1e9) : 0ull;
+  in.wait_ns = o.wait_limit_us == 0 ? kBarrierTimeoutNs
+                                    : 1000ull * (unsigned long long)(o.wait_limit_us > 0 ? (long long)o.wait_limit_us
+                                                                                       : -(long long)o.wait_limit_us);
+  in.wait_extra = o.wait_limit_us < 0 ? 1 : 0;
   in.eval_every = o.eval_every;
   in.adaptive_restart = o.adaptive_restart;
   in.pw_update = o.pw_update;
@@ -296,8 +350,10 @@ int ensure_float_matrix(pdlp_ctx *ctx, Precision<float> &pr, Precision<float> *s
     v = reinterpret_cast<const float *>(share->val.ptr());
     tv = reinterpret_cast<const float *>(share->tval.ptr());
   } else {
-    float *a = dalloc<float>(pr.val, ctx->nnz), *b = dalloc<float>(pr.tval, ctx->nnz);
+    float *a = dalloc<float>(pr.val, ctx->nnz + kSlabNnz), *b = dalloc<float>(pr.tval, ctx->nnz + kSlabNnz);
     if (!a || !b) return fail(ctx, PDLP_ERR_OOM, "float matrix allocation failed");
+    CK(cudaMemsetAsync(a + ctx->nnz, 0, sizeof(float) * kSlabNnz, ctx->st), "pad");
+    CK(cudaMemsetAsync(b + ctx->nnz, 0, sizeof(float) * kSlabNnz, ctx->st), "pad");
     CK(to_float(reinterpret_cast<const double *>(ctx->val.ptr()), ctx->nnz, a, ctx->st), "to_float");
     CK(to_float(reinterpret_cast<const double *>(ctx->tval.ptr()), ctx->nnz, b, ctx->st), "to_float");
     v = a;
@@ -374,6 +430,12 @@ void read_result(const Scalars &s, double seconds, pdlp_result *res) {
   res->primal_weight = s.omega;
 }
 
+// Step engine of one precision (pdlp_result.engine).
+template <typename T>
+int engine_of(const Precision<T> &pr) {
+  return pr.K.slab_on ? 2 : (pr.pg.grid > 0 ? 1 : 0);
+}
+
 // Launches one precision's solve graph from the staged start point.
 template <typename T>
 int run_graph(pdlp_ctx *ctx, Precision<T> &pr, Scalars *hs) {
@@ -405,7 +467,7 @@ int check_options(const pdlp_options *o, std::string &why) {
   if (!(o->rel_tol >= 0.0)) { why = "rel_tol must be >= 0"; return 0; }
   if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
   if (o->eval_every < 1 || o->eval_every > kMaxEval) { why = "eval_every must be in [1, 256]"; return 0; }
-  if (o->persistent < 0 || o->persistent > 1) { why = "persistent must be 0 or 1"; return 0; }
+  if (o->persistent < 0 || o->persistent > 3) { why = "persistent must be 0, 1, 2 or 3"; return 0; }
   if (o->step_policy < 0 || o->step_policy > 2) { why = "step_policy must be 0, 1 or 2"; return 0; }
   if (o->restart_to_current < 0 || o->restart_to_current > 1) { why = "restart_to_current must be 0 or 1"; return 0; }
   if (o->step_policy == 2 && o->unroll_T > 0) { why = "step_policy 2 does not combine with unroll_T > 0"; return 0; }
@@ -600,13 +662,17 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
   const int64_t nnz = K->nnz;
   cudaStream_t st = ctx->st;
   // device copies of the input (host or device pointers)
-  int32_t *rp = dalloc<int32_t>(ctx->rp, (size_t)m + 1), *ci = dalloc<int32_t>(ctx->ci, nnz);
-  double *val = dalloc<double>(ctx->val, nnz);
+  // index and value arrays are zero-padded by kSlabNnz entries (the slab kernels
+  // read whole slabs)
+  int32_t *rp = dalloc<int32_t>(ctx->rp, (size_t)m + 1), *ci = dalloc<int32_t>(ctx->ci, nnz + kSlabNnz);
+  double *val = dalloc<double>(ctx->val, nnz + kSlabNnz);
   double *dc = dalloc<double>(ctx->c, n), *dq = dalloc<double>(ctx->q, m), *dl = dalloc<double>(ctx->l, n),
          *du = dalloc<double>(ctx->u, n), *dylo = dalloc<double>(ctx->ylo, m);
   uint8_t *mask = dalloc<uint8_t>(ctx->mask, m);
   if (!rp || !ci || !val || !dc || !dq || !dl || !du || !dylo || !mask)
     return fail(ctx, PDLP_ERR_OOM, "input allocation failed");
+  CK(cudaMemsetAsync(ci + nnz, 0, sizeof(int32_t) * kSlabNnz, st), "pad");
+  CK(cudaMemsetAsync(val + nnz, 0, sizeof(double) * kSlabNnz, st), "pad");
   CK(cudaMemcpyAsync(rp, K->row_ptr, sizeof(int32_t) * ((size_t)m + 1), cudaMemcpyDefault, st), "copy row_ptr");
   if (nnz > 0) {
     CK(cudaMemcpyAsync(ci, K->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDefault, st), "copy col_idx");
@@ -627,10 +693,12 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
   if (herr) return fail(ctx, PDLP_ERR_INVALID_ARG, validate_message(herr));
   CK(ylo_from_mask(m, mask, dylo, st), "ylo");
   // K^T
-  int32_t *trp = dalloc<int32_t>(ctx->trp, (size_t)n + 1), *tci = dalloc<int32_t>(ctx->tci, nnz),
+  int32_t *trp = dalloc<int32_t>(ctx->trp, (size_t)n + 1), *tci = dalloc<int32_t>(ctx->tci, nnz + kSlabNnz),
           *perm = dalloc<int32_t>(ctx->perm, nnz);
-  double *tval = dalloc<double>(ctx->tval, nnz);
+  double *tval = dalloc<double>(ctx->tval, nnz + kSlabNnz);
   if (!trp || !tci || !perm || !tval) return fail(ctx, PDLP_ERR_OOM, "transpose allocation failed");
+  CK(cudaMemsetAsync(tci + nnz, 0, sizeof(int32_t) * kSlabNnz, st), "pad");
+  CK(cudaMemsetAsync(tval + nnz, 0, sizeof(double) * kSlabNnz, st), "pad");
   {
     DevBuf tmp;
     CK(build_transpose(m, n, nnz, rp, ci, trp, tci, perm, tmp, st), "transpose");
@@ -695,6 +763,38 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     if (!lKT.empty()) CK(cudaMemcpy(LKT, lKT.data(), sizeof(LongRow) * lKT.size(), cudaMemcpyHostToDevice), "long rows");
     CK(cudaMemset(cK, 0, sizeof(unsigned) * std::max<size_t>(lK.size(), 1)), "memset");
     CK(cudaMemset(cKT, 0, sizeof(unsigned) * std::max<size_t>(lKT.size(), 1)), "memset");
+    // fixed-size slabs
+    {
+      auto build = [&](int32_t rows, const std::vector<int32_t> &hr, DevBuf &slab, DevBuf &split, DevBuf &spart,
+                       DevBuf &scnt, DevBuf &sacc, int32_t &nslab, int32_t &nsplit) -> int {
+        std::vector<int32_t> first, head, tail;
+        std::vector<SplitRow> sp;
+        int32_t nparts = 0;
+        build_slabs(rows, hr.data(), first, head, tail, sp, nparts);
+        nslab = (int32_t)head.size();
+        nsplit = (int32_t)sp.size();
+        std::vector<int32_t> meta(first);
+        meta.insert(meta.end(), head.begin(), head.end());
+        meta.insert(meta.end(), tail.begin(), tail.end());
+        int32_t *dm = dalloc<int32_t>(slab, meta.size());
+        SplitRow *ds = dalloc<SplitRow>(split, sp.size());
+        double *dp = dalloc<double>(spart, (size_t)nparts);
+        const size_t nsp = std::max<size_t>(sp.size(), 1);
+        unsigned *dc2 = dalloc<unsigned>(scnt, nsp);
+        double *da = dalloc<double>(sacc, kLrAcc * nsp);
+        if (!dm || !ds || !dp || !dc2 || !da) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+        CK(cudaMemcpy(dm, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice), "slabs");
+        if (!sp.empty()) CK(cudaMemcpy(ds, sp.data(), sizeof(SplitRow) * sp.size(), cudaMemcpyHostToDevice), "slabs");
+        CK(cudaMemset(dc2, 0, sizeof(unsigned) * nsp), "memset");
+        CK(cudaMemset(da, 0, sizeof(double) * kLrAcc * nsp), "memset");
+        return PDLP_OK;
+      };
+      int rc2 = build(m, hrp, ctx->slabK, ctx->splitK, ctx->spartK, ctx->scntK, ctx->saccK, ctx->nslabK,
+                      ctx->nsplitK);
+      if (!rc2) rc2 = build(n, htrp, ctx->slabKT, ctx->splitKT, ctx->spartKT, ctx->scntKT, ctx->saccKT,
+                            ctx->nslabKT, ctx->nsplitKT);
+      if (rc2) return rc2;
+    }
     // balanced chunk lists for the persistent kernel's warps
     const int nw = persist_warps();
     if (nw > 0) {
@@ -746,12 +846,14 @@ extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, dou
     xo = ctx->p64.S.xo;
     yo = ctx->p64.S.yo;
     read_result(hs, 0.0, &r);
+    r.engine = engine_of(ctx->p64);
   } else if (prec == PDLP_FP32) {
     if ((rc = setup_fp32(ctx))) return rc;
     if ((rc = run_graph<float>(ctx, ctx->p32, &hs))) return rc;
     xo = ctx->p32.S.xo;
     yo = ctx->p32.S.yo;
     read_result(hs, 0.0, &r);
+    r.engine = engine_of(ctx->p32);
   } else {
     if ((rc = setup_refine(ctx))) return rc;
     RefineOutcome ro;
@@ -771,6 +873,7 @@ extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, dou
     r.kkt_passes = ro.kkt_passes;
     r.restarts = ro.restarts;
     r.refine_rounds = ro.rounds;
+    r.engine = engine_of(ctx->pc32);
     r.primal_obj = ro.kkt[0];
     r.dual_obj = ro.kkt[1];
     r.gap = ro.kkt[2];
@@ -875,12 +978,15 @@ extern "C" int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, i
   const int avail = total < kTraceCap ? total : kTraceCap;
   const int take = max_records < avail ? max_records : avail;
   if (count) *count = total;
-  // oldest record first
-  for (int r = 0; r < take; ++r) {
-    const int idx = (total - avail + r) % kTraceCap;
-    CK(cudaMemcpy(out + (size_t)r * kTraceLen, tr + (size_t)idx * kTraceLen, sizeof(double) * kTraceLen,
+  // oldest record first: the ring from its oldest slot to the end, then from slot 0
+  const int first = (total - avail) % kTraceCap;
+  const int n1 = take < kTraceCap - first ? take : kTraceCap - first;
+  if (n1 > 0)
+    CK(cudaMemcpy(out, tr + (size_t)first * kTraceLen, sizeof(double) * kTraceLen * (size_t)n1,
                   cudaMemcpyDeviceToHost), "trace");
-  }
+  if (take > n1)
+    CK(cudaMemcpy(out + (size_t)n1 * kTraceLen, tr, sizeof(double) * kTraceLen * (size_t)(take - n1),
+                  cudaMemcpyDeviceToHost), "trace");
   return PDLP_OK;
 }
 

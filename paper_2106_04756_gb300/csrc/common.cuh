@@ -32,6 +32,7 @@ constexpr int kGapThreads = 512;
 constexpr int kGapSlots = 3;           // current, average, restart point
 constexpr int kMaxEval = 256;          // largest eval_every (step-factor table size)
 constexpr int kLrAcc = 8;              // epilogue sums kept per long row
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // default bound of a grid-barrier wait
 
 // CSR matrix plus its warp-chunk schedule.
 template <typename T>
@@ -51,6 +52,16 @@ struct Mat {
   // for its assign_nw warps (a cost-balanced static assignment)
   const int32_t *wchunk = nullptr, *woff = nullptr;
   int32_t assign_nw = 0;
+  // fixed-size slabs of kSlabNnz nonzeros (build_slabs; the index and value
+  // arrays are zero-padded to nslab * kSlabNnz entries).  slab_on: the step
+  // attempts of this precision run on the slab kernels.
+  int32_t nslab = 0, nsplit = 0, slab_on = 0;
+  const int32_t *slab_first = nullptr;  // [nslab + 1]
+  const int32_t *slab_head = nullptr, *slab_tail = nullptr;  // [nslab]
+  const SplitRow *splits = nullptr;     // [nsplit]
+  double *split_part = nullptr;         // one partial per (split row, slab)
+  unsigned int *split_cnt = nullptr;    // arrival counter per split row
+  double *split_acc = nullptr;          // epilogue sums of each split row [nsplit][kLrAcc]
 };
 
 // Solver outcome codes (same values as the public PDLP_* status codes).
@@ -119,13 +130,17 @@ struct Scalars {
   // --- stall test of refinement inner solves (stall_evals > 0)
   double stall_best;          // smallest relative Eq. (15) error at an evaluation so far
   int stall_count, stall_evals;
+  // --- bounded device waits
+  unsigned long long wait_ns; // bound of each grid-barrier wait
+  int wait_extra;             // 1: the first barrier of each persistent launch waits for
+                              // one arrival more than the grid has (timeout-path test)
 };
 
 // One record per restart evaluation: k, t, mu_cur, mu_avg, mu0, candidate,
 // restart (0/1), omega after the update, then the radii r_cur, r_avg, and
 // the relative Eq. (15) terms (gap, primal, dual) of the current and the
 // average iterate.
-constexpr int kTraceCap = 256;
+constexpr int kTraceCap = 2048;
 constexpr int kTraceLen = 16;
 
 // An LP in the form of Eq. (1) on the device: preconditioned data (type T,
@@ -148,6 +163,7 @@ struct State {
   T *KTy_cur, *KTys, *Kxbar;   // products at the evaluation
   double *part_p, *part_d;     // per-CTA partials of the primal / dual kernels
   double *part_cp;             // per-CTA partials of the persistent kernel [CTA][3]
+  double *part_sp, *part_sd;   // per-CTA partials of the slab step kernels (primal [CTA], dual [CTA][2])
   double *part_ec, *part_er;   // per-CTA partials of the evaluation kernels
   unsigned int *tickets;       // arrival counters (one per kernel kind)
   Scalars *s;
@@ -226,17 +242,53 @@ __device__ __forceinline__ void block_sum_lean(double (&v)[NV], double *red) {
   }
 }
 
+// Fixed-order sum of np partials p[0], p[stride], ... by one warp, with
+// eight independent loads in flight per lane (a row split into thousands of
+// segments would otherwise leave one warp waiting on a long chain of
+// dependent loads at the end of a phase); the total is valid in lane 0.
+__device__ __forceinline__ double warp_sum_parts(const double *p, int np, int stride = 1) {
+  const int lane = threadIdx.x & 31;
+  double a[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a[u] = 0.0;
+  for (int b = 0; b < np; b += 256) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = b + 32 * u + lane;
+      if (k < np) a[u] += __ldcg(p + (size_t)k * stride);
+    }
+  }
+  double t = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  return t;
+}
+
 // Fixed-order sum of `count` partials (stride `stride`, offset `off`) by one
 // CTA; result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void sum_partials(const double *part, int count, int stride,
                                              double (&out)[NV], double *red) {
+  // four independent accumulators per thread keep four loads in flight
+  double acc[4][NV];
 #pragma unroll
-  for (int a = 0; a < NV; ++a) out[a] = 0.0;
-  for (int b = threadIdx.x; b < count; b += blockDim.x) {
+  for (int u = 0; u < 4; ++u) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) out[a] += __ldcg(part + (size_t)b * stride + a);
+    for (int a = 0; a < NV; ++a) acc[u][a] = 0.0;
   }
+  const int nt = blockDim.x;
+  for (int b0 = threadIdx.x; b0 < count; b0 += 4 * nt) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + u * nt;
+      if (b < count) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) acc[u][a] += __ldcg(part + (size_t)b * stride + a);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) out[a] = (acc[0][a] + acc[1][a]) + (acc[2][a] + acc[3][a]);
   block_sum<NV>(out, red);
 }
 
@@ -628,16 +680,7 @@ __device__ __forceinline__ void spmv_chunk(const Mat<T> &A, int chunk, const T *
   __threadfence();
   double tot[NV];
 #pragma unroll
-  for (int a = 0; a < NV; ++a) tot[a] = 0.0;
-  for (int sg = lane; sg < L.nseg; sg += 32) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) tot[a] += __ldcg(A.seg_part + (size_t)(L.part_off + sg) * NV + a);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) tot[a] += __shfl_down_sync(0xffffffffu, tot[a], o);
-  }
+  for (int a = 0; a < NV; ++a) tot[a] = warp_sum_parts(A.seg_part + (size_t)L.part_off * NV + a, L.nseg, NV);
   if (lane == 0) {
     T t2[NV];
 #pragma unroll
@@ -666,11 +709,11 @@ __device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)
 // Grid-wide barrier of a cooperative launch on a monotonic 64-bit arrival
 // counter: the n-th barrier of a launch whose counter started at `base`
 // completes when the counter reaches base + n * gridDim.x.  The wait is
-// bounded by kBarrierTimeoutNs of %globaltimer: on expiry (or when another
-// CTA has already failed) it records the failure in *err and returns false.
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
-
-__device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned long long target, int *err) {
+// bounded by limit_ns of %globaltimer (kBarrierTimeoutNs unless the options
+// say otherwise): on expiry (or when another CTA has already failed) it
+// records the failure in *err and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned long long target, int *err,
+                                             unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -683,7 +726,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned
       const unsigned long long t0 = global_timer_ns();
       unsigned spins = 0;
       while (*vc < target) {
-        if ((++spins & 63u) == 0u && (*verr || global_timer_ns() - t0 > kBarrierTimeoutNs)) {
+        if ((++spins & 63u) == 0u && (*verr || global_timer_ns() - t0 > limit_ns)) {
           atomicExch(err, 1);
           ok = 0;
           break;

@@ -58,7 +58,9 @@ struct Item {
 
 // Coordinate i of the trust-region problem (Section 3.2): a (coefficient of t^2
 // in phi and of t in the gap while unclipped), w, v (contributions once
-// clipped) and the breakpoint key.  Same definitions as the library's gap.
+// clipped) and the breakpoint key.  Same item set as the library's gap: a
+// coordinate that cannot move, or whose float breakpoint is not positive,
+// gives no item.
 __device__ __forceinline__ Item make_item(const Inputs &in, double om, int i) {
   Item it;
   it.key = 0xffffffffu;
@@ -75,15 +77,19 @@ __device__ __forceinline__ Item make_item(const Inputs &in, double om, int i) {
     if (g == 0.0) return it;
     dist = g > 0.0 ? INFINITY : in.y[r] - in.ylo[r];
   }
-  if (!(dist > 0.0)) dist = 0.0;
+  // a coordinate on its bound in the ascent direction (or an ulp past it)
+  // cannot move: no item, as in the library's gap
+  if (!(dist > 0.0)) return it;
   const double ag = fabs(g);
-  it.a = primal ? g * g / om : om * g * g;
   if (isinf(dist)) {
+    it.a = primal ? g * g / om : om * g * g;
     it.key = 0x7f800000u;
     return it;
   }
   const float tf = primal ? (float)(om * dist) / (float)ag : (float)dist / ((float)om * (float)ag);
-  it.key = __float_as_uint(tf > 0.0f ? tf : 0.0f);
+  if (!(tf > 0.0f)) return it;  // breakpoint below float resolution: no item, as in the library's gap
+  it.a = primal ? g * g / om : om * g * g;
+  it.key = __float_as_uint(tf);
   it.w = primal ? om * dist * dist : dist * dist / om;
   it.v = ag * dist;
   return it;

@@ -200,10 +200,7 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
   last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
   __threadfence();
-  double tot = 0.0;
-  for (int sg = lane; sg < LR.nseg; sg += 32) tot += __ldcg(A.seg_part + LR.part_off + sg);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+  const double tot = warp_sum_parts(A.seg_part + LR.part_off, LR.nseg);
   if (lane == 0) {
     double la[Ph::NA];
 #pragma unroll
@@ -317,7 +314,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
   __shared__ StepCtl ctl;
   __shared__ long long s_fac_k0, s_iter_limit, s_attempt_limit;
   __shared__ int s_eval_every;
-  __shared__ unsigned long long s_base;
+  __shared__ unsigned long long s_base, s_wait_ns;
+  __shared__ int s_wait_extra;
   Scalars *sc = S.s;
   const int wid = threadIdx.x >> 5;
   const int gw = blockIdx.x * kPWarps + wid;
@@ -332,6 +330,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     s_iter_limit = sc->iter_limit;
     s_attempt_limit = sc->attempt_limit;
     s_eval_every = sc->eval_every;
+    s_wait_ns = sc->wait_ns;
+    s_wait_extra = sc->wait_extra;
     // the counter is a multiple of G between launches; CTAs that already
     // arrived at the first barrier add less than G
     const unsigned long long c0 = *reinterpret_cast<volatile unsigned long long *>(bar);
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     PrimalPhase<T> pp{S.x[cur], S.xs[cur], P.cs, P.ls, P.us, S.x[cur ^ 1], S.xs[cur ^ 1],
                       (T)ctl.tau, (T)ctl.eta, {0.0}};
     run_phase<T>(KT, dp, cnt_p, S.y[cur], wsm, pp);
-    target += G;
-    if (!grid_barrier(bar, target, &sc->err)) break;
+    target += G + (att == 0 && s_wait_extra ? 1ull : 0ull);
+    if (!grid_barrier(bar, target, &sc->err, s_wait_ns)) break;
     DualPhase<T> dph{S.y[cur], S.Kx[cur], S.ys[cur], P.qs, P.ylos, S.y[cur ^ 1], S.Kx[cur ^ 1], S.ys[cur ^ 1],
                      (T)ctl.sigma, (T)ctl.eta, {0.0, 0.0}};
     run_phase<T>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       }
     }
     target += G;
-    if (!grid_barrier(bar, target, &sc->err)) break;
+    if (!grid_barrier(bar, target, &sc->err, s_wait_ns)) break;
     {
       // the same fixed-order sum in every CTA, all loads in one round: each
       // thread adds its per-CTA partials, then its rows split into segments

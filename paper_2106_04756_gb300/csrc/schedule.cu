@@ -54,6 +54,43 @@ void build_schedule(int32_t rows, const int32_t *rp, std::vector<Chunk> &chunks,
   }
 }
 
+void build_slabs(int32_t rows, const int32_t *rp, std::vector<int32_t> &first_row, std::vector<int32_t> &head_split,
+                 std::vector<int32_t> &tail_split, std::vector<SplitRow> &splits, int32_t &nparts) {
+  const int64_t nnz = rp[rows];
+  const int32_t nslab = (int32_t)(nnz / kSlabNnz + 1);
+  first_row.assign((size_t)nslab + 1, rows);
+  head_split.assign((size_t)nslab, -1);
+  tail_split.assign((size_t)nslab, -1);
+  splits.clear();
+  nparts = 0;
+  // first_row[s]: first row whose start position is >= kSlabNnz s (rows of
+  // slab s start in [kSlabNnz s, kSlabNnz (s + 1)); the last slab also owns
+  // the empty rows at position nnz)
+  int32_t r = 0;
+  for (int32_t s = 0; s < nslab; ++s) {
+    const int64_t pos = (int64_t)s * kSlabNnz;
+    while (r < rows && rp[r] < pos) ++r;
+    first_row[s] = r;
+  }
+  first_row[nslab] = rows;
+  for (int32_t i = 0; i < rows; ++i) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    if (e <= b) continue;
+    const int32_t sf = (int32_t)(b / kSlabNnz), sl = (int32_t)((e - 1) / kSlabNnz);
+    if (sf == sl) continue;
+    if (sl == sf + 1) {  // extended: the start slab reads the remainder
+      tail_split[sf] = kSlabExtend - i;
+      head_split[sl] = kSlabSkip;
+      continue;
+    }
+    const int32_t id = (int32_t)splits.size();
+    splits.push_back(SplitRow{i, sf, sl, nparts});
+    nparts += sl - sf + 1;
+    tail_split[sf] = id;
+    for (int32_t s = sf + 1; s <= sl; ++s) head_split[s] = id;
+  }
+}
+
 double chunk_cost(const Chunk &c, const int32_t *rp) {
   const int nnz = c.nnz_end - c.nnz_begin;
   if (c.row_end < 0) return nnz / 32.0 + 2.0 * 13.0 + 30.0;

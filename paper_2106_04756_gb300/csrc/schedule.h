@@ -53,6 +53,34 @@ double chunk_cost(const Chunk &c, const int32_t *rp);
 void assign_chunks(const std::vector<Chunk> &chunks, const int32_t *rp, int nw, int warps_per_cta,
                    std::vector<int32_t> &idx, std::vector<int32_t> &off, int &cmax);
 
+// Fixed-size slabs of a CSR matrix (the slab step kernels).  Slab s covers
+// the nonzeros [kSlabNnz s, kSlabNnz (s + 1)) whatever the row boundaries,
+// so every slab carries the same work however long the rows are; the value
+// and index arrays are padded with zeros to nslab * kSlabNnz entries.  A row
+// belongs to the slab that holds its first nonzero (an empty row to the slab
+// holding position rp[r]); rows [first_row[s], first_row[s + 1]) belong to
+// slab s.  A row that crosses one slab boundary and ends in the next slab
+// is extended: the slab holding its start also reads its remaining nonzeros,
+// and the next slab skips them (tail_split[s] = kSlabExtend - row,
+// head_split[s+1] = kSlabSkip).  A row that reaches further is a split row:
+// every slab it touches contributes one partial sum (slot part_off + s -
+// s_first), and the last of them to finish adds the partials in slab order.
+// head_split[s] is the split row that slab s's first nonzero continues (-1:
+// the slab starts with a row start or holds no nonzero; kSlabSkip: an
+// extended row's remainder), tail_split[s] the split row that starts in slab
+// s and continues past its end (-1: none; <= kSlabExtend: the extended row
+// kSlabExtend - tail_split[s]).  nslab = nnz / kSlabNnz + 1.
+constexpr int kSlabNnz = 256;
+constexpr int32_t kSlabSkip = -2;
+constexpr int32_t kSlabExtend = -3;
+
+struct SplitRow {
+  int32_t row, s_first, s_last, part_off;
+};
+
+void build_slabs(int32_t rows, const int32_t *rp, std::vector<int32_t> &first_row, std::vector<int32_t> &head_split,
+                 std::vector<int32_t> &tail_split, std::vector<SplitRow> &splits, int32_t &nparts);
+
 // Scales of the correction problem from the primal / dual violations:
 // dP = 1 / pv and dD = 1 / dv, each clipped to [1, dmax].
 void refine_scales(double pv, double dv, double dmax, double *dP, double *dD);

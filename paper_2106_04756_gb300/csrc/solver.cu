@@ -17,6 +17,7 @@
 #include <stdlib.h>
 
 #include "common.cuh"
+#include "slab.cuh"
 #include "solver.cuh"
 
 namespace pdlp {
@@ -130,6 +131,94 @@ __global__ void __launch_bounds__(kThreads) k_dual(Mat<T> K, Mat<T> KT, Problem<
     sum_long_rows<2>(K, ld, red);
     if (threadIdx.x == 0) accept_step(sc, p[0] + lp[0], d[0] + ld[0], d[1] + ld[1], h, has_cond, S.eta_log);
   }
+}
+
+// Slab step kernels (slab.cuh): the same half-steps and epilogues as
+// k_primal / k_dual over fixed-size slabs, one warp per slab; the dual
+// kernel's last CTA runs the step test on the partials of both launches
+// and the split-row slots, in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kSlabThreads, 5) k_primal_slab(Mat<T> KT, Problem<T> P, State<T> S) {
+  __shared__ unsigned bits[kSlabWarps][8];
+  __shared__ __align__(16) T srow[kSlabWarps][kSlabNnz];
+  __shared__ double red[kSlabThreads];
+  const Scalars *sc = S.s;
+  const int cur = sc->cur, wid = threadIdx.x >> 5;
+  const T tau = (T)sc->tau, et = (T)sc->eta;
+  const T *x = S.x[cur];
+  T *xn = S.x[cur ^ 1];
+  const T *xs = S.xs[cur];
+  T *xsn = S.xs[cur ^ 1];
+  double acc[1] = {0.0};
+  auto epi = [&](int j, T g, double(&a)[1]) {
+    const T xj = x[j];
+    const T xp = clampv<T>(xj - tau * (P.cs[j] - g), P.ls[j], P.us[j]);
+    xn[j] = xp;
+    xsn[j] = xs[j] + et * xp;
+    const T d = xp - xj;
+    a[0] += (double)(d * d);
+  };
+  const int s = blockIdx.x * kSlabWarps + wid;
+  if (s < KT.nslab) slab_warp<T, 1>(KT, s, S.y[cur], bits[wid], srow[wid], acc, epi);
+  block_sum_lean<1>(acc, red);
+  if (threadIdx.x == 0) S.part_sp[blockIdx.x] = acc[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSlabThreads, 5) k_dual_slab(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S,
+                                                            cudaGraphConditionalHandle h, int has_cond) {
+  __shared__ unsigned bits[kSlabWarps][8];
+  __shared__ __align__(16) T srow[kSlabWarps][kSlabNnz];
+  __shared__ double red[2 * kSlabThreads];
+  Scalars *sc = S.s;
+  const int cur = sc->cur, wid = threadIdx.x >> 5;
+  const T sig = (T)sc->sigma, et = (T)sc->eta;
+  const T *y = S.y[cur], *Kx = S.Kx[cur], *ys = S.ys[cur];
+  T *yn = S.y[cur ^ 1], *Kxn = S.Kx[cur ^ 1], *ysn = S.ys[cur ^ 1];
+  double acc[2] = {0.0, 0.0};
+  auto epi = [&](int i, T kxn, double(&a)[2]) {
+    const T kx = Kx[i], yi = y[i], lo = P.ylos[i];
+    const T v = yi + sig * (P.qs[i] - T(2) * kxn + kx);
+    const T yp = v > lo ? v : lo;
+    yn[i] = yp;
+    Kxn[i] = kxn;
+    ysn[i] = ys[i] + et * yp;
+    const T dy = yp - yi, dk = kxn - kx;
+    a[0] += (double)(dy * dy);
+    a[1] += (double)dy * (double)dk;
+  };
+  const int s = blockIdx.x * kSlabWarps + wid;
+  if (s < K.nslab) slab_warp<T, 2>(K, s, S.x[cur ^ 1], bits[wid], srow[wid], acc, epi);
+  block_sum_lean<2>(acc, red);
+  if (threadIdx.x == 0) {
+    S.part_sd[2 * blockIdx.x] = acc[0];
+    S.part_sd[2 * blockIdx.x + 1] = acc[1];
+  }
+  if (last_block(S.tickets + kTicketDual)) {
+    double p[1], d[2], lp[1], ld[2];
+    sum_partials<1>(S.part_sp, slab_ctas(KT.nslab), 1, p, red);
+    __syncthreads();
+    sum_partials<2>(S.part_sd, gridDim.x, 2, d, red);
+    __syncthreads();
+    sum_split_rows<1>(KT, lp, red);
+    __syncthreads();
+    sum_split_rows<2>(K, ld, red);
+    if (threadIdx.x == 0) accept_step(sc, p[0] + lp[0], d[0] + ld[0], d[1] + ld[1], h, has_cond, S.eta_log);
+  }
+}
+
+// One step attempt on the engine the matrices select (slab kernels or the
+// warp-chunk kernels), as graph nodes when has_cond.
+template <typename T>
+void launch_attempt(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
+                    cudaGraphConditionalHandle h, int has_cond, cudaStream_t st) {
+  if (K.slab_on) {
+    k_primal_slab<T><<<slab_ctas(KT.nslab), kSlabThreads, 0, st>>>(KT, P, S);
+    k_dual_slab<T><<<slab_ctas(K.nslab), kSlabThreads, 0, st>>>(K, KT, P, S, h, has_cond);
+    return;
+  }
+  if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem_bytes<T>(1), st>>>(KT, P, S);
+  k_dual<T><<<K.nblocks, kThreads, spmv_smem_bytes<T>(1), st>>>(K, KT, P, S, h, has_cond);
 }
 
 // -------------------------------------- Malitsky-Pock line search (App. C.1)
@@ -1042,6 +1131,8 @@ __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->stall_best = INFINITY;
   s->stall_count = 0;
   s->stall_evals = in.stall_evals;
+  s->wait_ns = in.wait_ns ? in.wait_ns : kBarrierTimeoutNs;
+  s->wait_extra = in.wait_extra;
 }
 
 // Returned point in the original space: x = D2 x~, y = D1 y~.
@@ -1123,8 +1214,7 @@ static void launch_mp_trial(const Mat<T> &K, const Mat<T> &KT, const Problem<T> 
 template <typename T>
 cudaError_t launch_step_pair(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                              cudaStream_t st) {
-  if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
-  k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
+  launch_attempt<T>(K, KT, P, S, 0, 0, st);
   return cudaGetLastError();
 }
 template cudaError_t launch_step_pair<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
@@ -1322,8 +1412,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
       if (in.mp) {
         launch_mp_trial<T>(K, KT, P, S, h_inner, 1, st3);
       } else {
-        if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st3>>>(KT, P, S);
-        k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st3>>>(K, KT, P, S, h_inner, 1);
+        launch_attempt<T>(K, KT, P, S, h_inner, 1, st3);
       }
       cudaGraph_t tmp;
       e = cudaStreamEndCapture(st3, &tmp);
@@ -1362,9 +1451,11 @@ cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   double tp = 0.0, td = 0.0;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, st);
-    if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
+    if (K.slab_on) k_primal_slab<T><<<slab_ctas(KT.nslab), kSlabThreads, 0, st>>>(KT, P, S);
+    else if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
     cudaEventRecord(e1, st);
-    k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
+    if (K.slab_on) k_dual_slab<T><<<slab_ctas(K.nslab), kSlabThreads, 0, st>>>(K, KT, P, S, 0, 0);
+    else k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
     cudaEventRecord(e2, st);
     if ((e = cudaEventSynchronize(e2))) break;
     float a = 0.f, b = 0.f;
@@ -1435,8 +1526,7 @@ cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, 
       } else if (pg.grid > 0) {
         if ((e = launch_persist<T>(K, KT, P, S, pg, st))) return e;
       } else {
-        if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
-        k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
+        launch_attempt<T>(K, KT, P, S, 0, 0, st);
       }
       if ((e = cudaGetLastError()) || (e = read())) return e;
       const bool go = host->status == kRunning && !host->err && host->chunk_acc < host->eval_every &&

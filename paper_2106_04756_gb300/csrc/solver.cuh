@@ -12,6 +12,8 @@ struct ScalarInit {
   double eta0, rel_tol, beta_suff, beta_nec, beta_art, pw_theta, eps_zero;
   long long iter_limit, attempt_limit;
   unsigned long long time_limit_ns;
+  unsigned long long wait_ns;  // bound of device-side waits (grid barriers)
+  int wait_extra;              // 1: the first barrier of a persistent launch cannot complete (timeout test)
   int eval_every, adaptive_restart, pw_update, const_step;
   double omega0;  // > 0: initial primal weight instead of InitializePrimalWeight
   int restart_to_current;  // 0: restart candidate always the average (Appendix C.2)

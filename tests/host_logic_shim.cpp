@@ -45,3 +45,20 @@ extern "C" int hl_assign(int n, const int32_t *chunks4, const int32_t *rp, int n
 extern "C" double hl_round_tol(double rel, double tol, double inner) { return refine_round_tol(rel, tol, inner); }
 
 extern "C" void hl_scales(double pv, double dv, double dmax, double *out) { refine_scales(pv, dv, dmax, out, out + 1); }
+
+extern "C" int hl_build_slabs(int rows, const int32_t *rp, int32_t *first, int32_t *head, int32_t *tail,
+                              int32_t *split4, int cap_split, int32_t *counts /* nslab, nsplit, nparts */) {
+  std::vector<int32_t> f, h, t;
+  std::vector<SplitRow> sp;
+  int32_t nparts = 0;
+  build_slabs(rows, rp, f, h, t, sp, nparts);
+  counts[0] = (int32_t)h.size();
+  counts[1] = (int32_t)sp.size();
+  counts[2] = nparts;
+  if ((int)sp.size() > cap_split) return -1;
+  memcpy(first, f.data(), sizeof(int32_t) * f.size());
+  memcpy(head, h.data(), sizeof(int32_t) * h.size());
+  memcpy(tail, t.data(), sizeof(int32_t) * t.size());
+  memcpy(split4, sp.data(), sizeof(SplitRow) * sp.size());
+  return 0;
+}

@@ -112,13 +112,14 @@ def test_normalized_gap_at_bound_points_matches_oracle(gpu_lib, oracle_lib, name
             assert abs(mu - mu_ref) <= 1e-6 * abs(mu_ref), (trial, mu, mu_ref)
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 @pytest.mark.parametrize("name", ["planted_200x500", "mip_2000x5000", "dense_row"])
 @pytest.mark.parametrize("iters", [20, 39, 120])
 def test_first_iterates_match_oracle(gpu_lib, oracle_lib, name, iters, persistent):
     """Same algorithm, float64: iterates agree up to the rounding growth above
-    for the first steps; step and restart decisions match exactly.  Both step
-    engines: the persistent cooperative kernel and one launch per half-step."""
+    for the first steps; step and restart decisions match exactly.  Every step
+    engine: the persistent cooperative kernel (1), one launch per half-step
+    (0), and the fixed-size slab kernels (2)."""
     lp = CASES[name]()
     x_g, y_g, r_g = P.solve(lp, iter_limit=iters, persistent=persistent)
     x_o, y_o, r_o = oracle.solve(lp, iter_limit=iters)
@@ -244,7 +245,7 @@ def test_restart_trace_matches_oracle(gpu_lib, oracle_lib, name):
         assert a[5] == b[5] and a[6] == b[6], (a, b)
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 @pytest.mark.parametrize("prec", [P.PDLP_FP64, P.PDLP_FP32_REFINE])
 def test_host_stepped_mode_equals_graph(gpu_lib, prec, persistent):
     """use_graph = 0 launches the graph's kernels from a host loop: the same
@@ -281,6 +282,36 @@ def test_persistent_kernel_agrees_with_per_launch_steps(gpu_lib, prec):
     assert ra["status_name"] == rb["status_name"] == "OPTIMAL"
 
 
+@pytest.mark.parametrize("prec,name", [(P.PDLP_FP64, "dense_row"), (P.PDLP_FP64, "mip_2000x5000"),
+                                       (P.PDLP_FP32, "mip_2000x5000")])
+def test_slab_engine_agrees_with_chunk_engine(gpu_lib, prec, name):
+    """The slab kernels run the same half-steps with different summation
+    orders, so over the first steps they take the same step and restart
+    decisions as the per-launch warp-chunk kernels and reach the same point
+    up to rounding, and a solve to tolerance ends OPTIMAL; repeated solves on
+    the slab engine give the same bits.  (In float32 the rounding differences
+    of the 6000-term row of the dense-row LP grow past any useful bound
+    within 100 steps, so float32 is compared on the MIP-shaped LP.)"""
+    lp = CASES[name]()
+    xa, ya, ra = P.solve(lp, precision=prec, persistent=2, iter_limit=100)
+    xb, yb, rb = P.solve(lp, precision=prec, persistent=0, iter_limit=100)
+    assert ra["iters"] == rb["iters"] == 100
+    assert ra["kkt_passes"] == rb["kkt_passes"] and ra["restarts"] == rb["restarts"]
+    # float32: the two engines add each row in a different order, so every
+    # product differs by a few float32 ulps (6e-8 relative) and the difference
+    # grows along the trajectory; after 100 steps on this LP it is about 1e-2
+    # of the largest entry, 1e5 ulps, with every decision still identical
+    tol = 1e-6 if prec == P.PDLP_FP64 else 3e-2
+    assert np.abs(xa - xb).max() <= tol * max(1.0, np.abs(xb).max())
+    assert np.abs(ya - yb).max() <= tol * max(1.0, np.abs(yb).max())
+    xc, yc, rc = P.solve(lp, precision=prec, persistent=2, iter_limit=100)
+    assert np.array_equal(xa, xc) and np.array_equal(ya, yc)
+    lp = lpgen.small_planted()
+    tol = 1e-8 if prec == P.PDLP_FP64 else 1e-4
+    _, _, ra = P.solve(lp, precision=prec, persistent=2, rel_tol=tol)
+    assert ra["status_name"] == "OPTIMAL"
+
+
 def test_step_kernel_timing_reports_the_persistent_attempt(gpu_lib):
     lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
     with P.Context.from_lp(lp, iter_limit=100, persistent=1) as ctx:
@@ -292,7 +323,7 @@ def test_step_kernel_timing_reports_the_persistent_attempt(gpu_lib):
         assert ctx.time_step_kernels(5)[2] == 0.0
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 def test_constant_step_policy_matches_oracle(gpu_lib, oracle_lib, persistent):
     """step_policy 1: eta = 0.9 / ||K~||_2 by power iteration (Section 2's
     baseline step), every attempt accepted, restarts as configured."""
@@ -348,7 +379,7 @@ def _lp_midsize_rows(m=3000, n=6000, seed=74):
                         A.data, base.ineq, base.l, base.u, "midsize_rows")
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 def test_segmented_row_sums_match_oracle(gpu_lib, oracle_lib, persistent):
     """First iterates on rows that exercise the segmented float64 row sums
     (empty rows, rows across lanes, a full lane of one row), through one

@@ -56,7 +56,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_degenerate_inputs_solve_to_1e8(gpu_lib, oracle_lib, name, persistent):
     lp = CASES[name]()

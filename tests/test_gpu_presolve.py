@@ -74,7 +74,7 @@ def test_presolve_fixed_and_empty_solves_original(gpu_lib, oracle_lib, precision
     _check_optimal(lp, x0, y0, r0)
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 def test_presolve_engines_and_start_point(gpu_lib, oracle_lib, persistent):
     lp, _ = _with_fixed(91)
     x, y, r = P.solve(lp, rel_tol=1e-8, iter_limit=200000, presolve=1, persistent=persistent)

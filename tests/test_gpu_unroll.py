@@ -36,7 +36,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_unrolled_map_matches_oracle(gpu_lib, oracle_lib, name, persistent):
     lp = CASES[name]()
@@ -164,6 +164,42 @@ def test_autograd_function_backward_is_pdlp_grad(gpu_lib):
     assert np.array_equal(c.grad.cpu().numpy(), dc)
     assert np.array_equal(q.grad.cpu().numpy(), dq)
     assert np.array_equal(kv.grad.cpu().numpy(), dK)
+
+
+def test_autograd_backward_twice_and_shared_context(gpu_lib):
+    """The autograd node keeps its library context: backward runs twice with
+    retain_graph (the same gradient both times), and with a caller's shared
+    context, a second forward on that context before the first node's
+    backward does not change the first node's gradient (the backward repeats
+    its unroll)."""
+    import torch
+    from paper_2106_04756_gb300.autograd import unrolled_pdhg
+    lp = CASES["mip_2000x5000"]()
+    dev = "cuda"
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.asarray(a)).to(dev, dt)
+    args = lambda c, q, kv: (c, q, kv, t(lp.row_ptr, torch.int32), t(lp.col_idx, torch.int32), t(lp.l), t(lp.u),
+                             t(lp.ineq, torch.uint8))
+    target = t(np.random.default_rng(5).standard_normal(lp.n))
+    c = t(lp.c).requires_grad_()
+    q = t(lp.q).requires_grad_()
+    kv = t(lp.val).requires_grad_()
+    x, _ = unrolled_pdhg(*args(c, q, kv), 60, 20)
+    loss = 0.5 * ((x - target) ** 2).sum()
+    loss.backward(retain_graph=True)
+    g1 = [a.grad.clone() for a in (c, q, kv)]
+    for a in (c, q, kv):
+        a.grad = None
+    loss.backward()
+    for a, b in zip(g1, (c.grad, q.grad, kv.grad)):
+        assert torch.equal(a, b)
+    with P.Context.from_lp(lp) as shared:
+        c2, q2, k2 = [t(a).requires_grad_() for a in (lp.c, lp.q, lp.val)]
+        xa, _ = unrolled_pdhg(*args(c2, q2, k2), 60, 20, context=shared)
+        xb, _ = unrolled_pdhg(*args(t(lp.c), t(lp.q), t(lp.val)), 30, 10, context=shared)  # another unroll
+        (0.5 * ((xa - target) ** 2).sum()).backward()
+        assert torch.equal(xa, x)
+        for a, b in zip(g1, (c2.grad, q2.grad, k2.grad)):
+            assert torch.equal(a, b)
 
 
 def test_float32_forward_float64_adjoint(gpu_lib, oracle_lib):

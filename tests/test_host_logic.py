@@ -1,7 +1,7 @@
 """Host-side planning of the library (csrc/schedule.h), built here with the
 host compiler alone: the warp-chunk schedule, the balanced assignment of
-chunks to the persistent kernel's warps, and the refinement's tolerance and
-scale rules."""
+chunks to the persistent kernel's warps, the fixed-size slabs of the slab
+kernels, and the refinement's tolerance and scale rules."""
 import ctypes as C
 import os
 import shutil
@@ -32,6 +32,7 @@ def hl(tmp_path_factory):
     L.hl_round_tol.argtypes = [C.c_double, C.c_double, C.c_double]
     L.hl_round_tol.restype = C.c_double
     L.hl_scales.argtypes = [C.c_double, C.c_double, C.c_double, P]
+    L.hl_build_slabs.argtypes = [C.c_int, P, P, P, P, P, C.c_int, P]
     return L
 
 
@@ -179,3 +180,61 @@ def test_refinement_scales(hl):
     assert out[0] == 1.0 and out[1] == 2.0
     hl.hl_scales(0.0, 1e-20, 1e12, out.ctypes.data)  # clipped at dmax
     assert out[0] == 1e12 and out[1] == 1e12
+
+
+def _slabs(hl, rp):
+    rp = np.ascontiguousarray(rp, np.int32)
+    rows = rp.size - 1
+    ns = int(rp[-1]) // 256 + 1
+    first = np.zeros(ns + 1, np.int32)
+    head = np.zeros(ns, np.int32)
+    tail = np.zeros(ns, np.int32)
+    cap = rows + 1
+    sp = np.zeros((cap, 4), np.int32)
+    cnt = np.zeros(3, np.int32)
+    assert hl.hl_build_slabs(rows, rp.ctypes.data, first.ctypes.data, head.ctypes.data, tail.ctypes.data,
+                             sp.ctypes.data, cap, cnt.ctypes.data) == 0
+    assert cnt[0] == ns
+    return first, head, tail, sp[:cnt[1]], int(cnt[2])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_slabs_follow_their_definition(hl, seed):
+    """Slab s covers nonzeros [256 s, 256 (s+1)); a row belongs to the slab of
+    its start position; a row crossing one slab boundary and ending in the
+    next slab is extended (tail -3 - row in its slab, head -2 in the next);
+    a row reaching further is a split row with one partial slot per slab it
+    touches; head / tail name the split row a slab continues / starts.  Checked against the definitions written
+    out per row, on power-law rows with empty rows, rows of exactly 256 and
+    rows longer than a slab."""
+    rng = np.random.default_rng(seed)
+    rp = _powerlaw_rp(rng, 3000)
+    if seed == 3:  # nonzero count a multiple of 256, then empty rows
+        lens = np.array([256] * 10 + [0] * 5)
+        rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    first, head, tail, sp, nparts = _slabs(hl, rp)
+    rows = rp.size - 1
+    ns = head.size
+    owner = np.minimum(rp[:-1] // 256, ns - 1)
+    for s in range(ns):
+        assert np.array_equal(np.flatnonzero(owner == s), np.arange(first[s], first[s + 1]))
+    exp_head = -np.ones(ns, np.int64)
+    exp_tail = -np.ones(ns, np.int64)
+    slot = 0
+    k = 0
+    for r in range(rows):
+        b, e = int(rp[r]), int(rp[r + 1])
+        if e <= b or b // 256 == (e - 1) // 256:
+            continue
+        sf, sl = b // 256, (e - 1) // 256
+        if sl == sf + 1:  # ends in the next slab: extended, no split record
+            exp_tail[sf] = -3 - r
+            exp_head[sl] = -2
+            continue
+        assert tuple(sp[k]) == (r, sf, sl, slot)
+        slot += sl - sf + 1
+        exp_tail[sf] = k
+        exp_head[sf + 1:sl + 1] = k
+        k += 1
+    assert k == sp.shape[0] and slot == nparts
+    assert np.array_equal(head, exp_head) and np.array_equal(tail, exp_tail)

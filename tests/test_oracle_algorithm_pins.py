@@ -168,7 +168,7 @@ def test_first_restart_updates_weight_and_mu0(oracle_lib):
     x40, y40, r40 = oracle.solve(lp, iter_limit=40, **kw)
     assert r40["iters"] == 40
     _, _, _, tr = oracle.solve_traced(lp, iter_limit=200, **kw)
-    k, t, mu_cur, mu_avg, mu0, cand, restarted, omega1 = tr[0]
+    k, t, mu_cur, mu_avg, mu0, cand, restarted, omega1 = tr[0][:8]
     assert (k, t, cand, restarted) == (40, 40, 0, 1)      # current candidate, restart
     assert mu0 == math.inf and mu_cur < mu_avg
     omega0 = np.linalg.norm(lp.c) / np.linalg.norm(lp.q)
