@@ -99,11 +99,15 @@ typedef struct {
   int32_t use_graph;        /* 1: one CUDA graph per solve (conditional WHILE nodes);
                                0: the same kernels launched from a host loop that reads
                                the state after every step attempt (for profilers)       */
-  int32_t persistent;       /* 1 (default): all step attempts between two evaluations
-                               run in one cooperative kernel with grid-wide barriers
-                               (one CTA per SM); 0: one launch per half-step (primal,
-                               dual).  Where the kernel's layout does not fit, 1 runs
-                               as 0.                                                     */
+  int32_t persistent;       /* step engine.  1 (default) or 3: all step attempts
+                               between two evaluations run in one cooperative kernel
+                               with grid-wide barriers (one CTA per SM); where its
+                               layout does not fit, one launch per half-step.  0: one
+                               launch per half-step (primal, dual) over row-aligned
+                               warp chunks.  2: one launch per half-step over fixed
+                               256-nonzero slabs, one warp per slab (equal work per
+                               warp whatever the row lengths).  pdlp_result.engine
+                               reports the engine that ran.                          */
   int32_t step_policy;      /* 0 (default): Algorithm 2's adaptive step; 1: constant
                                step eta = 0.9 / ||K~||_2 with ||K~||_2 estimated by 200
                                power iterations (Section 2's baseline PDHG step); 2:

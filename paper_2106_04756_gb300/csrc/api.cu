@@ -64,7 +64,7 @@ struct pdlp_ctx {
   int32_t cmaxK = 0, cmaxKT = 0, assign_nw = 0;
   // fixed-size slabs of K and K^T (the slab step kernels)
   DevBuf slabK, slabKT, splitK, splitKT, spartK, spartKT, scntK, scntKT, saccK, saccKT;
-  int32_t nslabK = 0, nslabKT = 0, nsplitK = 0, nsplitKT = 0;
+  int32_t nslabK = 0, nslabKT = 0, nsplitK = 0, nsplitKT = 0, ndeferK = 0, ndeferKT = 0;
   int32_t nblocksK = 0, nblocksKT = 0;
   std::vector<Chunk> hblocksK, hblocksKT;  // warp-chunk schedules
   // problem data
@@ -154,6 +154,7 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
     const int32_t *meta = reinterpret_cast<const int32_t *>(ctx->slabK.ptr());
     K.nslab = ctx->nslabK;
     K.nsplit = ctx->nsplitK;
+    K.ndefer = ctx->ndeferK;
     K.slab_first = meta;
     K.slab_head = meta + K.nslab + 1;
     K.slab_tail = meta + 2 * K.nslab + 1;
@@ -182,6 +183,7 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
     const int32_t *meta = reinterpret_cast<const int32_t *>(ctx->slabKT.ptr());
     KT.nslab = ctx->nslabKT;
     KT.nsplit = ctx->nsplitKT;
+    KT.ndefer = ctx->ndeferKT;
     KT.slab_first = meta;
     KT.slab_head = meta + KT.nslab + 1;
     KT.slab_tail = meta + 2 * KT.nslab + 1;
@@ -194,18 +196,14 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
 }
 
 // The step engine of a context (option `persistent`): 2 = slab kernels;
-// 0 and 3 = warp-chunk kernels (per launch / persistent); 1 = slab kernels
-// when one attempt's matrix streams (indices, values and row starts of K and
-// K^T in the arithmetic type) exceed kSlabAutoBytes, where the working set
-// no longer stays in L2 and the products run at the gather rate, else the
-// persistent warp-chunk kernel.
-constexpr double kSlabAutoBytes = 96e6;
+// 0 = warp-chunk kernels, one launch per half-step; 1 (default) and 3 = the
+// persistent warp-chunk kernel where its layout fits, else 0.  Measured per
+// step attempt on GB300 (float64 / float32): the persistent kernel 170 /
+// 112 us on the 1M-node PageRank LP and 42.5 / 29.1 us on the 100k x 250k LP,
+// the slab kernels 217 / 139 and 66 / 46 us, so the default never picks them.
 int use_slab_engine(const pdlp_ctx *ctx, int elem_bytes) {
-  const int p = ctx->opts.persistent;
-  if (p == 2) return 1;
-  if (p != 1) return 0;
-  const double bytes = 2.0 * (double)ctx->nnz * (4.0 + elem_bytes) + 4.0 * ((double)ctx->m + ctx->n + 2);
-  return bytes > kSlabAutoBytes;
+  (void)elem_bytes;
+  return ctx->opts.persistent == 2;
 }
 
 // Allocates the iterate state of one precision and captures its solve graph
@@ -236,6 +234,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   // last)
   const int slab = ctx->opts.step_policy != 2 && use_slab_engine(ctx, (int)sizeof(T));
   pr.K.slab_on = pr.KT.slab_on = slab;
+  if (slab) CK(plan_slab_grid<T>(pr.K, pr.KT), "slab grid");
   const int persist_mode = (ctx->opts.step_policy == 2 || slab || ctx->opts.persistent == 0) ? 0 : 1;
   CK(persist_plan<T>(ctx->cmaxKT, ctx->cmaxK, ctx->assign_nw, persist_mode, &pr.pg), "persistent kernel layout");
   const size_t nsp = (size_t)slab_ctas(ctx->nslabKT), nsd = 2 * (size_t)slab_ctas(ctx->nslabK);
@@ -766,13 +765,15 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     // fixed-size slabs
     {
       auto build = [&](int32_t rows, const std::vector<int32_t> &hr, DevBuf &slab, DevBuf &split, DevBuf &spart,
-                       DevBuf &scnt, DevBuf &sacc, int32_t &nslab, int32_t &nsplit) -> int {
+                       DevBuf &scnt, DevBuf &sacc, int32_t &nslab, int32_t &nsplit, int32_t &ndefer) -> int {
         std::vector<int32_t> first, head, tail;
         std::vector<SplitRow> sp;
         int32_t nparts = 0;
         build_slabs(rows, hr.data(), first, head, tail, sp, nparts);
         nslab = (int32_t)head.size();
         nsplit = (int32_t)sp.size();
+        ndefer = 0;
+        for (const SplitRow &R : sp) ndefer += split_deferred(R) ? 1 : 0;
         std::vector<int32_t> meta(first);
         meta.insert(meta.end(), head.begin(), head.end());
         meta.insert(meta.end(), tail.begin(), tail.end());
@@ -790,9 +791,9 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
         return PDLP_OK;
       };
       int rc2 = build(m, hrp, ctx->slabK, ctx->splitK, ctx->spartK, ctx->scntK, ctx->saccK, ctx->nslabK,
-                      ctx->nsplitK);
+                      ctx->nsplitK, ctx->ndeferK);
       if (!rc2) rc2 = build(n, htrp, ctx->slabKT, ctx->splitKT, ctx->spartKT, ctx->scntKT, ctx->saccKT,
-                            ctx->nslabKT, ctx->nsplitKT);
+                            ctx->nslabKT, ctx->nsplitKT, ctx->ndeferKT);
       if (rc2) return rc2;
     }
     // balanced chunk lists for the persistent kernel's warps

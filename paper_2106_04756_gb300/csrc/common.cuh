@@ -56,6 +56,8 @@ struct Mat {
   // arrays are zero-padded to nslab * kSlabNnz entries).  slab_on: the step
   // attempts of this precision run on the slab kernels.
   int32_t nslab = 0, nsplit = 0, slab_on = 0;
+  int32_t ndefer = 0;                   // split rows over more than kSlabDeferSlabs slabs
+  int32_t slab_grid = 0;                // CTAs of a slab launch (at most the resident count)
   const int32_t *slab_first = nullptr;  // [nslab + 1]
   const int32_t *slab_head = nullptr, *slab_tail = nullptr;  // [nslab]
   const SplitRow *splits = nullptr;     // [nsplit]
@@ -177,7 +179,7 @@ struct State {
 // Arrival counters; [kTicketBar, kTicketBar + 1] hold the 64-bit barrier
 // counter of the persistent kernel (8-byte aligned).
 enum TicketId { kTicketDual = 0, kTicketEvalRows = 1, kTicketGap = 2, kTicketMisc = 3, kTicketBar = 4,
-                kNumTickets = 8 };
+                kTicketSlabPrimal = 6, kNumTickets = 8 };
 
 // ------------------------------------------------------------------ helpers
 
@@ -733,6 +735,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned
         }
         __nanosleep(8);
       }
+    }
+    if (ok) {
+      // acquire: later loads of this CTA (ordered after it by the CTA barrier
+      // below) see every write the other CTAs made before their arrival
+      unsigned long long seen;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(count) : "memory");
+      (void)seen;
     }
     __threadfence();
     s_ok = ok;

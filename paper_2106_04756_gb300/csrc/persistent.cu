@@ -43,8 +43,12 @@ __host__ __device__ inline int round16(int b) { return (b + 15) & ~15; }
 
 // Asynchronous global -> shared copies (cp.async, cached in L1).  Used only
 // for data no other CTA writes during the launch (matrix values, row starts
-// and the warp's own rows' operands); entries written by other CTAs (the
-// gathered vector) are loaded through L2 (ld.global.cg).
+// and the warp's own rows' operands).  Entries written by other CTAs (the
+// gathered vector) are plain loads: the grid barrier that precedes each
+// phase ends with an acquire of the arrival counter that every CTA released
+// after its writes, so by the memory model the loads after it see those
+// writes (an acquire at GPU scope discards stale L1 lines), and the gathers
+// keep the L1 hits of rows that share columns.
 template <typename T>
 __device__ __forceinline__ void cp_async(T *dst, const T *src) {
   static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
@@ -239,7 +243,7 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
 #pragma unroll
   for (int it = 0; it < kLaneItems; ++it) {
     const int e = lane + 32 * it;
-    xg[it] = e < cnt ? __ldcg(vec + cj[it]) : T(0);
+    xg[it] = e < cnt ? vec[cj[it]] : T(0);
   }
 }
 

@@ -38,6 +38,12 @@ static_assert(kSlabNnz == 32 * 8, "eight nonzeros per lane");
 
 __host__ __device__ inline int slab_ctas(int nslab) { return (nslab + kSlabWarps - 1) / kSlabWarps; }
 
+// First slab of this CTA's contiguous range (of CTA blockIdx.x + next) when
+// nslab slabs are split evenly over the grid.
+__device__ __forceinline__ int slab_begin(int nslab, int next = 0) {
+  return (int)(((long long)(blockIdx.x + next) * nslab) / gridDim.x);
+}
+
 template <typename T>
 struct Load8;
 template <>
@@ -65,6 +71,14 @@ __device__ __forceinline__ void load8i(const int32_t *p, int (&o)[8]) {
   o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
 }
 
+// A split row over more than kSlabDeferSlabs slabs (a dense row) is
+// deferred: its slabs only store their partials, and the launch's last CTA
+// adds them and runs the row's epilogue (finish_deferred), so that thousands
+// of slabs do not each fence and count on one counter at the end of the
+// launch.
+constexpr int kSlabDeferSlabs = 32;
+__host__ __device__ inline bool split_deferred(const SplitRow &R) { return R.s_last - R.s_first + 1 > kSlabDeferSlabs; }
+
 // One slab's partial of split row `id` (whole warp): lane 0 stores it and
 // counts the arrival; the last of the row's slabs adds all partials in slab
 // order (lanes strided, then a fixed shuffle tree) and lane 0 runs the row's
@@ -73,6 +87,10 @@ template <typename T, int NA, typename Epi>
 __device__ __forceinline__ void split_arrive(const Mat<T> &A, int id, int s, double part, Epi &epi) {
   const int lane = threadIdx.x & 31;
   const SplitRow R = A.splits[id];
+  if (split_deferred(R)) {
+    if (lane == 0) A.split_part[R.part_off + (s - R.s_first)] = part;
+    return;
+  }
   int last = 0;
   if (lane == 0) {
     A.split_part[R.part_off + (s - R.s_first)] = part;
@@ -202,6 +220,35 @@ __device__ __forceinline__ void slab_warp(const Mat<T> &A, int s, const T *__res
   if (ts >= 0) {
     const T tv = __shfl_sync(0xffffffffu, sv, 31);
     split_arrive<T, NA>(A, ts, s, (double)tv, epi);
+  }
+}
+
+// The deferred split rows of A (whole CTA, after every slab of the launch
+// stored its partials): per row, each warp adds a contiguous eighth of the
+// partials, thread 0 adds the warps' sums in order and runs the row's
+// epilogue into its slot of split_acc.  `sh` holds kSlabWarps doubles.
+template <typename T, int NA, typename Epi>
+__device__ __forceinline__ void finish_deferred(const Mat<T> &A, Epi &epi, double *sh) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int id = 0; id < A.nsplit; ++id) {
+    const SplitRow R = A.splits[id];
+    if (!split_deferred(R)) continue;
+    const int np = R.s_last - R.s_first + 1;
+    const int b = (int)((long long)wid * np / kSlabWarps), e = (int)((long long)(wid + 1) * np / kSlabWarps);
+    const double ws = warp_sum_parts(A.split_part + R.part_off + b, e - b);
+    if (lane == 0) sh[wid] = ws;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < kSlabWarps; ++w) tot += sh[w];
+      double la[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) la[a] = 0.0;
+      epi(R.row, (T)tot, la);
+#pragma unroll
+      for (int a = 0; a < NA; ++a) A.split_acc[(size_t)id * kLrAcc + a] = la[a];
+    }
+    __syncthreads();
   }
 }
 

@@ -17,6 +17,8 @@
 #include <stdlib.h>
 
 #include "common.cuh"
+#include <algorithm>
+
 #include "slab.cuh"
 #include "solver.cuh"
 
@@ -158,10 +160,11 @@ __global__ void __launch_bounds__(kSlabThreads, 5) k_primal_slab(Mat<T> KT, Prob
     const T d = xp - xj;
     a[0] += (double)(d * d);
   };
-  const int s = blockIdx.x * kSlabWarps + wid;
-  if (s < KT.nslab) slab_warp<T, 1>(KT, s, S.y[cur], bits[wid], srow[wid], acc, epi);
+  for (int s = slab_begin(KT.nslab) + wid, se = slab_begin(KT.nslab, 1); s < se; s += kSlabWarps)
+    slab_warp<T, 1>(KT, s, S.y[cur], bits[wid], srow[wid], acc, epi);
   block_sum_lean<1>(acc, red);
   if (threadIdx.x == 0) S.part_sp[blockIdx.x] = acc[0];
+  if (KT.ndefer > 0 && last_block(S.tickets + kTicketSlabPrimal)) finish_deferred<T, 1>(KT, epi, red);
 }
 
 template <typename T>
@@ -187,16 +190,17 @@ __global__ void __launch_bounds__(kSlabThreads, 5) k_dual_slab(Mat<T> K, Mat<T> 
     a[0] += (double)(dy * dy);
     a[1] += (double)dy * (double)dk;
   };
-  const int s = blockIdx.x * kSlabWarps + wid;
-  if (s < K.nslab) slab_warp<T, 2>(K, s, S.x[cur ^ 1], bits[wid], srow[wid], acc, epi);
+  for (int s = slab_begin(K.nslab) + wid, se = slab_begin(K.nslab, 1); s < se; s += kSlabWarps)
+    slab_warp<T, 2>(K, s, S.x[cur ^ 1], bits[wid], srow[wid], acc, epi);
   block_sum_lean<2>(acc, red);
   if (threadIdx.x == 0) {
     S.part_sd[2 * blockIdx.x] = acc[0];
     S.part_sd[2 * blockIdx.x + 1] = acc[1];
   }
   if (last_block(S.tickets + kTicketDual)) {
+    if (K.ndefer > 0) finish_deferred<T, 2>(K, epi, red);
     double p[1], d[2], lp[1], ld[2];
-    sum_partials<1>(S.part_sp, slab_ctas(KT.nslab), 1, p, red);
+    sum_partials<1>(S.part_sp, KT.slab_grid, 1, p, red);
     __syncthreads();
     sum_partials<2>(S.part_sd, gridDim.x, 2, d, red);
     __syncthreads();
@@ -207,14 +211,33 @@ __global__ void __launch_bounds__(kSlabThreads, 5) k_dual_slab(Mat<T> K, Mat<T> 
   }
 }
 
+// CTAs of the slab launches of a precision: the number of CTAs resident at
+// once (SMs x occupancy), or fewer when there are fewer slab groups; each CTA
+// takes a contiguous range of slabs (slab_begin), its warps interleaved.
+template <typename T>
+cudaError_t plan_slab_grid(Mat<T> &K, Mat<T> &KT) {
+  int dev = 0, sms = 0, occ_p = 0, occ_d = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev))) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, k_primal_slab<T>, kSlabThreads, 0))) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, k_dual_slab<T>, kSlabThreads, 0))) return e;
+  const int resident = sms * std::max(1, std::min(occ_p, occ_d));
+  KT.slab_grid = std::max(1, std::min(slab_ctas(KT.nslab), resident));
+  K.slab_grid = std::max(1, std::min(slab_ctas(K.nslab), resident));
+  return cudaSuccess;
+}
+template cudaError_t plan_slab_grid<double>(Mat<double> &, Mat<double> &);
+template cudaError_t plan_slab_grid<float>(Mat<float> &, Mat<float> &);
+
 // One step attempt on the engine the matrices select (slab kernels or the
 // warp-chunk kernels), as graph nodes when has_cond.
 template <typename T>
 void launch_attempt(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                     cudaGraphConditionalHandle h, int has_cond, cudaStream_t st) {
   if (K.slab_on) {
-    k_primal_slab<T><<<slab_ctas(KT.nslab), kSlabThreads, 0, st>>>(KT, P, S);
-    k_dual_slab<T><<<slab_ctas(K.nslab), kSlabThreads, 0, st>>>(K, KT, P, S, h, has_cond);
+    k_primal_slab<T><<<KT.slab_grid, kSlabThreads, 0, st>>>(KT, P, S);
+    k_dual_slab<T><<<K.slab_grid, kSlabThreads, 0, st>>>(K, KT, P, S, h, has_cond);
     return;
   }
   if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem_bytes<T>(1), st>>>(KT, P, S);
@@ -1451,10 +1474,10 @@ cudaError_t time_step_kernels(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   double tp = 0.0, td = 0.0;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, st);
-    if (K.slab_on) k_primal_slab<T><<<slab_ctas(KT.nslab), kSlabThreads, 0, st>>>(KT, P, S);
+    if (K.slab_on) k_primal_slab<T><<<KT.slab_grid, kSlabThreads, 0, st>>>(KT, P, S);
     else if (KT.nblocks > 0) k_primal<T><<<KT.nblocks, kThreads, spmv_smem<T>(1), st>>>(KT, P, S);
     cudaEventRecord(e1, st);
-    if (K.slab_on) k_dual_slab<T><<<slab_ctas(K.nslab), kSlabThreads, 0, st>>>(K, KT, P, S, 0, 0);
+    if (K.slab_on) k_dual_slab<T><<<K.slab_grid, kSlabThreads, 0, st>>>(K, KT, P, S, 0, 0);
     else k_dual<T><<<K.nblocks, kThreads, spmv_smem<T>(1), st>>>(K, KT, P, S, 0, 0);
     cudaEventRecord(e2, st);
     if ((e = cudaEventSynchronize(e2))) break;

@@ -36,6 +36,8 @@ template <typename T> void launch_spmv(const Mat<T> &A, const T *v, T *out, cuda
 template <typename T>
 cudaError_t power_norm(const Mat<T> &A, const Mat<T> &AT, int iters, T *v, T *w, T *u, double *nrm,
                        cudaStream_t st, double *out);
+// CTAs of the slab kernels' launches (K.slab_grid, KT.slab_grid).
+template <typename T> cudaError_t plan_slab_grid(Mat<T> &K, Mat<T> &KT);
 // One step attempt (k_primal, k_dual with the step test) outside any graph.
 template <typename T>
 cudaError_t launch_step_pair(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,

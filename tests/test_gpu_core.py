@@ -293,18 +293,20 @@ def test_slab_engine_agrees_with_chunk_engine(gpu_lib, prec, name):
     of the 6000-term row of the dense-row LP grow past any useful bound
     within 100 steps, so float32 is compared on the MIP-shaped LP.)"""
     lp = CASES[name]()
-    xa, ya, ra = P.solve(lp, precision=prec, persistent=2, iter_limit=100)
-    xb, yb, rb = P.solve(lp, precision=prec, persistent=0, iter_limit=100)
-    assert ra["iters"] == rb["iters"] == 100
-    assert ra["kkt_passes"] == rb["kkt_passes"] and ra["restarts"] == rb["restarts"]
     # float32: the two engines add each row in a different order, so every
     # product differs by a few float32 ulps (6e-8 relative) and the difference
-    # grows along the trajectory; after 100 steps on this LP it is about 1e-2
-    # of the largest entry, 1e5 ulps, with every decision still identical
-    tol = 1e-6 if prec == P.PDLP_FP64 else 3e-2
+    # grows along this LP's trajectory by about 10x per 10 steps (1e-2 of the
+    # largest entry after 100 steps, every decision still identical); the
+    # float32 engines are compared over the first 20 steps
+    iters = 100 if prec == P.PDLP_FP64 else 20
+    xa, ya, ra = P.solve(lp, precision=prec, persistent=2, iter_limit=iters)
+    xb, yb, rb = P.solve(lp, precision=prec, persistent=0, iter_limit=iters)
+    assert ra["iters"] == rb["iters"] == iters
+    assert ra["kkt_passes"] == rb["kkt_passes"] and ra["restarts"] == rb["restarts"]
+    tol = 1e-6 if prec == P.PDLP_FP64 else 1e-4
     assert np.abs(xa - xb).max() <= tol * max(1.0, np.abs(xb).max())
     assert np.abs(ya - yb).max() <= tol * max(1.0, np.abs(yb).max())
-    xc, yc, rc = P.solve(lp, precision=prec, persistent=2, iter_limit=100)
+    xc, yc, rc = P.solve(lp, precision=prec, persistent=2, iter_limit=iters)
     assert np.array_equal(xa, xc) and np.array_equal(ya, yc)
     lp = lpgen.small_planted()
     tol = 1e-8 if prec == P.PDLP_FP64 else 1e-4
