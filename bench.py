@@ -43,10 +43,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "time-to-1e-8 rel KKT & PDHG iter/s (HBM GB/s vs peak); FP32+refine vs FP64"
-# dram__bytes_read.sum + dram__bytes_write.sum per step attempt of k_persist<double>
-# from one ncu capture (one launch = 40 attempts; see profiles/); reset to
-# None whenever the kernel changes
-CAPTURED_TRAFFIC = {"mip_100k": 1.341e6, "pagerank_1m": 3.275e8}
+# dram__bytes_read.sum + dram__bytes_write.sum per step attempt of the
+# persistent step kernel from one ncu capture each (one launch = one chunk of
+# about 40 attempts; see profiles/); drop an entry whenever the kernel changes
+CAPTURED_TRAFFIC = {"mip_100k": 1.337e6, "pagerank_1m_fp64": 3.275e8, "pagerank_1m_fp32": 1.939e8}
 L2_BYTES = 129e6  # GB300 L2 capacity
 WORKLOADS = ("mip_100k", "pagerank_1m", "planted_200x500")
 
@@ -326,23 +326,30 @@ def _pagerank_lines(P, T, dev, sptr, flush, peak, peak_src, reps=3):
 
 
 def _mip_time_to_tol(P, inputs, lp, dev, sptr, flush, cap_s):
-    """Time to 1e-8 on the 100k x 250k MIP-shaped LP, float64 against float32
-    + refinement, each stopped at cap_s seconds of solve time: status, accepted
-    iterations and the relative KKT error reached."""
+    """Time to 1e-8 on the 100k x 250k MIP-shaped LP, float32 + refinement
+    against float64: each run stops at OPTIMAL, at a limit of the method, or
+    at cap_s seconds of solve time; float64 is also run for exactly the wall
+    time the refinement took, so both precisions are compared at equal time
+    (status, accepted iterations, relative KKT error and its three terms)."""
     import torch
-    res = {"workload": "mip_100k", "rel_tol": 1e-8, "time_cap_s": cap_s}
-    for name, prec in (("fp64", P.PDLP_FP64), ("fp32_refine", P.PDLP_FP32_REFINE)):
+
+    def run(prec, cap):
         flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        c = P.Context(*inputs, lp.m, lp.n, precision=prec, stream=sptr, time_limit_s=cap_s, iter_limit=10 ** 9,
+        c = P.Context(*inputs, lp.m, lp.n, precision=prec, stream=sptr, time_limit_s=cap, iter_limit=10 ** 9,
                       kkt_pass_limit=10 ** 9)
         _, _, r = c.solve()
         torch.cuda.synchronize(dev)
-        res[name] = {"seconds": time.perf_counter() - t0, "status": r["status_name"], "iters": r["iters"],
-                     "rel_kkt": r["rel_kkt"], "rel_gap": r["rel_gap"], "rel_pres": r["rel_pres"],
-                     "rel_dres": r["rel_dres"], "refine_rounds": r["refine_rounds"]}
         c.close()
+        return {"seconds": time.perf_counter() - t0, "status": r["status_name"], "iters": r["iters"],
+                "rel_kkt": r["rel_kkt"], "rel_gap": r["rel_gap"], "rel_pres": r["rel_pres"],
+                "rel_dres": r["rel_dres"], "refine_rounds": r["refine_rounds"]}
+
+    res = {"workload": "mip_100k", "rel_tol": 1e-8, "time_cap_s": cap_s}
+    res["fp32_refine"] = run(P.PDLP_FP32_REFINE, cap_s)
+    res["fp64_same_time"] = run(P.PDLP_FP64, res["fp32_refine"]["seconds"])
+    res["fp64"] = run(P.PDLP_FP64, cap_s)
     return res
 
 

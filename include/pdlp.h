@@ -99,10 +99,13 @@ typedef struct {
   int32_t use_graph;        /* 1: one CUDA graph per solve (conditional WHILE nodes);
                                0: the same kernels launched from a host loop that reads
                                the state after every step attempt (for profilers)       */
-  int32_t persistent;       /* step engine.  1 (default) or 3: all step attempts
+  int32_t persistent;       /* step engine.  1 (default), 3, 4: all step attempts
                                between two evaluations run in one cooperative kernel
                                with grid-wide barriers (one CTA per SM); where its
-                               layout does not fit, one launch per half-step.  0: one
+                               layout does not fit, one launch per half-step.  Its
+                               gathers go through L1 (after acquiring barriers) when
+                               the working set of an attempt exceeds L2, else through
+                               L2 only; 3 forces L2-only, 4 forces L1 gathers.  0: one
                                launch per half-step (primal, dual) over row-aligned
                                warp chunks.  2: one launch per half-step over fixed
                                256-nonzero slabs, one warp per slab (equal work per

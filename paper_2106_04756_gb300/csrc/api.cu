@@ -201,6 +201,7 @@ int setup_matrix(pdlp_ctx *ctx, Mat<T> &K, Mat<T> &KT, const T *val, const T *tv
 // step attempt on GB300 (float64 / float32): the persistent kernel 170 /
 // 112 us on the 1M-node PageRank LP and 42.5 / 29.1 us on the 100k x 250k LP,
 // the slab kernels 217 / 139 and 66 / 46 us, so the default never picks them.
+constexpr double kL1GatherBytes = 96e6;  // working set above which the persistent kernel gathers through L1
 int use_slab_engine(const pdlp_ctx *ctx, int elem_bytes) {
   (void)elem_bytes;
   return ctx->opts.persistent == 2;
@@ -236,7 +237,11 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   pr.K.slab_on = pr.KT.slab_on = slab;
   if (slab) CK(plan_slab_grid<T>(pr.K, pr.KT), "slab grid");
   const int persist_mode = (ctx->opts.step_policy == 2 || slab || ctx->opts.persistent == 0) ? 0 : 1;
-  CK(persist_plan<T>(ctx->cmaxKT, ctx->cmaxK, ctx->assign_nw, persist_mode, &pr.pg), "persistent kernel layout");
+  // gathers through L1 when one attempt's working set exceeds L2 (see persistent.cu)
+  const double ws = 2.0 * (double)ctx->nnz * (4.0 + sizeof(T)) + 4.0 * ((double)ctx->m + ctx->n) +
+                    (double)sizeof(T) * (9.0 * ctx->n + 10.0 * ctx->m);
+  const int l1g = ctx->opts.persistent == 4 ? 1 : (ctx->opts.persistent == 3 ? 0 : (ws > kL1GatherBytes ? 1 : 0));
+  CK(persist_plan<T>(ctx->cmaxKT, ctx->cmaxK, ctx->assign_nw, persist_mode, l1g, &pr.pg), "persistent kernel layout");
   const size_t nsp = (size_t)slab_ctas(ctx->nslabKT), nsd = 2 * (size_t)slab_ctas(ctx->nslabK);
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
                     8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + nsp + nsd + 16;
@@ -466,7 +471,7 @@ int check_options(const pdlp_options *o, std::string &why) {
   if (!(o->rel_tol >= 0.0)) { why = "rel_tol must be >= 0"; return 0; }
   if (o->precision < PDLP_FP64 || o->precision > PDLP_FP32_REFINE) { why = "unknown precision"; return 0; }
   if (o->eval_every < 1 || o->eval_every > kMaxEval) { why = "eval_every must be in [1, 256]"; return 0; }
-  if (o->persistent < 0 || o->persistent > 3) { why = "persistent must be 0, 1, 2 or 3"; return 0; }
+  if (o->persistent < 0 || o->persistent > 4) { why = "persistent must be 0, 1, 2, 3 or 4"; return 0; }
   if (o->step_policy < 0 || o->step_policy > 2) { why = "step_policy must be 0, 1 or 2"; return 0; }
   if (o->restart_to_current < 0 || o->restart_to_current > 1) { why = "restart_to_current must be 0 or 1"; return 0; }
   if (o->step_policy == 2 && o->unroll_T > 0) { why = "step_policy 2 does not combine with unroll_T > 0"; return 0; }

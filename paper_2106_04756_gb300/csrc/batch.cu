@@ -76,9 +76,12 @@ struct Work {
   double *D1, *D2, *kv, *ktv, *cs, *qs, *ls, *us, *ylos, *tmpm, *tmpn;
   int32_t *trp, *tci, *perm, *fill, *rpk;
   T *k, *kt;  // K~ and K~^T values in the arithmetic type
-  T *x[2], *y[2], *Kx[2], *xs[2], *ys[2], *x0, *y0, *KTy, *KTys, *Kxs, *xa, *ya;
+  T *x[2], *y[2], *Kx[2], *xs[2], *ys[2], *x0, *y0, *xa, *ya;
   T *csT, *lsT, *usT, *qsT, *yloT;  // scaled data in the arithmetic type
   double *gt, *ga, *gw, *gv;  // gap items
+  // products of the evaluation (Eq. (15), normalized gap), float64 whatever
+  // T: K^T y and K x of the current iterate, of the average
+  double *KTyd, *Kxd, *KTysd, *Kxsd;
 };
 
 template <typename T>
@@ -98,7 +101,8 @@ __device__ Work<T> carve(char *base, int mm, int nn, long long zz) {
   w.cs = tk(nn); w.qs = tk(mm); w.ls = tk(nn); w.us = tk(nn); w.ylos = tk(mm);
   w.tmpm = tk(mm); w.tmpn = tk(nn);
   w.gt = tk(nn + mm); w.ga = tk(nn + mm); w.gw = tk(nn + mm); w.gv = tk(nn + mm);
-  tk(2 * zz); tk(2 * (size_t)nn); tk(2 * (size_t)mm);  // spare (keeps the formula simple)
+  tk(2 * zz);  // spare (keeps the formula simple)
+  w.KTyd = tk(nn); w.KTysd = tk(nn); w.Kxd = tk(mm); w.Kxsd = tk(mm);
   int32_t *ip = reinterpret_cast<int32_t *>(d);
   w.trp = ip; ip += nn + 1;
   w.tci = ip; ip += zz;
@@ -108,10 +112,10 @@ __device__ Work<T> carve(char *base, int mm, int nn, long long zz) {
   T *t = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(ip) + 15) & ~uintptr_t(15));
   auto tt = [&](size_t k) { T *r = t; t += k; return r; };
   w.k = tt(zz); w.kt = tt(zz);
-  w.x[0] = tt(nn); w.x[1] = tt(nn); w.xs[0] = tt(nn); w.xs[1] = tt(nn); w.x0 = tt(nn); w.KTy = tt(nn);
-  w.KTys = tt(nn); w.xa = tt(nn); tt(nn);
+  w.x[0] = tt(nn); w.x[1] = tt(nn); w.xs[0] = tt(nn); w.xs[1] = tt(nn); w.x0 = tt(nn);
+  w.xa = tt(nn);
   w.y[0] = tt(mm); w.y[1] = tt(mm); w.Kx[0] = tt(mm); w.Kx[1] = tt(mm); w.ys[0] = tt(mm); w.ys[1] = tt(mm);
-  w.y0 = tt(mm); w.Kxs = tt(mm); w.ya = tt(mm);
+  w.y0 = tt(mm); w.ya = tt(mm);
   w.csT = tt(nn); w.lsT = tt(nn); w.usT = tt(nn); w.qsT = tt(mm); w.yloT = tt(mm);
   return w;
 }
@@ -201,8 +205,8 @@ __device__ __forceinline__ double cta_max(double v, double *red) {
 // is summed from shared memory (fixed order: lane gl takes k = s + gl,
 // s + gl + L, ..., then a shuffle tree).  A row longer than `cap` is summed
 // directly from global memory.
-template <typename T, typename Epi>
-__device__ __forceinline__ void cta_spmv(int rows, const int32_t *rp, const int32_t *ci, const T *a, const T *v,
+template <typename T, typename TV = T, typename Epi>
+__device__ __forceinline__ void cta_spmv(int rows, const int32_t *rp, const int32_t *ci, const T *a, const TV *v,
                                          int L, T *prod, int cap, Epi &&epi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = 32 / L, g = lane / L, gl = lane % L;
@@ -220,7 +224,7 @@ __device__ __forceinline__ void cta_spmv(int rows, const int32_t *rp, const int3
     if (r1 == r0) {  // one row longer than the tile: direct sum by warp 0
       if (warp == 0) {
         T acc = T(0);
-        for (int k = base + lane; k < rp[r0 + 1]; k += 32) acc = fma(a[k], v[ci[k]], acc);
+        for (int k = base + lane; k < rp[r0 + 1]; k += 32) acc = fma(a[k], (T)v[ci[k]], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) epi(r0, acc);
@@ -236,7 +240,7 @@ __device__ __forceinline__ void cta_spmv(int rows, const int32_t *rp, const int3
       for (int u = 0; u < 4; ++u) {
         const int e = e0 + u * kBThreads;
         av[u] = e < cnt ? a[base + e] : T(0);
-        vv[u] = e < cnt ? v[ci[base + e]] : T(0);
+        vv[u] = e < cnt ? (T)v[ci[base + e]] : T(0);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -273,8 +277,8 @@ __device__ __forceinline__ double lam_of(double rc, double l, double u) {
 // shared memory, then the first breakpoint whose phi reaches r^2 by prefix
 // sums.  Returns +inf for r = 0.
 template <typename T>
-__device__ double cta_gap(const Work<T> &w, int n, int m, const T *x, const T *y, const T *KTy, const T *Kx,
-                          double om, double r, double *skey, int *sidx, double *red) {
+__device__ double cta_gap(const Work<T> &w, int n, int m, const T *x, const T *y, const double *KTy,
+                          const double *Kx, double om, double r, double *skey, int *sidx, double *red) {
   if (!(r > 0.0)) return INFINITY;
   const int N = n + m;
   int P = 1;
@@ -633,14 +637,22 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
         const bool avg = sum_eta > 0.0;
         const double inv = avg ? 1.0 / sum_eta : 0.0;
         const T *x = w.x[cur], *y = w.y[cur], *Kx = w.Kx[cur];
-        // K^T y (current), K^T ys, K xs
-        cta_spmv<T>(n, w.trp, w.tci, w.kt, y, Lt, prod, cap, [&](int j, T s) { w.KTy[j] = s; });
+        // K^T y (current), K x (current), K^T ys, K xs: in float64 from the
+        // float64 K~ whatever T, since float32 products cannot resolve the
+        // residuals of Eq. (15) below about 1e-7 of their terms (in float64
+        // the step's own K x is that product already)
+        double *prodd = reinterpret_cast<double *>(prod);
+        const int capd = (int)(kBatchSmem / sizeof(double));
+        cta_spmv<double, T>(n, w.trp, w.tci, w.ktv, y, Lt, prodd, capd, [&](int j, double s) { w.KTyd[j] = s; });
+        const double *Kxd = w.Kxd;
+        if constexpr (sizeof(T) == 8) Kxd = reinterpret_cast<const double *>(Kx);
+        else cta_spmv<double, T>(m, rpk, ci, w.kv, x, Lk, prodd, capd, [&](int i, double s) { w.Kxd[i] = s; });
         if (avg) {
           for (int j = threadIdx.x; j < n; j += blockDim.x) w.xa[j] = (T)((double)w.xs[cur][j] * inv);
           for (int i = threadIdx.x; i < m; i += blockDim.x) w.ya[i] = (T)((double)w.ys[cur][i] * inv);
           __syncthreads();
-          cta_spmv<T>(n, w.trp, w.tci, w.kt, w.ya, Lt, prod, cap, [&](int j, T s) { w.KTys[j] = s; });
-          cta_spmv<T>(m, rpk, ci, w.k, w.xa, Lk, prod, cap, [&](int i, T s) { w.Kxs[i] = s; });
+          cta_spmv<double, T>(n, w.trp, w.tci, w.ktv, w.ya, Lt, prodd, capd, [&](int j, double s) { w.KTysd[j] = s; });
+          cta_spmv<double, T>(m, rpk, ci, w.kv, w.xa, Lk, prodd, capd, [&](int i, double s) { w.Kxsd[i] = s; });
         }
         __syncthreads();
         // Eq. (15) terms for both candidates on the original problem
@@ -652,7 +664,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           for (int cnd = 0; cnd < 2; ++cnd) {
             if (cnd == 1 && !avg) break;
             const double xt = cnd == 0 ? (double)x[j] : (double)w.xa[j];
-            const double kt = cnd == 0 ? (double)w.KTy[j] : (double)w.KTys[j];
+            const double kt = cnd == 0 ? w.KTyd[j] : w.KTysd[j];
             const double rc = c[j] - kt / w.D2[j];
             const double lam = lam_of(rc, l[j], u[j]);
             acc[6 * cnd + 0] += c[j] * (w.D2[j] * xt);
@@ -665,7 +677,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           for (int cnd = 0; cnd < 2; ++cnd) {
             if (cnd == 1 && !avg) break;
             const double yt = cnd == 0 ? (double)y[i] : (double)w.ya[i];
-            const double kx = cnd == 0 ? (double)Kx[i] : (double)w.Kxs[i];
+            const double kx = cnd == 0 ? Kxd[i] : w.Kxsd[i];
             double r = q[i] - kx / w.D1[i];
             if (ineq[i]) r = r > 0.0 ? r : 0.0;
             acc[6 * cnd + 3] += r * r;
@@ -722,8 +734,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           }
           cta_sum<4>(d2, red);
           const double rcur = sqrt(omega * d2[0] + d2[1] / omega), ravg = sqrt(omega * d2[2] + d2[3] / omega);
-          const double mu_cur = cta_gap<T>(w, n, m, x, y, w.KTy, Kx, omega, rcur, skey, sidx, red);
-          const double mu_avg = cta_gap<T>(w, n, m, w.xa, w.ya, w.KTys, w.Kxs, omega, ravg, skey, sidx, red);
+          const double mu_cur = cta_gap<T>(w, n, m, x, y, w.KTyd, Kxd, omega, rcur, skey, sidx, red);
+          const double mu_avg = cta_gap<T>(w, n, m, w.xa, w.ya, w.KTysd, w.Kxsd, omega, ravg, skey, sidx, red);
           const int cand = o.restart_to_current ? (mu_cur < mu_avg ? 0 : 1) : 1;
           const double muc = cand == 0 ? mu_cur : mu_avg;
           bool restart = false;
@@ -733,22 +745,22 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           muc_prev = muc;
           if (restart) {
             const double Dx = sqrt(cand == 0 ? d2[0] : d2[2]), Dy = sqrt(cand == 0 ? d2[1] : d2[3]);
+            const double *kty0 = w.KTyd, *kx0 = Kxd;  // products at the new restart point
             if (cand == 1) {  // the average becomes the current iterate
-              for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                w.x[cur][j] = w.xa[j];
-                w.KTy[j] = w.KTys[j];
-              }
+              for (int j = threadIdx.x; j < n; j += blockDim.x) w.x[cur][j] = w.xa[j];
               for (int i = threadIdx.x; i < m; i += blockDim.x) {
                 w.y[cur][i] = w.ya[i];
-                w.Kx[cur][i] = w.Kxs[i];
+                w.Kx[cur][i] = (T)w.Kxsd[i];
               }
+              kty0 = w.KTysd;
+              kx0 = w.Kxsd;
               __syncthreads();
             }
             if (o.pw_update && Dx > o.eps_zero && Dy > o.eps_zero)
               omega = exp(o.pw_theta * log(Dy / Dx) + (1.0 - o.pw_theta) * log(omega));
             // mu_0 of the new outer loop: the new start against the old one, new omega
             const double r0 = sqrt(omega * (cand == 0 ? d2[0] : d2[2]) + (cand == 0 ? d2[1] : d2[3]) / omega);
-            mu0 = cta_gap<T>(w, n, m, w.x[cur], w.y[cur], w.KTy, w.Kx[cur], omega, r0, skey, sidx, red);
+            mu0 = cta_gap<T>(w, n, m, w.x[cur], w.y[cur], kty0, kx0, omega, r0, skey, sidx, red);
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
               w.x0[j] = w.x[cur][j];
               w.xs[cur][j] = T(0);

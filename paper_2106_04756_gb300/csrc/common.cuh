@@ -715,7 +715,7 @@ __device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)
 // say otherwise): on expiry (or when another CTA has already failed) it
 // records the failure in *err and returns false.
 __device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned long long target, int *err,
-                                             unsigned long long limit_ns) {
+                                             unsigned long long limit_ns, bool acquire = true) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -736,7 +736,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned
         __nanosleep(8);
       }
     }
-    if (ok) {
+    if (ok && acquire) {
       // acquire: later loads of this CTA (ordered after it by the CTA barrier
       // below) see every write the other CTAs made before their arrival
       unsigned long long seen;
@@ -844,6 +844,7 @@ struct PersistGeo {
   int32_t smem;   // dynamic shared memory per CTA
   int32_t warp_bytes;
   int32_t o_desc_p, o_desc_d;
+  int32_t l1_gather;  // 1: gathers through L1 after acquiring barriers; 0: through L2 only
 };
 
 // Algorithm 2's factors 1 - (k+1)^-0.3 and 1 + (k+1)^-0.6 for the next

@@ -44,11 +44,15 @@ __host__ __device__ inline int round16(int b) { return (b + 15) & ~15; }
 // Asynchronous global -> shared copies (cp.async, cached in L1).  Used only
 // for data no other CTA writes during the launch (matrix values, row starts
 // and the warp's own rows' operands).  Entries written by other CTAs (the
-// gathered vector) are plain loads: the grid barrier that precedes each
-// phase ends with an acquire of the arrival counter that every CTA released
-// after its writes, so by the memory model the loads after it see those
-// writes (an acquire at GPU scope discards stale L1 lines), and the gathers
-// keep the L1 hits of rows that share columns.
+// gathered vector) are plain loads when L1G: the grid barrier that precedes
+// each phase then ends with an acquire of the arrival counter that every CTA
+// released after its writes, so by the memory model the loads after it see
+// those writes (an acquire at GPU scope discards stale L1 lines), and the
+// gathers keep the L1 hits of rows that share columns.  That pays where the
+// working set exceeds L2 (1M-node PageRank: 144 -> 112 us per float32
+// attempt); where it stays in L2 the L2-only loads (ld.global.cg) without the
+// acquire are faster (100k x 250k LP: 40.8 against 42.8 us in float64), so
+// the choice is made per context (PersistGeo::l1_gather).
 template <typename T>
 __device__ __forceinline__ void cp_async(T *dst, const T *src) {
   static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
@@ -218,8 +222,9 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
 
 // Starts the loads of one chunk: column indices (global, to registers), then
 // values, row starts and epilogue operands by cp.async into the staging
-// buffer `buf`, and the gathered vector entries (through L2) into xg.
-template <typename T, typename Ph>
+// buffer `buf`, and the gathered vector entries into xg (through L1 when
+// L1G, else through L2 only).
+template <typename T, bool L1G, typename Ph>
 __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *vec, const Ph &ph, char *buf,
                                       T (&xg)[kLaneItems]) {
   const int lane = threadIdx.x & 31;
@@ -243,7 +248,7 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
 #pragma unroll
   for (int it = 0; it < kLaneItems; ++it) {
     const int e = lane + 32 * it;
-    xg[it] = e < cnt ? vec[cj[it]] : T(0);
+    xg[it] = e < cnt ? (L1G ? vec[cj[it]] : __ldcg(vec + cj[it])) : T(0);
   }
 }
 
@@ -280,13 +285,13 @@ __device__ __forceinline__ void cta_sum3(const double (&v)[3], char *sm, int war
 // One phase over the warp's chunks with two chunks in flight (two staging
 // buffers, gathered entries in registers a / b): the loads of chunk i + 2
 // start once chunk i is done.
-template <typename T, typename Ph>
+template <typename T, bool L1G, typename Ph>
 __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, int count, const T *vec, char *wsm,
                                           Ph &ph) {
   char *b0 = wsm, *b1 = wsm + buf_bytes<T>();
   T ga[kLaneItems], gb[kLaneItems];
-  if (count > 0) issue<T>(A, desc[0], vec, ph, b0, ga);
-  if (count > 1) issue<T>(A, desc[1], vec, ph, b1, gb);
+  if (count > 0) issue<T, L1G>(A, desc[0], vec, ph, b0, ga);
+  if (count > 1) issue<T, L1G>(A, desc[1], vec, ph, b1, gb);
   for (int i = 0; i < count; i += 2) {
     if (i + 1 < count)
       cp_async_wait<1>();
@@ -295,7 +300,7 @@ __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, in
     __syncwarp();
     finish<T>(A, desc[i], b0, ph, ga);
     __syncwarp();
-    if (i + 2 < count) issue<T>(A, desc[i + 2], vec, ph, b0, ga);
+    if (i + 2 < count) issue<T, L1G>(A, desc[i + 2], vec, ph, b0, ga);
     if (i + 1 < count) {
       if (i + 2 < count)
         cp_async_wait<1>();
@@ -304,12 +309,12 @@ __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, in
       __syncwarp();
       finish<T>(A, desc[i + 1], b1, ph, gb);
       __syncwarp();
-      if (i + 3 < count) issue<T>(A, desc[i + 3], vec, ph, b1, gb);
+      if (i + 3 < count) issue<T, L1G>(A, desc[i + 3], vec, ph, b1, gb);
     }
   }
 }
 
-template <typename T>
+template <typename T, bool L1G>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_persist(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S, PersistGeo geo) {
   extern __shared__ __align__(16) char sm[];
@@ -357,12 +362,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const int cur = ctl.cur;
     PrimalPhase<T> pp{S.x[cur], S.xs[cur], P.cs, P.ls, P.us, S.x[cur ^ 1], S.xs[cur ^ 1],
                       (T)ctl.tau, (T)ctl.eta, {0.0}};
-    run_phase<T>(KT, dp, cnt_p, S.y[cur], wsm, pp);
+    run_phase<T, L1G>(KT, dp, cnt_p, S.y[cur], wsm, pp);
     target += G + (att == 0 && s_wait_extra ? 1ull : 0ull);
-    if (!grid_barrier(bar, target, &sc->err, s_wait_ns)) break;
+    if (!grid_barrier(bar, target, &sc->err, s_wait_ns, L1G)) break;
     DualPhase<T> dph{S.y[cur], S.Kx[cur], S.ys[cur], P.qs, P.ylos, S.y[cur ^ 1], S.Kx[cur ^ 1], S.ys[cur ^ 1],
                      (T)ctl.sigma, (T)ctl.eta, {0.0, 0.0}};
-    run_phase<T>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
+    run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
     {
       const double v[3] = {pp.acc[0], dph.acc[0], dph.acc[1]};
       cta_sum3(v, sm, geo.warp_bytes, s_tot);
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       }
     }
     target += G;
-    if (!grid_barrier(bar, target, &sc->err, s_wait_ns)) break;
+    if (!grid_barrier(bar, target, &sc->err, s_wait_ns, L1G)) break;
     {
       // the same fixed-order sum in every CTA, all loads in one round: each
       // thread adds its per-CTA partials, then its rows split into segments
@@ -451,7 +456,7 @@ int persist_warps() {
 }
 
 template <typename T>
-cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, PersistGeo *pg) {
+cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, int l1_gather, PersistGeo *pg) {
   *pg = PersistGeo{};
   if (mode == 0) return cudaSuccess;
   cudaError_t e;
@@ -460,18 +465,22 @@ cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, Persi
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
   cudaFuncAttributes fa;
-  if ((e = cudaFuncGetAttributes(&fa, k_persist<T>))) return e;
+  if ((e = cudaFuncGetAttributes(&fa, k_persist<T, true>))) return e;
   const int budget = optin - (int)fa.sharedSizeBytes;
   const int grid = sms;
   if (grid * kPWarps != assign_nw) return cudaSuccess;  // no assignment for this grid
   PersistGeo g{};
   g.grid = grid;
+  g.l1_gather = l1_gather;
   layout<T>(g, cmax_kt, cmax_k);
   if (g.smem > budget) return cudaSuccess;  // too many chunks per warp: one launch per half-step
   // the attribute is per kernel, shared by every context: set it to the budget
-  if ((e = cudaFuncSetAttribute(k_persist<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
+  if ((e = cudaFuncSetAttribute(k_persist<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
+  if ((e = cudaFuncSetAttribute(k_persist<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
   int per = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist<T>, kPThreads, g.smem))) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist<T, true>, kPThreads, g.smem))) return e;
+  if (per < 1) return cudaSuccess;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist<T, false>, kPThreads, g.smem))) return e;
   if (per < 1) return cudaSuccess;
   *pg = g;
   return cudaSuccess;
@@ -490,7 +499,8 @@ cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_persist<T>, K, KT, P, S, pg);
+  if (pg.l1_gather) return cudaLaunchKernelEx(&cfg, k_persist<T, true>, K, KT, P, S, pg);
+  return cudaLaunchKernelEx(&cfg, k_persist<T, false>, K, KT, P, S, pg);
 }
 
 // Mean duration of one step attempt inside the persistent kernel: `reps`
@@ -531,7 +541,7 @@ cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P,
 }
 
 #define PDLP_INST(T)                                                                                        \
-  template cudaError_t persist_plan<T>(int, int, int, int, PersistGeo *);                                   \
+  template cudaError_t persist_plan<T>(int, int, int, int, int, PersistGeo *);                                   \
   template cudaError_t launch_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &, \
                                          const PersistGeo &, cudaStream_t);                                 \
   template cudaError_t time_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &,   \

@@ -62,7 +62,7 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
 int persist_warps();  // warps of the persistent grid on the current device (0 on error)
 int persist_warps_per_cta();
 template <typename T>
-cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, PersistGeo *pg);
+cudaError_t persist_plan(int cmax_kt, int cmax_k, int assign_nw, int mode, int l1_gather, PersistGeo *pg);
 template <typename T>
 cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                            const PersistGeo &pg, cudaStream_t st);

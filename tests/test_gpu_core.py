@@ -112,13 +112,14 @@ def test_normalized_gap_at_bound_points_matches_oracle(gpu_lib, oracle_lib, name
             assert abs(mu - mu_ref) <= 1e-6 * abs(mu_ref), (trial, mu, mu_ref)
 
 
-@pytest.mark.parametrize("persistent", [1, 0, 2])
+@pytest.mark.parametrize("persistent", [1, 0, 2, 4])
 @pytest.mark.parametrize("name", ["planted_200x500", "mip_2000x5000", "dense_row"])
 @pytest.mark.parametrize("iters", [20, 39, 120])
 def test_first_iterates_match_oracle(gpu_lib, oracle_lib, name, iters, persistent):
     """Same algorithm, float64: iterates agree up to the rounding growth above
     for the first steps; step and restart decisions match exactly.  Every step
-    engine: the persistent cooperative kernel (1), one launch per half-step
+    engine: the persistent cooperative kernel (1: gathers through L2 at these
+    sizes; 4: through L1 after acquiring barriers), one launch per half-step
     (0), and the fixed-size slab kernels (2)."""
     lp = CASES[name]()
     x_g, y_g, r_g = P.solve(lp, iter_limit=iters, persistent=persistent)
@@ -245,7 +246,7 @@ def test_restart_trace_matches_oracle(gpu_lib, oracle_lib, name):
         assert a[5] == b[5] and a[6] == b[6], (a, b)
 
 
-@pytest.mark.parametrize("persistent", [1, 0, 2])
+@pytest.mark.parametrize("persistent", [1, 0, 2, 4])
 @pytest.mark.parametrize("prec", [P.PDLP_FP64, P.PDLP_FP32_REFINE])
 def test_host_stepped_mode_equals_graph(gpu_lib, prec, persistent):
     """use_graph = 0 launches the graph's kernels from a host loop: the same

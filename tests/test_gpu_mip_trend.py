@@ -45,7 +45,7 @@ def _best_kkt(tr):
     return np.minimum(cur, avg)
 
 
-@pytest.mark.parametrize("persistent", [1, 0, 2])
+@pytest.mark.parametrize("persistent", [1, 0, 2, 4])
 def test_long_solve_tracks_oracle(gpu_lib, oracle_trace, persistent):
     lp, to = oracle_trace
     with P.Context.from_lp(lp, iter_limit=ITERS, persistent=persistent) as ctx:
