@@ -65,6 +65,10 @@ def _args():
     ap.add_argument("--stepped", action="store_true", help="host-stepped kernels instead of one graph per solve")
     ap.add_argument("--mip-cap-s", type=float, default=20.0,
                     help="time cap of each time-to-1e-8 solve of the MIP-shaped LP")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                    help="only solve the first N LPs of the 4096-LP batch twice (tuning, then one launch "
+                         "between cudaProfilerStart / Stop, for ncu --profile-from-start off) and exit")
+    ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "fp32"])
     return ap.parse_args()
 
 
@@ -405,6 +409,20 @@ def main():
     import paper_2106_04756_gb300 as P
     from paper_2106_04756_gb300 import build
     build.build()
+    if args.profile_batch > 0:
+        import lpgen
+        lps = lpgen.batch_4096()[:args.profile_batch]
+        prec = P.PDLP_FP64 if args.profile_precision == "fp64" else P.PDLP_FP32
+        P.solve_batch(lps, precision=prec, rel_tol=1e-6, iter_limit=20000)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        _, _, rs = P.solve_batch(lps, precision=prec, rel_tol=1e-6, iter_limit=20000)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_batch": len(lps), "precision": args.profile_precision,
+                          "optimal": sum(r["status_name"] == "OPTIMAL" for r in rs),
+                          "iters": sum(r["iters"] for r in rs)}))
+        return
     lp = _make(args.workload)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
