@@ -69,6 +69,9 @@ def _args():
                     help="only solve the first N LPs of the 4096-LP batch twice (tuning, then one launch "
                          "between cudaProfilerStart / Stop, for ncu --profile-from-start off) and exit")
     ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--profile-unroll", action="store_true",
+                    help="only run the unrolled map (T = 500, checkpoint 50) and its adjoint on the 20k x 50k "
+                         "LP twice, the second time between cudaProfilerStart / Stop, and exit")
     return ap.parse_args()
 
 
@@ -409,6 +412,21 @@ def main():
     import paper_2106_04756_gb300 as P
     from paper_2106_04756_gb300 import build
     build.build()
+    if args.profile_unroll:
+        import lpgen
+        lp = lpgen.unroll_20k()
+        target = np.random.default_rng(4).standard_normal(lp.n)
+        with P.Context.from_lp(lp) as ctx:
+            x, _, _ = ctx.unroll(500, 50)
+            ctx.grad(x - target)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            x, _, _ = ctx.unroll(500, 50)
+            ctx.grad(x - target)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+        print(json.dumps({"profile_unroll": "mip_20k_50k", "T": 500, "ckpt_every": 50}))
+        return
     if args.profile_batch > 0:
         import lpgen
         lps = lpgen.batch_4096()[:args.profile_batch]

@@ -76,7 +76,8 @@ struct Work {
   double *D1, *D2, *kv, *ktv, *cs, *qs, *ls, *us, *ylos, *tmpm, *tmpn;
   int32_t *trp, *tci, *perm, *fill, *rpk;
   T *k, *kt;  // K~ and K~^T values in the arithmetic type
-  T *x[2], *y[2], *Kx[2], *xs[2], *ys[2], *x0, *y0, *xa, *ya;
+  T *x[2], *y[2], *Kx[2], *x0, *y0, *xa, *ya;
+  double *xs[2], *ys[2];  // running sums of the average, float64 whatever T
   T *csT, *lsT, *usT, *qsT, *yloT;  // scaled data in the arithmetic type
   double *gt, *ga, *gw, *gv;  // gap items
   // products of the evaluation (Eq. (15), normalized gap), float64 whatever
@@ -86,7 +87,7 @@ struct Work {
 
 template <typename T>
 size_t work_bytes(int mm, int nn, long long zz) {
-  const size_t d = sizeof(double) * (size_t)(4 * zz + 8 * (size_t)nn + 6 * (size_t)mm + 4 * (size_t)(nn + mm));
+  const size_t d = sizeof(double) * (size_t)(4 * zz + 10 * (size_t)nn + 8 * (size_t)mm + 4 * (size_t)(nn + mm));
   const size_t i = sizeof(int32_t) * (size_t)(2 * zz + 2 * (size_t)nn + (size_t)mm + 3);
   const size_t t = sizeof(T) * (size_t)(2 * zz + 12 * (size_t)nn + 11 * (size_t)mm) + 64;
   return (d + i + t + 255) / 256 * 256;
@@ -103,6 +104,7 @@ __device__ Work<T> carve(char *base, int mm, int nn, long long zz) {
   w.gt = tk(nn + mm); w.ga = tk(nn + mm); w.gw = tk(nn + mm); w.gv = tk(nn + mm);
   tk(2 * zz);  // spare (keeps the formula simple)
   w.KTyd = tk(nn); w.KTysd = tk(nn); w.Kxd = tk(mm); w.Kxsd = tk(mm);
+  w.xs[0] = tk(nn); w.xs[1] = tk(nn); w.ys[0] = tk(mm); w.ys[1] = tk(mm);
   int32_t *ip = reinterpret_cast<int32_t *>(d);
   w.trp = ip; ip += nn + 1;
   w.tci = ip; ip += zz;
@@ -112,9 +114,9 @@ __device__ Work<T> carve(char *base, int mm, int nn, long long zz) {
   T *t = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(ip) + 15) & ~uintptr_t(15));
   auto tt = [&](size_t k) { T *r = t; t += k; return r; };
   w.k = tt(zz); w.kt = tt(zz);
-  w.x[0] = tt(nn); w.x[1] = tt(nn); w.xs[0] = tt(nn); w.xs[1] = tt(nn); w.x0 = tt(nn);
+  w.x[0] = tt(nn); w.x[1] = tt(nn); w.x0 = tt(nn);
   w.xa = tt(nn);
-  w.y[0] = tt(mm); w.y[1] = tt(mm); w.Kx[0] = tt(mm); w.Kx[1] = tt(mm); w.ys[0] = tt(mm); w.ys[1] = tt(mm);
+  w.y[0] = tt(mm); w.y[1] = tt(mm); w.Kx[0] = tt(mm); w.Kx[1] = tt(mm);
   w.y0 = tt(mm); w.ya = tt(mm);
   w.csT = tt(nn); w.lsT = tt(nn); w.usT = tt(nn); w.qsT = tt(mm); w.yloT = tt(mm);
   return w;
@@ -603,16 +605,16 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
       const T x = clampv<T>(T(0), (T)w.ls[j], (T)w.us[j]);
       w.x[0][j] = x;
       w.x0[j] = x;
-      w.xs[0][j] = T(0);
-      w.xs[1][j] = T(0);
+      w.xs[0][j] = 0.0;
+      w.xs[1][j] = 0.0;
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const T lo = (T)w.ylos[i];
       const T y = T(0) > lo ? T(0) : lo;
       w.y[0][i] = y;
       w.y0[i] = y;
-      w.ys[0][i] = T(0);
-      w.ys[1][i] = T(0);
+      w.ys[0][i] = 0.0;
+      w.ys[1][i] = 0.0;
     }
     __syncthreads();
     // K's row_ptr with its end entry (the input holds the m row starts)
@@ -648,8 +650,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
         if constexpr (sizeof(T) == 8) Kxd = reinterpret_cast<const double *>(Kx);
         else cta_spmv<double, T>(m, rpk, ci, w.kv, x, Lk, prodd, capd, [&](int i, double s) { w.Kxd[i] = s; });
         if (avg) {
-          for (int j = threadIdx.x; j < n; j += blockDim.x) w.xa[j] = (T)((double)w.xs[cur][j] * inv);
-          for (int i = threadIdx.x; i < m; i += blockDim.x) w.ya[i] = (T)((double)w.ys[cur][i] * inv);
+          for (int j = threadIdx.x; j < n; j += blockDim.x) w.xa[j] = (T)(w.xs[cur][j] * inv);
+          for (int i = threadIdx.x; i < m; i += blockDim.x) w.ya[i] = (T)(w.ys[cur][i] * inv);
           __syncthreads();
           cta_spmv<double, T>(n, w.trp, w.tci, w.ktv, w.ya, Lt, prodd, capd, [&](int j, double s) { w.KTysd[j] = s; });
           cta_spmv<double, T>(m, rpk, ci, w.kv, w.xa, Lk, prodd, capd, [&](int i, double s) { w.Kxsd[i] = s; });
@@ -763,11 +765,11 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
             mu0 = cta_gap<T>(w, n, m, w.x[cur], w.y[cur], kty0, kx0, omega, r0, skey, sidx, red);
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
               w.x0[j] = w.x[cur][j];
-              w.xs[cur][j] = T(0);
+              w.xs[cur][j] = 0.0;
             }
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
               w.y0[i] = w.y[cur][i];
-              w.ys[cur][i] = T(0);
+              w.ys[cur][i] = 0.0;
             }
             sum_eta = 0.0;
             t = 0;
@@ -818,14 +820,16 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
         }
         __syncthreads();
         const T tau = (T)s_step[0], sig = (T)s_step[1], et = (T)eta;
-        const T *x = w.x[cur], *y = w.y[cur], *Kx = w.Kx[cur], *xs = w.xs[cur], *ys = w.ys[cur];
-        T *xn = w.x[cur ^ 1], *yn = w.y[cur ^ 1], *Kxn = w.Kx[cur ^ 1], *xsn = w.xs[cur ^ 1], *ysn = w.ys[cur ^ 1];
+        const T *x = w.x[cur], *y = w.y[cur], *Kx = w.Kx[cur];
+        const double *xs = w.xs[cur], *ys = w.ys[cur];
+        T *xn = w.x[cur ^ 1], *yn = w.y[cur ^ 1], *Kxn = w.Kx[cur ^ 1];
+        double *xsn = w.xs[cur ^ 1], *ysn = w.ys[cur ^ 1];
         double s3[3] = {0.0, 0.0, 0.0};
         cta_spmv<T>(n, w.trp, w.tci, w.kt, y, Lt, prod, cap, [&](int j, T g) {
           const T xj = x[j];
           const T xp = clampv<T>(xj - tau * (w.csT[j] - g), w.lsT[j], w.usT[j]);
           xn[j] = xp;
-          xsn[j] = xs[j] + et * xp;
+          xsn[j] = xs[j] + (double)et * (double)xp;
           const T d = xp - xj;
           s3[0] += (double)(d * d);
         });
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           const T yp = v > lo ? v : lo;
           yn[i] = yp;
           Kxn[i] = kxn;
-          ysn[i] = ys[i] + et * yp;
+          ysn[i] = ys[i] + (double)et * (double)yp;
           const T dy = yp - yi, dk = kxn - kx;
           s3[1] += (double)(dy * dy);
           s3[2] += (double)dy * (double)dk;
