@@ -254,7 +254,10 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   S.part_cp = S.part_er + 8 * (size_t)ctx->nblocksK;
   S.part_sp = S.part_cp + 3 * (size_t)pr.pg.grid;
   S.part_sd = S.part_sp + nsp;
-  S.tickets = dalloc<unsigned>(pr.tickets, kNumTickets);
+  // fixed tickets, then one counter per group of 32 evaluation CTAs
+  const size_t nticket = kNumTickets + ((size_t)ctx->nblocksKT + 31) / 32 + ((size_t)ctx->nblocksK + 31) / 32;
+  S.tickets = dalloc<unsigned>(pr.tickets, nticket);
+  S.gtickets = S.tickets ? S.tickets + kNumTickets : nullptr;
   S.gkeys = dalloc<unsigned>(pr.gkeys, (size_t)kGapSlots * N);
   S.ghist = dalloc<double>(pr.ghist, (size_t)kGapSlots * kGapBuckets * 3);
   S.xo = dalloc<double>(pr.xo, n);
@@ -265,7 +268,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   double *normpart = dalloc<double>(pr.normpart, 4 * 152 + 8);
   if (!S.tickets || !S.gkeys || !S.ghist || !S.xo || !S.yo || !normpart)
     return fail(ctx, PDLP_ERR_OOM, "state allocation failed");
-  CK(cudaMemsetAsync(S.tickets, 0, sizeof(unsigned) * kNumTickets, ctx->st), "memset");
+  CK(cudaMemsetAsync(S.tickets, 0, sizeof(unsigned) * nticket, ctx->st), "memset");
   CK(cudaMemsetAsync(S.ghist, 0, sizeof(double) * kGapSlots * kGapBuckets * 3, ctx->st), "memset");
   CK(cudaMemsetAsync(normpart, 0, sizeof(double) * (4 * 152 + 8), ctx->st), "memset");
   CK(set_kernel_attributes<T>(), "kernel attributes");
@@ -954,6 +957,7 @@ extern "C" int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double 
   hs.g_active[0] = 1;
   hs.g_r2[0] = r * r;
   hs.g_omega[0] = omega;
+  hs.g_inv_omega[0] = 1.0 / omega;
   hs.g_W[0] = hs.g_V[0] = hs.g_A[0] = 0.0;
   hs.g_prefix[0] = 0u;
   CK(cudaMemcpyAsync(S.s, &hs, sizeof(Scalars), cudaMemcpyHostToDevice, st), "scalars");

@@ -93,10 +93,11 @@ struct Scalars {
   // --- evaluation (Eq. (15) on the original problem), [candidate][term]
   double kkt[2][8];
   double cand_dx2[2], cand_dy2[2];  // squared distances to z^{n,0} (scaled space)
+  double pw_omega[2], pw_inv[2], pw_r2[2];  // Algorithm 3 per candidate (primal weight, 1/it, slot-2 radius^2)
   double qnorm, cnorm;              // ||q||_2, ||c||_2 of the original problem
   double rel_tol;
   // --- gap radix selection per slot
-  double g_r2[kGapSlots], g_omega[kGapSlots];
+  double g_r2[kGapSlots], g_omega[kGapSlots], g_inv_omega[kGapSlots];
   double g_W[kGapSlots], g_V[kGapSlots], g_A[kGapSlots];
   unsigned int g_prefix[kGapSlots];
   int g_active[kGapSlots];
@@ -168,9 +169,10 @@ struct State {
   double *part_sp, *part_sd;   // per-CTA partials of the slab step kernels (primal [CTA], dual [CTA][2])
   double *part_ec, *part_er;   // per-CTA partials of the evaluation kernels
   unsigned int *tickets;       // arrival counters (one per kernel kind)
+  unsigned int *gtickets;      // arrival counters of the evaluation CTA groups (columns, then rows)
   Scalars *s;
   unsigned int *gkeys;         // gap keys [kGapSlots][n + m]
-  double *ghist;               // gap histogram [kGapSlots][kGapBuckets][3]
+  double *ghist;               // gap histogram [kGapSlots][3][kGapBuckets] (w, v, a)
   double *xo, *yo;             // returned point (original space, float64)
   double *trace;               // [kTraceCap][kTraceLen]
   double *eta_log;             // nullable: step size of each accepted step, by step index

@@ -377,40 +377,75 @@ __global__ void __launch_bounds__(kThreads) k_mp_test(Mat<T> KT, State<T> S, int
 // Columns: K^T y (current) and K^T ys (sum for the average) in one pass, and
 // the column terms of Eq. (15) for both candidates.
 // Partial layout per CTA (8): [cand][pobj, dres^2, dobj(lambda), |x - x0|^2].
-__device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er)[8], double *trace);
+__device__ void eval_finish(Scalars *s, const double *ecr, double *trace);
 
-// The column and row kernels of an evaluation may run concurrently; the last
-// of their CTAs sums both sets of partials and the long-row slots in a fixed
-// order and finishes the evaluation.
+// The per-CTA partials of an evaluation (8 terms per CTA of k_eval_cols and
+// of k_eval_rows) are summed in a fixed-order two-level tree: the last CTA of
+// each group of kEvalGroup CTAs sums its group's partials (one warp per
+// term) into the group's first slot, and the last group to finish, over both
+// kernels (which may run concurrently), sums the group partials and the
+// long-row slots and finishes the evaluation.  A one-CTA sum of all partials
+// would cost thousands of float64 instructions on one SM.
+constexpr int kEvalGroup = 32;
+static_assert(kThreads == 8 * 32, "one warp per evaluation term");
+
 template <typename T>
-__device__ void eval_finalize(const Mat<T> &K, const Mat<T> &KT, const State<T> &S, double *red) {
-  double ec[8], er[8], lc[8], lr[8];
-  sum_partials<8>(S.part_ec, KT.nblocks, 8, ec, red);
-  __syncthreads();
-  sum_partials<8>(S.part_er, K.nblocks, 8, er, red);
-  __syncthreads();
-  sum_long_rows<8>(KT, lc, red);
-  __syncthreads();
-  sum_long_rows<8>(K, lr, red);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      ec[a] += lc[a];
-      er[a] += lr[a];
-    }
-    eval_finish(S.s, ec, er, S.trace);
-  }
+__device__ __forceinline__ unsigned eval_groups(const Mat<T> &K, const Mat<T> &KT) {
+  const int gc = KT.nblocks > 0 ? (KT.nblocks + kEvalGroup - 1) / kEvalGroup : 0;
+  return (unsigned)(gc + (K.nblocks + kEvalGroup - 1) / kEvalGroup);
 }
 
+// Sum of one term over `ng` group partials (stride kEvalGroup CTAs) and the
+// long rows of A, by one warp; valid in lane 0.
 template <typename T>
-__device__ __forceinline__ unsigned eval_ctas(const Mat<T> &K, const Mat<T> &KT) {
-  return (unsigned)((KT.nblocks > 0 ? KT.nblocks : 0) + K.nblocks);
+__device__ __forceinline__ double eval_term(const double *part, int ng, const Mat<T> &A, int term) {
+  const int lane = threadIdx.x & 31;
+  double t = 0.0, l = 0.0;
+  for (int g = lane; g < ng; g += 32) t += __ldcg(part + (size_t)g * kEvalGroup * 8 + term);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (A.nlong > 0) {
+    for (int r = lane; r < A.nlong; r += 32) l += __ldcg(A.lr_acc + (size_t)r * kLrAcc + term);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    t += l;
+  }
+  return t;
+}
+
+// Called by every CTA of k_eval_cols (cols = true) and k_eval_rows after its
+// partials are stored at part[8 blockIdx.x].
+template <typename T>
+__device__ void eval_arrive(const Mat<T> &K, const Mat<T> &KT, const State<T> &S, bool cols) {
+  __shared__ double ecr[16];
+  double *part = cols ? S.part_ec : S.part_er;
+  const int nb = cols ? KT.nblocks : K.nblocks;
+  const int grp = blockIdx.x / kEvalGroup, g0 = grp * kEvalGroup;
+  const int gsize = nb - g0 < kEvalGroup ? nb - g0 : kEvalGroup;
+  const int gc = KT.nblocks > 0 ? (KT.nblocks + kEvalGroup - 1) / kEvalGroup : 0;
+  if (!last_of(S.gtickets + (cols ? grp : gc + grp), (unsigned)gsize)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp = term
+  double v = lane < gsize ? __ldcg(part + (size_t)(g0 + lane) * 8 + warp) : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // every term of the group is read before its first slot is overwritten
+  if (lane == 0) part[(size_t)g0 * 8 + warp] = v;
+  if (!last_of(S.tickets + kTicketEvalRows, eval_groups(K, KT))) return;
+  // warp w: terms 2w and 2w + 1 of [column terms (8), row terms (8)]
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int a = 2 * warp + q, term = a & 7;
+    const double t = a < 8 ? eval_term(S.part_ec, gc, KT, term)
+                           : eval_term(S.part_er, (K.nblocks + kEvalGroup - 1) / kEvalGroup, K, term);
+    if (lane == 0) ecr[a] = t;
+  }
+  __syncthreads();
+  eval_finish(S.s, ecr, S.trace);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[8 * (kThreads / 32)];
   const Scalars *sc = S.s;
   const int cur = sc->cur;
   const bool avg = sc->sum_eta > 0.0;
@@ -443,33 +478,58 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> K, Mat<T> KT, Pro
 #pragma unroll
     for (int a = 0; a < 8; ++a) S.part_ec[8 * blockIdx.x + a] = acc[a];
   }
-  if (last_of(S.tickets + kTicketEvalRows, eval_ctas(K, KT))) eval_finalize(K, KT, S, red);
+  eval_arrive(K, KT, S, true);
 }
 
-// Finalisation of one evaluation (thread 0 of the last CTA of k_eval_rows).
-__device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er)[8], double *trace) {
+// Finalisation of one evaluation, by every thread of the CTA that finishes
+// it; ecr holds the column terms [8] then the row terms [8] (shared memory).
+// Float64 square roots and divisions take hundreds of cycles each on this
+// part, so each candidate's terms are split over threads of distinct warps
+// (thread 0 of warp 4 c + part), and the restart radius and 1 / sum_eta are
+// computed beside them; thread 0 then takes the decisions.
+__device__ void eval_finish(Scalars *s, const double *ecr, double *trace) {
+  __shared__ double s_pre[3];  // r^2 of both candidates under the current omega, 1 / sum_eta
   const bool avg = s->sum_eta > 0.0;
+  const double *ec = ecr, *er = ecr + 8;
+  if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) < 8) {
+    const int c = threadIdx.x >> 7, part = (threadIdx.x >> 5) & 3;
+    if (!(c == 1 && !avg)) {
+      double *k = s->kkt[c];
+      if (part == 0) {
+        const double pobj = ec[4 * c + 0] + er[4 * c + 3];
+        const double dobj = ec[4 * c + 2] + er[4 * c + 1];
+        const double gap = fabs(dobj - pobj);
+        k[0] = pobj;
+        k[1] = dobj;
+        k[2] = gap;
+        k[5] = gap / (1.0 + fabs(dobj) + fabs(pobj));
+      } else if (part == 1) {
+        const double pres = sqrt(er[4 * c + 0]);
+        k[3] = pres;
+        k[6] = pres / (1.0 + s->qnorm);
+      } else if (part == 2) {
+        const double dres = sqrt(ec[4 * c + 1]);
+        k[4] = dres;
+        k[7] = dres / (1.0 + s->cnorm);
+      } else {
+        s->cand_dx2[c] = ec[4 * c + 3];
+        s->cand_dy2[c] = er[4 * c + 2];
+        s_pre[c] = s->omega * ec[4 * c + 3] + er[4 * c + 2] / s->omega;
+        if (c == 0) s_pre[2] = avg ? 1.0 / s->sum_eta : 0.0;
+      }
+    } else if (part == 3) {
+      s_pre[1] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   bool pass[2] = {false, false};
   for (int c = 0; c < 2; ++c) {
     if (c == 1 && !avg) break;
-    const double pobj = ec[4 * c + 0] + er[4 * c + 3];
-    const double dobj = ec[4 * c + 2] + er[4 * c + 1];
-    const double pres = sqrt(er[4 * c + 0]), dres = sqrt(ec[4 * c + 1]);
-    const double gap = fabs(dobj - pobj);
-    double *k = s->kkt[c];
-    k[0] = pobj;
-    k[1] = dobj;
-    k[2] = gap;
-    k[3] = pres;
-    k[4] = dres;
-    k[5] = gap / (1.0 + fabs(dobj) + fabs(pobj));
-    k[6] = pres / (1.0 + s->qnorm);
-    k[7] = dres / (1.0 + s->cnorm);
-    s->cand_dx2[c] = ec[4 * c + 3];
-    s->cand_dy2[c] = er[4 * c + 2];
+    const double *k = s->kkt[c];
     pass[c] = k[5] <= s->rel_tol && k[6] <= s->rel_tol && k[7] <= s->rel_tol;
   }
-  s->inv_avg = avg ? 1.0 / s->sum_eta : 0.0;
+  s->inv_avg = s_pre[2];
   if (s->status == kRunning || s->status == kNumErr) {
     if (pass[0]) { s->status = kOptimal; s->ret_which = 0; }
     else if (pass[1]) { s->status = kOptimal; s->ret_which = 1; }
@@ -530,10 +590,12 @@ __device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er
     }
   }
   if (s->do_gap) {
+    // (do_gap needs adaptive restarts: omega did not change above)
     for (int c = 0; c < 2; ++c) {
-      const double r2 = (c == 1 && !avg) ? 0.0 : s->omega * s->cand_dx2[c] + s->cand_dy2[c] / s->omega;
+      const double r2 = s_pre[c];
       s->g_r2[c] = r2;
       s->g_omega[c] = s->omega;
+      s->g_inv_omega[c] = s->inv_omega;
       s->g_W[c] = s->g_V[c] = s->g_A[c] = 0.0;
       s->g_prefix[c] = 0u;
       s->g_active[c] = r2 > 0.0 ? 1 : 0;
@@ -549,7 +611,6 @@ __device__ void eval_finish(Scalars *s, const double (&ec)[8], const double (&er
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ double red[8 * (kThreads / 32)];
   Scalars *sc = S.s;
   const int cur = sc->cur;
   const bool avg = sc->sum_eta > 0.0;
@@ -596,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
 #pragma unroll
     for (int a = 0; a < 8; ++a) S.part_er[8 * blockIdx.x + a] = acc[a];
   }
-  if (last_of(S.tickets + kTicketEvalRows, eval_ctas(K, KT))) eval_finalize(K, KT, S, red);
+  eval_arrive(K, KT, S, false);
 }
 
 // --------------------------------------------- normalized gap (Section 3.2)
@@ -680,224 +741,441 @@ __device__ __forceinline__ void gap_digits(int pass, int &shift, int &nb, int &p
   pshift = pass == 0 ? 32 : (pass == 1 ? 21 : 10);
 }
 
-// Exclusive prefix (reverse = false: over lower threads; true: over higher
-// threads) of one double per thread, CTA-wide, fixed order.  `sh` holds 32
-// doubles.  Every thread of the CTA must call it.
-__device__ __forceinline__ double block_scan_excl(double v, bool reverse, double *sh) {
-  (void)v;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    if (!reverse) {
-      const double t = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += t;
-    } else {
-      const double t = __shfl_down_sync(0xffffffffu, x, o);
-      if (lane + o < 32) x += t;
-    }
-  }
-  __syncthreads();
-  if ((!reverse && lane == 31) || (reverse && lane == 0)) sh[warp] = x;  // warp totals
-  __syncthreads();
-  if (warp == 0) {
-    double w = lane < nw ? sh[lane] : 0.0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      if (!reverse) {
-        const double t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += t;
-      } else {
-        const double t = __shfl_down_sync(0xffffffffu, w, o);
-        if (lane + o < 32) w += t;
-      }
-    }
-    sh[lane] = w;  // inclusive scan of the warp totals (in the scan direction)
-  }
-  __syncthreads();
-  double before;
-  if (!reverse) before = warp > 0 ? sh[warp - 1] : 0.0;
-  else before = warp + 1 < nw ? sh[warp + 1] : 0.0;
-  // exclusive value: the neighbour's inclusive value (no subtraction, so no
-  // cancellation when this thread's own term dominates)
-  double ex;
-  if (!reverse) {
-    ex = __shfl_up_sync(0xffffffffu, x, 1);
-    if (lane == 0) ex = 0.0;
-  } else {
-    ex = __shfl_down_sync(0xffffffffu, x, 1);
-    if (lane == 31) ex = 0.0;
-  }
-  const double r = before + ex;
-  __syncthreads();
-  return r;
+// The last CTA of a gap pass selects up to two slots at once, one per group
+// of kSelThreads threads with its own named barrier.  A float64 instruction
+// holds its sub-partition's float64 unit for tens of cycles on this part
+// however few lanes are active, so the selection is written for few float64
+// instructions per warp: the groups take alternate warps (warp parity), so
+// that the two selections run on different sub-partitions; entries are
+// spread over as many warps as they fill; prefixes inside a thread are
+// sequential; sign, NaN and ordering tests on nonnegative values are integer
+// tests on their bits.
+constexpr int kSelThreads = 256;
+constexpr int kSelWarps = kSelThreads / 32;
+constexpr int kSelPer = kGapBuckets / kSelThreads;  // up to 8 buckets, then entries, per thread
+constexpr int kSelSmem = 3 * kGapBuckets + kGapBuckets / 2;  // doubles per group (w, v, a, bucket ids)
+static_assert(kGapThreads == 2 * kSelThreads, "two selection groups per CTA");
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kSelThreads) : "memory");
 }
 
-// Selection over one slot's global histogram, whole CTA (kGapThreads threads,
-// 4 consecutive buckets per thread).
-__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *sh) {
+// For nonnegative doubles (and +inf) the bit patterns order as the values;
+// a NaN pattern orders above +inf.
+__device__ __forceinline__ bool nonneg_less(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+__device__ __forceinline__ bool nonneg_positive(double a) { return __double_as_longlong(a) > 0ll; }
+
+// Exclusive scans over the first `nwa` warps of group g (group-local warp
+// index wg): wex and vex sum tw and tv over lower threads, asuf sums ta over
+// higher threads (inclusive scans by shuffles, then the neighbour's inclusive
+// value, so no subtraction).  Warps at and above nwa hold no entries and run
+// no float64 instruction; every thread of the group must call it.  `sh`
+// holds 6 x 32 doubles.
+__device__ __forceinline__ void scan3_active(double tw, double tv, double ta, int nwa, int g, int wg, double &wex,
+                                             double &vex, double &asuf, double *sh) {
+  const int lane = threadIdx.x & 31;
+  double xw = tw, xv = tv, xa = ta;
+  if (wg < nwa) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double pw = __shfl_up_sync(0xffffffffu, xw, o);
+      const double pv = __shfl_up_sync(0xffffffffu, xv, o);
+      const double pa = __shfl_down_sync(0xffffffffu, xa, o);
+      if (lane >= o) { xw += pw; xv += pv; }
+      if (lane + o < 32) xa += pa;
+    }
+    if (lane == 31) { sh[wg] = xw; sh[32 + wg] = xv; }
+    if (lane == 0) sh[64 + wg] = xa;
+  }
+  if (nwa > 1) {
+    group_sync(g);
+    if (wg == 0) {  // scans of the warp totals (at most kSelWarps of them)
+      double w = lane < nwa ? sh[lane] : 0.0, v = lane < nwa ? sh[32 + lane] : 0.0;
+      double a = lane < nwa ? sh[64 + lane] : 0.0;
+      for (int o = 1; o < nwa; o <<= 1) {
+        const double pw = __shfl_up_sync(0xffffffffu, w, o);
+        const double pv = __shfl_up_sync(0xffffffffu, v, o);
+        const double pa = __shfl_down_sync(0xffffffffu, a, o);
+        if (lane >= o) { w += pw; v += pv; }
+        if (lane + o < nwa) a += pa;
+      }
+      sh[96 + lane] = w;  // inclusive, in the scan direction
+      sh[128 + lane] = v;
+      sh[160 + lane] = a;
+    }
+    group_sync(g);
+  }
+  wex = vex = asuf = 0.0;
+  if (wg < nwa) {
+    double ew = __shfl_up_sync(0xffffffffu, xw, 1), ev = __shfl_up_sync(0xffffffffu, xv, 1);
+    double ea = __shfl_down_sync(0xffffffffu, xa, 1);
+    if (lane == 0) ew = ev = 0.0;
+    if (lane == 31) ea = 0.0;
+    wex = wg > 0 ? sh[96 + wg - 1] + ew : ew;
+    vex = wg > 0 ? sh[128 + wg - 1] + ev : ev;
+    asuf = wg + 1 < nwa ? sh[160 + wg + 1] + ea : ea;
+  }
+}
+
+// True when a bucket's three sums are all +0 (bit test: no float64 compare).
+__device__ __forceinline__ bool bucket_empty(double w, double v, double a) {
+  return (__double_as_longlong(w) | __double_as_longlong(v) | __double_as_longlong(a)) == 0ll;
+}
+
+// The slot's value mu = g^T d / r from the clipped sums (Wf, Vf) and the
+// unclipped coefficient Aa at the crossing t* (phi(t*) = r^2); r = sqrt(r^2)
+// computed beforehand.
+__device__ __forceinline__ void gap_final(Scalars *s, int slot, double Wf, double Vf, double Aa, double r2,
+                                          double r) {
+  double val = Vf;
+  if (nonneg_positive(Aa)) {
+    const double rem = r2 - Wf;
+    val = Vf + sqrt((nonneg_positive(rem) ? rem : 0.0) / Aa) * Aa;
+  }
+  s->gval[slot] = val;
+  s->mu[slot] = val / r;
+  s->g_active[slot] = 0;  // finished: later passes skip the slot
+}
+
+// Selection over one slot's global histogram ([3][kGapBuckets]: w, v, a) by
+// group g of the last CTA, which also clears the histogram for the next
+// pass; gin holds the slot's (W, V, A, r^2) below / after the range and
+// gpref its key prefix, as they stood when the pass started.  phi at bucket
+// lower edges is nondecreasing, and the crossing's clipped set only changes
+// at nonempty buckets, so the last NONEMPTY bucket whose lower edge has
+// phi < r^2 gives the same partition of the items as the last bucket of any
+// kind: the nonempty buckets are compacted in bucket order (ballots and
+// integer prefixes) and only they enter the float64 scans.  When the chosen
+// bucket holds no item (the crossing falls between nonempty buckets) or this
+// is the last digit, the slot's value is final.  `sh` is the group's part of
+// the kernel's histogram area (free after the flush), kSelSmem doubles.
+__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *sh, const double *gin, unsigned gpref,
+                           int g) {
   int shift, nb, pshift;
   gap_digits(pass, shift, nb, pshift);
-  constexpr int kPer = kGapBuckets / kGapThreads;  // 4
-  __shared__ double scan_sh[32];
-  __shared__ int s_best;
-  double w[kPer], v[kPer], a[kPer];
-  const int b0 = threadIdx.x * kPer;
+  __shared__ double scan_sh[2][6 * 32];
+  __shared__ double s_r[2];
+  __shared__ int s_cnt[2][kSelPer * kSelWarps];
+  __shared__ int s_off[2][kSelPer * kSelWarps + 1];
+  __shared__ int s_ff[2][kSelWarps];
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 6, t = wg * 32 + lane;  // group warps: parity g
+  double *cw = sh, *cv = sh + kGapBuckets, *ca = sh + 2 * kGapBuckets;
+  int *cb = reinterpret_cast<int *>(sh + 3 * kGapBuckets);
+  const double W0 = gin[0], V0 = gin[1], A0 = gin[2], r2 = gin[3];
+  // 1. load and clear the slot's buckets (thread t holds buckets t + r
+  // kSelThreads, so each warp load is contiguous); compact the nonempty ones
+  double w[kSelPer], v[kSelPer], a[kSelPer];
+  unsigned bal[kSelPer];
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const int b = b0 + k;
-    w[k] = b < nb ? __ldcg(gh + (size_t)b * 3 + 0) : 0.0;
-    v[k] = b < nb ? __ldcg(gh + (size_t)b * 3 + 1) : 0.0;
-    a[k] = b < nb ? __ldcg(gh + (size_t)b * 3 + 2) : 0.0;
-    gh[(size_t)b * 3 + 0] = 0.0;  // clear for the next pass
-    gh[(size_t)b * 3 + 1] = 0.0;
-    gh[(size_t)b * 3 + 2] = 0.0;
-  }
-  double tw = 0.0, tv = 0.0, ta = 0.0;
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) { tw += w[k]; tv += v[k]; ta += a[k]; }
-  const double W0 = s->g_W[slot], V0 = s->g_V[slot], A0 = s->g_A[slot], r2 = s->g_r2[slot];
-  const double wex = W0 + block_scan_excl(tw, false, scan_sh);
-  const double vex = V0 + block_scan_excl(tv, false, scan_sh);
-  const double asuf = A0 + block_scan_excl(ta, true, scan_sh);  // buckets after this thread's
-  const unsigned base = pass == 0 ? 0u : (s->g_prefix[slot] >> pshift) << pshift;
-  // per bucket: W below, V below, A at and after, A after
-  double Wb[kPer], Vb[kPer], Ain[kPer], Aout[kPer];
-  {
-    double cw = wex, cv = vex;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) { Wb[k] = cw; Vb[k] = cv; cw += w[k]; cv += v[k]; }
-    double ca = asuf;
-#pragma unroll
-    for (int k = kPer - 1; k >= 0; --k) { Aout[k] = ca; ca += a[k]; Ain[k] = ca; }
-  }
-  // phi is nondecreasing over the buckets with a real lower edge; the chosen
-  // bucket is the one before the first whose edge fails phi < r^2 (edges past
-  // +inf are NaN bit patterns and fail)
-  int first_fail = nb;
-#pragma unroll
-  for (int k = kPer - 1; k >= 0; --k) {
-    const int b = b0 + k;
-    if (b >= nb) continue;
-    const float Tf = __uint_as_float(base | ((unsigned)b << shift));
-    const double Tb = (double)Tf;
-    const double phi = Ain[k] > 0.0 ? Wb[k] + Tb * Tb * Ain[k] : Wb[k];
-    if (isnan(Tf) || !(phi < r2)) first_fail = b;
-  }
-  int bm = first_fail;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) bm = min(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-  __shared__ int wbest[32];
-  if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = bm;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int m = nb;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = min(m, wbest[q]);
-    s_best = m > 0 ? m - 1 : 0;  // bucket 0's lower edge has phi < r^2 by construction
-  }
-  __syncthreads();
-  const int bsel = s_best;
-  if (bsel >= b0 && bsel < b0 + kPer) {
-    const int k = bsel - b0;
-    s->g_W[slot] = Wb[k];
-    s->g_V[slot] = Vb[k];
-    s->g_A[slot] = Aout[k];
-    s->g_prefix[slot] = base | ((unsigned)bsel << shift);
-    if (pass == 2) {
-      // the items of the final bucket share one float key: count them as clipped
-      const double Wf = Wb[k] + w[k], Vf = Vb[k] + v[k], Aa = Aout[k];
-      double val = Vf;
-      if (Aa > 0.0) {
-        const double rem = r2 - Wf;
-        val = Vf + sqrt((rem > 0.0 ? rem : 0.0) / Aa) * Aa;
-      }
-      s->gval[slot] = val;
-      s->mu[slot] = val / sqrt(r2);
+  for (int r = 0; r < kSelPer; ++r) {
+    const int b = t + r * kSelThreads;
+    w[r] = v[r] = a[r] = 0.0;
+    if (b < nb) {
+      w[r] = __ldcg(gh + b);
+      v[r] = __ldcg(gh + kGapBuckets + b);
+      a[r] = __ldcg(gh + 2 * kGapBuckets + b);
     }
   }
-  __syncthreads();
-  (void)sh;
+  if (wg == kSelWarps - 1 && lane == 0) s_r[g] = sqrt(r2);  // for the final value, off the critical path
+#pragma unroll
+  for (int r = 0; r < kSelPer; ++r) {
+    const int b = t + r * kSelThreads;
+    if (b < nb) {
+      gh[b] = 0.0;
+      gh[kGapBuckets + b] = 0.0;
+      gh[2 * kGapBuckets + b] = 0.0;
+    }
+    bal[r] = __ballot_sync(0xffffffffu, b < nb && !bucket_empty(w[r], v[r], a[r]));
+    if (lane == 0) s_cnt[g][r * kSelWarps + wg] = __popc(bal[r]);
+  }
+  group_sync(g);
+  if (wg == 0) {  // exclusive prefix of the 64 (round, warp) counts, bucket order
+    const int c0 = s_cnt[g][2 * lane], c1 = s_cnt[g][2 * lane + 1];
+    int incl = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int p = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += p;
+    }
+    const int ex = incl - c0 - c1;
+    s_off[g][2 * lane] = ex;
+    s_off[g][2 * lane + 1] = ex + c0;
+    if (lane == 31) s_off[g][kSelPer * kSelWarps] = incl;
+  }
+  group_sync(g);
+  const int M = s_off[g][kSelPer * kSelWarps];
+  {
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSelPer; ++r) {
+      if (bal[r] & (1u << lane)) {
+        const int e = s_off[g][r * kSelWarps + wg] + __popc(bal[r] & below);
+        cw[e] = w[r];
+        cv[e] = v[r];
+        ca[e] = a[r];
+        cb[e] = t + r * kSelThreads;
+      }
+    }
+    // zeros after the last entry, up to the end of the last thread's entries
+    const int Mp = (M + 32 * kSelPer - 1) / (32 * kSelPer) * (32 * kSelPer);
+    for (int e = M + t; e < Mp && e < kGapBuckets; e += kSelThreads) {
+      cw[e] = 0.0;
+      cv[e] = 0.0;
+      ca[e] = 0.0;
+      cb[e] = 0;
+    }
+  }
+  group_sync(g);
+  if (M == 0) {
+    // no item in this digit's range: every edge gives the same partition
+    if (t == 0) gap_final(s, slot, W0, V0, A0, r2, s_r[g]);
+    return;
+  }
+  // 2. float64 scans over the M compacted entries: E consecutive ones per
+  // thread, E the smallest power of two with M <= E kSelThreads
+  const int E = M <= kSelThreads ? 1 : (M <= 2 * kSelThreads ? 2 : (M <= 4 * kSelThreads ? 4 : 8));
+  const int nwa = (M + 32 * E - 1) / (32 * E);  // warps holding entries
+  const int e0 = t * E;
+  const unsigned base = pass == 0 ? 0u : (gpref >> pshift) << pshift;
+  // entries past M read as zeros (the compacted area is zero-padded below)
+  double pw[kSelPer], pv[kSelPer], sa[kSelPer];  // inclusive prefixes (w, v) and suffix (a) in the thread
+  double tw = 0.0, tv = 0.0, ta = 0.0;
+  if (wg < nwa) {
+    pw[0] = tw = cw[e0];
+    pv[0] = tv = cv[e0];
+#pragma unroll
+    for (int k = 1; k < kSelPer; ++k) {
+      if (k >= E) break;
+      pw[k] = tw = pw[k - 1] + cw[e0 + k];
+      pv[k] = tv = pv[k - 1] + cv[e0 + k];
+    }
+#pragma unroll
+    for (int k = kSelPer - 1; k >= 0; --k) {
+      if (k >= E) continue;
+      sa[k] = k + 1 < E ? sa[k + 1 < kSelPer ? k + 1 : k] + ca[e0 + k] : ca[e0 + k];
+    }
+    ta = sa[0];
+  }
+  double wex, vex, asuf;
+  scan3_active(tw, tv, ta, nwa, g, wg, wex, vex, asuf, scan_sh[g]);
+  int ff = M;  // first compacted entry whose lower edge fails phi < r^2
+  double Wlo = 0.0, Vlo = 0.0, Ahi = 0.0;
+  if (wg < nwa) {
+    Wlo = W0 + wex;  // W below this thread's first entry
+    Vlo = V0 + vex;
+    Ahi = A0 + asuf;  // A after this thread's last entry
+#pragma unroll
+    for (int k = kSelPer - 1; k >= 0; --k) {
+      const int e = e0 + k;
+      if (k >= E || e >= M) continue;
+      // edges past +inf are NaN bit patterns and fail
+      const unsigned Tbits = base | ((unsigned)cb[e] << shift);
+      const double Tb = (double)__uint_as_float(Tbits);
+      const double Wb = k > 0 ? Wlo + pw[k > 0 ? k - 1 : 0] : Wlo;
+      const double Ain = Ahi + sa[k];
+      const double phi = nonneg_positive(Ain) ? fma(Tb * Tb, Ain, Wb) : Wb;
+      if ((Tbits & 0x7fffffffu) > 0x7f800000u || !nonneg_less(phi, r2)) ff = e;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ff = min(ff, __shfl_xor_sync(0xffffffffu, ff, o));
+  if (lane == 0) s_ff[g][wg] = ff;
+  group_sync(g);
+  ff = M;
+#pragma unroll
+  for (int q = 0; q < kSelWarps; ++q) ff = min(ff, s_ff[g][q]);
+  // 3. the chosen bucket and the sums below / after it
+  const int sel = ff > 0 ? ff - 1 : 0;
+  if (wg >= nwa || sel < e0 || sel >= e0 + E) return;
+  const int k = sel - e0;
+  // the chosen entry's in-thread sums (static register indices)
+  double pw_b = 0.0, pv_b = 0.0, sa_a = 0.0;
+  const double lw_k = cw[sel], lv_k = cv[sel];
+#pragma unroll
+  for (int kk = 0; kk < kSelPer; ++kk) {
+    if (kk != k) continue;
+    if (kk > 0) { pw_b = pw[kk > 0 ? kk - 1 : 0]; pv_b = pv[kk > 0 ? kk - 1 : 0]; }
+    if (kk + 1 < kSelPer) sa_a = sa[kk + 1 < kSelPer ? kk + 1 : kk];
+  }
+  const double Wb = k > 0 ? Wlo + pw_b : Wlo;
+  const double Vb = k > 0 ? Vlo + pv_b : Vlo;
+  const double Aout = k + 1 < E ? Ahi + sa_a : Ahi;
+  if (ff == 0 && cb[0] > 0) {
+    // the first nonempty bucket's edge already fails and it lies above the
+    // range's start: the crossing is in the empty buckets below it, and no
+    // item of the range is clipped
+    s->g_prefix[slot] = base | ((unsigned)(cb[0] - 1) << shift);
+    gap_final(s, slot, Wb, Vb, Ahi + sa[0], r2, s_r[g]);
+    return;
+  }
+  // (ff = 0 with the first bucket at the range's start: its own edge failed
+  // by rounding, and it is taken, as in a dense selection)
+  s->g_W[slot] = Wb;
+  s->g_V[slot] = Vb;
+  s->g_A[slot] = Aout;
+  s->g_prefix[slot] = base | ((unsigned)cb[sel] << shift);
+  // the items of the last digit's bucket share one float key: clipped
+  if (pass == 2) gap_final(s, slot, Wb + lw_k, Vb + lv_k, Aout, r2, s_r[g]);
 }
 
 __device__ void decide(Scalars *s, double *trace);
+__device__ void pw_candidate(Scalars *s, int c);
 
 template <typename T>
-__global__ void __launch_bounds__(kGapThreads) k_gap_pass(Problem<T> P, State<T> S, int pass, int s_begin,
+__global__ void __launch_bounds__(kGapThreads, 1) k_gap_pass(Problem<T> P, State<T> S, int pass, int s_begin,
                                                           int s_end, int when_restart, int with_decide) {
   extern __shared__ __align__(16) double hist[];  // [slots][3][kGapBuckets]
+  __shared__ double s_gin[kGapSlots][4];
+  __shared__ unsigned s_gpref[kGapSlots];
   Scalars *sc = S.s;
   if (when_restart ? !sc->restart : !sc->do_gap) return;  // uniform over the grid
+  // a launch covers slots s_begin + q, q < 2; per-slot state by q (registers)
+  bool act[2];
+  for (int q = 0; q < 2; ++q) act[q] = s_begin + q < s_end && sc->g_active[s_begin + q];
+  // every slot finished in an earlier pass (its decision, if any, was taken
+  // there); pass 0 still runs the decision when no slot was active at all
+  if (!act[0] && !act[1] && (pass > 0 || !with_decide)) return;
   const int ns = s_end - s_begin;
   int shift, nb, pshift;
   gap_digits(pass, shift, nb, pshift);
   for (int e = threadIdx.x; e < ns * 3 * kGapBuckets; e += blockDim.x) hist[e] = 0.0;
+  if (threadIdx.x < kGapSlots) {
+    const int q = threadIdx.x;
+    // the slot's selection state, read once here rather than by the last
+    // CTA's selection after the ticket
+    s_gin[q][0] = sc->g_W[q];
+    s_gin[q][1] = sc->g_V[q];
+    s_gin[q][2] = sc->g_A[q];
+    s_gin[q][3] = sc->g_r2[q];
+    s_gpref[q] = sc->g_prefix[q];
+  }
+  // Algorithm 3 for both candidates, beside this CTA's items (lanes 0 of
+  // warps 1 and 3: distinct sub-partitions)
+  if (pass == 0 && with_decide && blockIdx.x == gridDim.x - 1 && (threadIdx.x == 32 || threadIdx.x == 96))
+    pw_candidate(sc, threadIdx.x == 32 ? 0 : 1);
   __syncthreads();
   const int N = P.n + P.m;
-  bool act[kGapSlots];
-  unsigned pref[kGapSlots];
-  double om[kGapSlots], inv_om[kGapSlots], ainf[kGapSlots];
-  for (int s = 0; s < kGapSlots; ++s) {
-    act[s] = s >= s_begin && s < s_end && sc->g_active[s];
-    pref[s] = pass == 0 ? 0u : sc->g_prefix[s] >> pshift;
-    om[s] = sc->g_omega[s];
-    inv_om[s] = act[s] ? 1.0 / om[s] : 0.0;
-    ainf[s] = 0.0;
+  unsigned pref[2];
+  double om[2], inv_om[2], ainf[2];
+  int slot[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    slot[q] = act[q] ? s_begin + q : 0;
+    pref[q] = pass == 0 ? 0u : s_gpref[slot[q]] >> pshift;
+    om[q] = sc->g_omega[slot[q]];
+    inv_om[q] = sc->g_inv_omega[slot[q]];
+    ainf[q] = 0.0;
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    for (int s = s_begin; s < s_end; ++s) {
-      if (!act[s]) continue;
-      unsigned *keys = S.gkeys + (size_t)s * N;
-      GapItem it;
-      if (pass == 0) {
-        it = gap_item<T>(P, S, sc, s, i, om[s], inv_om[s]);
-        keys[i] = it.key;
+  const int stride = gridDim.x * blockDim.x;
+  if (pass == 0) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!act[q]) continue;
+        const GapItem it = gap_item<T>(P, S, sc, slot[q], i, om[q], inv_om[q]);
+        S.gkeys[(size_t)slot[q] * N + i] = it.key;
         if (it.key == kKeyNone) continue;
-        if (it.key == kKeyInf) { ainf[s] += it.a; continue; }
-      } else {
-        const unsigned key = keys[i];
-        if (key >= kKeyInf || (key >> pshift) != pref[s]) continue;  // none, inf, other bucket
-        it = gap_item<T>(P, S, sc, s, i, om[s], inv_om[s]);
+        if (it.key == kKeyInf) { ainf[q] += it.a; continue; }
+        const int b = (int)((it.key >> shift) & (unsigned)(nb - 1));
+        double *h = hist + (size_t)q * 3 * kGapBuckets;
+        atomicAdd(h + b, it.w);
+        atomicAdd(h + kGapBuckets + b, it.v);
+        atomicAdd(h + 2 * kGapBuckets + b, it.a);
       }
-      const int b = (int)((it.key >> shift) & (unsigned)(nb - 1));
-      double *h = hist + (size_t)(s - s_begin) * 3 * kGapBuckets;
-      atomicAdd(h + b, it.w);
-      atomicAdd(h + kGapBuckets + b, it.v);
-      atomicAdd(h + 2 * kGapBuckets + b, it.a);
+    }
+  } else {
+    // later digits: only the items of the selected bucket; the keys of
+    // kKeyBatch strided items are loaded together (the loop is bound by
+    // their latency, not by the few items that match)
+    constexpr int kKeyBatch = 4;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += kKeyBatch * stride) {
+      unsigned key[kKeyBatch][2];
+#pragma unroll
+      for (int u = 0; u < kKeyBatch; ++u) {
+        const int i = i0 + u * stride;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) key[u][q] = (act[q] && i < N) ? S.gkeys[(size_t)slot[q] * N + i] : kKeyNone;
+      }
+#pragma unroll
+      for (int u = 0; u < kKeyBatch; ++u) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const unsigned k = key[u][q];
+          if (k >= kKeyInf || (k >> pshift) != pref[q]) continue;  // none, inf, other bucket
+          const GapItem it = gap_item<T>(P, S, sc, slot[q], i0 + u * stride, om[q], inv_om[q]);
+          const int b = (int)((it.key >> shift) & (unsigned)(nb - 1));
+          double *h = hist + (size_t)q * 3 * kGapBuckets;
+          atomicAdd(h + b, it.w);
+          atomicAdd(h + kGapBuckets + b, it.v);
+          atomicAdd(h + 2 * kGapBuckets + b, it.a);
+        }
+      }
     }
   }
   if (pass == 0) {  // unbounded directions: their a goes to the +inf bucket, one atomic per warp
-    for (int s = s_begin; s < s_end; ++s) {
-      if (!act[s]) continue;
-      double t = ainf[s];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!act[q]) continue;
+      double t = ainf[q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if ((threadIdx.x & 31) == 0 && t != 0.0)
-        atomicAdd(hist + (size_t)(s - s_begin) * 3 * kGapBuckets + 2 * kGapBuckets + (kKeyInf >> 21), t);
+      if ((threadIdx.x & 31) == 0 && nonneg_positive(t))
+        atomicAdd(hist + (size_t)q * 3 * kGapBuckets + 2 * kGapBuckets + (kKeyInf >> 21), t);
     }
   }
   __syncthreads();
-  for (int s = s_begin; s < s_end; ++s) {
-    if (!act[s]) continue;
-    const double *h = hist + (size_t)(s - s_begin) * 3 * kGapBuckets;
-    double *gh = S.ghist + (size_t)s * kGapBuckets * 3;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      for (int a = 0; a < 3; ++a) {
-        const double v = h[a * kGapBuckets + b];
-        if (v != 0.0) atomicAdd(gh + (size_t)b * 3 + a, v);
-      }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!act[q]) continue;
+    const double *h = hist + (size_t)q * 3 * kGapBuckets;
+    double *gh = S.ghist + (size_t)slot[q] * kGapBuckets * 3;
+    for (int e = threadIdx.x; e < 3 * kGapBuckets; e += blockDim.x) {
+      if ((e & (kGapBuckets - 1)) >= nb) continue;
+      const double v = h[e];
+      if (__double_as_longlong(v) != 0ll) atomicAdd(gh + e, v);  // bit test, no float64 compare
     }
   }
   if (last_block(S.tickets + kTicketGap)) {
-    for (int s = s_begin; s < s_end; ++s) {
-      if (!act[s]) continue;
-      gap_select(sc, s, pass, S.ghist + (size_t)s * kGapBuckets * 3, hist);
+    // the active slots, one per selection group (group g = warp parity)
+    const int g = (threadIdx.x >> 5) & 1;
+    const int q = (act[0] && act[1]) ? g : (act[1] ? 1 : 0);
+    if (act[q] && (g == 0 || (act[0] && act[1]))) {
+      const int s = slot[q];
+      gap_select(sc, s, pass, S.ghist + (size_t)s * kGapBuckets * 3, hist + (size_t)g * kSelSmem, s_gin[s],
+                 s_gpref[s], g);
     }
-    // the restart decision as soon as the candidates' gaps are known
-    if (pass == 2 && with_decide && threadIdx.x == 0) decide(sc, S.trace);
+    __syncthreads();
+    // the restart decision as soon as the candidates' gaps are known (the
+    // pass in which the last of them finished; later passes return at once)
+    if (with_decide && threadIdx.x == 0) {
+      bool done = true;
+      for (int s = s_begin; s < s_end; ++s) done = done && !sc->g_active[s];
+      if (done) decide(sc, S.trace);
+    }
   }
 }
 
 // --------------------------------------------------- restart (Section 3.2)
+
+// Algorithm 3 for candidate c (Delta = the candidate's distances to
+// z^{n,0}), should the restart take it: the new primal weight, its
+// reciprocal and the radius^2 of the restart point's gap under it.  Computed
+// early in the candidates' first gap pass (a float64 square root, logarithm
+// or exponential takes several hundred cycles on this part), so that the
+// decision itself is a choice.
+__device__ void pw_candidate(Scalars *s, int c) {
+  if (c == 1 && !(s->sum_eta > 0.0)) return;
+  const double dx2 = s->cand_dx2[c], dy2 = s->cand_dy2[c];
+  const double Dx = sqrt(dx2), Dy = sqrt(dy2);
+  double om = s->omega;
+  if (s->pw_update && Dx > s->eps_zero && Dy > s->eps_zero)
+    om = exp(s->pw_theta * log(Dy / Dx) + (1.0 - s->pw_theta) * log(om));
+  s->pw_omega[c] = om;
+  s->pw_inv[c] = 1.0 / om;
+  s->pw_r2[c] = om * dx2 + dy2 / om;
+}
 
 // GetRestartCandidate, criteria (i)-(iii) and Algorithm 3.  One thread (of
 // the last CTA of the candidates' final gap pass).
@@ -934,18 +1212,17 @@ __device__ void decide(Scalars *s, double *trace) {
   rec[14] = s->kkt[1][6];
   rec[15] = s->kkt[1][7];
   if (!restart) return;
-  const double dx2 = s->cand_dx2[cand], dy2 = s->cand_dy2[cand];
-  const double Dx = sqrt(dx2), Dy = sqrt(dy2);
-  if (s->pw_update && Dx > s->eps_zero && Dy > s->eps_zero)
-    s->omega = exp(s->pw_theta * log(Dy / Dx) + (1.0 - s->pw_theta) * log(s->omega));
-  s->inv_omega = 1.0 / s->omega;
+  // Algorithm 3 for the chosen candidate, computed by pw_candidate
+  s->omega = s->pw_omega[cand];
+  s->inv_omega = s->pw_inv[cand];
   s->tau = s->eta * s->inv_omega;
   s->sigma = s->eta * s->omega;
   rec[7] = s->omega;
   // slot 2: mu_n(z^{n+1,0}, z^{n,0}) under the new primal weight
-  const double r2 = s->omega * dx2 + dy2 / s->omega;
+  const double r2 = s->pw_r2[cand];
   s->g_r2[2] = r2;
   s->g_omega[2] = s->omega;
+  s->g_inv_omega[2] = s->inv_omega;
   s->g_W[2] = s->g_V[2] = s->g_A[2] = 0.0;
   s->g_prefix[2] = 0u;
   s->g_active[2] = r2 > 0.0 ? 1 : 0;
@@ -1182,8 +1459,8 @@ __global__ void k_output(Problem<T> P, State<T> S) {
 
 // histogram of `ns` slots; the selection also needs room for 2049 suffix sums
 static size_t gap_smem(int ns) {
-  const int rows = 3 * ns > 4 ? 3 * ns : 4;
-  return sizeof(double) * ((size_t)rows * kGapBuckets + 8);
+  const size_t hist = (size_t)3 * ns * kGapBuckets, sel = (size_t)ns * kSelSmem;
+  return sizeof(double) * ((hist > sel ? hist : sel) + 8);
 }
 
 template <typename T>
