@@ -54,7 +54,7 @@ struct pdlp_ctx {
   int64_t nnz = 0;
   pdlp_options opts;
   cudaStream_t st = nullptr;           // caller's stream
-  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams (library-owned)
+  cudaStream_t cap[4] = {nullptr, nullptr, nullptr, nullptr};  // capture streams (library-owned)
   std::string err;
   // matrix (float64 master copy, preconditioned in place)
   DevBuf rp, ci, val, trp, tci, tval, perm, rowid;  // rowid: row of every nonzero of K
@@ -259,7 +259,10 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   S.tickets = dalloc<unsigned>(pr.tickets, nticket);
   S.gtickets = S.tickets ? S.tickets + kNumTickets : nullptr;
   S.gkeys = dalloc<unsigned>(pr.gkeys, (size_t)kGapSlots * N);
-  S.ghist = dalloc<double>(pr.ghist, (size_t)kGapSlots * kGapBuckets * 3);
+  // the gap histograms, then their bitmaps of nonempty buckets (1 bit each)
+  const size_t ghist_n = (size_t)kGapSlots * kGapBuckets * 3 + (size_t)kGapSlots * kGapBuckets / 64;
+  S.ghist = dalloc<double>(pr.ghist, ghist_n);
+  S.gmask = S.ghist ? reinterpret_cast<unsigned *>(S.ghist + (size_t)kGapSlots * kGapBuckets * 3) : nullptr;
   S.xo = dalloc<double>(pr.xo, n);
   S.yo = dalloc<double>(pr.yo, m);
   S.s = reinterpret_cast<Scalars *>(ctx->scal.ptr());
@@ -269,7 +272,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   if (!S.tickets || !S.gkeys || !S.ghist || !S.xo || !S.yo || !normpart)
     return fail(ctx, PDLP_ERR_OOM, "state allocation failed");
   CK(cudaMemsetAsync(S.tickets, 0, sizeof(unsigned) * nticket, ctx->st), "memset");
-  CK(cudaMemsetAsync(S.ghist, 0, sizeof(double) * kGapSlots * kGapBuckets * 3, ctx->st), "memset");
+  CK(cudaMemsetAsync(S.ghist, 0, sizeof(double) * ghist_n, ctx->st), "memset");
   CK(cudaMemsetAsync(normpart, 0, sizeof(double) * (4 * 152 + 8), ctx->st), "memset");
   CK(set_kernel_attributes<T>(), "kernel attributes");
   CK(cudaStreamSynchronize(ctx->st), "sync");
@@ -315,7 +318,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   CK(build_solve_graph<T>(pr.K, pr.KT, pr.P, pr.S, in, o.primal_importance, normpart,
                           reinterpret_cast<const double *>(ctx->xin.ptr()),
                           reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.pg, ctx->cap[0],
-                          ctx->cap[1], ctx->cap[2], &pr.graph),
+                          ctx->cap[1], ctx->cap[2], ctx->cap[3], &pr.graph),
      "graph capture");
   pr.ready = true;
   return PDLP_OK;

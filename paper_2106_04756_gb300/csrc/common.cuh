@@ -173,6 +173,7 @@ struct State {
   Scalars *s;
   unsigned int *gkeys;         // gap keys [kGapSlots][n + m]
   double *ghist;               // gap histogram [kGapSlots][3][kGapBuckets] (w, v, a)
+  unsigned int *gmask;         // nonempty buckets of the gap histogram [kGapSlots][kGapBuckets / 32]
   double *xo, *yo;             // returned point (original space, float64)
   double *trace;               // [kTraceCap][kTraceLen]
   double *eta_log;             // nullable: step size of each accepted step, by step index

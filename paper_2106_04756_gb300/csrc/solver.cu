@@ -395,22 +395,45 @@ __device__ __forceinline__ unsigned eval_groups(const Mat<T> &K, const Mat<T> &K
   return (unsigned)(gc + (K.nblocks + kEvalGroup - 1) / kEvalGroup);
 }
 
-// Sum of one term over `ng` group partials (stride kEvalGroup CTAs) and the
-// long rows of A, by one warp; valid in lane 0.
+// Sums of two terms (t0, t0 + 1) over `ng` group partials (stride kEvalGroup
+// CTAs) and the long rows of A, by one warp, valid in lane 0: every load is
+// issued before any sum (one round trip), and each term takes one shuffle
+// reduction.
 template <typename T>
-__device__ __forceinline__ double eval_term(const double *part, int ng, const Mat<T> &A, int term) {
+__device__ __forceinline__ void eval_terms2(const double *part, int ng, const Mat<T> &A, int t0, double (&out)[2]) {
   const int lane = threadIdx.x & 31;
-  double t = 0.0, l = 0.0;
-  for (int g = lane; g < ng; g += 32) t += __ldcg(part + (size_t)g * kEvalGroup * 8 + term);
+  double acc[2][4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-  if (A.nlong > 0) {
-    for (int r = lane; r < A.nlong; r += 32) l += __ldcg(A.lr_acc + (size_t)r * kLrAcc + term);
+  for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    t += l;
+    for (int u = 0; u < 4; ++u) acc[q][u] = 0.0;
+  for (int g0 = lane; g0 < ng; g0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int g = g0 + 32 * u;
+      if (g < ng) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q][u] += __ldcg(part + (size_t)g * kEvalGroup * 8 + t0 + q);
+      }
+    }
   }
-  return t;
+  for (int r0 = lane; r0 < A.nlong; r0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + 32 * u;
+      if (r < A.nlong) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q][u] += __ldcg(A.lr_acc + (size_t)r * kLrAcc + t0 + q);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double t = (acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    out[q] = t;
+  }
 }
 
 // Called by every CTA of k_eval_cols (cols = true) and k_eval_rows after its
@@ -432,12 +455,12 @@ __device__ void eval_arrive(const Mat<T> &K, const Mat<T> &KT, const State<T> &S
   if (lane == 0) part[(size_t)g0 * 8 + warp] = v;
   if (!last_of(S.tickets + kTicketEvalRows, eval_groups(K, KT))) return;
   // warp w: terms 2w and 2w + 1 of [column terms (8), row terms (8)]
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int a = 2 * warp + q, term = a & 7;
-    const double t = a < 8 ? eval_term(S.part_ec, gc, KT, term)
-                           : eval_term(S.part_er, (K.nblocks + kEvalGroup - 1) / kEvalGroup, K, term);
-    if (lane == 0) ecr[a] = t;
+  double t2[2];
+  if (warp < 4) eval_terms2(S.part_ec, gc, KT, 2 * warp, t2);
+  else eval_terms2(S.part_er, (K.nblocks + kEvalGroup - 1) / kEvalGroup, K, 2 * warp - 8, t2);
+  if (lane == 0) {
+    ecr[2 * warp] = t2[0];
+    ecr[2 * warp + 1] = t2[1];
   }
   __syncthreads();
   eval_finish(S.s, ecr, S.trace);
@@ -755,6 +778,7 @@ constexpr int kSelWarps = kSelThreads / 32;
 constexpr int kSelPer = kGapBuckets / kSelThreads;  // up to 8 buckets, then entries, per thread
 constexpr int kSelSmem = 3 * kGapBuckets + kGapBuckets / 2;  // doubles per group (w, v, a, bucket ids)
 static_assert(kGapThreads == 2 * kSelThreads, "two selection groups per CTA");
+static_assert(1024 % kGapThreads == 0 && kGapBuckets % kGapThreads == 0, "flush ballots: whole warps per bucket");
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(kSelThreads) : "memory");
@@ -850,49 +874,34 @@ __device__ __forceinline__ void gap_final(Scalars *s, int slot, double Wf, doubl
 // integer prefixes) and only they enter the float64 scans.  When the chosen
 // bucket holds no item (the crossing falls between nonempty buckets) or this
 // is the last digit, the slot's value is final.  `sh` is the group's part of
-// the kernel's histogram area (free after the flush), kSelSmem doubles.
-__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *sh, const double *gin, unsigned gpref,
-                           int g) {
+// the kernel's histogram area (free after the flush), kSelSmem doubles; mk
+// the slot's bitmap of nonempty buckets.
+__device__ void gap_select(Scalars *s, int slot, int pass, double *gh, unsigned *mk, double *sh, const double *gin,
+                           unsigned gpref, int g) {
   int shift, nb, pshift;
   gap_digits(pass, shift, nb, pshift);
   __shared__ double scan_sh[2][6 * 32];
   __shared__ double s_r[2];
-  __shared__ int s_cnt[2][kSelPer * kSelWarps];
-  __shared__ int s_off[2][kSelPer * kSelWarps + 1];
+  __shared__ unsigned s_word[2][kGapBuckets / 32];
+  __shared__ int s_off[2][kGapBuckets / 32 + 1];
   __shared__ int s_ff[2][kSelWarps];
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 6, t = wg * 32 + lane;  // group warps: parity g
   double *cw = sh, *cv = sh + kGapBuckets, *ca = sh + 2 * kGapBuckets;
   int *cb = reinterpret_cast<int *>(sh + 3 * kGapBuckets);
   const double W0 = gin[0], V0 = gin[1], A0 = gin[2], r2 = gin[3];
-  // 1. load and clear the slot's buckets (thread t holds buckets t + r
-  // kSelThreads, so each warp load is contiguous); compact the nonempty ones
-  double w[kSelPer], v[kSelPer], a[kSelPer];
-  unsigned bal[kSelPer];
-#pragma unroll
-  for (int r = 0; r < kSelPer; ++r) {
-    const int b = t + r * kSelThreads;
-    w[r] = v[r] = a[r] = 0.0;
-    if (b < nb) {
-      w[r] = __ldcg(gh + b);
-      v[r] = __ldcg(gh + kGapBuckets + b);
-      a[r] = __ldcg(gh + 2 * kGapBuckets + b);
-    }
+  // 1. the nonempty buckets, from the slot's bitmap (every CTA's flush sets
+  // the bits of the buckets it added to), compacted in bucket order; only
+  // they are loaded from the histogram, then cleared with their bits
+  constexpr int kWords = kGapBuckets / 32;
+  if (t < kWords) {
+    const unsigned wv = t < nb / 32 ? __ldcg(mk + t) : 0u;
+    s_word[g][t] = wv;
+    if (wv) mk[t] = 0u;
   }
   if (wg == kSelWarps - 1 && lane == 0) s_r[g] = sqrt(r2);  // for the final value, off the critical path
-#pragma unroll
-  for (int r = 0; r < kSelPer; ++r) {
-    const int b = t + r * kSelThreads;
-    if (b < nb) {
-      gh[b] = 0.0;
-      gh[kGapBuckets + b] = 0.0;
-      gh[2 * kGapBuckets + b] = 0.0;
-    }
-    bal[r] = __ballot_sync(0xffffffffu, b < nb && !bucket_empty(w[r], v[r], a[r]));
-    if (lane == 0) s_cnt[g][r * kSelWarps + wg] = __popc(bal[r]);
-  }
   group_sync(g);
-  if (wg == 0) {  // exclusive prefix of the 64 (round, warp) counts, bucket order
-    const int c0 = s_cnt[g][2 * lane], c1 = s_cnt[g][2 * lane + 1];
+  if (wg == 0) {  // exclusive prefix of the 64 word populations
+    const int c0 = __popc(s_word[g][2 * lane]), c1 = __popc(s_word[g][2 * lane + 1]);
     int incl = c0 + c1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -902,21 +911,27 @@ __device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *s
     const int ex = incl - c0 - c1;
     s_off[g][2 * lane] = ex;
     s_off[g][2 * lane + 1] = ex + c0;
-    if (lane == 31) s_off[g][kSelPer * kSelWarps] = incl;
+    if (lane == 31) s_off[g][kWords] = incl;
   }
   group_sync(g);
-  const int M = s_off[g][kSelPer * kSelWarps];
+  const int M = s_off[g][kWords];
   {
-    const unsigned below = (1u << lane) - 1u;
+    const int w = t >> 2, qd = t & 3;  // word w, bits [8 qd, 8 qd + 8)
+    const unsigned word = s_word[g][w];
+    const unsigned bits = (word >> (8 * qd)) & 0xffu;
+    const int ew = s_off[g][w] + __popc(word & ((1u << (8 * qd)) - 1u));
 #pragma unroll
-    for (int r = 0; r < kSelPer; ++r) {
-      if (bal[r] & (1u << lane)) {
-        const int e = s_off[g][r * kSelWarps + wg] + __popc(bal[r] & below);
-        cw[e] = w[r];
-        cv[e] = v[r];
-        ca[e] = a[r];
-        cb[e] = t + r * kSelThreads;
-      }
+    for (int j = 0; j < 8; ++j) {
+      if (!(bits & (1u << j))) continue;
+      const int b = 32 * w + 8 * qd + j;
+      const int e = ew + __popc(bits & ((1u << j) - 1u));
+      cw[e] = __ldcg(gh + b);
+      cv[e] = __ldcg(gh + kGapBuckets + b);
+      ca[e] = __ldcg(gh + 2 * kGapBuckets + b);
+      cb[e] = b;
+      gh[b] = 0.0;
+      gh[kGapBuckets + b] = 0.0;
+      gh[2 * kGapBuckets + b] = 0.0;
     }
     // zeros after the last entry, up to the end of the last thread's entries
     const int Mp = (M + 32 * kSelPer - 1) / (32 * kSelPer) * (32 * kSelPer);
@@ -935,7 +950,9 @@ __device__ void gap_select(Scalars *s, int slot, int pass, double *gh, double *s
   }
   // 2. float64 scans over the M compacted entries: E consecutive ones per
   // thread, E the smallest power of two with M <= E kSelThreads
-  const int E = M <= kSelThreads ? 1 : (M <= 2 * kSelThreads ? 2 : (M <= 4 * kSelThreads ? 4 : 8));
+  // (each warp pays a fixed shuffle scan: as few warps as the entries
+  // allow, but not fewer than the group's two sub-partitions can run)
+  const int E = M <= 64 ? 1 : (M <= 128 ? 2 : (M <= 256 ? 4 : 8));
   const int nwa = (M + 32 * E - 1) / (32 * E);  // warps holding entries
   const int e0 = t * E;
   const unsigned base = pass == 0 ? 0u : (gpref >> pshift) << pshift;
@@ -1131,10 +1148,16 @@ __global__ void __launch_bounds__(kGapThreads, 1) k_gap_pass(Problem<T> P, State
     if (!act[q]) continue;
     const double *h = hist + (size_t)q * 3 * kGapBuckets;
     double *gh = S.ghist + (size_t)slot[q] * kGapBuckets * 3;
-    for (int e = threadIdx.x; e < 3 * kGapBuckets; e += blockDim.x) {
-      if ((e & (kGapBuckets - 1)) >= nb) continue;
-      const double v = h[e];
-      if (__double_as_longlong(v) != 0ll) atomicAdd(gh + e, v);  // bit test, no float64 compare
+    unsigned *gm = S.gmask + (size_t)slot[q] * (kGapBuckets / 32);
+    // nb is a multiple of the CTA size: every lane takes each ballot
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const double hw = h[b], hv = h[kGapBuckets + b], ha = h[2 * kGapBuckets + b];
+      // bit tests, no float64 compares
+      if (__double_as_longlong(hw) != 0ll) atomicAdd(gh + b, hw);
+      if (__double_as_longlong(hv) != 0ll) atomicAdd(gh + kGapBuckets + b, hv);
+      if (__double_as_longlong(ha) != 0ll) atomicAdd(gh + 2 * kGapBuckets + b, ha);
+      const unsigned bal = __ballot_sync(0xffffffffu, !bucket_empty(hw, hv, ha));
+      if ((threadIdx.x & 31) == 0 && bal) atomicOr(gm + (b >> 5), bal);
     }
   }
   if (last_block(S.tickets + kTicketGap)) {
@@ -1143,8 +1166,8 @@ __global__ void __launch_bounds__(kGapThreads, 1) k_gap_pass(Problem<T> P, State
     const int q = (act[0] && act[1]) ? g : (act[1] ? 1 : 0);
     if (act[q] && (g == 0 || (act[0] && act[1]))) {
       const int s = slot[q];
-      gap_select(sc, s, pass, S.ghist + (size_t)s * kGapBuckets * 3, hist + (size_t)g * kSelSmem, s_gin[s],
-                 s_gpref[s], g);
+      gap_select(sc, s, pass, S.ghist + (size_t)s * kGapBuckets * 3, S.gmask + (size_t)s * (kGapBuckets / 32),
+                 hist + (size_t)g * kSelSmem, s_gin[s], s_gpref[s], g);
     }
     __syncthreads();
     // the restart decision as soon as the candidates' gaps are known (the
@@ -1265,17 +1288,11 @@ __global__ void k_apply_restart(Problem<T> P, State<T> S) {
 }
 
 __device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
-                             int has_inner, int has_cond);
+                             int has_inner, int has_cond, cudaGraphConditionalHandle h_rs, int has_rs);
 
-// End of an evaluation: book-keeping of the restart and the loop conditions
-// (the Algorithm 2 factors of the next chunk are filled by k_eval_rows).
-__global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
-                         int has_inner, int has_cond = 1) {
-  if (threadIdx.x == 0) finish_state(s, h_outer, h_inner, has_inner, has_cond);
-}
-
-__device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
-                             int has_inner, int has_cond) {
+// After the restart point's gap (slot 2): mu_0 of the new outer loop, empty
+// running sums, the restart counted.
+__device__ __forceinline__ void restart_done(Scalars *s) {
   if (s->restart) {
     s->mu0 = s->mu[2];
     s->sum_eta = 0.0;
@@ -1284,8 +1301,28 @@ __device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cud
     s->restarts += 1;
     s->restart = 0;
   }
-  s->do_gap = 0;
   s->vrestart = 0;
+}
+
+// End of an evaluation: the loop conditions, and (has_rs) the condition of
+// the graph's restart branch (apply restart, restart point's gap,
+// k_restart_done), which then follows; without has_rs that branch already
+// ran and its book-keeping happens here.  (The Algorithm 2 factors of the
+// next chunk are filled by k_eval_rows.)
+__global__ void k_finish(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
+                         int has_inner, int has_cond = 1, cudaGraphConditionalHandle h_rs = 0, int has_rs = 0) {
+  if (threadIdx.x == 0) finish_state(s, h_outer, h_inner, has_inner, has_cond, h_rs, has_rs);
+}
+
+__global__ void k_restart_done(Scalars *s) {
+  if (threadIdx.x == 0) restart_done(s);
+}
+
+__device__ void finish_state(Scalars *s, cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner,
+                             int has_inner, int has_cond, cudaGraphConditionalHandle h_rs, int has_rs) {
+  if (has_rs) cudaGraphSetConditional(h_rs, (s->restart || s->vrestart) ? 1u : 0u);
+  else restart_done(s);
+  s->do_gap = 0;
   s->chunk_acc = 0;
   if (s->err) s->status = kWaitTimeout;
   if (s->status == kRunning && time_up(s)) s->status = kTimeLimit;
@@ -1625,7 +1662,8 @@ static cudaError_t capture_graph(cudaStream_t st, cudaGraph_t *g) {
 
 // Appends a conditional WHILE node on handle h (created in the capturing
 // graph) after everything captured so far on `st`; returns its body graph.
-static cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+static cudaError_t add_cond(cudaStream_t st, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            cudaGraph_t *body) {
   cudaError_t e;
   cudaStreamCaptureStatus cs;
   cudaGraph_t g;
@@ -1635,12 +1673,30 @@ static cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cuda
   cudaGraphNodeParams p = {};
   p.type = cudaGraphNodeTypeConditional;
   p.conditional.handle = h;
-  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.type = type;
   p.conditional.size = 1;
   cudaGraphNode_t node;
   if ((e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p))) return e;
   *body = p.conditional.phGraph_out[0];
   return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// IF (restart or virtual restart) { apply restart, gap of the restart point
+// (slot 2), restart book-keeping }, captured on st4 into the branch's body.
+template <typename T>
+static cudaError_t add_restart_branch(const Problem<T> &P, const State<T> &S, int gap_grid,
+                                      cudaGraphConditionalHandle h_rs, cudaStream_t st2, cudaStream_t st4) {
+  cudaGraph_t body = nullptr;
+  cudaError_t e = add_cond(st2, h_rs, cudaGraphCondTypeIf, &body);
+  if (!e) e = cudaStreamBeginCaptureToGraph(st4, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e) return e;
+  const int N = P.n + P.m;
+  k_apply_restart<T><<<(N + 255) / 256, 256, 0, st4>>>(P, S);
+  launch_gap<T>(P, S, 2, 3, 1, gap_grid, st4);
+  k_restart_done<<<1, 32, 0, st4>>>(S.s);
+  cudaGraph_t tmp;
+  cudaError_t e2 = cudaStreamEndCapture(st4, &tmp);
+  return e2;
 }
 
 // The whole solve as one graph:
@@ -1657,7 +1713,8 @@ template <typename T>
 cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               const ScalarInit &in, double primal_importance, double *norm_part,
                               const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
-                              cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec) {
+                              cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaStream_t st4,
+                              cudaGraphExec_t *exec) {
   cudaError_t e;
   cudaGraph_t graph = nullptr;
   *exec = nullptr;
@@ -1682,14 +1739,16 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
   k_init_point<T><<<(N + 255) / 256, 256, 0, st>>>(P, S, x0_dev, y0_dev);
   launch_spmv<T>(K, S.x[0], S.Kx[0], st);
   launch_eval<T>(K, KT, P, S, st);
-  cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
+  cudaGraphConditionalHandle h_outer = 0, h_inner = 0, h_rs = 0;
   cudaGraph_t g = nullptr, body_outer = nullptr, body_inner = nullptr;
   e = capture_graph(st, &g);
   if (!e) e = cudaGraphConditionalHandleCreate(&h_outer, g, 0u, cudaGraphCondAssignDefault);
   if (!e) {
     k_finish<<<1, 64, 0, st>>>(S.s, h_outer, h_outer, 0);  // loop entry decided by the check at the start
-    e = add_while(st, h_outer, &body_outer);
+    e = add_cond(st, h_outer, cudaGraphCondTypeWhile, &body_outer);
   }
+  // the restart branch's condition: set by k_finish in every evaluation
+  if (!e) e = cudaGraphConditionalHandleCreate(&h_rs, body_outer, 0u, 0u);
   if (!e) e = cudaStreamBeginCaptureToGraph(st2, body_outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (!e && pg.grid > 0) {
     // one persistent cooperative kernel per chunk of step attempts
@@ -1697,16 +1756,15 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     if (!e) {
       launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
       launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2, 1);  // with the restart decision
-      k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
-      launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
-      k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_outer, 0);
+      k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_outer, 0, 1, h_rs, 1);
+      e = add_restart_branch<T>(P, S, gap_grid, h_rs, st2, st4);
     }
     cudaGraph_t tmp2;
     cudaError_t e2 = cudaStreamEndCapture(st2, &tmp2);
     if (!e) e = e2;
   } else if (!e) {
     e = cudaGraphConditionalHandleCreate(&h_inner, body_outer, 1u, cudaGraphCondAssignDefault);
-    if (!e) e = add_while(st2, h_inner, &body_inner);
+    if (!e) e = add_cond(st2, h_inner, cudaGraphCondTypeWhile, &body_inner);
     if (!e) e = cudaStreamBeginCaptureToGraph(st3, body_inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (!e) {
       if (in.mp) {
@@ -1720,9 +1778,8 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     if (!e) {
       launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
       launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2, 1);  // with the restart decision
-      k_apply_restart<T><<<(N + 255) / 256, 256, 0, st2>>>(P, S);
-      launch_gap<T>(P, S, 2, 3, 1, gap_grid, st2);
-      k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_inner, 1);
+      k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_inner, 1, 1, h_rs, 1);
+      e = add_restart_branch<T>(P, S, gap_grid, h_rs, st2, st4);
     }
     cudaGraph_t tmp2;
     cudaError_t e2 = cudaStreamEndCapture(st2, &tmp2);
@@ -1854,10 +1911,10 @@ template cudaError_t run_stepped<float>(const Mat<float> &, const Mat<float> &, 
 template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
                                                const State<double> &, const ScalarInit &, double, double *,
                                                const double *, const double *, int, const PersistGeo &, cudaStream_t,
-                                               cudaStream_t, cudaStream_t, cudaGraphExec_t *);
+                                               cudaStream_t, cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 template cudaError_t build_solve_graph<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                               const State<float> &, const ScalarInit &, double, double *,
                                               const double *, const double *, int, const PersistGeo &, cudaStream_t,
-                                              cudaStream_t, cudaStream_t, cudaGraphExec_t *);
+                                              cudaStream_t, cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 
 }  // namespace pdlp

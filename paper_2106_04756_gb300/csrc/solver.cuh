@@ -55,7 +55,8 @@ template <typename T>
 cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                               const ScalarInit &in, double primal_importance, double *norm_part,
                               const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
-                              cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaGraphExec_t *exec);
+                              cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaStream_t st4,
+                              cudaGraphExec_t *exec);
 // Persistent step kernel (persistent.cu).  mode 0: off.  Leaves pg->grid = 0
 // when the kernel's layout does not fit or no chunk assignment exists for
 // its grid (assign_nw warps).  cmax_*: most chunks of one warp.
