@@ -31,11 +31,13 @@ struct Precision {
   DevBuf vecs;       // every iterate vector, one allocation
   DevBuf parts, gkeys, ghist, xo, yo, tickets, normpart, trace;
   Mat<T> K, KT;
+  Mat<T> KTb;       // KT with the second long-row buffers (the persistent evaluation's phase B)
   Problem<T> P;
   State<T> S;
   ScalarInit init{};
   double *normpart_ptr = nullptr;
   PersistGeo pg{};  // persistent step kernel layout (grid 0: one launch per half-step)
+  PersistGeo pe{};  // persistent evaluation kernel layout (grid 0: the separate evaluation kernels)
   cudaGraphExec_t graph = nullptr;
   ~Precision() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -60,6 +62,7 @@ struct pdlp_ctx {
   DevBuf rp, ci, val, trp, tci, tval, perm, rowid;  // rowid: row of every nonzero of K
   DevBuf blocksK, blocksKT, longK, longKT, segK, segKT, segcntK, segcntKT, lraccK, lraccKT;
   int32_t nlongK = 0, nlongKT = 0;
+  int32_t nsegKT = 0;  // segment partials of K^T's long rows (per gathered vector)
   DevBuf wchunkK, woffK, wchunkKT, woffKT;  // chunk lists of the persistent kernel's warps
   int32_t cmaxK = 0, cmaxKT = 0, assign_nw = 0;
   // fixed-size slabs of K and K^T (the slab step kernels)
@@ -242,9 +245,17 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
                     (double)sizeof(T) * (9.0 * ctx->n + 10.0 * ctx->m);
   const int l1g = ctx->opts.persistent == 4 ? 1 : (ctx->opts.persistent == 3 ? 0 : (ws > kL1GatherBytes ? 1 : 0));
   CK(persist_plan<T>(ctx->cmaxKT, ctx->cmaxK, ctx->assign_nw, persist_mode, l1g, &pr.pg), "persistent kernel layout");
+  CK(eval_plan<T>(pr.pg, ctx->cmaxKT, ctx->cmaxK, &pr.pe), "persistent evaluation layout");
+  // K^T for the persistent evaluation's second walk: segment partials in the
+  // second half of the (two-vector) area, the second set of counters, and
+  // epilogue slots 4..7 of each long row
+  pr.KTb = pr.KT;
+  pr.KTb.seg_part = pr.KT.seg_part + ctx->nsegKT;
+  pr.KTb.seg_cnt = pr.KT.seg_cnt + ctx->nlongKT;
+  pr.KTb.lr_acc = pr.KT.lr_acc + 4;
   const size_t nsp = (size_t)slab_ctas(ctx->nslabKT), nsd = 2 * (size_t)slab_ctas(ctx->nslabK);
   const size_t np = (size_t)ctx->nblocksKT + 2 * (size_t)ctx->nblocksK + 8 * (size_t)ctx->nblocksKT +
-                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + nsp + nsd + 16;
+                    8 * (size_t)ctx->nblocksK + 3 * (size_t)pr.pg.grid + nsp + nsd + 16 * (size_t)pr.pe.grid + 16;
   double *parts = dalloc<double>(pr.parts, np);
   if (!parts) return fail(ctx, PDLP_ERR_OOM, "partials allocation failed");
   S.part_p = parts;
@@ -254,6 +265,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   S.part_cp = S.part_er + 8 * (size_t)ctx->nblocksK;
   S.part_sp = S.part_cp + 3 * (size_t)pr.pg.grid;
   S.part_sd = S.part_sp + nsp;
+  S.part_ce = S.part_sd + nsd;
   // fixed tickets, then one counter per group of 32 evaluation CTAs
   const size_t nticket = kNumTickets + ((size_t)ctx->nblocksKT + 31) / 32 + ((size_t)ctx->nblocksK + 31) / 32;
   S.tickets = dalloc<unsigned>(pr.tickets, nticket);
@@ -315,9 +327,9 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
     pr.ready = true;
     return PDLP_OK;
   }
-  CK(build_solve_graph<T>(pr.K, pr.KT, pr.P, pr.S, in, o.primal_importance, normpart,
+  CK(build_solve_graph<T>(pr.K, pr.KT, pr.KTb, pr.P, pr.S, in, o.primal_importance, normpart,
                           reinterpret_cast<const double *>(ctx->xin.ptr()),
-                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.pg, ctx->cap[0],
+                          reinterpret_cast<const double *>(ctx->yin.ptr()), 152, pr.pg, pr.pe, ctx->cap[0],
                           ctx->cap[1], ctx->cap[2], ctx->cap[3], &pr.graph),
      "graph capture");
   pr.ready = true;
@@ -761,10 +773,12 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     Chunk *bK = dalloc<Chunk>(ctx->blocksK, ctx->hblocksK.size()), *bKT = dalloc<Chunk>(ctx->blocksKT, ctx->hblocksKT.size());
     LongRow *LK = dalloc<LongRow>(ctx->longK, lK.size()), *LKT = dalloc<LongRow>(ctx->longKT, lKT.size());
     double *sK = dalloc<double>(ctx->segK, 2 * (size_t)segK), *sKT = dalloc<double>(ctx->segKT, 2 * (size_t)segKT);
-    unsigned *cK = dalloc<unsigned>(ctx->segcntK, lK.size()), *cKT = dalloc<unsigned>(ctx->segcntKT, lKT.size());
+    // K^T: two sets of arrival counters (the persistent evaluation walks K^T twice)
+    unsigned *cK = dalloc<unsigned>(ctx->segcntK, lK.size()), *cKT = dalloc<unsigned>(ctx->segcntKT, 2 * lKT.size());
     double *aK = dalloc<double>(ctx->lraccK, kLrAcc * lK.size()), *aKT = dalloc<double>(ctx->lraccKT, kLrAcc * lKT.size());
     ctx->nlongK = (int32_t)lK.size();
     ctx->nlongKT = (int32_t)lKT.size();
+    ctx->nsegKT = segKT;
     if (!bK || !bKT || !LK || !LKT || !sK || !sKT || !cK || !cKT || !aK || !aKT)
       return fail(ctx, PDLP_ERR_OOM, "allocation failed");
     CK(cudaMemcpy(bK, ctx->hblocksK.data(), sizeof(Chunk) * ctx->hblocksK.size(), cudaMemcpyHostToDevice), "chunks");
@@ -772,7 +786,7 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     if (!lK.empty()) CK(cudaMemcpy(LK, lK.data(), sizeof(LongRow) * lK.size(), cudaMemcpyHostToDevice), "long rows");
     if (!lKT.empty()) CK(cudaMemcpy(LKT, lKT.data(), sizeof(LongRow) * lKT.size(), cudaMemcpyHostToDevice), "long rows");
     CK(cudaMemset(cK, 0, sizeof(unsigned) * std::max<size_t>(lK.size(), 1)), "memset");
-    CK(cudaMemset(cKT, 0, sizeof(unsigned) * std::max<size_t>(lKT.size(), 1)), "memset");
+    CK(cudaMemset(cKT, 0, sizeof(unsigned) * std::max<size_t>(2 * lKT.size(), 1)), "memset");
     // fixed-size slabs
     {
       auto build = [&](int32_t rows, const std::vector<int32_t> &hr, DevBuf &slab, DevBuf &split, DevBuf &spart,

@@ -168,6 +168,7 @@ struct State {
   double *part_cp;             // per-CTA partials of the persistent kernel [CTA][3]
   double *part_sp, *part_sd;   // per-CTA partials of the slab step kernels (primal [CTA], dual [CTA][2])
   double *part_ec, *part_er;   // per-CTA partials of the evaluation kernels
+  double *part_ce;             // per-CTA partials of the persistent evaluation kernel [CTA][16]
   unsigned int *tickets;       // arrival counters (one per kernel kind)
   unsigned int *gtickets;      // arrival counters of the evaluation CTA groups (columns, then rows)
   Scalars *s;
@@ -191,6 +192,24 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+
+// Comparisons of a float64 with zero and infinity by tests on its bits,
+// with the results of the float64 comparisons for every input (signed
+// zeros, infinities, NaN): a float64 comparison holds a sub-partition's
+// float64 unit for tens of cycles on this part, an integer test does not.
+__device__ __forceinline__ bool d_gt0(double v) {  // v > 0
+  const long long b = __double_as_longlong(v);
+  return b > 0ll && b <= 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool d_lt0(double v) {  // v < 0
+  const long long b = __double_as_longlong(v), m = b & 0x7fffffffffffffffll;
+  return b < 0ll && m != 0ll && m <= 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool d_finite(double v) {
+  return (__double_as_longlong(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool d_is_neginf(double v) { return __double_as_longlong(v) == (long long)0xfff0000000000000ull; }
+__device__ __forceinline__ bool d_is_posinf(double v) { return __double_as_longlong(v) == 0x7ff0000000000000ll; }
 
 template <typename T>
 __device__ __forceinline__ T clampv(T v, T lo, T hi) {

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "evaluate.cuh"
 #include "solver.cuh"
 
 namespace pdlp {
@@ -66,13 +67,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Per-warp staging buffer of one chunk in flight (kBufElems elements of T,
-// then kChunkRows + 1 ints of row starts in streaming mode).
-constexpr int kPre = 5;  // epilogue operands per row
-constexpr int kBufElems = 2 * kChunkNnz + kChunkRows + kPre * kChunkRows;
-template <typename T>
+// Per-warp staging buffer of one chunk in flight (buf_elems<PRE>() elements
+// of T: values, gathered entries, row sums, then PRE epilogue operands per
+// row; then kChunkRows + 1 ints of row starts).  A phase's PRE is its
+// operands per row: 5 for the step phases.
+constexpr int kPre = 5;
+template <int PRE>
+__host__ __device__ constexpr int buf_elems() {
+  return 2 * kChunkNnz + kChunkRows + PRE * kChunkRows;
+}
+template <typename T, int PRE = kPre>
 __host__ __device__ constexpr int buf_bytes() {
-  return (int)((kBufElems * sizeof(T) + (kChunkRows + 1) * 4 + 15) / 16 * 16);
+  return (int)((buf_elems<PRE>() * sizeof(T) + (kChunkRows + 1) * 4 + 15) / 16 * 16);
 }
 
 // Primal epilogue of eq. (3) for column j of K (row j of K^T).  Operands
@@ -82,7 +88,7 @@ struct PrimalPhase {
   const T *x, *xs, *cs, *ls, *us;
   T *xn, *xsn;
   T tau, et;
-  static constexpr int NA = 1;
+  static constexpr int NA = 1, PRE = kPre;
   double acc[NA];
   __device__ __forceinline__ void stage(int j, T *pre) const {
     cp_async(pre, x + j);
@@ -115,7 +121,7 @@ struct DualPhase {
   const T *y, *Kx, *ys, *qs, *ylos;
   T *yn, *Kxn, *ysn;
   T sig, et;
-  static constexpr int NA = 2;
+  static constexpr int NA = 2, PRE = kPre;
   double acc[NA];
   __device__ __forceinline__ void stage(int i, T *pre) const {
     cp_async(pre, Kx + i);
@@ -166,7 +172,7 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
   T *sx = sval + kChunkNnz;
   T *srow = sx + kChunkNnz;
   T *pre = srow + kChunkRows;
-  const int *srp = reinterpret_cast<const int *>(sval + kBufElems);
+  const int *srp = reinterpret_cast<const int *>(sval + buf_elems<Ph::PRE>());
   const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
   if (c.row_end >= 0) {
     const int nrows = c.row_end - c.row_begin;
@@ -230,7 +236,7 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
   const int lane = threadIdx.x & 31;
   T *sval = reinterpret_cast<T *>(buf);
   T *pre = sval + 2 * kChunkNnz + kChunkRows;
-  int *srp = reinterpret_cast<int *>(sval + kBufElems);
+  int *srp = reinterpret_cast<int *>(sval + buf_elems<Ph::PRE>());
   const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
   const int nrows = c.row_end >= 0 ? c.row_end - c.row_begin : 0;
   int cj[kLaneItems];
@@ -288,7 +294,7 @@ __device__ __forceinline__ void cta_sum3(const double (&v)[3], char *sm, int war
 template <typename T, bool L1G, typename Ph>
 __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, int count, const T *vec, char *wsm,
                                           Ph &ph) {
-  char *b0 = wsm, *b1 = wsm + buf_bytes<T>();
+  char *b0 = wsm, *b1 = wsm + buf_bytes<T, Ph::PRE>();
   T ga[kLaneItems], gb[kLaneItems];
   if (count > 0) issue<T, L1G>(A, desc[0], vec, ph, b0, ga);
   if (count > 1) issue<T, L1G>(A, desc[1], vec, ph, b1, gb);
@@ -419,6 +425,243 @@ __global__ void __launch_bounds__(kPThreads, 1)
   if (blockIdx.x == 0 && threadIdx.x == 0) store_step(sc, ctl);
 }
 
+// ------------------------------------------------ persistent evaluation
+//
+// The products and Eq. (15) terms of an evaluation in one launch of one
+// 512-thread CTA per SM, on the step kernel's balanced chunk lists, with two
+// chunks in flight per warp (separate evaluation kernels ran in 1.6 and 1.15
+// waves of CTAs, with idle SMs in their tails):
+//   A  K^T y  (current iterate): (K~^T y)_j stored, column terms of candidate 0
+//   B  K^T ys (average, when there is one): (K~^T ys)_j stored, candidate 1
+//   C  K xs   (average): (K~ xs)_i stored, row terms of both candidates
+// The phases share no data, so no grid barrier separates them; B uses its
+// own long-row segment partials, arrival counters and epilogue slots (4..7)
+// (the matrix KTb), so that a warp in B never meets a warp still in A on a
+// long row.  Per-CTA sums go to S.part_ce; the last CTA adds them and the
+// long-row slots in a fixed order and finishes the evaluation.  The
+// epilogue arithmetic is that of k_eval_cols / k_eval_rows.  Float64 only:
+// the operands are staged with the chunk as float64.
+constexpr int kEvalPre = 8;
+
+// Column terms for candidate c (scale 1: the current iterate; 1 / sum_eta:
+// the average, from its running sums): [c^T x, ||rc - lambda||^2,
+// l^T lambda+ - u^T lambda-, ||x - x0||^2 (scaled)].
+struct ColEvalPhase {
+  const double *xv, *x0, *c, *l, *u, *D2, *D2inv;
+  double *prod;
+  double scale;
+  static constexpr int NA = 4, PRE = kEvalPre;
+  double acc[NA];
+  __device__ __forceinline__ void stage(int j, double *pre) const {
+    cp_async(pre, xv + j);
+    cp_async(pre + 32, x0 + j);
+    cp_async(pre + 64, c + j);
+    cp_async(pre + 96, l + j);
+    cp_async(pre + 128, u + j);
+    cp_async(pre + 160, D2 + j);
+    cp_async(pre + 192, D2inv + j);
+  }
+  __device__ __forceinline__ void load(int j, double *pre) const {
+    pre[0] = __ldcg(xv + j);
+    pre[32] = __ldcg(x0 + j);
+    pre[64] = c[j];
+    pre[96] = l[j];
+    pre[128] = u[j];
+    pre[160] = D2[j];
+    pre[192] = D2inv[j];
+  }
+  __device__ __forceinline__ void epi(int j, double g, const double *pre, double *a) {
+    prod[j] = g;
+    const double xt = pre[0] * scale, kt = g * scale;  // (exact for scale 1)
+    const double xr = pre[32], cj = pre[64], lj = pre[96], uj = pre[128], D2j = pre[160], iD2 = pre[192];
+    const bool lf = !d_is_neginf(lj), uf = !d_is_posinf(uj);
+    const double xo = D2j * xt, rc = cj - kt * iD2;
+    const bool lam_rc = lf ? (uf || d_gt0(rc)) : (uf && d_lt0(rc));
+    const double lam = lam_rc ? rc : 0.0;
+    const double d = lam_rc ? (d_finite(rc) ? 0.0 : __longlong_as_double(0x7ff8000000000000ll)) : rc;
+    a[0] += cj * xo;
+    a[1] = fma(d, d, a[1]);
+    if (d_gt0(lam) || d_lt0(lam)) a[2] = __dadd_rn(a[2], __dmul_rn(d_gt0(lam) ? lj : uj, lam));
+    a[3] += (xt - xr) * (xt - xr);
+  }
+};
+
+// Row terms of both candidates: [||(q - K x)+||^2, q^T y, ||y - y0||^2
+// (scaled), general dual bound term] for the current iterate, then the
+// average.
+struct RowEvalPhase {
+  const double *y, *ys, *Kx, *y0, *q, *D1, *D1inv, *ylo;
+  double *Kxbar;
+  double inv;
+  bool avg;
+  static constexpr int NA = 8, PRE = kEvalPre;
+  double acc[NA];
+  __device__ __forceinline__ void stage(int i, double *pre) const {
+    cp_async(pre, y + i);
+    cp_async(pre + 32, ys + i);
+    cp_async(pre + 64, Kx + i);
+    cp_async(pre + 96, y0 + i);
+    cp_async(pre + 128, q + i);
+    cp_async(pre + 160, D1 + i);
+    cp_async(pre + 192, D1inv + i);
+    cp_async(pre + 224, ylo + i);
+  }
+  __device__ __forceinline__ void load(int i, double *pre) const {
+    pre[0] = __ldcg(y + i);
+    pre[32] = __ldcg(ys + i);
+    pre[64] = __ldcg(Kx + i);
+    pre[96] = __ldcg(y0 + i);
+    pre[128] = q[i];
+    pre[160] = D1[i];
+    pre[192] = D1inv[i];
+    pre[224] = ylo[i];
+  }
+  __device__ __forceinline__ void epi(int i, double s, const double *pre, double *a) {
+    Kxbar[i] = s;
+    const double yr = pre[96], qi = pre[128], D1i = pre[160], iD1 = pre[192], lo = pre[224];
+    const bool ineq = !d_is_neginf(lo), lo_nz = d_gt0(lo) || d_lt0(lo);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c == 1 && !avg) break;
+      const double yt = c == 0 ? pre[0] : pre[32] * inv;
+      const double kx = c == 0 ? pre[64] : s * inv;
+      double r = qi - kx * iD1;
+      if (ineq) {
+        if (lo_nz) a[4 * c + 3] += lo * r;
+        r = d_gt0(r) ? r : 0.0;
+      }
+      a[4 * c + 0] += r * r;
+      a[4 * c + 1] += qi * (D1i * yt);
+      a[4 * c + 2] += (yt - yr) * (yt - yr);
+    }
+  }
+};
+
+// Terms t0 and t0 + 1 (of 16) summed over `nb` CTA partials (stride 16) and
+// terms l0, l0 + 1 of the long-row slots `lr` ([nlong][kLrAcc]), by one
+// warp, valid in lane 0; every load before any sum.
+__device__ __forceinline__ void pe_terms2(const double *part, int nb, int t0, const double *lr, int nlong, int l0,
+                                          double (&out)[2]) {
+  const int lane = threadIdx.x & 31;
+  double acc[2][4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[q][u] = 0.0;
+  for (int b0 = lane; b0 < nb; b0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + 32 * u;
+      if (b < nb) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q][u] += __ldcg(part + (size_t)b * 16 + t0 + q);
+      }
+    }
+  }
+  for (int r0 = lane; r0 < nlong; r0 += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + 32 * u;
+      if (r < nlong) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q][u] += __ldcg(lr + (size_t)r * kLrAcc + l0 + q);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double t = (acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    out[q] = t;
+  }
+}
+
+template <bool L1G>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_eval_persist(Mat<double> K, Mat<double> KT, Mat<double> KTb, Problem<double> P, State<double> S,
+                   PersistGeo geo) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ double ecr[16];
+  Scalars *sc = S.s;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kPWarps + wid;
+  char *wsm = sm + (size_t)geo.warp_bytes * wid;
+  Chunk *dp = reinterpret_cast<Chunk *>(wsm + geo.o_desc_p);
+  Chunk *dd = reinterpret_cast<Chunk *>(wsm + geo.o_desc_d);
+  const int cur = sc->cur;
+  const bool avg = sc->sum_eta > 0.0;
+  const double inv = avg ? 1.0 / sc->sum_eta : 0.0;
+  {
+    // Algorithm 2's factors for the next chunk's steps (k does not change
+    // until then): entry i by lane 0 of the last warp of CTA i mod grid
+    const long long k0 = sc->k;
+    const int ne = sc->eval_every < kMaxEval ? sc->eval_every : kMaxEval;
+    if (wid == kPWarps - 1 && lane == 0) {
+      for (int i = blockIdx.x; i < ne; i += gridDim.x) {
+        const double kk = (double)(k0 + i + 1);
+        sc->fac_tab[0][i] = 1.0 - pow(kk + 1.0, -0.3);
+        sc->fac_tab[1][i] = 1.0 + pow(kk + 1.0, -0.6);
+      }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->fac_k0 = k0;
+  }
+  const int cnt_p = load_desc(KT, gw, dp);
+  const int cnt_d = load_desc(K, gw, dd);
+  ColEvalPhase pa{S.x[cur], S.x0, P.c, P.l, P.u, P.D2, P.D2inv, S.KTy_cur, 1.0, {0.0, 0.0, 0.0, 0.0}};
+  run_phase<double, L1G>(KT, dp, cnt_p, S.y[cur], wsm, pa);
+  ColEvalPhase pb{S.xs[cur], S.x0, P.c, P.l, P.u, P.D2, P.D2inv, S.KTys, inv, {0.0, 0.0, 0.0, 0.0}};
+  if (avg) run_phase<double, L1G>(KTb, dp, cnt_p, S.ys[cur], wsm, pb);
+  RowEvalPhase pc{S.y[cur], S.ys[cur], S.Kx[cur], S.y0, P.q, P.D1, P.D1inv, P.ylo, S.Kxbar, inv, avg, {}};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) pc.acc[a] = 0.0;
+  run_phase<double, L1G>(K, dd, cnt_d, S.xs[cur], wsm, pc);
+  // fixed-order CTA sums of the 16 terms: term a's 512 values go to area a
+  // of the (now idle) staging space, which warp a adds
+  double v[16];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    v[a] = pa.acc[a];
+    v[4 + a] = pb.acc[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) v[8 + a] = pc.acc[a];
+  __syncthreads();
+  double *red = reinterpret_cast<double *>(sm);
+#pragma unroll
+  for (int a = 0; a < 16; ++a) red[a * kPThreads + threadIdx.x] = v[a];
+  __syncthreads();
+  {
+    const double *r = red + wid * kPThreads;
+    double p[kPThreads / 32];
+#pragma unroll
+    for (int k = 0; k < kPThreads / 32; ++k) p[k] = r[lane + 32 * k];
+#pragma unroll
+    for (int s = kPThreads / 64; s >= 1; s >>= 1) {
+#pragma unroll
+      for (int k = 0; k < s; ++k) p[k] += p[k + s];
+    }
+    double t = p[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) S.part_ce[(size_t)blockIdx.x * 16 + wid] = t;
+  }
+  if (!last_block(S.tickets + kTicketMisc)) return;
+  // warp w < 8: terms 2w, 2w + 1 (columns: slots of KT's long rows, phase B
+  // in slots 4..7; rows: slots of K's long rows)
+  if (wid < 8) {
+    double t2[2];
+    if (wid < 4) pe_terms2(S.part_ce, gridDim.x, 2 * wid, KT.lr_acc, KT.nlong, 2 * wid, t2);
+    else pe_terms2(S.part_ce, gridDim.x, 2 * wid, K.lr_acc, K.nlong, 2 * wid - 8, t2);
+    if (lane == 0) {
+      ecr[2 * wid] = t2[0];
+      ecr[2 * wid + 1] = t2[1];
+    }
+  }
+  __syncthreads();
+  eval_finish(sc, ecr, S.trace);
+}
+
 // Reopens a finished state for timing: running status, no limits, a zero
 // barrier counter and the step factors of the next steps.
 __global__ void k_persist_reopen(Scalars *s, unsigned *tickets) {
@@ -503,6 +746,61 @@ cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &
   return cudaLaunchKernelEx(&cfg, k_persist<T, false>, K, KT, P, S, pg);
 }
 
+// Layout of the persistent evaluation kernel on the step kernel's grid and
+// chunk lists (8 staged operands per row); pe->grid = 0 (the separate
+// evaluation kernels run instead) for float32 or when it does not fit.
+template <typename T>
+cudaError_t eval_plan(const PersistGeo &pg, int cmax_kt, int cmax_k, PersistGeo *pe) {
+  *pe = PersistGeo{};
+  if constexpr (sizeof(T) != 8) {
+    return cudaSuccess;
+  } else {
+    if (pg.grid <= 0) return cudaSuccess;
+    cudaError_t e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k_eval_persist<true>))) return e;
+    const int budget = optin - (int)fa.sharedSizeBytes;
+    PersistGeo g{};
+    g.grid = pg.grid;
+    g.l1_gather = pg.l1_gather;
+    g.o_desc_p = 2 * buf_bytes<double, kEvalPre>();
+    g.o_desc_d = g.o_desc_p + 16 * cmax_kt;
+    g.warp_bytes = round16(g.o_desc_d + 16 * cmax_k);
+    g.smem = g.warp_bytes * kPWarps;
+    // the CTA sums reuse the staging space: 16 terms x kPThreads doubles
+    if (g.smem > budget || g.smem < 16 * kPThreads * (int)sizeof(double)) return cudaSuccess;
+    if ((e = cudaFuncSetAttribute(k_eval_persist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
+    if ((e = cudaFuncSetAttribute(k_eval_persist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, budget))) return e;
+    int per = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_eval_persist<true>, kPThreads, g.smem))) return e;
+    if (per < 1) return cudaSuccess;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_eval_persist<false>, kPThreads, g.smem))) return e;
+    if (per < 1) return cudaSuccess;
+    *pe = g;
+    return cudaSuccess;
+  }
+}
+
+// One evaluation by the persistent evaluation kernel (float64 contexts with
+// pe.grid > 0).  KTb is KT with the second set of long-row buffers.
+template <typename T>
+cudaError_t launch_eval_persist(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
+                                const State<T> &S, const PersistGeo &pe, cudaStream_t st) {
+  if constexpr (sizeof(T) != 8) {
+    return cudaErrorNotSupported;
+  } else {
+    if (pe.grid <= 0) return cudaErrorInvalidValue;
+    if (pe.l1_gather)
+      k_eval_persist<true><<<pe.grid, kPThreads, pe.smem, st>>>(K, KT, KTb, P, S, pe);
+    else
+      k_eval_persist<false><<<pe.grid, kPThreads, pe.smem, st>>>(K, KT, KTb, P, S, pe);
+    return cudaGetLastError();
+  }
+}
+
 // Mean duration of one step attempt inside the persistent kernel: `reps`
 // launches (each runs until eval_every steps are accepted), event-timed on
 // `st`, divided by the attempts they made.
@@ -545,7 +843,10 @@ cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P,
   template cudaError_t launch_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &, \
                                          const PersistGeo &, cudaStream_t);                                 \
   template cudaError_t time_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &,   \
-                                       const PersistGeo &, int, cudaStream_t, float *);
+                                       const PersistGeo &, int, cudaStream_t, float *);                                      \
+  template cudaError_t eval_plan<T>(const PersistGeo &, int, int, PersistGeo *);                                  \
+  template cudaError_t launch_eval_persist<T>(const Mat<T> &, const Mat<T> &, const Mat<T> &, const Problem<T> &, \
+                                              const State<T> &, const PersistGeo &, cudaStream_t);
 PDLP_INST(double)
 PDLP_INST(float)
 #undef PDLP_INST

@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include <algorithm>
 
+#include "evaluate.cuh"
 #include "slab.cuh"
 #include "solver.cuh"
 
@@ -26,18 +27,6 @@ namespace pdlp {
 
 // ---------------------------------------------------------------- helpers
 
-__device__ __forceinline__ double proj_lambda(double rc, double l, double u) {
-  // Lambda_j from the finiteness of l_j and u_j (Section 2)
-  const bool lf = l > -INFINITY, uf = u < INFINITY;
-  if (!lf && !uf) return 0.0;
-  if (!lf) return rc < 0.0 ? rc : 0.0;
-  if (!uf) return rc > 0.0 ? rc : 0.0;
-  return rc;
-}
-
-__device__ __forceinline__ bool time_up(const Scalars *s) {
-  return s->time_limit_ns != 0ull && global_timer_ns() - s->t0_ns > s->time_limit_ns;
-}
 
 // Algorithm 2's test and step-size update (step_update), run by one thread
 // after the reductions of an attempt, on the scalars in global memory; the
@@ -377,7 +366,6 @@ __global__ void __launch_bounds__(kThreads) k_mp_test(Mat<T> KT, State<T> S, int
 // Columns: K^T y (current) and K^T ys (sum for the average) in one pass, and
 // the column terms of Eq. (15) for both candidates.
 // Partial layout per CTA (8): [cand][pobj, dres^2, dobj(lambda), |x - x0|^2].
-__device__ void eval_finish(Scalars *s, const double *ecr, double *trace);
 
 // The per-CTA partials of an evaluation (8 terms per CTA of k_eval_cols and
 // of k_eval_rows) are summed in a fixed-order two-level tree: the last CTA of
@@ -482,16 +470,23 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> K, Mat<T> KT, Pro
     S.KTy_cur[j] = g[0];
     S.KTys[j] = g[1];
     const double D2 = P.D2[j], iD2 = P.D2inv[j], cj = P.c[j], lj = P.l[j], uj = P.u[j], xr = (double)x0[j];
+    // Lambda_j from the finiteness of l_j and u_j (Section 2); lambda =
+    // proj_Lambda(rc) is rc or 0, so rc - lambda is 0 (rc - rc) or rc, and
+    // at most one of l_j lambda+ and u_j lambda- is nonzero: the same values
+    // as the plain formulas, with bit tests instead of float64 compares
+    const bool lf = !d_is_neginf(lj), uf = !d_is_posinf(uj);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (c == 1 && !avg) break;
       const double xt = c == 0 ? (double)x[j] : (double)xs[j] * inv;
       const double kt = c == 0 ? (double)g[0] : (double)g[1] * inv;
       const double xo = D2 * xt, rc = cj - kt * iD2;
-      const double lam = proj_lambda(rc, lj, uj);
+      const bool lam_rc = lf ? (uf || d_gt0(rc)) : (uf && d_lt0(rc));
+      const double lam = lam_rc ? rc : 0.0;
+      const double d = lam_rc ? (d_finite(rc) ? 0.0 : __longlong_as_double(0x7ff8000000000000ll)) : rc;
       acc[4 * c + 0] += cj * xo;
-      acc[4 * c + 1] += (rc - lam) * (rc - lam);
-      acc[4 * c + 2] += (lam > 0.0 ? lj * lam : 0.0) + (lam < 0.0 ? uj * lam : 0.0);
+      acc[4 * c + 1] = fma(d, d, acc[4 * c + 1]);
+      if (d_gt0(lam) || d_lt0(lam)) acc[4 * c + 2] = __dadd_rn(acc[4 * c + 2], __dmul_rn(d_gt0(lam) ? lj : uj, lam));
       acc[4 * c + 3] += (xt - xr) * (xt - xr);
     }
   });
@@ -504,130 +499,6 @@ __global__ void __launch_bounds__(kThreads) k_eval_cols(Mat<T> K, Mat<T> KT, Pro
   eval_arrive(K, KT, S, true);
 }
 
-// Finalisation of one evaluation, by every thread of the CTA that finishes
-// it; ecr holds the column terms [8] then the row terms [8] (shared memory).
-// Float64 square roots and divisions take hundreds of cycles each on this
-// part, so each candidate's terms are split over threads of distinct warps
-// (thread 0 of warp 4 c + part), and the restart radius and 1 / sum_eta are
-// computed beside them; thread 0 then takes the decisions.
-__device__ void eval_finish(Scalars *s, const double *ecr, double *trace) {
-  __shared__ double s_pre[3];  // r^2 of both candidates under the current omega, 1 / sum_eta
-  const bool avg = s->sum_eta > 0.0;
-  const double *ec = ecr, *er = ecr + 8;
-  if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) < 8) {
-    const int c = threadIdx.x >> 7, part = (threadIdx.x >> 5) & 3;
-    if (!(c == 1 && !avg)) {
-      double *k = s->kkt[c];
-      if (part == 0) {
-        const double pobj = ec[4 * c + 0] + er[4 * c + 3];
-        const double dobj = ec[4 * c + 2] + er[4 * c + 1];
-        const double gap = fabs(dobj - pobj);
-        k[0] = pobj;
-        k[1] = dobj;
-        k[2] = gap;
-        k[5] = gap / (1.0 + fabs(dobj) + fabs(pobj));
-      } else if (part == 1) {
-        const double pres = sqrt(er[4 * c + 0]);
-        k[3] = pres;
-        k[6] = pres / (1.0 + s->qnorm);
-      } else if (part == 2) {
-        const double dres = sqrt(ec[4 * c + 1]);
-        k[4] = dres;
-        k[7] = dres / (1.0 + s->cnorm);
-      } else {
-        s->cand_dx2[c] = ec[4 * c + 3];
-        s->cand_dy2[c] = er[4 * c + 2];
-        s_pre[c] = s->omega * ec[4 * c + 3] + er[4 * c + 2] / s->omega;
-        if (c == 0) s_pre[2] = avg ? 1.0 / s->sum_eta : 0.0;
-      }
-    } else if (part == 3) {
-      s_pre[1] = 0.0;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  bool pass[2] = {false, false};
-  for (int c = 0; c < 2; ++c) {
-    if (c == 1 && !avg) break;
-    const double *k = s->kkt[c];
-    pass[c] = k[5] <= s->rel_tol && k[6] <= s->rel_tol && k[7] <= s->rel_tol;
-  }
-  s->inv_avg = s_pre[2];
-  if (s->status == kRunning || s->status == kNumErr) {
-    if (pass[0]) { s->status = kOptimal; s->ret_which = 0; }
-    else if (pass[1]) { s->status = kOptimal; s->ret_which = 1; }
-  }
-  if (s->status == kRunning) {
-    if (s->k >= s->iter_limit) s->status = kIterLimit;
-    else if (s->attempts >= s->attempt_limit) s->status = kKktLimit;
-    else if (time_up(s)) s->status = kTimeLimit;
-  }
-  if (s->status == kRunning && s->stall_evals > 0 && s->phase == 1) {
-    // the solve has reached what its arithmetic allows when the better
-    // candidate's relative error has not dropped by 10% for stall_evals
-    // evaluations; it stops and returns that candidate.  (A float32
-    // correction problem can keep its relative gap near 1 while its
-    // residuals are tiny: its objective terms cancel to below float32
-    // resolution; the outer update still gains from such a point.)
-    const double e0 = fmax(s->kkt[0][5], fmax(s->kkt[0][6], s->kkt[0][7]));
-    const double e1 = avg ? fmax(s->kkt[1][5], fmax(s->kkt[1][6], s->kkt[1][7])) : INFINITY;
-    const double err = fmin(e0, e1);
-    if (err < 0.9 * s->stall_best) {
-      s->stall_best = err;
-      s->stall_count = 0;
-    } else if (++s->stall_count >= s->stall_evals) {
-      s->status = kStalled;
-      s->ret_which = e1 < e0 ? 1 : 0;
-    }
-  }
-  s->do_gap = (s->status == kRunning && s->phase == 1 && s->adaptive_restart) ? 1 : 0;
-  s->restart = 0;
-  s->vrestart = 0;
-  if (s->status == kRunning && s->phase == 1 && !s->adaptive_restart && s->pw_update &&
-      (double)(s->k - s->k_virt) >= s->beta_art * (double)s->k) {
-    // Appendix C.2 "no restart": Algorithm 3 where the artificial criterion
-    // would restart, from the point of the previous update (z^{n,0} slots)
-    const double Dx = sqrt(s->cand_dx2[0]), Dy = sqrt(s->cand_dy2[0]);
-    if (Dx > s->eps_zero && Dy > s->eps_zero)
-      s->omega = exp(s->pw_theta * log(Dy / Dx) + (1.0 - s->pw_theta) * log(s->omega));
-    s->inv_omega = 1.0 / s->omega;
-    s->tau = s->eta * s->inv_omega;
-    s->sigma = s->eta * s->omega;
-    s->vrestart = 1;
-    s->k_virt = s->k;
-    double *rec = trace + (size_t)(s->trace_n % kTraceCap) * kTraceLen;
-    s->trace_n += 1;
-    {
-      rec[0] = (double)s->k;
-      rec[1] = (double)s->t;
-      rec[2] = rec[3] = rec[4] = NAN;
-      rec[5] = 0.0;
-      rec[6] = 2.0;
-      rec[7] = s->omega;
-      rec[8] = sqrt(s->omega * s->cand_dx2[0] + s->cand_dy2[0] / s->omega);
-      rec[9] = NAN;
-      for (int a = 0; a < 3; ++a) {
-        rec[10 + a] = s->kkt[0][5 + a];
-        rec[13 + a] = s->kkt[1][5 + a];
-      }
-    }
-  }
-  if (s->do_gap) {
-    // (do_gap needs adaptive restarts: omega did not change above)
-    for (int c = 0; c < 2; ++c) {
-      const double r2 = s_pre[c];
-      s->g_r2[c] = r2;
-      s->g_omega[c] = s->omega;
-      s->g_inv_omega[c] = s->inv_omega;
-      s->g_W[c] = s->g_V[c] = s->g_A[c] = 0.0;
-      s->g_prefix[c] = 0u;
-      s->g_active[c] = r2 > 0.0 ? 1 : 0;
-      s->mu[c] = INFINITY;  // r = 0 gives mu = +inf
-      s->gval[c] = 0.0;
-    }
-  }
-  s->phase = 1;
-}
 
 // Rows: K xs (for K x_avg) and the row terms of Eq. (15) for both candidates.
 // Partial layout per CTA (8): [cand][pres^2, dobj(q^T y), |y - y0|^2, pobj extra].
@@ -659,15 +530,16 @@ __global__ void __launch_bounds__(kThreads) k_eval_rows(Mat<T> K, Mat<T> KT, Pro
   spmv_warp<T, 1>(K, vec, sm, acc, [&](int i, const T(&s)[1], double(&acc)[8]) {
     S.Kxbar[i] = s[0];
     const double D1 = P.D1[i], iD1 = P.D1inv[i], qi = P.q[i], lo = P.ylo[i], yr = (double)y0[i];
+    const bool ineq = !d_is_neginf(lo), lo_nz = d_gt0(lo) || d_lt0(lo);  // bit tests, as in the columns
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (c == 1 && !avg) break;
       const double yt = c == 0 ? (double)y[i] : (double)ys[i] * inv;
       const double kx = c == 0 ? (double)Kx[i] : (double)s[0] * inv;
       double r = qi - kx * iD1;
-      if (lo > -INFINITY) {                      // inequality row
-        if (lo != 0.0) acc[4 * c + 3] += lo * r;  // general dual bound only
-        r = r > 0.0 ? r : 0.0;
+      if (ineq) {                                 // inequality row
+        if (lo_nz) acc[4 * c + 3] += lo * r;      // general dual bound only
+        r = d_gt0(r) ? r : 0.0;
       }
       acc[4 * c + 0] += r * r;
       acc[4 * c + 1] += qi * (D1 * yt);
@@ -1710,10 +1582,10 @@ static cudaError_t add_restart_branch(const Problem<T> &P, const State<T> &S, in
 // the status to a limit once k or the attempts reach their limits, and the
 // outer condition is the status.
 template <typename T>
-cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
-                              const ScalarInit &in, double primal_importance, double *norm_part,
+cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
+                              const State<T> &S, const ScalarInit &in, double primal_importance, double *norm_part,
                               const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
-                              cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaStream_t st4,
+                              const PersistGeo &pe, cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaStream_t st4,
                               cudaGraphExec_t *exec) {
   cudaError_t e;
   cudaGraph_t graph = nullptr;
@@ -1754,7 +1626,14 @@ cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T
     // one persistent cooperative kernel per chunk of step attempts
     e = launch_persist<T>(K, KT, P, S, pg, st2);
     if (!e) {
-      launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
+      // the evaluation: one persistent launch on the step kernel's grid
+      // (float64), else the column and row kernels on two streams
+      if (pe.grid > 0)
+        e = launch_eval_persist<T>(K, KT, KTb, P, S, pe, st2);
+      else
+        launch_eval_fork<T>(K, KT, P, S, st2, st3, ev_fork, ev_join);
+    }
+    if (!e) {
       launch_gap<T>(P, S, 0, 2, 0, gap_grid, st2, 1);  // with the restart decision
       k_finish<<<1, 64, 0, st2>>>(S.s, h_outer, h_outer, 0, 1, h_rs, 1);
       e = add_restart_branch<T>(P, S, gap_grid, h_rs, st2, st4);
@@ -1908,13 +1787,13 @@ template cudaError_t run_stepped<double>(const Mat<double> &, const Mat<double> 
 template cudaError_t run_stepped<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
                                         const State<float> &, const ScalarInit &, double, double *,
                                         const double *, const double *, int, const PersistGeo &, cudaStream_t, Scalars *);
-template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Problem<double> &,
-                                               const State<double> &, const ScalarInit &, double, double *,
-                                               const double *, const double *, int, const PersistGeo &, cudaStream_t,
+template cudaError_t build_solve_graph<double>(const Mat<double> &, const Mat<double> &, const Mat<double> &,
+                                               const Problem<double> &, const State<double> &, const ScalarInit &, double, double *,
+                                               const double *, const double *, int, const PersistGeo &, const PersistGeo &, cudaStream_t,
                                                cudaStream_t, cudaStream_t, cudaStream_t, cudaGraphExec_t *);
-template cudaError_t build_solve_graph<float>(const Mat<float> &, const Mat<float> &, const Problem<float> &,
-                                              const State<float> &, const ScalarInit &, double, double *,
-                                              const double *, const double *, int, const PersistGeo &, cudaStream_t,
+template cudaError_t build_solve_graph<float>(const Mat<float> &, const Mat<float> &, const Mat<float> &,
+                                              const Problem<float> &, const State<float> &, const ScalarInit &, double, double *,
+                                              const double *, const double *, int, const PersistGeo &, const PersistGeo &, cudaStream_t,
                                               cudaStream_t, cudaStream_t, cudaStream_t, cudaGraphExec_t *);
 
 }  // namespace pdlp

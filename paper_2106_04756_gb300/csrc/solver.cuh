@@ -52,9 +52,10 @@ template <typename T>
 void launch_eval(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S, cudaStream_t st);
 template <typename T> void launch_output(const Problem<T> &P, const State<T> &S, cudaStream_t st);
 template <typename T>
-cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
-                              const ScalarInit &in, double primal_importance, double *norm_part,
+cudaError_t build_solve_graph(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
+                              const State<T> &S, const ScalarInit &in, double primal_importance, double *norm_part,
                               const double *x0_dev, const double *y0_dev, int gap_grid, const PersistGeo &pg,
+                              const PersistGeo &pe,
                               cudaStream_t st, cudaStream_t st2, cudaStream_t st3, cudaStream_t st4,
                               cudaGraphExec_t *exec);
 // Persistent step kernel (persistent.cu).  mode 0: off.  Leaves pg->grid = 0
@@ -70,6 +71,14 @@ cudaError_t launch_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &
 template <typename T>
 cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
                          const PersistGeo &pg, int reps, cudaStream_t st, float *ms_attempt);
+// Persistent evaluation kernel (persistent.cu): the evaluation's products and
+// Eq. (15) terms on the step kernel's grid; float64 contexts only
+// (pe->grid = 0 otherwise, and the separate evaluation kernels run).
+template <typename T>
+cudaError_t eval_plan(const PersistGeo &pg, int cmax_kt, int cmax_k, PersistGeo *pe);
+template <typename T>
+cudaError_t launch_eval_persist(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
+                                const State<T> &S, const PersistGeo &pe, cudaStream_t st);
 
 template <typename T>
 cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,
