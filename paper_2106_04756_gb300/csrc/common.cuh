@@ -108,6 +108,7 @@ struct Scalars {
   long long iter_limit, attempt_limit;
   unsigned long long t0_ns, time_limit_ns, t_end_ns;
   int cur;        // which of the two buffers holds the current iterate
+  int kty_valid;  // KTy_cur holds K^T y of the current y, from the persistent evaluation
   int chunk_acc;  // accepted iterations since the last evaluation
   int eval_every;
   int status;

@@ -320,6 +320,42 @@ __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, in
   }
 }
 
+// A phase whose product A v the persistent evaluation just stored (prod):
+// the epilogues of the warp's chunks in the same order as run_phase, on the
+// stored sums (bit-identical to the gathered ones: the same chunk lists and
+// row sums), without the gathers; a long row's epilogue once, by the warp of
+// its first segment.
+template <typename T, typename Ph>
+__device__ __forceinline__ void reuse_phase(const Mat<T> &A, const Chunk *desc, int count, const T *prod,
+                                            char *wsm, Ph &ph) {
+  const int lane = threadIdx.x & 31;
+  T *pre = reinterpret_cast<T *>(wsm) + 2 * kChunkNnz + kChunkRows;
+  for (int i = 0; i < count; ++i) {
+    const Chunk c = desc[i];
+    if (c.row_end >= 0) {
+      const int nrows = c.row_end - c.row_begin;
+      if (lane < nrows) {
+        const int j = c.row_begin + lane;
+        ph.load(j, pre + lane);
+        ph.epi(j, __ldcg(prod + j), pre + lane, ph.acc);
+      }
+    } else if (lane == 0) {
+      const int lr = -(c.row_end + 1);
+      const LongRow LR = A.longrows[lr];
+      if (c.nnz_begin == __ldg(A.rp + LR.row)) {
+        double la[Ph::NA];
+#pragma unroll
+        for (int a = 0; a < Ph::NA; ++a) la[a] = 0.0;
+        ph.load(LR.row, pre);
+        ph.epi(LR.row, __ldcg(prod + LR.row), pre, la);
+#pragma unroll
+        for (int a = 0; a < Ph::NA; ++a) A.lr_acc[(size_t)lr * kLrAcc + a] = la[a];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <typename T, bool L1G>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_persist(Mat<T> K, Mat<T> KT, Problem<T> P, State<T> S, PersistGeo geo) {
@@ -330,7 +366,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   __shared__ long long s_fac_k0, s_iter_limit, s_attempt_limit;
   __shared__ int s_eval_every;
   __shared__ unsigned long long s_base, s_wait_ns;
-  __shared__ int s_wait_extra;
+  __shared__ int s_wait_extra, s_reuse;
   Scalars *sc = S.s;
   const int wid = threadIdx.x >> 5;
   const int gw = blockIdx.x * kPWarps + wid;
@@ -347,6 +383,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     s_eval_every = sc->eval_every;
     s_wait_ns = sc->wait_ns;
     s_wait_extra = sc->wait_extra;
+    s_reuse = sc->kty_valid;  // K^T y of the current y stored by the persistent evaluation
     // the counter is a multiple of G between launches; CTAs that already
     // arrived at the first barrier add less than G
     const unsigned long long c0 = *reinterpret_cast<volatile unsigned long long *>(bar);
@@ -368,7 +405,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const int cur = ctl.cur;
     PrimalPhase<T> pp{S.x[cur], S.xs[cur], P.cs, P.ls, P.us, S.x[cur ^ 1], S.xs[cur ^ 1],
                       (T)ctl.tau, (T)ctl.eta, {0.0}};
-    run_phase<T, L1G>(KT, dp, cnt_p, S.y[cur], wsm, pp);
+    if (att == 0 && s_reuse)
+      reuse_phase<T>(KT, dp, cnt_p, S.KTy_cur, wsm, pp);
+    else
+      run_phase<T, L1G>(KT, dp, cnt_p, S.y[cur], wsm, pp);
     target += G + (att == 0 && s_wait_extra ? 1ull : 0ull);
     if (!grid_barrier(bar, target, &sc->err, s_wait_ns, L1G)) break;
     DualPhase<T> dph{S.y[cur], S.Kx[cur], S.ys[cur], P.qs, P.ylos, S.y[cur ^ 1], S.Kx[cur ^ 1], S.ys[cur ^ 1],
@@ -422,7 +462,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
       __syncthreads();
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) store_step(sc, ctl);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    store_step(sc, ctl);
+    sc->kty_valid = 0;  // y moved (or the stored product was used)
+  }
 }
 
 // ------------------------------------------------ persistent evaluation
@@ -659,6 +702,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     }
   }
   __syncthreads();
+  if (threadIdx.x == 0) sc->kty_valid = 1;  // phase A's K^T y serves the next chunk's first step
   eval_finish(sc, ecr, S.trace);
 }
 
@@ -672,6 +716,7 @@ __global__ void k_persist_reopen(Scalars *s, unsigned *tickets) {
     s->iter_limit = 1ll << 62;
     s->attempt_limit = 1ll << 62;
     s->fac_k0 = s->k;
+    s->kty_valid = 0;  // timed attempts gather K^T y
     tickets[kTicketBar] = 0u;
     tickets[kTicketBar + 1] = 0u;
   }

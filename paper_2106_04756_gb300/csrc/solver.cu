@@ -1140,6 +1140,8 @@ __global__ void k_apply_restart(Problem<T> P, State<T> S) {
   if (!sc->restart) return;
   const int cur = sc->cur, cand = sc->cand;
   const double inv = sc->inv_avg;
+  // to the average: y moves, and the stored K^T y no longer holds
+  if (cand == 1 && blockIdx.x == 0 && threadIdx.x == 0) S.s->kty_valid = 0;
   const int n = P.n, N = P.n + P.m;
   T *x = S.x[cur], *xs = S.xs[cur], *y = S.y[cur], *ys = S.ys[cur], *Kx = S.Kx[cur];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -1290,6 +1292,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Mat<T> A, const T *v, T *out)
 
 __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->eta = in.eta0;
+  s->kty_valid = 0;
   if (in.omega0 > 0.0) s->omega = in.omega0;  // else omega^0 as set by k_problem_norms
   s->inv_omega = 1.0 / s->omega;
   s->const_step = in.const_step;

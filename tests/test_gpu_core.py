@@ -395,3 +395,20 @@ def test_segmented_row_sums_match_oracle(gpu_lib, oracle_lib, persistent):
         assert r_g["restarts"] == r_o["restarts"]
         assert np.abs(x_g - x_o).max() <= TRAJ_TOL[iters] * max(1.0, np.abs(x_o).max())
         assert np.abs(y_g - y_o).max() <= TRAJ_TOL[iters] * max(1.0, np.abs(y_o).max())
+
+
+def test_stored_product_reuse_keeps_iterates_bit_identical(gpu_lib):
+    """The persistent evaluation stores K^T y of the current iterate, and the
+    next chunk's first step attempt uses it instead of gathering it again.
+    The stored sums are those the step would form (the same chunk lists and
+    row sums), so with nothing else feeding back from the evaluation (no
+    restarts, fixed omega) the graph solve, which reuses them, and the
+    host-stepped solve, which gathers in every attempt, give bit-identical
+    iterates."""
+    lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
+    kw = dict(iter_limit=200, rel_tol=1e-12, adaptive_restart=0, pw_update=0, persistent=1)
+    x1, y1, r1 = P.solve(lp, use_graph=1, **kw)
+    x2, y2, r2 = P.solve(lp, use_graph=0, **kw)
+    assert r1["engine"] == r2["engine"] == 1
+    assert r1["iters"] == r2["iters"] == 200 and r1["kkt_passes"] == r2["kkt_passes"]
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
