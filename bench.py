@@ -270,7 +270,7 @@ def _attempt_ms(ctx, reps=30):
     """Mean CUDA-event time of one step attempt on the context's step engine
     (the persistent kernel's per-attempt time, or the two launches of the
     per-launch engines) and the engine's name."""
-    kp, kd, kc = ctx.time_step_kernels(reps)
+    kp, kd, kc, _ = ctx.time_step_kernels(reps)
     if kc > 0:
         return kc, "k_persist (persistent warp-chunk kernel)"
     slab = ctx.last_engine == 2
@@ -497,7 +497,7 @@ def main():
     # per attempt comes from CUDA events around `reps` launches on this
     # stream, continuing from the state of a solve of the same workload.
     ctx, _ = step(args.iter_cap, keep=True)
-    kp, kd, kc = ctx.time_step_kernels(50)
+    kp, kd, kc, ke = ctx.time_step_kernels(50)
     ctx.close()
     bp, bd = _alg_bytes(lp, 64)
     peak, peak_src = _peaks()
@@ -518,10 +518,24 @@ def main():
                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
                     "algorithmic_bytes_per_launch": dom[2], "launch_ms": dom[1]}
     kernels = {"persistent_attempt_ms": kc, "primal_ms": kp, "dual_ms": kd, "primal_bytes": bp, "dual_bytes": bd,
-               "primal_gbs": bp / (kp * 1e-3) / 1e9, "dual_gbs": bd / (kd * 1e-3) / 1e9}
+               "primal_gbs": bp / (kp * 1e-3) / 1e9, "dual_gbs": bd / (kd * 1e-3) / 1e9,
+               "persistent_evaluation_ms": ke}
+    # cost of an evaluation (every 40 iterations: Eq. (15) terms, normalized
+    # gaps, restart decision, restart) from the timed solves: solve time minus
+    # the step attempts at the timed attempt duration, per evaluation
+    evaluation = None
+    if kc > 0:
+        per = [((r["seconds"] - r["kkt_passes"] * kc * 1e-3) / (r["iters"] // 40 + 1), r["seconds"],
+                r["iters"] // 40 + 1) for r in results]
+        us = float(np.median([p[0] for p in per])) * 1e6
+        evaluation = {"us_per_evaluation": us,
+                      "share_of_solve": float(np.median([p[0] * p[2] / p[1] for p in per])),
+                      "basis": "device-timed solve minus kkt_passes x the timed persistent attempt, per "
+                               "evaluation (a chunk's first attempt that reuses the evaluation's K^T y counts as "
+                               "evaluation time saved)"}
     # float32 arithmetic on the same workload
     ctx32, r32 = step(args.iter_cap, precision=P.PDLP_FP32, keep=True)
-    kp32, kd32, kc32 = ctx32.time_step_kernels(50)
+    kp32, kd32, kc32, _ = ctx32.time_step_kernels(50)
     ctx32.close()
     bp32, bd32 = _alg_bytes(lp, 32)
     kernels.update({"fp32_persistent_attempt_ms": kc32, "fp32_primal_ms": kp32, "fp32_dual_ms": kd32,
@@ -573,9 +587,11 @@ def main():
         extra["unroll"] = _unroll_line(P, dev, sptr)
         extra["ablation"] = _ablation_line(P)
 
-    # per solve: ~120 create/setup launches, 13 per evaluation (persistent
-    # step kernel, 2 evaluation, 6 gap passes, decide, restart, finish) + 8
-    launches_per_step = 120 + 13 * evals / args.steps + 8
+    # per solve: ~120 create/setup launches, 6 per evaluation (persistent
+    # step kernel, persistent evaluation, 3 gap passes, finish), 5 more per
+    # restart (apply, 3 gap passes of the restart point, book-keeping) + 8
+    restarts = sum(r["restarts"] for r in results)
+    launches_per_step = 120 + (6 * evals + 5 * restarts) / args.steps + 8
     out = {"metric": METRIC, "value": value, "unit": "PDHG iter/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -583,12 +599,13 @@ def main():
                       "iter_cap": args.iter_cap, "parallelism": f"replicas x{ws}",
                       "l2": "flushed between steps (256 MiB write)",
                       "rel_kkt_at_cap": float(np.median([r["rel_kkt"] for r in results]))},
-           "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+           "roofline": roofline, "kernels": kernels, "evaluation": evaluation, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches_per_step * args.steps),
            "gpu_launches_basis": ("not a profiler count: kernel nodes the solve graph executes per create + solve "
-                                  "(about 120 set-up launches, 13 per evaluation: persistent step kernel, two "
-                                  "evaluation kernels, six gap passes, decision, restart, finish; 8 at the end), "
-                                  "times the evaluations the device counted"),
+                                  "(about 120 set-up launches; 6 per evaluation: persistent step kernel, persistent "
+                                  "evaluation, three gap passes, finish; 5 more per restart: apply, three gap passes "
+                                  "of the restart point, book-keeping; 8 at the end), times the evaluations and "
+                                  "restarts the device counted"),
            "clocks": clk, "time_to_tol": tol, **pagerank, **extra}
     print(json.dumps(out), flush=True)
 

@@ -276,8 +276,12 @@ int pdlp_get_trace(pdlp_ctx *ctx, double *out, int32_t max_records, int32_t *cou
  * milliseconds of the primal and the dual kernel; ms[2] receives the mean
  * duration of one step attempt inside the persistent step kernel, timed over
  * `reps` launches of it that each run up to eval_every accepted steps (0 when
- * the context's `persistent` option is 0).  This call leaves the state
- * advanced: solve again before reading results. */
+ * the context's `persistent` option is 0); ms[3] receives the mean duration
+ * of one launch of the persistent evaluation kernel (the products and
+ * Eq. (15) terms of one evaluation; float64 contexts with the persistent
+ * step kernel, else 0), timed over `reps` launches on the state as it
+ * stands.  `ms` holds 4 floats.  This call leaves the state advanced: solve
+ * again before reading results. */
 int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms);
 
 /* The normalized duality gap of pdlp_normalized_gap, for callers that cannot

@@ -201,11 +201,12 @@ class Context:
 
     def pdlp_time_step_kernels(self, reps: int = 50):
         """Mean CUDA-event durations (ms): the primal and the dual step kernels
-        launched alone, and one step attempt inside the persistent kernel
-        (0.0 when the context runs without it)."""
-        ms = np.zeros(3, np.float32)
+        launched alone, one step attempt inside the persistent kernel, and one
+        launch of the persistent evaluation kernel (each 0.0 when the context
+        runs without that kernel)."""
+        ms = np.zeros(4, np.float32)
         check(self._lib.pdlp_time_step_kernels(self._h, int(reps), ms.ctypes.data), self._h)
-        return float(ms[0]), float(ms[1]), float(ms[2])
+        return float(ms[0]), float(ms[1]), float(ms[2]), float(ms[3])
 
     time_step_kernels = pdlp_time_step_kernels
 

@@ -1044,6 +1044,11 @@ extern "C" int pdlp_time_step_kernels(pdlp_ctx *ctx, int32_t reps, float *ms) {
     e = time_persist<float>(ctx->pc32.K, ctx->pc32.KT, ctx->pc32.P, ctx->pc32.S, ctx->pc32.pg, reps, ctx->st,
                             ms + 2);
   if (e) return cuda_fail(ctx, e, "time_persist");
+  ms[3] = 0.f;
+  if (prec == PDLP_FP64 && ctx->p64.pe.grid > 0)
+    e = time_eval_persist<double>(ctx->p64.K, ctx->p64.KT, ctx->p64.KTb, ctx->p64.P, ctx->p64.S, ctx->p64.pe, reps,
+                                  ctx->st, ms + 3);
+  if (e) return cuda_fail(ctx, e, "time_eval_persist");
   return PDLP_OK;
 }
 

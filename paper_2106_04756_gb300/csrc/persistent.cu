@@ -846,6 +846,34 @@ cudaError_t launch_eval_persist(const Mat<T> &K, const Mat<T> &KT, const Mat<T> 
   }
 }
 
+// Mean duration of one launch of the persistent evaluation kernel, event-timed
+// over `reps` launches on `st` after one untimed launch (each evaluates the
+// state as it stands; 0 when the context has no such kernel).
+template <typename T>
+cudaError_t time_eval_persist(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
+                              const State<T> &S, const PersistGeo &pe, int reps, cudaStream_t st, float *ms) {
+  *ms = 0.f;
+  if (pe.grid <= 0) return cudaSuccess;
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0))) return e;
+  if ((e = cudaEventCreate(&e1))) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  e = launch_eval_persist<T>(K, KT, KTb, P, S, pe, st);
+  if (!e) e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && !e; ++r) e = launch_eval_persist<T>(K, KT, KTb, P, S, pe, st);
+  if (!e) e = cudaEventRecord(e1, st);
+  if (!e) e = cudaEventSynchronize(e1);
+  float a = 0.f;
+  if (!e) e = cudaEventElapsedTime(&a, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!e) *ms = a / (float)reps;
+  return e;
+}
+
 // Mean duration of one step attempt inside the persistent kernel: `reps`
 // launches (each runs until eval_every steps are accepted), event-timed on
 // `st`, divided by the attempts they made.
@@ -890,6 +918,8 @@ cudaError_t time_persist(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P,
   template cudaError_t time_persist<T>(const Mat<T> &, const Mat<T> &, const Problem<T> &, const State<T> &,   \
                                        const PersistGeo &, int, cudaStream_t, float *);                                      \
   template cudaError_t eval_plan<T>(const PersistGeo &, int, int, PersistGeo *);                                  \
+  template cudaError_t time_eval_persist<T>(const Mat<T> &, const Mat<T> &, const Mat<T> &, const Problem<T> &,   \
+                                            const State<T> &, const PersistGeo &, int, cudaStream_t, float *); \
   template cudaError_t launch_eval_persist<T>(const Mat<T> &, const Mat<T> &, const Mat<T> &, const Problem<T> &, \
                                               const State<T> &, const PersistGeo &, cudaStream_t);
 PDLP_INST(double)

@@ -79,6 +79,9 @@ cudaError_t eval_plan(const PersistGeo &pg, int cmax_kt, int cmax_k, PersistGeo 
 template <typename T>
 cudaError_t launch_eval_persist(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
                                 const State<T> &S, const PersistGeo &pe, cudaStream_t st);
+template <typename T>
+cudaError_t time_eval_persist(const Mat<T> &K, const Mat<T> &KT, const Mat<T> &KTb, const Problem<T> &P,
+                              const State<T> &S, const PersistGeo &pe, int reps, cudaStream_t st, float *ms);
 
 template <typename T>
 cudaError_t run_stepped(const Mat<T> &K, const Mat<T> &KT, const Problem<T> &P, const State<T> &S,

@@ -319,11 +319,16 @@ def test_step_kernel_timing_reports_the_persistent_attempt(gpu_lib):
     lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
     with P.Context.from_lp(lp, iter_limit=100, persistent=1) as ctx:
         ctx.solve()
-        kp, kd, kc = ctx.time_step_kernels(5)
+        kp, kd, kc, ke = ctx.time_step_kernels(5)
         assert kp > 0 and kd > 0 and kc > 0
+        assert ke > 0  # the persistent evaluation kernel (float64)
     with P.Context.from_lp(lp, iter_limit=100, persistent=0) as ctx:
         ctx.solve()
-        assert ctx.time_step_kernels(5)[2] == 0.0
+        ms = ctx.time_step_kernels(5)
+        assert ms[2] == 0.0 and ms[3] == 0.0
+    with P.Context.from_lp(lp, iter_limit=100, persistent=1, precision=P.PDLP_FP32) as ctx:
+        ctx.solve()
+        assert ctx.time_step_kernels(5)[3] == 0.0  # float32: the separate evaluation kernels
 
 
 @pytest.mark.parametrize("persistent", [1, 0, 2])
