@@ -193,14 +193,16 @@ def aggregate_over_ranks(elapsed, iters, device=None):
 
 def _batch_line(P):
     """4096 planted LPs (m in [20, 400], n in [50, 1000], 5% density) in one
-    persistent launch per call: LPs/s and iterations/s to 1e-6 and 1e-8."""
+    persistent launch per call (two for float32 + float64 refinement): LPs/s
+    and iterations/s to 1e-6 and 1e-8."""
     import lpgen
     import torch
     lps = lpgen.batch_4096()
     out = {"workload": "batch_4096", "count": len(lps), "nnz_total": int(sum(lp.nnz for lp in lps))}
     P.solve_batch(lps[:256], rel_tol=1e-6, iter_limit=2000)  # autotuner + warm-up on a slice
     for name, prec, tol in (("fp64_1e-6", P.PDLP_FP64, 1e-6), ("fp64_1e-8", P.PDLP_FP64, 1e-8),
-                            ("fp32_1e-6", P.PDLP_FP32, 1e-6)):
+                            ("fp32_1e-6", P.PDLP_FP32, 1e-6), ("fp32_refine_1e-6", P.PDLP_FP32_REFINE, 1e-6),
+                            ("fp32_refine_1e-8", P.PDLP_FP32_REFINE, 1e-8)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, _, rs = P.solve_batch(lps, precision=prec, rel_tol=tol, iter_limit=20000)

@@ -54,6 +54,10 @@ struct BatchIn {
   const uint8_t *ineq;
   const int32_t *order;  // LP processing order
   const int32_t *lanes;  // per LP: lanes per row for K (low byte) and K^T (next byte)
+  // nullable: starting points (original space, packed like c / q) and the
+  // iterations / KKT passes each LP already spent (its limits shrink by them)
+  const double *x0, *y0;
+  const long long *used_iters, *used_passes;
 };
 
 struct BatchOpts {
@@ -61,6 +65,7 @@ struct BatchOpts {
   long long iter_limit, kkt_pass_limit;
   int ruiz_iters, pock_chambolle, eval_every, adaptive_restart, pw_update;
   int restart_to_current;  // 0: the restart candidate is always the average (Appendix C.2)
+  int stall_evals;         // > 0: stop (kStalled) after this many evaluations without a 10% gain
 };
 
 struct BatchOut {
@@ -470,6 +475,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     const double *val = in.val + zo, *c = in.c + co, *q = in.q + ro, *l = in.l + co, *u = in.u + co;
     const uint8_t *ineq = in.ineq + ro;
     const int Lk = in.lanes[b] & 0xff, Lt = (in.lanes[b] >> 8) & 0xff;
+    const long long iter_limit = o.iter_limit - (in.used_iters ? in.used_iters[b] : 0ll);
+    const long long pass_limit = o.kkt_pass_limit - (in.used_passes ? in.used_passes[b] : 0ll);
     // ---- validation (column range and order, finite data, l <= u)
     {
       int badl = 0;
@@ -602,7 +609,9 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     }
     double eta_hat = kmax > 0.0 ? 1.0 / kmax : 1.0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const T x = clampv<T>(T(0), (T)w.ls[j], (T)w.us[j]);
+      // z^0 = proj(0), or the projection of the given start (scaled space)
+      const T xs0 = in.x0 ? (T)(in.x0[co + j] / w.D2[j]) : T(0);
+      const T x = clampv<T>(xs0, (T)w.ls[j], (T)w.us[j]);
       w.x[0][j] = x;
       w.x0[j] = x;
       w.xs[0][j] = 0.0;
@@ -610,7 +619,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const T lo = (T)w.ylos[i];
-      const T y = T(0) > lo ? T(0) : lo;
+      const T ys0 = in.y0 ? (T)(in.y0[ro + i] / w.D1[i]) : T(0);
+      const T y = ys0 > lo ? ys0 : lo;
       w.y[0][i] = y;
       w.y0[i] = y;
       w.ys[0][i] = 0.0;
@@ -629,12 +639,14 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
     double sum_eta = 0.0, mu0 = INFINITY, muc_prev = INFINITY;
     int status = kRunning, ret_avg = 0;
     double kkt[2][8];
+    double stall_best = INFINITY;
+    int stall_cnt = 0;
     bool first_eval = true;
     long long fac_k0 = 0;
     for (;;) {
       // ---------- evaluation (at the start and every eval_every steps)
-      const bool eval_now = first_eval || (k % o.eval_every == 0) || k >= o.iter_limit ||
-                            passes_used >= o.kkt_pass_limit;
+      const bool eval_now = first_eval || (k % o.eval_every == 0) || k >= iter_limit ||
+                            passes_used >= pass_limit;
       if (eval_now) {
         const bool avg = sum_eta > 0.0;
         const double inv = avg ? 1.0 / sum_eta : 0.0;
@@ -713,13 +725,28 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
           status = kNumErr;
           break;
         }
-        if (k >= o.iter_limit) {
+        if (k >= iter_limit) {
           status = kIterLimit;
           break;
         }
-        if (passes_used >= o.kkt_pass_limit) {
+        if (passes_used >= pass_limit) {
           status = kKktLimit;
           break;
+        }
+        if (o.stall_evals > 0) {
+          // the better candidate's relative error has not dropped by 10%
+          // for stall_evals evaluations: the arithmetic's floor (float32)
+          const double e0 = fmax(kkt[0][5], fmax(kkt[0][6], kkt[0][7]));
+          const double e1 = avg ? fmax(kkt[1][5], fmax(kkt[1][6], kkt[1][7])) : INFINITY;
+          const double err = fmin(e0, e1);
+          if (err < 0.9 * stall_best) {
+            stall_best = err;
+            stall_cnt = 0;
+          } else if (++stall_cnt >= o.stall_evals) {
+            status = kStalled;
+            ret_avg = e1 < e0 ? 1 : 0;
+            break;
+          }
         }
         if (!first_eval && o.adaptive_restart && avg) {
           // restart candidate and criteria (Section 3.2)
@@ -882,13 +909,13 @@ __global__ void __launch_bounds__(kBThreads) k_batch(BatchIn in, BatchOpts o, Ba
         }
         eta_hat = eta_next;
         eta = eta_next;
-        if (!accepted && passes_used >= o.kkt_pass_limit) break;
+        if (!accepted && passes_used >= pass_limit) break;
       }
       if (status != kRunning) break;
       if (!accepted) continue;  // pass limit: the evaluation reports it
     }
     // ---------- output: the returned candidate in the original space
-    if (status != kOptimal) ret_avg = 0;
+    if (status != kOptimal && status != kStalled) ret_avg = 0;
     {
       const bool avg_out = ret_avg == 1;
       const T *x = avg_out ? w.xa : w.x[cur], *y = avg_out ? w.ya : w.y[cur];
@@ -948,7 +975,12 @@ constexpr int kNumCand = sizeof(kCand) / sizeof(kCand[0]);
 
 struct DevBatch {
   DevBuf mm, nn, ro, co, zo, rp, ci, val, c, q, l, u, ineq, order, lanes, x, y, res, ctr, slab;
+  DevBuf x0, y0, used;  // PDLP_FP32_REFINE: the float64 stage's starts and spent budgets
 };
+
+// PDLP_FP32_REFINE batches: the float32 stage of an LP stops at this many
+// evaluations (40 steps each) without a 10% gain in its relative error
+constexpr int kBatchStallEvals = 50;
 
 template <typename T>
 cudaError_t launch_batch(const BatchIn &in, const BatchOpts &o, BatchOut out, char *slab, size_t wb, int grid,
@@ -1000,6 +1032,7 @@ int solve_batch_t(int32_t count, const std::vector<int32_t> &hm, const std::vect
     ot.rel_tol = 0.0;  // never stops early
     ot.iter_limit = 100;
     ot.kkt_pass_limit = 1ll << 40;
+    ot.stall_evals = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1015,6 +1048,8 @@ int solve_batch_t(int32_t count, const std::vector<int32_t> &hm, const std::vect
       int best_c = 0;
       BatchIn it = in;
       it.count = (int32_t)sample.size();
+      it.x0 = it.y0 = nullptr;  // timed from cold starts with full budgets
+      it.used_iters = it.used_passes = nullptr;
       if ((e = cudaMemcpyAsync(order, sample.data(), sizeof(int32_t) * sample.size(), cudaMemcpyHostToDevice, st)))
         break;
       for (int cnd = 0; cnd < kNumCand && !e; ++cnd) {
@@ -1083,8 +1118,8 @@ extern "C" int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *
   if (count < 1 || !m || !n || !row_off || !col_off || !nnz_off || !row_ptr || !col_idx || !val || !c || !q ||
       !l || !u || !ineq_mask || !opts)
     return bfail(PDLP_ERR_INVALID_ARG, "NULL argument or count < 1");
-  if (opts->precision != PDLP_FP64 && opts->precision != PDLP_FP32)
-    return bfail(PDLP_ERR_INVALID_ARG, "batch precision must be PDLP_FP64 or PDLP_FP32");
+  if (opts->precision != PDLP_FP64 && opts->precision != PDLP_FP32 && opts->precision != PDLP_FP32_REFINE)
+    return bfail(PDLP_ERR_INVALID_ARG, "batch precision must be PDLP_FP64, PDLP_FP32 or PDLP_FP32_REFINE");
   if (opts->eval_every < 1 || !(opts->rel_tol >= 0.0) || opts->ruiz_iters < 0)
     return bfail(PDLP_ERR_INVALID_ARG, "bad options");
   if (opts->step_policy != 0 || opts->omega0 != 0.0)
@@ -1158,16 +1193,71 @@ extern "C" int pdlp_solve_batch(int32_t count, const int32_t *m, const int32_t *
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return hzo[a + 1] - hzo[a] > hzo[b + 1] - hzo[b]; });
   std::string why;
-  const int rc = opts->precision == PDLP_FP64
-                     ? solve_batch_t<double>(count, hm, hn, hzo, in, o, out, db, order.data(), st, why)
-                     : solve_batch_t<float>(count, hm, hn, hzo, in, o, out, db, order.data(), st, why);
+  auto check_bad = [&]() -> int {
+    unsigned bad = 0;
+    if ((e = cudaMemcpy(&bad, out.bad, sizeof(unsigned), cudaMemcpyDeviceToHost)))
+      return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
+    if (bad) return bfail(PDLP_ERR_INVALID_ARG, "LP " + std::to_string(bad - 1) +
+                                                    ": invalid data (column index range or order, non-finite "
+                                                    "value, or l > u)");
+    return PDLP_OK;
+  };
+  std::vector<pdlp_result> r1;  // float32 stage of PDLP_FP32_REFINE
+  int rc;
+  if (opts->precision == PDLP_FP32_REFINE) {
+    // float32 steps until Eq. (15) holds at rel_tol or the float32 floor (a
+    // stall), then float64 steps from each LP's float32 point with what is
+    // left of its iteration and KKT-pass budgets (an LP already solved
+    // passes the float64 check at its start)
+    BatchOpts o1 = o;
+    o1.stall_evals = kBatchStallEvals;
+    rc = solve_batch_t<float>(count, hm, hn, hzo, in, o1, out, db, order.data(), st, why);
+    if (rc) return bfail(rc, why);
+    if ((rc = check_bad())) return rc;
+    r1.resize(count);
+    if ((e = cudaMemcpy(r1.data(), out.res, sizeof(pdlp_result) * count, cudaMemcpyDeviceToHost)))
+      return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
+    std::vector<long long> used(2 * (size_t)count);
+    for (int b = 0; b < count; ++b) {
+      used[b] = r1[b].iters;
+      used[count + b] = r1[b].kkt_passes;
+    }
+    double *x0 = reinterpret_cast<double *>(db.x0.get(sizeof(double) * Cc));
+    double *y0 = reinterpret_cast<double *>(db.y0.get(sizeof(double) * R));
+    long long *du = reinterpret_cast<long long *>(db.used.get(sizeof(long long) * 2 * count));
+    if (!x0 || !y0 || !du) return bfail(PDLP_ERR_OOM, "allocation failed");
+    e = cudaMemcpyAsync(x0, out.x, sizeof(double) * Cc, cudaMemcpyDeviceToDevice, st);
+    if (!e) e = cudaMemcpyAsync(y0, out.y, sizeof(double) * R, cudaMemcpyDeviceToDevice, st);
+    if (!e) e = cudaMemcpyAsync(du, used.data(), sizeof(long long) * 2 * count, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
+    in.x0 = x0;
+    in.y0 = y0;
+    in.used_iters = du;
+    in.used_passes = du + count;
+    rc = solve_batch_t<double>(count, hm, hn, hzo, in, o, out, db, order.data(), st, why);
+  } else {
+    rc = opts->precision == PDLP_FP64
+             ? solve_batch_t<double>(count, hm, hn, hzo, in, o, out, db, order.data(), st, why)
+             : solve_batch_t<float>(count, hm, hn, hzo, in, o, out, db, order.data(), st, why);
+  }
   if (rc) return bfail(rc, why);
-  unsigned bad = 0;
-  if ((e = cudaMemcpy(&bad, out.bad, sizeof(unsigned), cudaMemcpyDeviceToHost)))
-    return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
-  if (bad) return bfail(PDLP_ERR_INVALID_ARG, "LP " + std::to_string(bad - 1) +
-                                                  ": invalid data (column index range or order, non-finite "
-                                                  "value, or l > u)");
+  if ((rc = check_bad())) return rc;
+  if (!r1.empty()) {
+    // the float64 stage's outcome, with both stages' counts
+    std::vector<pdlp_result> r2(count);
+    if ((e = cudaMemcpy(r2.data(), out.res, sizeof(pdlp_result) * count, cudaMemcpyDeviceToHost)))
+      return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
+    for (int b = 0; b < count; ++b) {
+      r2[b].iters += r1[b].iters;
+      r2[b].kkt_passes += r1[b].kkt_passes;
+      r2[b].restarts += r1[b].restarts;
+      r2[b].refine_rounds = 1;
+    }
+    if (res && (e = cudaMemcpy(res, r2.data(), sizeof(pdlp_result) * count, cudaMemcpyDefault)))
+      return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
+    res = nullptr;  // written
+  }
   if (x_out && (e = cudaMemcpy(x_out, out.x, sizeof(double) * Cc, cudaMemcpyDefault)))
     return bfail(PDLP_ERR_CUDA, cudaGetErrorString(e));
   if (y_out && (e = cudaMemcpy(y_out, out.y, sizeof(double) * R, cudaMemcpyDefault)))

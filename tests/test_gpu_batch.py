@@ -84,6 +84,27 @@ def test_batch_fp32_arithmetic(gpu_lib, oracle_lib):
         _check_point(lps[b], xs[b], ys[b], 2e-5, b)
 
 
+def test_batch_fp32_refine_to_1e8(gpu_lib, oracle_lib):
+    """PDLP_FP32_REFINE: float32 steps until Eq. (15) holds or float32 stalls,
+    then float64 steps from that point with the rest of each LP's budget.
+    Members are solved to 1e-8 by the oracle's Eq. (15) at the returned
+    points, about as many as by the float64 batch, within the iteration cap
+    counted over both stages."""
+    lps = lpgen.batch_planted(count=96, seed_key=(3, 7))
+    cap = 20000
+    xs, ys, rs = P.solve_batch(lps, precision=P.PDLP_FP32_REFINE, rel_tol=1e-8, iter_limit=cap)
+    _, _, r64 = P.solve_batch(lps, rel_tol=1e-8, iter_limit=cap)
+    solved = [b for b in range(len(lps)) if rs[b]["status_name"] == "OPTIMAL"]
+    solved64 = [b for b in range(len(lps)) if r64[b]["status_name"] == "OPTIMAL"]
+    assert len(solved) >= len(solved64) - 2, (len(solved), len(solved64))
+    for b in solved:
+        _check_point(lps[b], xs[b], ys[b], 1e-8, b)
+    for b, r in enumerate(rs):
+        assert r["iters"] <= cap and r["refine_rounds"] == 1, (b, r)
+        if r["status_name"] != "OPTIMAL":
+            assert r["status_name"] == "ITER_LIMIT" and r["iters"] == cap, (b, r)
+
+
 def test_batch_ragged_and_degenerate_members(gpu_lib, oracle_lib):
     lps = lpgen.batch_planted(count=6, seed_key=(3, 10))
     tiny = lpgen.planted_uniform(1, 1, 1.0, frac_boxed=1.0, seed_key=(3, 11))
