@@ -91,8 +91,11 @@ typedef struct {
   double inner_tol;         /* PDLP_FP32_REFINE: Eq. (15) tolerance of the first inner
                                solve, 1e-5; a later round that can reach rel_tol uses
                                the loosest tolerance that should get there (see
-                               refine.cu), and the loop ends when an inner solve stops
-                               at a limit                                               */
+                               refine.cu).  When a round divides the relative error by
+                               less than 10, makes it worse, or refine_rounds is
+                               reached, float64 PDLP finishes from the refined point.
+                               iter_limit, kkt_pass_limit and time_limit_s bound the
+                               whole solve (all rounds and the finish)                 */
   int32_t refine_rounds;    /* PDLP_FP32_REFINE: maximum outer rounds                    */
   int32_t unroll_T;         /* >0: pdlp_solve runs T unrolled steps for pdlp_grad        */
   int32_t ckpt_every;       /* unrolled steps between stored checkpoints                 */
@@ -157,6 +160,9 @@ typedef struct {
   double rel_gap, rel_pres, rel_dres; /* each divided by its right-hand factor            */
   double seconds;                 /* device wall time of the solve                        */
   double step_size, primal_weight; /* eta and omega at the end of the solve              */
+  int64_t finish_iters;           /* PDLP_FP32_REFINE: iterations of the float64 finish
+                                     (counted in iters too); 0 if the float32 rounds
+                                     reached rel_tol or a limit                          */
 } pdlp_result;
 
 /* ---------------------------------------------------------------- calls */

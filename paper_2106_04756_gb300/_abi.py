@@ -55,7 +55,8 @@ class pdlp_result(C.Structure):
                 ("engine", C.c_int32), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("gap", C.c_double), ("pres", C.c_double), ("dres", C.c_double),
                 ("rel_gap", C.c_double), ("rel_pres", C.c_double), ("rel_dres", C.c_double),
-                ("seconds", C.c_double), ("step_size", C.c_double), ("primal_weight", C.c_double)]
+                ("seconds", C.c_double), ("step_size", C.c_double), ("primal_weight", C.c_double),
+                ("finish_iters", C.c_int64)]
 
     def asdict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ }

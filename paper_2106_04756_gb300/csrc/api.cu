@@ -214,7 +214,7 @@ int use_slab_engine(const pdlp_ctx *ctx, int elem_bytes) {
 // on the problem `P` (already filled in).
 template <typename T>
 int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_dev = nullptr,
-                int stall_evals = 0) {
+                int stall_evals = 0, const long long *lim_dev = nullptr) {
   const int n = ctx->n, m = ctx->m, N = n + m;
   const size_t nv = 2 * (size_t)n + 2 * (size_t)m + 2 * (size_t)m + 2 * (size_t)n + 2 * (size_t)m +
                     (size_t)n + (size_t)m + 2 * (size_t)n + (size_t)m;
@@ -294,6 +294,7 @@ int setup_state(pdlp_ctx *ctx, Precision<T> &pr, double tol, const double *tol_d
   in.rel_tol = tol;
   in.tol_dev = tol_dev;
   in.stall_evals = stall_evals;
+  in.lim_dev = lim_dev;
   in.beta_suff = o.beta_suff;
   in.beta_nec = o.beta_nec;
   in.beta_art = o.beta_art;
@@ -356,13 +357,29 @@ void fill_problem64(pdlp_ctx *ctx, Problem<double> &P) {
   P.D2inv = reinterpret_cast<const double *>(ctx->D2inv.ptr());
 }
 
+// PDLP_FP32_REFINE: the device limits shared by the inner float32 solves and
+// the float64 finish (refine.cu), set to the caller's limits until a solve
+// writes what is left of them.
+const long long *refine_limits(pdlp_ctx *ctx) {
+  if (ctx->opts.precision != PDLP_FP32_REFINE) return nullptr;
+  long long *d = refine_limits_dev(ctx->ref);
+  if (!d) return nullptr;
+  const pdlp_options &o = ctx->opts;
+  const long long full[4] = {o.iter_limit, o.kkt_pass_limit,
+                             o.time_limit_s > 0 ? (long long)(o.time_limit_s * 1e9) : 0ll, 0ll};
+  if (cudaMemcpy(d, full, sizeof(full), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+  return d;
+}
+
 int setup_fp64(pdlp_ctx *ctx) {
   Precision<double> &pr = ctx->p64;
   if (pr.ready) return PDLP_OK;
   setup_matrix<double>(ctx, pr.K, pr.KT, reinterpret_cast<const double *>(ctx->val.ptr()),
                        reinterpret_cast<const double *>(ctx->tval.ptr()));
   fill_problem64(ctx, pr.P);
-  return setup_state<double>(ctx, pr, ctx->opts.rel_tol);
+  const long long *lim = refine_limits(ctx);
+  if (ctx->opts.precision == PDLP_FP32_REFINE && !lim) return fail(ctx, PDLP_ERR_OOM, "limits allocation failed");
+  return setup_state<double>(ctx, pr, ctx->opts.rel_tol, nullptr, 0, lim);
 }
 
 // float32 copies of K~, K~^T (shared by the plain float32 and the refinement paths)
@@ -428,7 +445,7 @@ int setup_refine(pdlp_ctx *ctx) {
   // correction problem) returns to the outer loop after 250 evaluations
   // (10,000 iterations) without a 10% gain; windows of 50 cut off plateaus
   // that restarted PDHG passes through on its way (measured on PageRank)
-  return setup_state<float>(ctx, pr, ctx->opts.inner_tol, tol_dev, 250);
+  return setup_state<float>(ctx, pr, ctx->opts.inner_tol, tol_dev, 250, refine_limits(ctx));
 }
 
 void read_result(const Scalars &s, double seconds, pdlp_result *res) {
@@ -886,10 +903,14 @@ extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, dou
     auto run_inner = [ctx](Scalars *h) -> cudaError_t {
       return run_graph<float>(ctx, ctx->pc32, h) == PDLP_OK ? cudaSuccess : cudaErrorUnknown;
     };
+    RefineLimits lim;
+    lim.iter_limit = ctx->opts.iter_limit;
+    lim.kkt_limit = ctx->opts.kkt_pass_limit;
+    lim.time_limit_s = ctx->opts.time_limit_s;
+    double *xi = reinterpret_cast<double *>(ctx->xin.ptr()), *yi = reinterpret_cast<double *>(ctx->yin.ptr());
     cudaError_t e = refine_solve(ctx->ref, ctx->p64.K, ctx->p64.KT, ctx->p64.P, ctx->pc32.S, run_inner,
-                                 ctx->opts.rel_tol, ctx->opts.inner_tol, ctx->opts.refine_rounds,
-                                 reinterpret_cast<const double *>(ctx->xin.ptr()),
-                                 reinterpret_cast<const double *>(ctx->yin.ptr()), ctx->st, &ro);
+                                 ctx->opts.rel_tol, ctx->opts.inner_tol, ctx->opts.refine_rounds, lim, xi, yi,
+                                 ctx->st, &ro);
     if (e) return cuda_fail(ctx, e, "refinement");
     xo = ro.x;
     yo = ro.y;
@@ -908,6 +929,36 @@ extern "C" int pdlp_solve(pdlp_ctx *ctx, const double *x0, const double *y0, dou
     r.rel_gap = ro.kkt[5];
     r.rel_pres = ro.kkt[6];
     r.rel_dres = ro.kkt[7];
+    int spent = 0;
+    if (ro.finish) {
+      // the float32 corrections stopped paying: float64 PDLP from the refined
+      // point (staged as the start point) with what is left of the budget
+      if (refine_set_limits(ctx->ref, lim, ro.iters, ro.kkt_passes, ro.seconds, ctx->st, &spent, &e)) {
+        CK(cudaMemcpyAsync(xi, ro.x, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, ctx->st), "finish x0");
+        CK(cudaMemcpyAsync(yi, ro.y, sizeof(double) * ctx->m, cudaMemcpyDeviceToDevice, ctx->st), "finish y0");
+        if ((rc = run_graph<double>(ctx, ctx->p64, &hs))) return rc;
+        pdlp_result rf;
+        read_result(hs, 0.0, &rf);
+        const double e_ref = fmax(r.rel_gap, fmax(r.rel_pres, r.rel_dres));
+        const double e_fin = fmax(rf.rel_gap, fmax(rf.rel_pres, rf.rel_dres));
+        if (rf.status == kOptimal || e_fin <= e_ref) {
+          r = rf;
+          r.engine = engine_of(ctx->p64);
+          xo = ctx->p64.S.xo;
+          yo = ctx->p64.S.yo;
+        } else {
+          r.status = rf.status;  // the finish ended at a limit further from Eq. (15): keep the refined point
+        }
+        r.iters = ro.iters + hs.k;
+        r.kkt_passes = ro.kkt_passes + hs.attempts;
+        r.restarts = ro.restarts + hs.restarts;
+        r.refine_rounds = ro.rounds;
+        r.finish_iters = hs.k;
+      } else {
+        if (e) return cuda_fail(ctx, e, "refinement limits");
+        r.status = spent;
+      }
+    }
   }
   CK(cudaEventRecord(ctx->ev1, ctx->st), "event");
   if (x_out) CK(cudaMemcpyAsync(x_out, xo, sizeof(double) * ctx->n, cudaMemcpyDefault, ctx->st), "x_out");

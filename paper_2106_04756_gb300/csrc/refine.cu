@@ -13,9 +13,15 @@
 // of the original problem: x = xh + a/dP, y = yh + b/dD.  Each round solves
 // the correction problem in float32 to a loose tolerance and applies the
 // correction in float64; the loop stops when Eq. (15) holds on the original
-// problem, evaluated in float64.
+// problem, evaluated in float64.  When a round divides the error by less than
+// kRefineMinGain (the float32 solves of the corrections have stalled), makes
+// it worse, or the round cap is reached, the loop hands the best point to a
+// float64 PDLP finish (run by the caller) with what is left of the budget:
+// every inner solve and the finish share the caller's iteration, KKT-pass
+// and time limits.
 #include <math.h>
 
+#include <chrono>
 #include <vector>
 
 #include "refine.cuh"
@@ -219,6 +225,29 @@ cudaError_t refine_alloc(RefineBuffers &R, int32_t m, int32_t n, int32_t nbK, in
   return cudaSuccess;
 }
 
+long long *refine_limits_dev(RefineBuffers &R) {
+  return reinterpret_cast<long long *>(R.lim.get(4 * sizeof(long long)));
+}
+
+int refine_set_limits(RefineBuffers &R, const RefineLimits &L, long long iters, long long passes, double secs,
+                      cudaStream_t st, int *spent, cudaError_t *err) {
+  long long left[3];
+  const int why = refine_remaining(L.iter_limit, L.kkt_limit, L.time_limit_s, iters, passes, secs, left);
+  *err = cudaSuccess;
+  if (why) {
+    *spent = why == 1 ? kIterLimit : (why == 2 ? kKktLimit : kTimeLimit);
+    return 0;
+  }
+  long long *d = refine_limits_dev(R);
+  if (!d) {
+    *err = cudaErrorMemoryAllocation;
+    return 0;
+  }
+  // pageable source: the copy is staged before the call returns
+  *err = cudaMemcpyAsync(d, left, sizeof(left), cudaMemcpyHostToDevice, st);
+  return *err == cudaSuccess ? 1 : 0;
+}
+
 Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64) {
   Problem<float> P;
   P.m = P64.m;
@@ -242,9 +271,11 @@ Problem<float> refine_problem(RefineBuffers &R, const Problem<double> &P64) {
 
 cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<double> &KT, const Problem<double> &P,
                          const State<float> &Sc, const std::function<cudaError_t(Scalars *)> &run_inner,
-                         double tol, double inner_tol, int max_rounds, const double *x_stage,
-                         const double *y_stage, cudaStream_t st, RefineOutcome *out) {
+                         double tol, double inner_tol, int max_rounds, const RefineLimits &lim,
+                         const double *x_stage, const double *y_stage, cudaStream_t st, RefineOutcome *out) {
   cudaError_t e;
+  const auto t_start = std::chrono::steady_clock::now();
+  auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(); };
   const int N = P.n + P.m, grid = (N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024;
   RefView V = R.v;
   k_ref_start<<<grid, 256, 0, st>>>(P, V, x_stage, y_stage);
@@ -264,6 +295,7 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
   out->status = kIterLimit;
   out->iters = out->kkt_passes = out->restarts = 0;
   out->rounds = 0;
+  out->finish = false;
   double best = INFINITY;
   int inner_stop = 0;  // an inner solve stopped at a limit: end after evaluating its update
   for (int round = 0;; ++round) {
@@ -283,15 +315,24 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
       if ((e = cudaMemcpyAsync(V.xh, V.xb, sizeof(double) * P.n, cudaMemcpyDeviceToDevice, st))) return e;
       if ((e = cudaMemcpyAsync(V.yh, V.yb, sizeof(double) * P.m, cudaMemcpyDeviceToDevice, st))) return e;
       if ((e = cudaStreamSynchronize(st))) return e;
+      if (inner_stop) out->status = inner_stop;
+      else out->finish = isfinite(best);
       break;
     }
+    const double prev = best;
     best = rel;
     for (int a = 0; a < 8; ++a) out->kkt[a] = h[a];
     out->rounds = round;
     if (h[5] <= tol && h[6] <= tol && h[7] <= tol) { out->status = kOptimal; break; }
     if (!(isfinite(h[0]) && isfinite(h[1]))) { out->status = kNumErr; break; }
     if (inner_stop) { out->status = inner_stop; break; }
-    if (round >= max_rounds) break;
+    if (refine_finish_now(round, prev, rel, max_rounds)) { out->finish = true; break; }
+    int spent = 0;
+    if (!refine_set_limits(R, lim, out->iters, out->kkt_passes, elapsed(), st, &spent, &e)) {
+      if (e) return e;
+      out->status = spent;
+      break;
+    }
     if ((e = cudaMemcpyAsync(V.xb, V.xh, sizeof(double) * P.n, cudaMemcpyDeviceToDevice, st))) return e;
     if ((e = cudaMemcpyAsync(V.yb, V.yh, sizeof(double) * P.m, cudaMemcpyDeviceToDevice, st))) return e;
     double dP, dD;
@@ -313,6 +354,7 @@ cudaError_t refine_solve(RefineBuffers &R, const Mat<double> &K, const Mat<doubl
   }
   out->x = V.xh;
   out->y = V.yh;
+  out->seconds = elapsed();
   return cudaSuccess;
 }
 

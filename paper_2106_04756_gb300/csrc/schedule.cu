@@ -154,6 +154,26 @@ void refine_scales(double pv, double dv, double dmax, double *dP, double *dD) {
   *dD = D < 1.0 ? 1.0 : D;
 }
 
+int refine_finish_now(int round, double prev, double rel, int max_rounds) {
+  if (round >= max_rounds) return 1;
+  return round >= 1 && !(rel * kRefineMinGain <= prev) ? 1 : 0;
+}
+
+int refine_remaining(long long iter_limit, long long kkt_limit, double time_limit_s, long long iters,
+                     long long passes, double secs, long long out[3]) {
+  out[0] = iter_limit - iters;
+  out[1] = kkt_limit - passes;
+  out[2] = 0;
+  if (out[0] <= 0) return 1;
+  if (out[1] <= 0) return 2;
+  if (time_limit_s > 0.0) {
+    const double left = time_limit_s - secs;
+    if (!(left > 0.0)) return 3;
+    out[2] = (long long)(left * 1e9) > 0 ? (long long)(left * 1e9) : 1;
+  }
+  return 0;
+}
+
 double refine_round_tol(double rel, double tol, double inner_tol) {
   const double want = 0.1 * tol / rel;
   if (want < kInnerFloor) return inner_tol;  // no single round can finish

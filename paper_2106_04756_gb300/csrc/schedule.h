@@ -93,4 +93,21 @@ void refine_scales(double pv, double dv, double dmax, double *dP, double *dD);
 constexpr double kInnerFloor = 1e-6;
 double refine_round_tol(double rel, double tol, double inner_tol);
 
+// A float32 round that divides the relative Eq. (15) error by less than this
+// factor ends the float32 rounds: their corrections have stopped paying (the
+// inner solves stall at what float32 resolves of the correction problem),
+// and the solve finishes with float64 PDLP from the refined point.
+constexpr double kRefineMinGain = 10.0;
+// After the evaluation of round `round` (error `rel`; the previous round's
+// `prev`, the start point's for round 1): 1 if the float32 rounds end here
+// for the float64 finish (a round that gained less than kRefineMinGain, or
+// the round cap), else 0.
+int refine_finish_now(int round, double prev, double rel, int max_rounds);
+// Limits of the next solve of one refinement (iterations, KKT passes, time in
+// ns with 0 for none) from the caller's limits less what the earlier solves
+// spent; returns 0 when all three have some left, else 1 (iterations), 2 (KKT
+// passes) or 3 (time) for the first one spent.
+int refine_remaining(long long iter_limit, long long kkt_limit, double time_limit_s, long long iters,
+                     long long passes, double secs, long long out[3]);
+
 }  // namespace pdlp

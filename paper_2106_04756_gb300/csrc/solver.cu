@@ -1309,9 +1309,9 @@ __global__ void k_init_scalars(Scalars *s, ScalarInit in) {
   s->pw_theta = in.pw_theta;
   s->eps_zero = in.eps_zero;
   s->k = s->t = s->attempts = s->restarts = 0;
-  s->iter_limit = in.iter_limit;
-  s->attempt_limit = in.attempt_limit;
-  s->time_limit_ns = in.time_limit_ns;
+  s->iter_limit = in.lim_dev ? in.lim_dev[0] : in.iter_limit;
+  s->attempt_limit = in.lim_dev ? in.lim_dev[1] : in.attempt_limit;
+  s->time_limit_ns = in.lim_dev ? (unsigned long long)in.lim_dev[2] : in.time_limit_ns;
   s->t0_ns = global_timer_ns();
   s->t_end_ns = 0;
   s->cur = 0;

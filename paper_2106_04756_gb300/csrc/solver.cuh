@@ -20,6 +20,8 @@ struct ScalarInit {
   int mp;                  // 1: Malitsky-Pock line search (Appendix C.1)
   double mp_breaking, mp_downscaling, mp_interpolation;
   const double *tol_dev;  // non-null: read rel_tol from this device double at each solve
+  const long long *lim_dev;  // non-null: iter_limit, attempt_limit, time_limit_ns (0: none) read
+                             // from these three device values at each solve
   int stall_evals;        // > 0: stop (kStalled) after this many evaluations without a 10% gain
 };
 

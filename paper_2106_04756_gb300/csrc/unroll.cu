@@ -186,6 +186,7 @@ cudaError_t unroll_forward(UnrollBuffers &U, const Mat<F> &K, const Mat<F> &KT, 
   in2.iter_limit = T;
   in2.attempt_limit = 64ll * T + 64;  // Algorithm 2 accepts within a few attempts
   in2.time_limit_ns = 0ull;
+  in2.lim_dev = nullptr;  // the unrolled map's own limits, not a refinement budget
   in2.eval_every = ckpt;
   in2.adaptive_restart = 0;
   in2.pw_update = 0;  // omega fixed over the unrolled map

@@ -46,6 +46,15 @@ extern "C" double hl_round_tol(double rel, double tol, double inner) { return re
 
 extern "C" void hl_scales(double pv, double dv, double dmax, double *out) { refine_scales(pv, dv, dmax, out, out + 1); }
 
+extern "C" int hl_finish_now(int round, double prev, double rel, int max_rounds) {
+  return refine_finish_now(round, prev, rel, max_rounds);
+}
+
+extern "C" int hl_remaining(long long il, long long kl, double ts, long long it, long long kp, double secs,
+                            long long *out) {
+  return refine_remaining(il, kl, ts, it, kp, secs, out);
+}
+
 extern "C" int hl_build_slabs(int rows, const int32_t *rp, int32_t *first, int32_t *head, int32_t *tail,
                               int32_t *split4, int cap_split, int32_t *counts /* nslab, nsplit, nparts */) {
   std::vector<int32_t> f, h, t;

@@ -218,6 +218,28 @@ def test_float32_paths(gpu_lib, oracle_lib, prec):
         assert k["rel_kkt"] <= 1e-4
 
 
+def test_refinement_float64_finish(gpu_lib, oracle_lib):
+    """refine_rounds = 1: one float32 correction, then float64 PDLP from the
+    refined point; Eq. (15) holds to 1e-8 by the oracle and the finish's
+    iterations are counted within the total."""
+    lp = lpgen.small_planted()
+    x, y, r = P.solve(lp, precision=P.PDLP_FP32_REFINE, refine_rounds=1)
+    assert r["status_name"] == "OPTIMAL" and r["refine_rounds"] == 1, r
+    assert 0 < r["finish_iters"] < r["iters"], r
+    assert oracle.kkt(lp, x, y)["rel_kkt"] <= 1e-8
+
+
+@pytest.mark.parametrize("limit", ["iter_limit", "kkt_pass_limit"])
+def test_refinement_shares_the_budget(gpu_lib, limit):
+    """The caller's limit bounds the whole refinement (every inner solve and
+    the finish), not each inner solve."""
+    lp = lpgen.small_planted()
+    _, _, r = P.solve(lp, precision=P.PDLP_FP32_REFINE, **{limit: 300})
+    want = "ITER_LIMIT" if limit == "iter_limit" else "KKT_PASS_LIMIT"
+    assert r["status_name"] == want, r
+    assert (r["iters"] if limit == "iter_limit" else r["kkt_passes"]) <= 300, r
+
+
 @pytest.mark.parametrize("name", ["planted_200x500", "mip_2000x5000", "dense_row"])
 def test_restart_trace_matches_oracle(gpu_lib, oracle_lib, name):
     """Restart evaluations (Section 3.2, Algorithm 3) agree decision by decision:

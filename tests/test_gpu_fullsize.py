@@ -144,6 +144,21 @@ def test_pagerank_1m_float32_refinement_to_1e8(gpu_lib, oracle_lib, pagerank):
     assert np.abs(x - p).max() <= 1e-3 * p.max()
 
 
+def test_pagerank_100k_float32_refinement_to_1e8(gpu_lib, oracle_lib):
+    """The 100k-node PageRank LP (Table 2's family): the float32 rounds stall
+    after the first correction (the second divides the error by about 1.25),
+    so the solve finishes with float64 PDLP from the refined point and must
+    still end OPTIMAL by the oracle's Eq. (15), within the default budget."""
+    lp = lpgen.pagerank(100_000, seed_key=(2, 1), name="pagerank_100k")
+    x, y, r = P.solve(lp, precision=P.PDLP_FP32_REFINE)
+    assert r["status_name"] == "OPTIMAL", r
+    assert r["iters"] <= 1_000_000 and r["finish_iters"] <= r["iters"]
+    k = oracle.kkt(lp, x, y)
+    assert k["rel_kkt"] <= 1e-8, k
+    p = _pagerank_vector(lp)
+    assert np.abs(x - p).max() <= 1e-3 * p.max()
+
+
 def test_batch_4096_sampled_members_match_oracle(gpu_lib, oracle_lib):
     lps = lpgen.batch_4096()
     cap = 20000

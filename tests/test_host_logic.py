@@ -33,6 +33,8 @@ def hl(tmp_path_factory):
     L.hl_round_tol.restype = C.c_double
     L.hl_scales.argtypes = [C.c_double, C.c_double, C.c_double, P]
     L.hl_build_slabs.argtypes = [C.c_int, P, P, P, P, P, C.c_int, P]
+    L.hl_finish_now.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
+    L.hl_remaining.argtypes = [C.c_longlong, C.c_longlong, C.c_double, C.c_longlong, C.c_longlong, C.c_double, P]
     return L
 
 
@@ -180,6 +182,31 @@ def test_refinement_scales(hl):
     assert out[0] == 1.0 and out[1] == 2.0
     hl.hl_scales(0.0, 1e-20, 1e12, out.ctypes.data)  # clipped at dmax
     assert out[0] == 1e12 and out[1] == 1e12
+
+
+def test_refinement_finish_rule(hl):
+    # float32 rounds go on while each divides the error by at least 10
+    assert hl.hl_finish_now(0, float("inf"), 0.5, 12) == 0
+    assert hl.hl_finish_now(1, 0.5, 9.9e-6, 12) == 0
+    assert hl.hl_finish_now(2, 9.9e-6, 9.9e-7, 12) == 0   # exactly 10x
+    assert hl.hl_finish_now(2, 9.9e-6, 7.9e-6, 12) == 1   # 1.25x: float64 finish
+    assert hl.hl_finish_now(1, 1e-3, 2e-4, 12) == 1       # 5x
+    assert hl.hl_finish_now(3, 1e-4, 1e-7, 3) == 1        # round cap
+    assert hl.hl_finish_now(0, float("inf"), 0.5, 0) == 1  # no float32 round allowed
+    assert hl.hl_finish_now(2, 1e-6, float("nan"), 12) == 1
+
+
+def test_refinement_budget(hl):
+    out = np.zeros(3, np.int64)
+    assert hl.hl_remaining(1000, 5000, 0.0, 300, 400, 1.0, out.ctypes.data) == 0
+    assert list(out) == [700, 4600, 0]          # no time limit: 0
+    assert hl.hl_remaining(1000, 5000, 10.0, 300, 400, 2.5, out.ctypes.data) == 0
+    assert out[2] == 7_500_000_000
+    assert hl.hl_remaining(1000, 5000, 10.0, 1000, 400, 2.5, out.ctypes.data) == 1
+    assert hl.hl_remaining(1000, 5000, 10.0, 999, 5000, 2.5, out.ctypes.data) == 2
+    assert hl.hl_remaining(1000, 5000, 10.0, 999, 4999, 10.0, out.ctypes.data) == 3
+    assert hl.hl_remaining(1000, 5000, 10.0, 999, 4999, 10.0 - 1e-12, out.ctypes.data) == 0
+    assert out[2] >= 1                          # a sliver of time is still a limit, not "none"
 
 
 def _slabs(hl, rp):
