@@ -5,6 +5,8 @@ times (persistent step kernel inside one CUDA graph per solve): the
 oracle can afford at these sizes: bit-exact preprocessing, the first
 iterates, Eq. (15) at returned points, sampled batch members and the full
 adjoint."""
+import copy
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -179,6 +181,43 @@ def test_batch_4096_sampled_members_match_oracle(gpu_lib, oracle_lib):
         assert rs[b]["status_name"] == "ITER_LIMIT" and rs[b]["iters"] == cap
         _, _, ro = oracle.solve(lps[b], eps=1e-6, iter_limit=cap)
         assert ro["status_name"] == "ITER_LIMIT" or ro["iters"] >= cap // 4, (b, ro["iters"])
+
+
+@pytest.mark.parametrize("ruiz,pc,dirs,tol", [(0, 0, "cqK", 1e-5), (10, 1, "cq", 1e-3)])
+def test_unroll_20k_adjoint_matches_central_differences(gpu_lib, oracle_lib, ruiz, pc, dirs, tol):
+    """Central differences (h = 1e-6) of the unrolled map at the 20k x 50k
+    size against the library's adjoint (pdlp_grad), along random directions in
+    c, q and (without preconditioning, which the adjoint holds fixed) the
+    nonzeros of K.  T = 150: at T = 500 this map amplifies rounding by about
+    1e20 (two float64 evaluations of the same map differ by 0.2 in x_T), so
+    differences of size h measure chaos there, not the derivative; at T = 150
+    they agree with the adjoint to 1e-7..1e-6 (no preconditioning) and
+    3e-5..1e-4 (Ruiz + Pock-Chambolle, whose derivatives reach 1e21)."""
+    lp = lpgen.unroll_20k()
+    boxed = np.isfinite(lp.l) & np.isfinite(lp.u)
+    lp.c = lp.c + 0.05 * np.random.default_rng(4).standard_normal(lp.n) * boxed
+    T = 150
+    target = np.random.default_rng(5).standard_normal(lp.n)
+    with P.Context.from_lp(lp, ruiz_iters=ruiz, pock_chambolle=pc) as ctx:
+        x, _, eta = ctx.unroll(T, 50)
+        dc, dq, dK = ctx.grad(x - target, None)
+    omega = oracle.unroll_schedule(lp, 1, ruiz_iters=ruiz, pock_chambolle=pc)[1]
+
+    def loss(c, q, val):
+        lp2 = copy.copy(lp)
+        lp2.c, lp2.q, lp2.val = c, q, val
+        xx, _ = oracle.unroll_forward(lp2, eta, omega, ruiz_iters=ruiz, pock_chambolle=pc)
+        return 0.5 * np.sum((xx - target) ** 2)
+
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    for _ in range(3):
+        vc, vq = rng.standard_normal(lp.n), rng.standard_normal(lp.m)
+        vk = rng.standard_normal(lp.nnz) if "K" in dirs else np.zeros(lp.nnz)
+        fd = (loss(lp.c + h * vc, lp.q + h * vq, lp.val + h * vk) -
+              loss(lp.c - h * vc, lp.q - h * vq, lp.val - h * vk)) / (2 * h)
+        an = dc @ vc + dq @ vq + dK @ vk
+        assert abs(fd - an) <= tol * abs(an), (fd, an)
 
 
 def test_unroll_20k_T500_adjoint_matches_oracle(gpu_lib, oracle_lib):
