@@ -89,7 +89,9 @@ typedef struct {
   double beta_suff, beta_nec, beta_art; /* Section 3.2: 0.9, 0.1, 0.5                    */
   double eps_zero;          /* Section 3.3 epsilon_zero: 1e-10                           */
   double inner_tol;         /* PDLP_FP32_REFINE: Eq. (15) tolerance of the first inner
-                               solve, 1e-5; a later round that can reach rel_tol uses
+                               solve, 1e-7 (about what float32 resolves; a solve that
+                               stalls above it stops earlier); a later round that can
+                               reach rel_tol uses
                                the loosest tolerance that should get there (see
                                refine.cu).  When a round divides the relative error by
                                less than 10, makes it worse, or refine_rounds is

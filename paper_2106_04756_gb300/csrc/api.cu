@@ -656,7 +656,7 @@ extern "C" int pdlp_default_options(pdlp_options *o) {
   o->beta_nec = 0.1;
   o->beta_art = 0.5;
   o->eps_zero = 1e-10;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-7;
   o->refine_rounds = 12;
   o->unroll_T = 0;
   o->ckpt_every = 50;
