@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -742,49 +743,74 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     DevBuf tmp;
     CK(build_transpose(m, n, nnz, rp, ci, trp, tci, perm, tmp, st), "transpose");
   }
-  // Section 3.5 preconditioning and transform
+  // Section 3.5 preconditioning and transform, queued on st; the host plans
+  // the chunk schedules from the row starts of K and K^T meanwhile
   double *D1 = dalloc<double>(ctx->D1, m), *D2 = dalloc<double>(ctx->D2, n);
   double *cs = dalloc<double>(ctx->cs, n), *qs = dalloc<double>(ctx->qs, m), *ls = dalloc<double>(ctx->ls, n),
          *us = dalloc<double>(ctx->us, n), *ylos = dalloc<double>(ctx->ylos, m);
-  DevBuf rbuf, cbuf;
+  double *i1 = dalloc<double>(ctx->D1inv, m), *i2 = dalloc<double>(ctx->D2inv, n);
+  DevBuf rbuf, cbuf, mb;
   double *rb = dalloc<double>(rbuf, m), *cb = dalloc<double>(cbuf, n);
-  if (!D1 || !D2 || !cs || !qs || !ls || !us || !ylos || !rb || !cb)
+  unsigned long long *dmax = dalloc<unsigned long long>(mb, 1);
+  if (!D1 || !D2 || !cs || !qs || !ls || !us || !ylos || !rb || !cb || !i1 || !i2 || !dmax)
     return fail(ctx, PDLP_ERR_OOM, "allocation failed");
   CK(precondition(m, n, nnz, rp, ci, rowid, val, trp, tval, perm, o.ruiz_iters, o.pock_chambolle, D1, D2, rb, cb,
                   st),
      "precondition");
   CK(transform(m, n, D1, D2, dc, dq, dl, du, dylo, cs, qs, ls, us, ylos, st), "transform");
+  k_recip<<<std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(D1, m, i1);
+  k_recip<<<std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(D2, n, i2);
+  CK(cudaGetLastError(), "reciprocals");
+  // step size 1 / max |K~_ij| (Algorithm 1 initialisation), read after the planning
+  CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st), "memset");
+  if (nnz > 0) k_absmax_bits<<<std::min<int64_t>((nnz + 255) / 256, 1024), 256, 0, st>>>(val, nnz, dmax);
+  CK(cudaGetLastError(), "absmax");
+  // row starts of K and K^T (final since the transpose) on a stream of their
+  // own, so that the copy does not wait for the preconditioning
+  std::vector<int32_t> hrp((size_t)m + 1), htrp((size_t)n + 1);
+  CK(cudaMemcpyAsync(hrp.data(), rp, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost, ctx->cap[0]), "row_ptr");
+  CK(cudaMemcpyAsync(htrp.data(), trp, sizeof(int32_t) * htrp.size(), cudaMemcpyDeviceToHost, ctx->cap[0]), "row_ptr");
+  CK(cudaStreamSynchronize(ctx->cap[0]), "sync");
+  // host planning, K and K^T on two threads: warp-chunk schedules, the
+  // balanced chunk lists of the persistent kernel's warps, and (for the slab
+  // engine only) the fixed-size slabs
+  struct Plan {
+    std::vector<Chunk> chunks;
+    std::vector<LongRow> longrows;
+    int32_t nseg = 0;
+    std::vector<int32_t> widx, woff;
+    int32_t cmax = 0;
+    std::vector<int32_t> first, head, tail;
+    std::vector<SplitRow> splits;
+    int32_t nparts = 0;
+  };
+  Plan pK, pKT;
+  const int nw = persist_warps(), wpc = persist_warps_per_cta();
+  const bool slabs = o.persistent == 2;
+  auto plan = [nw, wpc, slabs](int32_t rows, const std::vector<int32_t> &hr, Plan &pl) {
+    build_schedule(rows, hr.data(), pl.chunks, pl.longrows, pl.nseg);
+    if (nw > 0) assign_chunks(pl.chunks, hr.data(), nw, wpc, pl.widx, pl.woff, pl.cmax);
+    if (slabs) build_slabs(rows, hr.data(), pl.first, pl.head, pl.tail, pl.splits, pl.nparts);
+  };
   {
-    double *i1 = dalloc<double>(ctx->D1inv, m), *i2 = dalloc<double>(ctx->D2inv, n);
-    if (!i1 || !i2) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
-    k_recip<<<std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(D1, m, i1);
-    k_recip<<<std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(D2, n, i2);
-    CK(cudaGetLastError(), "reciprocals");
+    std::thread tK([&] { plan(m, hrp, pK); });
+    plan(n, htrp, pKT);
+    tK.join();
   }
-  // step size 1 / max |K~_ij| (Algorithm 1 initialisation)
+  CK(cudaStreamSynchronize(st), "preconditioning");
   {
-    DevBuf mb;
-    unsigned long long *dmax = dalloc<unsigned long long>(mb, 1), hmax = 0ull;
-    if (!dmax) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
-    CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st), "memset");
-    if (nnz > 0) k_absmax_bits<<<std::min<int64_t>((nnz + 255) / 256, 1024), 256, 0, st>>>(val, nnz, dmax);
-    CK(cudaGetLastError(), "absmax");
-    CK(cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st), "absmax");
-    CK(cudaStreamSynchronize(st), "sync");
+    unsigned long long hmax = 0ull;
+    CK(cudaMemcpy(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost), "absmax");
     double kmax;
     memcpy(&kmax, &hmax, sizeof(kmax));
     ctx->eta0 = kmax > 0.0 ? 1.0 / kmax : 1.0;
   }
-  // row-block schedules of K and K^T
+  // upload the schedules
   {
-    std::vector<int32_t> hrp((size_t)m + 1), htrp((size_t)n + 1);
-    CK(cudaMemcpyAsync(hrp.data(), rp, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost, st), "row_ptr");
-    CK(cudaMemcpyAsync(htrp.data(), trp, sizeof(int32_t) * htrp.size(), cudaMemcpyDeviceToHost, st), "row_ptr");
-    CK(cudaStreamSynchronize(st), "sync");
-    std::vector<LongRow> lK, lKT;
-    int32_t segK = 0, segKT = 0;
-    build_schedule(m, hrp.data(), ctx->hblocksK, lK, segK);
-    build_schedule(n, htrp.data(), ctx->hblocksKT, lKT, segKT);
+    ctx->hblocksK = std::move(pK.chunks);
+    ctx->hblocksKT = std::move(pKT.chunks);
+    const std::vector<LongRow> &lK = pK.longrows, &lKT = pKT.longrows;
+    const int32_t segK = pK.nseg, segKT = pKT.nseg;
     ctx->nblocksK = (int32_t)((ctx->hblocksK.size() + kWarps - 1) / kWarps);
     ctx->nblocksKT = (int32_t)((ctx->hblocksKT.size() + kWarps - 1) / kWarps);
     Chunk *bK = dalloc<Chunk>(ctx->blocksK, ctx->hblocksK.size()), *bKT = dalloc<Chunk>(ctx->blocksKT, ctx->hblocksKT.size());
@@ -804,47 +830,42 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     if (!lKT.empty()) CK(cudaMemcpy(LKT, lKT.data(), sizeof(LongRow) * lKT.size(), cudaMemcpyHostToDevice), "long rows");
     CK(cudaMemset(cK, 0, sizeof(unsigned) * std::max<size_t>(lK.size(), 1)), "memset");
     CK(cudaMemset(cKT, 0, sizeof(unsigned) * std::max<size_t>(2 * lKT.size(), 1)), "memset");
-    // fixed-size slabs
-    {
-      auto build = [&](int32_t rows, const std::vector<int32_t> &hr, DevBuf &slab, DevBuf &split, DevBuf &spart,
-                       DevBuf &scnt, DevBuf &sacc, int32_t &nslab, int32_t &nsplit, int32_t &ndefer) -> int {
-        std::vector<int32_t> first, head, tail;
-        std::vector<SplitRow> sp;
-        int32_t nparts = 0;
-        build_slabs(rows, hr.data(), first, head, tail, sp, nparts);
-        nslab = (int32_t)head.size();
-        nsplit = (int32_t)sp.size();
+    // fixed-size slabs (slab engine only)
+    if (slabs) {
+      auto up = [&](Plan &pl, DevBuf &slab, DevBuf &split, DevBuf &spart, DevBuf &scnt, DevBuf &sacc, int32_t &nslab,
+                    int32_t &nsplit, int32_t &ndefer) -> int {
+        nslab = (int32_t)pl.head.size();
+        nsplit = (int32_t)pl.splits.size();
         ndefer = 0;
-        for (const SplitRow &R : sp) ndefer += split_deferred(R) ? 1 : 0;
-        std::vector<int32_t> meta(first);
-        meta.insert(meta.end(), head.begin(), head.end());
-        meta.insert(meta.end(), tail.begin(), tail.end());
+        for (const SplitRow &R : pl.splits) ndefer += split_deferred(R) ? 1 : 0;
+        std::vector<int32_t> meta(pl.first);
+        meta.insert(meta.end(), pl.head.begin(), pl.head.end());
+        meta.insert(meta.end(), pl.tail.begin(), pl.tail.end());
         int32_t *dm = dalloc<int32_t>(slab, meta.size());
-        SplitRow *ds = dalloc<SplitRow>(split, sp.size());
-        double *dp = dalloc<double>(spart, (size_t)nparts);
-        const size_t nsp = std::max<size_t>(sp.size(), 1);
+        SplitRow *ds = dalloc<SplitRow>(split, pl.splits.size());
+        double *dp = dalloc<double>(spart, (size_t)pl.nparts);
+        const size_t nsp = std::max<size_t>(pl.splits.size(), 1);
         unsigned *dc2 = dalloc<unsigned>(scnt, nsp);
         double *da = dalloc<double>(sacc, kLrAcc * nsp);
         if (!dm || !ds || !dp || !dc2 || !da) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
         CK(cudaMemcpy(dm, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice), "slabs");
-        if (!sp.empty()) CK(cudaMemcpy(ds, sp.data(), sizeof(SplitRow) * sp.size(), cudaMemcpyHostToDevice), "slabs");
+        if (!pl.splits.empty())
+          CK(cudaMemcpy(ds, pl.splits.data(), sizeof(SplitRow) * pl.splits.size(), cudaMemcpyHostToDevice), "slabs");
         CK(cudaMemset(dc2, 0, sizeof(unsigned) * nsp), "memset");
         CK(cudaMemset(da, 0, sizeof(double) * kLrAcc * nsp), "memset");
         return PDLP_OK;
       };
-      int rc2 = build(m, hrp, ctx->slabK, ctx->splitK, ctx->spartK, ctx->scntK, ctx->saccK, ctx->nslabK,
-                      ctx->nsplitK, ctx->ndeferK);
-      if (!rc2) rc2 = build(n, htrp, ctx->slabKT, ctx->splitKT, ctx->spartKT, ctx->scntKT, ctx->saccKT,
-                            ctx->nslabKT, ctx->nsplitKT, ctx->ndeferKT);
+      int rc2 = up(pK, ctx->slabK, ctx->splitK, ctx->spartK, ctx->scntK, ctx->saccK, ctx->nslabK, ctx->nsplitK,
+                   ctx->ndeferK);
+      if (!rc2) rc2 = up(pKT, ctx->slabKT, ctx->splitKT, ctx->spartKT, ctx->scntKT, ctx->saccKT, ctx->nslabKT,
+                         ctx->nsplitKT, ctx->ndeferKT);
       if (rc2) return rc2;
     }
     // balanced chunk lists for the persistent kernel's warps
-    const int nw = persist_warps();
     if (nw > 0) {
-      std::vector<int32_t> iK, oK, iKT, oKT;
-      const int wpc = persist_warps_per_cta();
-      assign_chunks(ctx->hblocksK, hrp.data(), nw, wpc, iK, oK, ctx->cmaxK);
-      assign_chunks(ctx->hblocksKT, htrp.data(), nw, wpc, iKT, oKT, ctx->cmaxKT);
+      const std::vector<int32_t> &iK = pK.widx, &oK = pK.woff, &iKT = pKT.widx, &oKT = pKT.woff;
+      ctx->cmaxK = pK.cmax;
+      ctx->cmaxKT = pKT.cmax;
       int32_t *wK = dalloc<int32_t>(ctx->wchunkK, iK.size()), *fK = dalloc<int32_t>(ctx->woffK, oK.size());
       int32_t *wKT = dalloc<int32_t>(ctx->wchunkKT, iKT.size()), *fKT = dalloc<int32_t>(ctx->woffKT, oKT.size());
       if (!wK || !fK || !wKT || !fKT) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
