@@ -743,8 +743,9 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     DevBuf tmp;
     CK(build_transpose(m, n, nnz, rp, ci, trp, tci, perm, tmp, st), "transpose");
   }
-  // Section 3.5 preconditioning and transform, queued on st; the host plans
-  // the chunk schedules from the row starts of K and K^T meanwhile
+  // Section 3.5 preconditioning and transform: Ruiz is queued on st and the
+  // host plans the chunk schedules meanwhile; then Pock-Chambolle (whose long
+  // rows are summed on the host), the transform and the step size
   double *D1 = dalloc<double>(ctx->D1, m), *D2 = dalloc<double>(ctx->D2, n);
   double *cs = dalloc<double>(ctx->cs, n), *qs = dalloc<double>(ctx->qs, m), *ls = dalloc<double>(ctx->ls, n),
          *us = dalloc<double>(ctx->us, n), *ylos = dalloc<double>(ctx->ylos, m);
@@ -754,23 +755,28 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
   unsigned long long *dmax = dalloc<unsigned long long>(mb, 1);
   if (!D1 || !D2 || !cs || !qs || !ls || !us || !ylos || !rb || !cb || !i1 || !i2 || !dmax)
     return fail(ctx, PDLP_ERR_OOM, "allocation failed");
-  CK(precondition(m, n, nnz, rp, ci, rowid, val, trp, tval, perm, o.ruiz_iters, o.pock_chambolle, D1, D2, rb, cb,
-                  st),
-     "precondition");
-  CK(transform(m, n, D1, D2, dc, dq, dl, du, dylo, cs, qs, ls, us, ylos, st), "transform");
-  k_recip<<<std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(D1, m, i1);
-  k_recip<<<std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(D2, n, i2);
-  CK(cudaGetLastError(), "reciprocals");
-  // step size 1 / max |K~_ij| (Algorithm 1 initialisation), read after the planning
-  CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st), "memset");
-  if (nnz > 0) k_absmax_bits<<<std::min<int64_t>((nnz + 255) / 256, 1024), 256, 0, st>>>(val, nnz, dmax);
-  CK(cudaGetLastError(), "absmax");
-  // row starts of K and K^T (final since the transpose) on a stream of their
-  // own, so that the copy does not wait for the preconditioning
+  // row starts of K and K^T (final since the transpose); the long rows that
+  // the preconditioning treats apart
   std::vector<int32_t> hrp((size_t)m + 1), htrp((size_t)n + 1);
-  CK(cudaMemcpyAsync(hrp.data(), rp, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost, ctx->cap[0]), "row_ptr");
-  CK(cudaMemcpyAsync(htrp.data(), trp, sizeof(int32_t) * htrp.size(), cudaMemcpyDeviceToHost, ctx->cap[0]), "row_ptr");
-  CK(cudaStreamSynchronize(ctx->cap[0]), "sync");
+  CK(cudaMemcpy(hrp.data(), rp, sizeof(int32_t) * hrp.size(), cudaMemcpyDeviceToHost), "row_ptr");
+  CK(cudaMemcpy(htrp.data(), trp, sizeof(int32_t) * htrp.size(), cudaMemcpyDeviceToHost), "row_ptr");
+  PrecondPlan pp;
+  plan_precondition(m, hrp.data(), n, htrp.data(), pp);
+  DevBuf segbuf;
+  ScanSeg *dseg = pp.segK.size() + pp.segKT.size() > 0
+                      ? dalloc<ScanSeg>(segbuf, pp.segK.size() + pp.segKT.size())
+                      : nullptr;
+  if (pp.segK.size() + pp.segKT.size() > 0) {
+    if (!dseg) return fail(ctx, PDLP_ERR_OOM, "allocation failed");
+    if (!pp.segK.empty())
+      CK(cudaMemcpy(dseg, pp.segK.data(), sizeof(ScanSeg) * pp.segK.size(), cudaMemcpyHostToDevice), "segments");
+    if (!pp.segKT.empty())
+      CK(cudaMemcpy(dseg + pp.segK.size(), pp.segKT.data(), sizeof(ScanSeg) * pp.segKT.size(),
+                    cudaMemcpyHostToDevice), "segments");
+  }
+  CK(ruiz(m, n, nnz, rp, ci, rowid, val, trp, tval, perm, o.ruiz_iters, D1, D2, rb, cb, dseg, (int)pp.segK.size(),
+          dseg ? dseg + pp.segK.size() : nullptr, (int)pp.segKT.size(), st),
+     "Ruiz");
   // host planning, K and K^T on two threads: warp-chunk schedules, the
   // balanced chunk lists of the persistent kernel's warps, and (for the slab
   // engine only) the fixed-size slabs
@@ -797,6 +803,18 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     plan(n, htrp, pKT);
     tK.join();
   }
+  if (o.pock_chambolle)
+    CK(pock_chambolle(m, n, nnz, rp, ci, rowid, val, trp, tval, perm, D1, D2, rb, cb, pp, hrp.data(), htrp.data(),
+                      st),
+       "Pock-Chambolle");
+  CK(transform(m, n, D1, D2, dc, dq, dl, du, dylo, cs, qs, ls, us, ylos, st), "transform");
+  k_recip<<<std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(D1, m, i1);
+  k_recip<<<std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(D2, n, i2);
+  CK(cudaGetLastError(), "reciprocals");
+  // step size 1 / max |K~_ij| (Algorithm 1 initialisation)
+  CK(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st), "memset");
+  if (nnz > 0) k_absmax_bits<<<std::min<int64_t>((nnz + 255) / 256, 1024), 256, 0, st>>>(val, nnz, dmax);
+  CK(cudaGetLastError(), "absmax");
   CK(cudaStreamSynchronize(st), "preconditioning");
   {
     unsigned long long hmax = 0ull;

@@ -311,20 +311,46 @@ __global__ void k_row_absmax(int32_t rows, const int32_t *rp, const double *val,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < rows; i += nw) {
     double mx = 0.0;
-    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) mx = fmax(mx, fabs(val[k]));
+    const int32_t k0 = rp[i], k1 = rp[i + 1];
+    if (k1 - k0 <= kLongScan)  // longer rows: 0 here, then k_row_absmax_long
+      for (int32_t k = k0 + lane; k < k1; k += 32) mx = fmax(mx, fabs(val[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
     if (lane == 0) out[i] = mx;
   }
 }
 
+// One CTA per segment of a long row: the segment's largest |value| merged
+// into out[row] by an atomic maximum on the bits (values are finite and
+// nonnegative, where the bit order is the numeric order).
+__global__ void k_row_absmax_long(const ScanSeg *segs, const double *val, double *out) {
+  __shared__ double red[32];
+  const ScanSeg g = segs[blockIdx.x];
+  double mx = 0.0;
+  for (int32_t k = g.k0 + threadIdx.x; k < g.k1; k += blockDim.x) mx = fmax(mx, fabs(val[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0)
+      atomicMax(reinterpret_cast<unsigned long long *>(out + g.row), (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
 // Pock-Chambolle alpha = 1: r_i = sum_j |K~_ij| accumulated sequentially in CSR
-// order (the order of a plain loop over the row).
+// order (the order of a plain loop over the row); rows longer than kLongScan
+// are left to the host (pock_chambolle).
 __global__ void k_row_abssum_seq(int32_t rows, const int32_t *rp, const double *val, double *out) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
+    const int32_t k0 = rp[i], k1 = rp[i + 1];
+    if (k1 - k0 > kLongScan) continue;
     double s = 0.0;
-    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) s = __dadd_rn(s, fabs(val[k]));
+    for (int32_t k = k0; k < k1; ++k) s = __dadd_rn(s, fabs(val[k]));
     out[i] = s;
   }
 }
@@ -353,33 +379,83 @@ __global__ void k_fill(double *v, int64_t n, double x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] = x;
 }
 
-cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                         const int32_t *rowid, double *val, const int32_t *trp, double *tval,
-                         const int32_t *perm, int ruiz_iters, int pock_chambolle, double *D1, double *D2,
-                         double *rbuf, double *cbuf, cudaStream_t st) {
+void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *htrp, PrecondPlan &pp) {
+  auto scan = [](int32_t rows, const int32_t *rp, std::vector<ScanSeg> &segs, std::vector<int32_t> &longr) {
+    segs.clear();
+    longr.clear();
+    for (int32_t i = 0; i < rows; ++i) {
+      const int32_t k0 = rp[i], k1 = rp[i + 1];
+      if (k1 - k0 <= kLongScan) continue;
+      longr.push_back(i);
+      for (int32_t k = k0; k < k1; k += kLongScan) segs.push_back(ScanSeg{i, k, k1 - k > kLongScan ? k + kLongScan : k1, 0});
+    }
+  };
+  scan(m, hrp, pp.segK, pp.longK);
+  scan(n, htrp, pp.segKT, pp.longKT);
+}
+
+cudaError_t ruiz(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci, const int32_t *rowid,
+                 double *val, const int32_t *trp, double *tval, const int32_t *perm, int ruiz_iters, double *D1,
+                 double *D2, double *rbuf, double *cbuf, const ScanSeg *dsegK, int nsegK, const ScanSeg *dsegKT,
+                 int nsegKT, cudaStream_t st) {
   const int gz = grid_for(nnz, 256);
   const int gm = grid_for(m, 256), gn = grid_for(n, 256);
   const int gmw = grid_for((int64_t)m * 32, 256), gnw = grid_for((int64_t)n * 32, 256);
   k_fill<<<gm, 256, 0, st>>>(D1, m, 1.0);
   k_fill<<<gn, 256, 0, st>>>(D2, n, 1.0);
-  auto sync_t = [&]() { if (nnz > 0) k_gather<double><<<grid_for(nnz, 256), 256, 0, st>>>(val, perm, nnz, tval); };
-  sync_t();
+  if (nnz > 0) k_gather<double><<<gz, 256, 0, st>>>(val, perm, nnz, tval);
   for (int it = 0; it < ruiz_iters; ++it) {
     k_row_absmax<<<gmw, 256, 0, st>>>(m, rp, val, rbuf);
     k_row_absmax<<<gnw, 256, 0, st>>>(n, trp, tval, cbuf);
+    if (nsegK > 0) k_row_absmax_long<<<nsegK, 256, 0, st>>>(dsegK, val, rbuf);
+    if (nsegKT > 0) k_row_absmax_long<<<nsegKT, 256, 0, st>>>(dsegKT, tval, cbuf);
     k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
     k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
     if (nnz > 0) k_scale_nnz<<<gz, 256, 0, st>>>(nnz, rowid, ci, val, rbuf, cbuf);
-    sync_t();
+    if (nnz > 0) k_gather<double><<<gz, 256, 0, st>>>(val, perm, nnz, tval);
   }
-  if (pock_chambolle) {
-    k_row_abssum_seq<<<gm, 256, 0, st>>>(m, rp, val, rbuf);
-    k_row_abssum_seq<<<gn, 256, 0, st>>>(n, trp, tval, cbuf);
-    k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
-    k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
-    if (nnz > 0) k_scale_nnz<<<gz, 256, 0, st>>>(nnz, rowid, ci, val, rbuf, cbuf);
-    sync_t();
+  return cudaGetLastError();
+}
+
+cudaError_t pock_chambolle(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                           const int32_t *rowid, double *val, const int32_t *trp, double *tval,
+                           const int32_t *perm, double *D1, double *D2, double *rbuf, double *cbuf,
+                           const PrecondPlan &pp, const int32_t *hrp, const int32_t *htrp, cudaStream_t st) {
+  cudaError_t e;
+  const int gz = grid_for(nnz, 256);
+  const int gm = grid_for(m, 256), gn = grid_for(n, 256);
+  // l1 sums of the long rows on the host, in CSR order, from the values Ruiz left
+  std::vector<double> sK(pp.longK.size()), sKT(pp.longKT.size());
+  if (!pp.longK.empty() || !pp.longKT.empty()) {
+    if ((e = cudaStreamSynchronize(st))) return e;
+    std::vector<double> buf;
+    auto host_sums = [&](const std::vector<int32_t> &rows, const int32_t *hr, const double *dv,
+                         std::vector<double> &out) -> cudaError_t {
+      for (size_t r = 0; r < rows.size(); ++r) {
+        const int32_t k0 = hr[rows[r]], k1 = hr[rows[r] + 1];
+        buf.resize((size_t)(k1 - k0));
+        cudaError_t e2 = cudaMemcpy(buf.data(), dv + k0, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost);
+        if (e2) return e2;
+        double acc = 0.0;
+        for (double v : buf) acc += fabs(v);
+        out[r] = acc;
+      }
+      return cudaSuccess;
+    };
+    if ((e = host_sums(pp.longK, hrp, val, sK))) return e;
+    if ((e = host_sums(pp.longKT, htrp, tval, sKT))) return e;
   }
+  k_row_abssum_seq<<<gm, 256, 0, st>>>(m, rp, val, rbuf);
+  k_row_abssum_seq<<<gn, 256, 0, st>>>(n, trp, tval, cbuf);
+  // pageable sources: each copy is staged before the call returns
+  for (size_t r = 0; r < sK.size(); ++r)
+    if ((e = cudaMemcpyAsync(rbuf + pp.longK[r], &sK[r], sizeof(double), cudaMemcpyHostToDevice, st))) return e;
+  for (size_t r = 0; r < sKT.size(); ++r)
+    if ((e = cudaMemcpyAsync(cbuf + pp.longKT[r], &sKT[r], sizeof(double), cudaMemcpyHostToDevice, st))) return e;
+  k_norm_to_div<<<gm, 256, 0, st>>>(m, rbuf, D1);
+  k_norm_to_div<<<gn, 256, 0, st>>>(n, cbuf, D2);
+  if (nnz > 0) k_scale_nnz<<<gz, 256, 0, st>>>(nnz, rowid, ci, val, rbuf, cbuf);
+  if (nnz > 0) k_gather<double><<<gz, 256, 0, st>>>(val, perm, nnz, tval);
   return cudaGetLastError();
 }
 

@@ -46,10 +46,36 @@ cudaError_t exclusive_scan(const int *in, int64_t n, int *out, int *total, int *
 int64_t scan_tmp_ints(int64_t n);
 cudaError_t build_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
                             int32_t *trp, int32_t *tci, int32_t *perm, DevBuf &tmp, cudaStream_t st);
-cudaError_t precondition(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                         const int32_t *rowid, double *val, const int32_t *trp, double *tval,
-                         const int32_t *perm, int ruiz_iters, int pock_chambolle, double *D1, double *D2,
-                         double *rbuf, double *cbuf, cudaStream_t st);
+// Section 3.5 preconditioning in two calls.  Rows longer than kLongScan
+// nonzeros (a dense row of a million entries, say) are handled apart: their
+// Ruiz maxima by one CTA per kLongScan-nonzero segment, combined with an
+// atomic maximum on the bits (the numeric order for nonnegative doubles, so
+// the result is the same in any order); their Pock-Chambolle l1 sums on the
+// host in CSR order, the order of the plain loop (one GPU thread, at this
+// part's float64 add rate, takes tens of milliseconds for a million terms).
+constexpr int32_t kLongScan = 8192;
+struct ScanSeg {
+  int32_t row, k0, k1, pad;  // [k0, k1): a segment of long row `row`
+};
+struct PrecondPlan {
+  std::vector<ScanSeg> segK, segKT;    // segments of the long rows of K, K^T
+  std::vector<int32_t> longK, longKT;  // the long rows of K, K^T
+};
+// From the host row starts of K (m rows) and K^T (n rows).
+void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *htrp, PrecondPlan &pp);
+// Ruiz equilibration (Section 3.5, ruiz_iters passes), queued on st: D1, D2
+// from 1, val / tval scaled in place; dsegK / dsegKT: the plan's segments on
+// the device.
+cudaError_t ruiz(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci, const int32_t *rowid,
+                 double *val, const int32_t *trp, double *tval, const int32_t *perm, int ruiz_iters, double *D1,
+                 double *D2, double *rbuf, double *cbuf, const ScanSeg *dsegK, int nsegK, const ScanSeg *dsegKT,
+                 int nsegKT, cudaStream_t st);
+// Pock-Chambolle alpha = 1 (Section 3.5) after ruiz(); waits for st when the
+// plan has long rows (their sums are taken on the host).
+cudaError_t pock_chambolle(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                           const int32_t *rowid, double *val, const int32_t *trp, double *tval,
+                           const int32_t *perm, double *D1, double *D2, double *rbuf, double *cbuf,
+                           const PrecondPlan &pp, const int32_t *hrp, const int32_t *htrp, cudaStream_t st);
 cudaError_t transform(int32_t m, int32_t n, const double *D1, const double *D2, const double *c,
                       const double *q, const double *l, const double *u, const double *ylo,
                       double *cs, double *qs, double *ls, double *us, double *ylos, cudaStream_t st);

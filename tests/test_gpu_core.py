@@ -30,11 +30,29 @@ def _lp_dense_row(m=300, n=6000, seed=70):
     return lp
 
 
+def _lp_long_row_and_column(m=12000, n=20000, seed=73):
+    """A planted LP with a row of 20,000 nonzeros and a column of 12,000 (both
+    longer than the 8,192 above which the preconditioning takes a row's
+    maximum in parallel segments and its l1 sum on the host)."""
+    base = lpgen.planted_uniform(m, n, 0.0004, frac_boxed=0.8, seed_key=(seed,))
+    A = base.scipy().tolil()
+    rng = np.random.default_rng(seed)
+    A[0, :] = rng.standard_normal(n)
+    A[:, 0] = rng.standard_normal((m, 1))
+    A = A.tocsr()
+    A.sort_indices()
+    lp = lpgen._plant(lpgen.rng_for(seed, 1), m, n, A.indptr.astype(np.int32), A.indices.astype(np.int32),
+                      A.data, base.ineq, base.l, base.u, "long_row_and_column")
+    return lp
+
+
 CASES = {
     "planted_200x500": lambda: lpgen.small_planted(),
     "mip_2000x5000": lambda: lpgen.mip_like(2000, 5000, 30000, seed_key=(71,)),
     "pagerank_5000": lambda: lpgen.pagerank(5000, seed_key=(72,)),
     "dense_row": _lp_dense_row,
+    "long_row_and_column": _lp_long_row_and_column,
+    "pagerank_20000": lambda: lpgen.pagerank(20000, seed_key=(74,)),
 }
 
 
