@@ -69,6 +69,10 @@ def _args():
                     help="only solve the first N LPs of the 4096-LP batch twice (tuning, then one launch "
                          "between cudaProfilerStart / Stop, for ncu --profile-from-start off) and exit")
     ap.add_argument("--profile-precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="only create and solve --workload once in --profile-precision, host-stepped "
+                         "(use_graph = 0, so that ncu sees every kernel), capped at --iter-cap iterations, "
+                         "and exit")
     ap.add_argument("--profile-unroll", action="store_true",
                     help="only run the unrolled map (T = 500, checkpoint 50) and its adjoint on the 20k x 50k "
                          "LP twice, the second time between cudaProfilerStart / Stop, and exit")
@@ -433,6 +437,14 @@ def main():
             torch.cuda.synchronize()
             torch.cuda.profiler.stop()
         print(json.dumps({"profile_unroll": "mip_20k_50k", "T": 500, "ckpt_every": 50}))
+        return
+    if args.profile_solve:
+        lp = _make(args.workload)
+        prec = P.PDLP_FP64 if args.profile_precision == "fp64" else P.PDLP_FP32
+        with P.Context.from_lp(lp, precision=prec, iter_limit=args.iter_cap, use_graph=0) as ctx:
+            _, _, r = ctx.solve()
+        print(json.dumps({"profile_solve": args.workload, "precision": args.profile_precision,
+                          "iters": r["iters"], "kkt_passes": r["kkt_passes"], "restarts": r["restarts"]}))
         return
     if args.profile_batch > 0:
         import lpgen

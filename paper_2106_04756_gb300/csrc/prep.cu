@@ -48,12 +48,19 @@ __global__ void k_validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp,
 
 // Row index of every nonzero (one warp per row, lanes strided: a long row
 // is written by its warp with coalesced stores).  Needs a valid row_ptr.
-__global__ void k_row_ids(int32_t m, const int32_t *rp, int32_t *rowid) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < m; i += nw)
-    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 32) rowid[k] = (int32_t)i;
+// rowid[k]: the row holding nonzero k, by a binary search of the (valid)
+// row starts per nonzero, so that a row of a million entries is spread over
+// the grid like any other
+__global__ void k_row_ids(int32_t m, int64_t nnz, const int32_t *rp, int32_t *rowid) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
+    int32_t lo = 0, hi = m;  // the last row with rp[row] <= k
+    while (hi - lo > 1) {
+      const int32_t mid = lo + (hi - lo) / 2;
+      if (rp[mid] <= k) lo = mid; else hi = mid;
+    }
+    rowid[k] = lo;
+  }
 }
 
 // Column indices strictly increasing within each row: one check per nonzero.
@@ -305,18 +312,26 @@ cudaError_t build_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *rp
 // ------------------------------------------------------ Section 3.5 scaling
 
 // Ruiz: r_i = max_j |K~_ij| over the row (any order gives the same maximum).
+// Largest |value| of each row, four lanes per row (rows of a few nonzeros
+// keep every lane busy; a maximum is exact in any order); rows longer than
+// kMaxSeg get 0 here and their maximum from k_row_absmax_long.
+constexpr int kMaxLanes = 4;
 __global__ void k_row_absmax(int32_t rows, const int32_t *rp, const double *val, double *out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < rows; i += nw) {
+  const int sub = threadIdx.x & (kMaxLanes - 1);
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kMaxLanes;
+  const int64_t ng = ((int64_t)gridDim.x * blockDim.x) / kMaxLanes;
+  const int64_t iters = (rows + ng - 1) / ng;  // the same count in every lane (full-warp shuffles)
+  for (int64_t t = 0; t < iters; ++t) {
+    const int64_t i = grp + t * ng;
     double mx = 0.0;
-    const int32_t k0 = rp[i], k1 = rp[i + 1];
-    if (k1 - k0 <= kLongScan)  // longer rows: 0 here, then k_row_absmax_long
-      for (int32_t k = k0 + lane; k < k1; k += 32) mx = fmax(mx, fabs(val[k]));
+    if (i < rows) {
+      const int32_t k0 = rp[i], k1 = rp[i + 1];
+      if (k1 - k0 <= kMaxSeg)
+        for (int32_t k = k0 + sub; k < k1; k += kMaxLanes) mx = fmax(mx, fabs(val[k]));
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if (lane == 0) out[i] = mx;
+    for (int o = kMaxLanes / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o, kMaxLanes));
+    if (sub == 0 && i < rows) out[i] = mx;
   }
 }
 
@@ -385,9 +400,9 @@ void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *
     longr.clear();
     for (int32_t i = 0; i < rows; ++i) {
       const int32_t k0 = rp[i], k1 = rp[i + 1];
-      if (k1 - k0 <= kLongScan) continue;
-      longr.push_back(i);
-      for (int32_t k = k0; k < k1; k += kLongScan) segs.push_back(ScanSeg{i, k, k1 - k > kLongScan ? k + kLongScan : k1, 0});
+      if (k1 - k0 <= kMaxSeg) continue;
+      if (k1 - k0 > kLongScan) longr.push_back(i);
+      for (int32_t k = k0; k < k1; k += kMaxSeg) segs.push_back(ScanSeg{i, k, k1 - k > kMaxSeg ? k + kMaxSeg : k1, 0});
     }
   };
   scan(m, hrp, pp.segK, pp.longK);
@@ -400,7 +415,7 @@ cudaError_t ruiz(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int
                  int nsegKT, cudaStream_t st) {
   const int gz = grid_for(nnz, 256);
   const int gm = grid_for(m, 256), gn = grid_for(n, 256);
-  const int gmw = grid_for((int64_t)m * 32, 256), gnw = grid_for((int64_t)n * 32, 256);
+  const int gmw = grid_for((int64_t)m * kMaxLanes, 256), gnw = grid_for((int64_t)n * kMaxLanes, 256);
   k_fill<<<gm, 256, 0, st>>>(D1, m, 1.0);
   k_fill<<<gn, 256, 0, st>>>(D2, n, 1.0);
   if (nnz > 0) k_gather<double><<<gz, 256, 0, st>>>(val, perm, nnz, tval);
@@ -518,7 +533,7 @@ cudaError_t validate(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const
   if ((e = cudaMemcpyAsync(herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
   if ((e = cudaStreamSynchronize(st))) return e;
   if (*herr & kBadRowPtr) return cudaSuccess;
-  k_row_ids<<<grid_for((int64_t)m * 32, 256), 256, 0, st>>>(m, rp, rowid);
+  if (nnz > 0) k_row_ids<<<grid_for(nnz, 256), 256, 0, st>>>(m, nnz, rp, rowid);
   if (nnz > 1) k_validate_sorted<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, rowid, ci, derr);
   if ((e = cudaMemcpyAsync(herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
   return cudaStreamSynchronize(st);
