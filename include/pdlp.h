@@ -244,10 +244,11 @@ int pdlp_normalized_gap(pdlp_ctx *ctx, const double *x, const double *y, double 
  * uint8[total rows].  x_out / y_out (float64[total cols] / [total rows],
  * nullable) receive the solutions, res[count] (nullable) the outcomes.
  * Uses opts.precision (PDLP_FP64 or PDLP_FP32 arithmetic in the SpMVs, or
- * PDLP_FP32_REFINE: float32 steps until Eq. (15) holds at rel_tol or an LP
- * stops gaining 10% in 50 evaluations, then a second launch of float64
- * steps from each LP's float32 point with what is left of its iteration and
- * KKT-pass budgets; res then counts both stages and refine_rounds = 1),
+ * PDLP_FP32_REFINE: float32 steps until Eq. (15) holds at
+ * max(rel_tol, inner_tol) or an LP stops gaining 10% in 10 evaluations, then
+ * a second launch of float64 steps to rel_tol from each LP's float32 point
+ * with what is left of its iteration and KKT-pass budgets; res then counts
+ * both stages and refine_rounds = 1),
  * rel_tol, iter_limit, kkt_pass_limit, the preconditioner, restart, primal
  * weight and step settings, and opts.stream (step_policy must be 0 and omega0
  * 0: Algorithm 2 and InitializePrimalWeight).  Each LP needs m + n <= 4096;
