@@ -248,6 +248,27 @@ def test_refinement_float64_finish(gpu_lib, oracle_lib):
     assert oracle.kkt(lp, x, y)["rel_kkt"] <= 1e-8
 
 
+def test_refinement_context_solves_twice_alike(gpu_lib):
+    """Two solves on one PDLP_FP32_REFINE context (limits written per solve,
+    float64 finish graph reused) return the same bits."""
+    lp = lpgen.small_planted()
+    with P.Context.from_lp(lp, precision=P.PDLP_FP32_REFINE, refine_rounds=1, inner_tol=1e-4) as ctx:
+        xa, ya, ra = ctx.solve()
+        xb, yb, rb = ctx.solve()
+    assert ra["status_name"] == rb["status_name"] == "OPTIMAL"
+    assert ra["iters"] == rb["iters"] and ra["finish_iters"] == rb["finish_iters"] > 0
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+
+
+def test_refinement_time_limit(gpu_lib):
+    """A time limit bounds the whole refinement: it ends with TIME_LIMIT."""
+    lp = lpgen.mip_like(2000, 5000, 30000, seed_key=(71,))
+    _, _, r = P.solve(lp, precision=P.PDLP_FP32_REFINE, time_limit_s=0.05, iter_limit=10 ** 9,
+                      kkt_pass_limit=10 ** 9)
+    assert r["status_name"] == "TIME_LIMIT", r
+    assert r["seconds"] < 1.0, r
+
+
 @pytest.mark.parametrize("limit", ["iter_limit", "kkt_pass_limit"])
 def test_refinement_shares_the_budget(gpu_lib, limit):
     """The caller's limit bounds the whole refinement (every inner solve and
