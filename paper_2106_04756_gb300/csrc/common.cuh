@@ -737,6 +737,48 @@ __device__ __forceinline__ void spmv_warp(const Mat<T> &A, const T *const (&vec)
 // bounded by limit_ns of %globaltimer (kBarrierTimeoutNs unless the options
 // say otherwise): on expiry (or when another CTA has already failed) it
 // records the failure in *err and returns false.
+// grid_arrive + grid_wait: a CTA's arrival (after all its threads' writes),
+// and the wait for the others; work between the two may read only data that
+// no other CTA writes before its arrival.
+__device__ __forceinline__ void grid_arrive(unsigned long long *count) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1ull);
+  }
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned long long *count, unsigned long long target, int *err,
+                                          unsigned long long limit_ns, bool acquire = true) {
+  __shared__ int s_okw;
+  if (threadIdx.x == 0) {
+    volatile unsigned long long *vc = count;
+    volatile int *verr = err;
+    int ok = 1;
+    if (*vc < target) {
+      const unsigned long long t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (*vc < target) {
+        if ((++spins & 63u) == 0u && (*verr || global_timer_ns() - t0 > limit_ns)) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(8);
+      }
+    }
+    if (ok && acquire) {
+      unsigned long long seen;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(count) : "memory");
+      (void)seen;
+    }
+    __threadfence();
+    s_okw = ok;
+  }
+  __syncthreads();
+  return s_okw != 0;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned long long *count, unsigned long long target, int *err,
                                              unsigned long long limit_ns, bool acquire = true) {
   __shared__ int s_ok;

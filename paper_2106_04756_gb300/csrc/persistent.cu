@@ -230,6 +230,46 @@ __device__ __forceinline__ void finish(const Mat<T> &A, const Chunk &c, char *bu
 // values, row starts and epilogue operands by cp.async into the staging
 // buffer `buf`, and the gathered vector entries into xg (through L1 when
 // L1G, else through L2 only).
+// issue() in two parts: issue_own starts every load but the gathers (data
+// no other CTA writes during the phase before it: the matrix, the row
+// starts, the warp's own rows' operands) and leaves the column indices in
+// cj; issue_gather then loads the gathered entries.
+template <typename T, typename Ph>
+__device__ __forceinline__ void issue_own(const Mat<T> &A, const Chunk &c, const Ph &ph, char *buf,
+                                          int (&cj)[kLaneItems]) {
+  const int lane = threadIdx.x & 31;
+  T *sval = reinterpret_cast<T *>(buf);
+  T *pre = sval + 2 * kChunkNnz + kChunkRows;
+  int *srp = reinterpret_cast<int *>(sval + buf_elems<Ph::PRE>());
+  const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
+  const int nrows = c.row_end >= 0 ? c.row_end - c.row_begin : 0;
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
+    if (e < cnt) cp_async(sval + stg<T>(e), A.val + nb + e);
+  }
+  if (lane < nrows) {
+    cp_async(srp + lane, A.rp + c.row_begin + lane);
+    ph.stage(c.row_begin + lane, pre + lane);
+  }
+  cp_async_commit();
+}
+
+template <typename T, bool L1G>
+__device__ __forceinline__ void issue_gather(const Chunk &c, const T *vec, const int (&cj)[kLaneItems],
+                                             T (&xg)[kLaneItems]) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = c.nnz_end - c.nnz_begin;
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    xg[it] = e < cnt ? (L1G ? vec[cj[it]] : __ldcg(vec + cj[it])) : T(0);
+  }
+}
+
+// issue_own then issue_gather in one (kept as one body: the split form
+// compiles to a slower float64 kernel, 162 -> 173 us per PageRank 1M attempt)
 template <typename T, bool L1G, typename Ph>
 __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *vec, const Ph &ph, char *buf,
                                       T (&xg)[kLaneItems]) {
@@ -256,6 +296,15 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
     const int e = lane + 32 * it;
     xg[it] = e < cnt ? (L1G ? vec[cj[it]] : __ldcg(vec + cj[it])) : T(0);
   }
+}
+
+// The first two chunks' issue_own before a grid wait (their column indices
+// in cj0 / cj1); run_phase(..., pre = true) then only gathers for them.
+template <typename T, typename Ph>
+__device__ __forceinline__ void issue_first(const Mat<T> &A, const Chunk *desc, int count, const Ph &ph, char *wsm,
+                                            int (&cj0)[kLaneItems], int (&cj1)[kLaneItems]) {
+  if (count > 0) issue_own<T>(A, desc[0], ph, wsm, cj0);
+  if (count > 1) issue_own<T>(A, desc[1], ph, wsm + buf_bytes<T, Ph::PRE>(), cj1);
 }
 
 // Fixed-order CTA sum of three values per thread with few float64 adds
@@ -293,11 +342,17 @@ __device__ __forceinline__ void cta_sum3(const double (&v)[3], char *sm, int war
 // start once chunk i is done.
 template <typename T, bool L1G, typename Ph>
 __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, int count, const T *vec, char *wsm,
-                                          Ph &ph) {
+                                          Ph &ph, bool pre = false, const int (&cj0)[kLaneItems] = {},
+                                          const int (&cj1)[kLaneItems] = {}) {
   char *b0 = wsm, *b1 = wsm + buf_bytes<T, Ph::PRE>();
   T ga[kLaneItems], gb[kLaneItems];
-  if (count > 0) issue<T, L1G>(A, desc[0], vec, ph, b0, ga);
-  if (count > 1) issue<T, L1G>(A, desc[1], vec, ph, b1, gb);
+  if (sizeof(T) == 4 && pre) {
+    if (count > 0) issue_gather<T, L1G>(desc[0], vec, cj0, ga);
+    if (count > 1) issue_gather<T, L1G>(desc[1], vec, cj1, gb);
+  } else {
+    if (count > 0) issue<T, L1G>(A, desc[0], vec, ph, b0, ga);
+    if (count > 1) issue<T, L1G>(A, desc[1], vec, ph, b1, gb);
+  }
   for (int i = 0; i < count; i += 2) {
     if (i + 1 < count)
       cp_async_wait<1>();
@@ -410,10 +465,27 @@ __global__ void __launch_bounds__(kPThreads, 1)
     else
       run_phase<T, L1G>(KT, dp, cnt_p, S.y[cur], wsm, pp);
     target += G + (att == 0 && s_wait_extra ? 1ull : 0ull);
-    if (!grid_barrier(bar, target, &sc->err, s_wait_ns, L1G)) break;
+    // float32: arrive, start the dual phase's first two chunks (everything
+    // but the gathers of x': the primal phase writes only x' and its running
+    // sum), then wait for the other CTAs.  float32 only: in float64 the
+    // column indices held across the wait spill (measured: 100k x 250k LP
+    // float32 attempt 30.9 -> 29.9 us, PageRank 1M float32 unchanged at
+    // 112 us; float64 162.1 -> 179.8 us on PageRank 1M)
+    if constexpr (sizeof(T) == 4) {
+      grid_arrive(bar);
+    } else {
+      if (!grid_barrier(bar, target, &sc->err, s_wait_ns, L1G)) break;
+    }
     DualPhase<T> dph{S.y[cur], S.Kx[cur], S.ys[cur], P.qs, P.ylos, S.y[cur ^ 1], S.Kx[cur ^ 1], S.ys[cur ^ 1],
                      (T)ctl.sigma, (T)ctl.eta, {0.0, 0.0}};
-    run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
+    if constexpr (sizeof(T) == 4) {
+      int cj0[kLaneItems], cj1[kLaneItems];
+      issue_first<T>(K, dd, cnt_d, dph, wsm, cj0, cj1);
+      if (!grid_wait(bar, target, &sc->err, s_wait_ns, L1G)) break;
+      run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph, true, cj0, cj1);
+    } else {
+      run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
+    }
     {
       const double v[3] = {pp.acc[0], dph.acc[0], dph.acc[1]};
       cta_sum3(v, sm, geo.warp_bytes, s_tot);
