@@ -46,7 +46,7 @@ METRIC = "time-to-1e-8 rel KKT & PDHG iter/s (HBM GB/s vs peak); FP32+refine vs 
 # dram__bytes_read.sum + dram__bytes_write.sum per step attempt of the
 # persistent step kernel from one ncu capture each (one launch = one chunk of
 # about 40 attempts; see profiles/); drop an entry whenever the kernel changes
-CAPTURED_TRAFFIC = {"mip_100k": 1.335e6, "pagerank_1m_fp64": 3.275e8, "pagerank_1m_fp32": 1.934e8}
+CAPTURED_TRAFFIC = {"mip_100k": 1.335e6, "pagerank_1m_fp64": 3.275e8, "pagerank_1m_fp32": 1.936e8}
 L2_BYTES = 129e6  # GB300 L2 capacity
 WORKLOADS = ("mip_100k", "pagerank_1m", "planted_200x500")
 
