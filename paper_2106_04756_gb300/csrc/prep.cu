@@ -394,21 +394,6 @@ __global__ void k_fill(double *v, int64_t n, double x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] = x;
 }
 
-void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *htrp, PrecondPlan &pp) {
-  auto scan = [](int32_t rows, const int32_t *rp, std::vector<ScanSeg> &segs, std::vector<int32_t> &longr) {
-    segs.clear();
-    longr.clear();
-    for (int32_t i = 0; i < rows; ++i) {
-      const int32_t k0 = rp[i], k1 = rp[i + 1];
-      if (k1 - k0 <= kMaxSeg) continue;
-      if (k1 - k0 > kLongScan) longr.push_back(i);
-      for (int32_t k = k0; k < k1; k += kMaxSeg) segs.push_back(ScanSeg{i, k, k1 - k > kMaxSeg ? k + kMaxSeg : k1, 0});
-    }
-  };
-  scan(m, hrp, pp.segK, pp.longK);
-  scan(n, htrp, pp.segKT, pp.longKT);
-}
-
 cudaError_t ruiz(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci, const int32_t *rowid,
                  double *val, const int32_t *trp, double *tval, const int32_t *perm, int ruiz_iters, double *D1,
                  double *D2, double *rbuf, double *cbuf, const ScanSeg *dsegK, int nsegK, const ScanSeg *dsegKT,

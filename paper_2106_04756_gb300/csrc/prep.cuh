@@ -46,24 +46,8 @@ cudaError_t exclusive_scan(const int *in, int64_t n, int *out, int *total, int *
 int64_t scan_tmp_ints(int64_t n);
 cudaError_t build_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci,
                             int32_t *trp, int32_t *tci, int32_t *perm, DevBuf &tmp, cudaStream_t st);
-// Section 3.5 preconditioning in two calls.  Long rows are handled apart:
-// the Ruiz maxima of rows longer than kMaxSeg nonzeros by one CTA per
-// kMaxSeg-nonzero segment, combined with an atomic maximum on the bits (the
-// numeric order for nonnegative doubles, so the result is the same in any
-// order); the Pock-Chambolle l1 sums of rows longer than kLongScan on the
-// host in CSR order, the order of the plain loop (one GPU thread, at this
-// part's float64 add rate, takes tens of milliseconds for a million terms).
-constexpr int32_t kMaxSeg = 256;
-constexpr int32_t kLongScan = 8192;
-struct ScanSeg {
-  int32_t row, k0, k1, pad;  // [k0, k1): a segment of row `row`
-};
-struct PrecondPlan {
-  std::vector<ScanSeg> segK, segKT;    // kMaxSeg-nonzero segments of the rows of K, K^T longer than kMaxSeg
-  std::vector<int32_t> longK, longKT;  // the rows of K, K^T longer than kLongScan
-};
-// From the host row starts of K (m rows) and K^T (n rows).
-void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *htrp, PrecondPlan &pp);
+// Section 3.5 preconditioning in two calls, with the long rows of a
+// PrecondPlan (schedule.h) handled apart.
 // Ruiz equilibration (Section 3.5, ruiz_iters passes), queued on st: D1, D2
 // from 1, val / tval scaled in place; dsegK / dsegKT: the plan's segments on
 // the device.

@@ -154,6 +154,21 @@ void refine_scales(double pv, double dv, double dmax, double *dP, double *dD) {
   *dD = D < 1.0 ? 1.0 : D;
 }
 
+void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *htrp, PrecondPlan &pp) {
+  auto scan = [](int32_t rows, const int32_t *rp, std::vector<ScanSeg> &segs, std::vector<int32_t> &longr) {
+    segs.clear();
+    longr.clear();
+    for (int32_t i = 0; i < rows; ++i) {
+      const int32_t k0 = rp[i], k1 = rp[i + 1];
+      if (k1 - k0 <= kMaxSeg) continue;
+      if (k1 - k0 > kLongScan) longr.push_back(i);
+      for (int32_t k = k0; k < k1; k += kMaxSeg) segs.push_back(ScanSeg{i, k, k1 - k > kMaxSeg ? k + kMaxSeg : k1, 0});
+    }
+  };
+  scan(m, hrp, pp.segK, pp.longK);
+  scan(n, htrp, pp.segKT, pp.longKT);
+}
+
 int refine_finish_now(int round, double prev, double rel, int max_rounds) {
   if (round >= max_rounds) return 1;
   return round >= 1 && !(rel * kRefineMinGain <= prev) ? 1 : 0;

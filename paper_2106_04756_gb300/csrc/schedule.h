@@ -1,7 +1,8 @@
 // Host-side planning shared by the library and its CPU tests: the warp-chunk
 // schedule of a CSR matrix, the balanced assignment of chunks to the warps
-// of the persistent kernel, and the tolerance and scale rules of the
-// float32 iterative refinement.  Plain C++ (no CUDA headers), so that the
+// of the persistent kernel, the long rows of the preconditioning, and the
+// tolerance, scale, stop and budget rules of the float32 iterative
+// refinement.  Plain C++ (no CUDA headers), so that the
 // tests can build it with the host compiler alone.
 #pragma once
 
@@ -28,6 +29,25 @@ struct Chunk {
 struct LongRow {
   int32_t row, nseg, part_off, pad;
 };
+
+// Long rows of the Section 3.5 preconditioning, handled apart: the Ruiz
+// maxima of rows longer than kMaxSeg nonzeros by one CTA per kMaxSeg-nonzero
+// segment, combined with an atomic maximum on the bits (the numeric order
+// for nonnegative doubles, so the result is the same in any order); the
+// Pock-Chambolle l1 sums of rows longer than kLongScan on the host in CSR
+// order, the order of the plain loop (one GPU thread, at GB300's float64 add
+// rate, takes tens of milliseconds for a million terms).
+constexpr int32_t kMaxSeg = 256;
+constexpr int32_t kLongScan = 8192;
+struct ScanSeg {
+  int32_t row, k0, k1, pad;  // [k0, k1): a segment of row `row`
+};
+struct PrecondPlan {
+  std::vector<ScanSeg> segK, segKT;    // kMaxSeg-nonzero segments of the rows of K, K^T longer than kMaxSeg
+  std::vector<int32_t> longK, longKT;  // the rows of K, K^T longer than kLongScan
+};
+// From the host row starts of K (m rows) and K^T (n rows).
+void plan_precondition(int32_t m, const int32_t *hrp, int32_t n, const int32_t *htrp, PrecondPlan &pp);
 
 // Warp-chunk schedule of a CSR matrix with `rows` rows and host row_ptr rp:
 // consecutive rows are grouped greedily into chunks of at most kChunkNnz

@@ -71,3 +71,22 @@ extern "C" int hl_build_slabs(int rows, const int32_t *rp, int32_t *first, int32
   memcpy(split4, sp.data(), sizeof(SplitRow) * sp.size());
   return 0;
 }
+
+// plan_precondition on one matrix (m = rows, n = 0): segments as (row, k0, k1)
+// triples and the rows whose l1 sums the host takes
+extern "C" int hl_plan_precondition(int rows, const int32_t *rp, int32_t *seg3, int cap_seg, int32_t *longr,
+                                    int cap_long, int32_t *counts /* nseg, nlong */) {
+  PrecondPlan pp;
+  const int32_t zero = 0;
+  plan_precondition(rows, rp, 0, &zero, pp);
+  counts[0] = (int32_t)pp.segK.size();
+  counts[1] = (int32_t)pp.longK.size();
+  if ((int)pp.segK.size() > cap_seg || (int)pp.longK.size() > cap_long) return -1;
+  for (size_t i = 0; i < pp.segK.size(); ++i) {
+    seg3[3 * i] = pp.segK[i].row;
+    seg3[3 * i + 1] = pp.segK[i].k0;
+    seg3[3 * i + 2] = pp.segK[i].k1;
+  }
+  for (size_t i = 0; i < pp.longK.size(); ++i) longr[i] = pp.longK[i];
+  return 0;
+}

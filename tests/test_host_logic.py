@@ -34,6 +34,7 @@ def hl(tmp_path_factory):
     L.hl_scales.argtypes = [C.c_double, C.c_double, C.c_double, P]
     L.hl_build_slabs.argtypes = [C.c_int, P, P, P, P, P, C.c_int, P]
     L.hl_finish_now.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
+    L.hl_plan_precondition.argtypes = [C.c_int, P, P, C.c_int, P, C.c_int, P]
     L.hl_remaining.argtypes = [C.c_longlong, C.c_longlong, C.c_double, C.c_longlong, C.c_longlong, C.c_double, P]
     return L
 
@@ -182,6 +183,36 @@ def test_refinement_scales(hl):
     assert out[0] == 1.0 and out[1] == 2.0
     hl.hl_scales(0.0, 1e-20, 1e12, out.ctypes.data)  # clipped at dmax
     assert out[0] == 1e12 and out[1] == 1e12
+
+
+def test_preconditioning_long_rows_plan(hl):
+    """Rows over 256 nonzeros are cut into 256-nonzero segments that tile the
+    row exactly (Ruiz maxima); rows over 8,192 are listed for the host's l1
+    sums; nothing else is listed."""
+    rng = np.random.default_rng(5)
+    lens = np.concatenate([rng.integers(0, 40, 500), [256, 257, 512, 513, 8192, 8193, 20000, 1_000_000, 0]])
+    rng.shuffle(lens)
+    rp = np.zeros(lens.size + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    rp = rp.astype(np.int32)
+    cap = int(lens.sum()) // 256 + 16
+    seg = np.zeros((cap, 3), np.int32)
+    longr = np.zeros(cap, np.int32)
+    cnt = np.zeros(2, np.int32)
+    assert hl.hl_plan_precondition(lens.size, rp.ctypes.data, seg.ctypes.data, cap, longr.ctypes.data, cap,
+                                   cnt.ctypes.data) == 0
+    seg, longr = seg[:cnt[0]], longr[:cnt[1]]
+    assert sorted(longr) == sorted(np.flatnonzero(lens > 8192).tolist())
+    covered = {}
+    for row, k0, k1 in seg:
+        assert lens[row] > 256 and 0 < k1 - k0 <= 256
+        covered.setdefault(row, []).append((k0, k1))
+    assert sorted(covered) == sorted(np.flatnonzero(lens > 256).tolist())
+    for row, parts in covered.items():
+        parts.sort()
+        assert parts[0][0] == rp[row] and parts[-1][1] == rp[row + 1]
+        assert all(a[1] == b[0] for a, b in zip(parts, parts[1:]))  # contiguous, no overlap
+        assert all(k1 - k0 == 256 for k0, k1 in parts[:-1])
 
 
 def test_refinement_finish_rule(hl):
