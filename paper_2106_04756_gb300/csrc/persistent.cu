@@ -298,6 +298,47 @@ __device__ __forceinline__ void issue(const Mat<T> &A, const Chunk &c, const T *
   }
 }
 
+// float64 form of the pre-barrier start: only the cp.async copies (values,
+// row starts, operands) before the wait, nothing held in registers across
+// it; issue_idx_gather then loads the column indices and the gathers.
+template <typename T, typename Ph>
+__device__ __forceinline__ void issue_copies(const Mat<T> &A, const Chunk &c, const Ph &ph, char *buf) {
+  const int lane = threadIdx.x & 31;
+  T *sval = reinterpret_cast<T *>(buf);
+  T *pre = sval + 2 * kChunkNnz + kChunkRows;
+  int *srp = reinterpret_cast<int *>(sval + buf_elems<Ph::PRE>());
+  const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
+  const int nrows = c.row_end >= 0 ? c.row_end - c.row_begin : 0;
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    if (e < cnt) cp_async(sval + stg<T>(e), A.val + nb + e);
+  }
+  if (lane < nrows) {
+    cp_async(srp + lane, A.rp + c.row_begin + lane);
+    ph.stage(c.row_begin + lane, pre + lane);
+  }
+  cp_async_commit();
+}
+
+template <typename T, bool L1G>
+__device__ __forceinline__ void issue_idx_gather(const Mat<T> &A, const Chunk &c, const T *vec,
+                                                 T (&xg)[kLaneItems]) {
+  const int lane = threadIdx.x & 31;
+  const int nb = c.nnz_begin, cnt = c.nnz_end - nb;
+  int cj[kLaneItems];
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    cj[it] = e < cnt ? __ldg(A.ci + nb + e) : 0;
+  }
+#pragma unroll
+  for (int it = 0; it < kLaneItems; ++it) {
+    const int e = lane + 32 * it;
+    xg[it] = e < cnt ? (L1G ? vec[cj[it]] : __ldcg(vec + cj[it])) : T(0);
+  }
+}
+
 // The first two chunks' issue_own before a grid wait (their column indices
 // in cj0 / cj1); run_phase(..., pre = true) then only gathers for them.
 template <typename T, typename Ph>
@@ -349,6 +390,9 @@ __device__ __forceinline__ void run_phase(const Mat<T> &A, const Chunk *desc, in
   if (sizeof(T) == 4 && pre) {
     if (count > 0) issue_gather<T, L1G>(desc[0], vec, cj0, ga);
     if (count > 1) issue_gather<T, L1G>(desc[1], vec, cj1, gb);
+  } else if (pre) {
+    if (count > 0) issue_idx_gather<T, L1G>(A, desc[0], vec, ga);
+    if (count > 1) issue_idx_gather<T, L1G>(A, desc[1], vec, gb);
   } else {
     if (count > 0) issue<T, L1G>(A, desc[0], vec, ph, b0, ga);
     if (count > 1) issue<T, L1G>(A, desc[1], vec, ph, b1, gb);
@@ -465,26 +509,31 @@ __global__ void __launch_bounds__(kPThreads, 1)
     else
       run_phase<T, L1G>(KT, dp, cnt_p, S.y[cur], wsm, pp);
     target += G + (att == 0 && s_wait_extra ? 1ull : 0ull);
-    // float32: arrive, start the dual phase's first two chunks (everything
-    // but the gathers of x': the primal phase writes only x' and its running
-    // sum), then wait for the other CTAs.  float32 only: in float64 the
-    // column indices held across the wait spill (measured: 100k x 250k LP
-    // float32 attempt 30.9 -> 29.9 us, PageRank 1M float32 unchanged at
-    // 112 us; float64 162.1 -> 179.8 us on PageRank 1M)
-    if constexpr (sizeof(T) == 4) {
-      grid_arrive(bar);
-    } else {
-      if (!grid_barrier(bar, target, &sc->err, s_wait_ns, L1G)) break;
-    }
+    // arrive, start the dual phase's first two chunks (data no other CTA
+    // writes in the primal phase, which writes only x' and its running sum),
+    // then wait for the other CTAs.  float32 also loads their column indices
+    // before the wait (100k x 250k LP float32 attempt 30.9 -> 29.9 us,
+    // PageRank 1M unchanged at 112 us); float64 only the copies, since its
+    // indices held across the wait spill (PageRank 1M 162.1 -> 179.8 us)
+    grid_arrive(bar);
     DualPhase<T> dph{S.y[cur], S.Kx[cur], S.ys[cur], P.qs, P.ylos, S.y[cur ^ 1], S.Kx[cur ^ 1], S.ys[cur ^ 1],
                      (T)ctl.sigma, (T)ctl.eta, {0.0, 0.0}};
     if constexpr (sizeof(T) == 4) {
       int cj0[kLaneItems], cj1[kLaneItems];
       issue_first<T>(K, dd, cnt_d, dph, wsm, cj0, cj1);
-      if (!grid_wait(bar, target, &sc->err, s_wait_ns, L1G)) break;
+      if (!grid_wait(bar, target, &sc->err, s_wait_ns, L1G)) {
+        cp_async_wait<0>();  // the copies in flight land before the kernel returns
+        break;
+      }
       run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph, true, cj0, cj1);
     } else {
-      run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph);
+      if (cnt_d > 0) issue_copies<T>(K, dd[0], dph, wsm);
+      if (cnt_d > 1) issue_copies<T>(K, dd[1], dph, wsm + buf_bytes<T, DualPhase<T>::PRE>());
+      if (!grid_wait(bar, target, &sc->err, s_wait_ns, L1G)) {
+        cp_async_wait<0>();  // the copies in flight land before the kernel returns
+        break;
+      }
+      run_phase<T, L1G>(K, dd, cnt_d, S.x[cur ^ 1], wsm, dph, true);
     }
     {
       const double v[3] = {pp.acc[0], dph.acc[0], dph.acc[1]};
