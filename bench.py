@@ -46,7 +46,12 @@ METRIC = "time-to-1e-8 rel KKT & PDHG iter/s (HBM GB/s vs peak); FP32+refine vs 
 # dram__bytes_read.sum + dram__bytes_write.sum per step attempt of the
 # persistent step kernel from one ncu capture each (one launch = one chunk of
 # about 40 attempts; see profiles/); drop an entry whenever the kernel changes
-CAPTURED_TRAFFIC = {"mip_100k": 1.335e6, "pagerank_1m_fp64": 3.275e8, "pagerank_1m_fp32": 1.936e8}
+# DRAM bytes per step attempt from one-pass ncu captures of the current
+# kernels (profiles/k_persist_pagerank1m_mip100k.md); a kernel changed since
+# its capture has no entry here (the bench line then reports null) and its
+# last figure in STALE_TRAFFIC, named in the line's note
+CAPTURED_TRAFFIC = {"pagerank_1m_fp32": 1.936e8}
+STALE_TRAFFIC = {"mip_100k": 1.335e6, "pagerank_1m_fp64": 3.275e8}
 L2_BYTES = 129e6  # GB300 L2 capacity
 WORKLOADS = ("mip_100k", "pagerank_1m", "planted_200x500")
 
@@ -306,7 +311,7 @@ def _pagerank_lines(P, T, dev, sptr, flush, peak, peak_src, reps=3):
                       "frac": ach / peak, "peak_source": peak_src + " burst copy (MEASURED_PEAKS.json hbm_gbs)",
                       "traffic": CAPTURED_TRAFFIC.get(f"pagerank_1m_{name}"),
                       "algorithmic_bytes_per_attempt": b, "attempt_ms": ms,
-                      "note": _roofline_note(b)}
+                      "note": _roofline_note(b, f"pagerank_1m_{name}")}
     out["roofline_hbm"] = {"workload": "pagerank_1m (n=1,000,000, nnz=7,999,982)", **roof}
 
     def to_tol(lp, pins, label):
@@ -371,12 +376,16 @@ def _mip_time_to_tol(P, inputs, lp, dev, sptr, flush, cap_s):
     return res
 
 
-def _roofline_note(ws_bytes):
-    """How to read `achieved` for a step attempt touching ws_bytes."""
+def _roofline_note(ws_bytes, key=None):
+    """How to read `achieved` for a step attempt touching ws_bytes (and where
+    `traffic` comes from for the capture key)."""
     where = ("fits in the 129 MB L2: algorithmic GB/s, not DRAM GB/s" if ws_bytes < L2_BYTES else
              "exceeds the 129 MB L2: streamed from DRAM every attempt")
-    return (f"working set ~{ws_bytes / 1e6:.0f} MB {where}; traffic = DRAM bytes per attempt from one ncu "
-            "capture of this kernel on this workload")
+    note = f"working set ~{ws_bytes / 1e6:.0f} MB {where}; "
+    if key in STALE_TRAFFIC:
+        return note + (f"traffic null: the kernel changed after its last ncu capture, which gave "
+                       f"{STALE_TRAFFIC[key] / 1e6:.4g} MB of DRAM per attempt")
+    return note + "traffic = DRAM bytes per attempt from one ncu capture of this kernel on this workload"
 
 
 def run_reference(args):
@@ -527,7 +536,7 @@ def main():
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": peak_src + " burst copy (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
                     "algorithmic_bytes_per_attempt": bp + bd, "attempt_ms": kc,
-                    "note": _roofline_note(bp + bd)}
+                    "note": _roofline_note(bp + bd, args.workload)}
         if args.workload in CAPTURED_TRAFFIC:
             roofline["traffic"] = CAPTURED_TRAFFIC[args.workload]
     else:
