@@ -799,9 +799,17 @@ extern "C" int pdlp_create(const pdlp_csr *K, const double *c, const double *q, 
     if (slabs) build_slabs(rows, hr.data(), pl.first, pl.head, pl.tail, pl.splits, pl.nparts);
   };
   {
-    std::thread tK([&] { plan(m, hrp, pK); });
+    // (no exception may cross the C ABI: without a second thread, plan both here)
+    std::thread tK;
+    bool threaded = true;
+    try {
+      tK = std::thread([&] { plan(m, hrp, pK); });
+    } catch (...) {
+      threaded = false;
+    }
     plan(n, htrp, pKT);
-    tK.join();
+    if (threaded) tK.join();
+    else plan(m, hrp, pK);
   }
   if (o.pock_chambolle)
     CK(pock_chambolle(m, n, nnz, rp, ci, rowid, val, trp, tval, perm, D1, D2, rb, cb, pp, hrp.data(), htrp.data(),
