@@ -530,13 +530,15 @@ def main():
     bp, bd = _alg_bytes(lp, 64)
     peak, peak_src = _peaks()
     if kc > 0:
-        achieved = (bp + bd) / (kc * 1e-3) / 1e9
+        # one attempt is one unit of the measurement plan's per-unit figure
+        ba = _survey_bytes(lp.m, lp.n, lp.nnz, 64)
+        achieved = ba / (kc * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": "k_persist<double> (persistent step attempts: K^T y + primal "
                     "projection, grid barrier, K x' + dual projection, step test)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": peak_src + " burst copy (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
-                    "algorithmic_bytes_per_attempt": bp + bd, "attempt_ms": kc,
-                    "note": _roofline_note(bp + bd, args.workload)}
+                    "algorithmic_bytes_per_attempt": ba, "attempt_ms": kc,
+                    "note": _roofline_note(ba, args.workload)}
         if args.workload in CAPTURED_TRAFFIC:
             roofline["traffic"] = CAPTURED_TRAFFIC[args.workload]
     else:
